@@ -1,0 +1,107 @@
+/*
+ * FP64 CPU oracle for Scalable Laplacian K-modes, SLK-BO variant
+ * (Ziko, Granger, Ben Ayed, NeurIPS 2018, arXiv:1810.13044).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA path.
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline and
+ * reference legs may load it.  It shares no code, header, table or constant
+ * with the CUDA library, and it never reads anything the CUDA path produced.
+ *
+ * Plain, slow, obviously correct: every function is the paper's definition
+ * written out with scalar loops in double precision, single-threaded.
+ * Inputs X are the float32 features; every other real value is double.
+ *
+ * Conventions: X is N x D row-major; A, Z, S are N x L row-major; the affinity
+ * graph is CSR (row_ptr[N+1] int64, col_idx[nnz] int32, w[nnz] double or NULL
+ * for binary weights).  Indices are 0-based.  Functions return 0 on success
+ * and a negative code on bad arguments (nothing is written then).
+ */
+#ifndef SLK_ORACLE_H
+#define SLK_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Exact kNN of Section 4.2: for each requested row p, the k points q != p with
+ * the smallest squared Euclidean distance, ascending by (distance, index). */
+int oracle_knn_rows(const float* X, int64_t N, int D, int k,
+                    const int64_t* rows, int64_t nrows,
+                    int32_t* idx_out, double* d2_out);
+int oracle_knn(const float* X, int64_t N, int D, int k, int32_t* idx_out, double* d2_out);
+
+/* Kernel width of Section 4.2.  rule 0: sigma = median of the n Euclidean
+ * kNN distances sqrt(d2) (mean of the two middle values for even n);
+ * rule 1: sigma^2 = mean of the squared kNN distances (the paper's estimator). */
+double oracle_sigma(const double* d2, int64_t n, int rule);
+
+/* Gaussian kernel of Section 4.2: exp(-d2 / (2 sigma^2)). */
+double oracle_gauss(double d2, double sigma);
+
+/* Heat-kernel edge weights w_e = exp(-d2_e / (2 sigma^2)). */
+void oracle_heat_weights(const double* d2, int64_t nnz, double sigma, double* w);
+
+/* Unary term, Eq. (general-second): a_{p,l} = k(x_p, m_l) with m_l = x_{modes[l]}. */
+int oracle_unary(const float* X, int64_t N, int D, const int32_t* modes, int L,
+                 double sigma, double* A);
+
+/* Row softmax z_p = exp(s_p) / 1^t exp(s_p) (Algorithm 1 initialisation with s = a). */
+void oracle_softmax_rows(const double* S, int64_t N, int L, double* Z);
+
+/* Pairwise term, Eq. (general-third): b_{p,l} = sum_q k(x_p, x_q) z_{q,l} over row p of K. */
+void oracle_pairwise(const int64_t* row_ptr, const int32_t* col_idx, const double* w,
+                     int64_t N, int L, const double* Z, double* B);
+
+/* Logits of the z-update, s_p = a_p + lambda b_p (argument of the soft-max update). */
+void oracle_logits(const double* A, const int64_t* row_ptr, const int32_t* col_idx,
+                   const double* w, int64_t N, int L, double lambda,
+                   const double* Z, double* S);
+
+/* Inner loop of Algorithm 1: repeat the soft-max z-update (Jacobi: every row
+ * from the previous Z) until max |z_new - z_old| <= tol or max_iters updates.
+ * Z is in/out.  If Zprev is not NULL it receives the iterate the last update
+ * started from (needed for the mode keys).  tol < 0 runs exactly max_iters. */
+int oracle_bound_iterate(const double* A, const int64_t* row_ptr, const int32_t* col_idx,
+                         const double* w, int64_t N, int L, double lambda,
+                         double* Z, int max_iters, double tol,
+                         double* Zprev, int* iters_done, double* last_delta);
+
+/* SLK-BO mode update, Eq. (mode_byproduct): m_l = argmax_q z_{q,l}, compared on
+ * log z_{q,l} computed from the logits S of the last update (ties -> smaller q).
+ * keys_out (nullable, N x L) receives log z_{q,l}. */
+void oracle_log_z(const double* S, int64_t N, int L, double* logZ);
+void oracle_mode_update(const double* S, int64_t N, int L, int32_t* modes_out, double* best_key);
+
+/* Discrete labels: argmax_l z_{p,l} (ties -> smaller l), compared on the logits. */
+void oracle_labels(const double* S, int64_t N, int L, int32_t* labels);
+
+/* Discrete energy, Eq. (1), at one-hot assignments given by labels and modes
+ * m_l = x_{modes[l]}:  -sum_p sum_l z_{p,l} k(x_p, m_l)
+ *                      + lambda/2 sum_p sum_{q in row p} w_pq ||z_p - z_q||^2. */
+double oracle_energy(const float* X, int D, const int32_t* labels,
+                     const int64_t* row_ptr, const int32_t* col_idx, const double* w,
+                     int64_t N, int L, const int32_t* modes, double sigma, double lambda);
+
+/* Relaxed objective, Eq. (2), with pairwise weight lam_pair:
+ * sum_p z_p^t log z_p - sum_{p,l} z_{p,l} a_{p,l} - lam_pair sum_p sum_{q in row p} w_pq z_p^t z_q. */
+double oracle_relaxed(const double* A, const double* Z, const int64_t* row_ptr,
+                      const int32_t* col_idx, const double* w, int64_t N, int L,
+                      double lam_pair);
+
+/* Algorithm 1 (SLK-BO) on a given graph and kernel width.
+ * Outer loop: a from the modes, z = softmax(a), inner z-updates, mode update,
+ * energy; stop when the modes do not change or after max_outer steps.
+ * Outputs: Z (N x L), labels[N], modes[L] (in: initial modes, out: final),
+ * energy, and counters.  Returns 1 if max_outer was hit without convergence. */
+int oracle_solve_graph(const float* X, int64_t N, int D, int L,
+                       const int64_t* row_ptr, const int32_t* col_idx, const double* w,
+                       double sigma, double lambda, int32_t* modes,
+                       int max_outer, int max_inner, double tol,
+                       double* Z, int32_t* labels, double* energy,
+                       int* outer_done, int* inner_total);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
