@@ -1,0 +1,328 @@
+#!/usr/bin/env python3
+"""Benchmark of the SLK-BO hot path on one GB300 (one JSON line on stdout).
+
+A step is one whole solve of the 70000 x 784, L=10, k=5 workload (synthetic,
+MNIST-shaped; see paper_1810_13044_gb300/inputs.py): kNN graph, sigma, and
+Algorithm 1's outer loop (unary, bound iterations, mode update, energy) until
+the modes stop changing.  The metric is solves/s; the bound iterations are
+also reported as N*L*iterations/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl slk|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+project) on a bounded sample of the same workload.  Under torchrun each rank
+solves its own copy of the workload (replicas: weak scaling), rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SLK N·L·iter/s and solves/s vs plain FP32 GPU at equal labels; p50/p99 latency"
+WORKLOAD = dict(name="mnist_like_70000x784_L10", N=70000, D=784, L=10, k=5, lam=1.0)
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP32_LANES_PER_SM = 128      # FP32 FMA units per SM (4 sub-partitions x 32)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["slk", "reference"], default="slk")
+    ap.add_argument("--precision", choices=["fp32", "bf16_rerank"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs():
+    from paper_1810_13044_gb300 import inputs
+    X, y = inputs.mnist_like(N=WORKLOAD["N"], D=WORKLOAD["D"])
+    m0 = inputs.kmeanspp(X, WORKLOAD["L"], seed=1810)
+    return X, m0
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle legs
+
+def oracle_sample(X, m0, n_rows=8, inner_per_outer=None, outer=None):
+    """Time the FP64 oracle on a bounded sample of one solve and extrapolate:
+    kNN on n_rows rows (scaled to N rows) + one outer iteration of
+    Algorithm 1 on the full-size problem (unary, z-updates, modes, energy)
+    scaled to the outer count.  Returns (seconds per solve, description)."""
+    import oracle
+    N, L, k, lam = WORKLOAD["N"], WORKLOAD["L"], WORKLOAD["k"], WORKLOAD["lam"]
+    rows = np.linspace(0, N - 1, n_rows).astype(np.int64)
+    t0 = time.perf_counter()
+    idx, d2 = oracle.knn(X, k, rows=rows)
+    t_knn = (time.perf_counter() - t0) * N / n_rows
+    # a kNN-shaped graph for the iteration leg (the exact graph is what costs hours)
+    from paper_1810_13044_gb300 import inputs
+    rp, ci, _ = inputs.random_graph(N, k, seed=3)
+    sig = float(np.sqrt(np.median(d2)))
+    inner = int(inner_per_outer or 20)
+    outer = int(outer or 1)
+    t0 = time.perf_counter()
+    oracle.solve_graph(X, L, rp, ci, None, sig, lam, m0, max_outer=1, max_inner=inner, tol=-1.0)
+    t_outer = time.perf_counter() - t0
+    total = t_knn + t_outer * outer
+    desc = (f"FP64 oracle, 1 thread: exact kNN of {n_rows} rows scaled x{N // n_rows}, plus one outer "
+            f"iteration ({inner} z-updates, unary, modes, energy) on the full {N}x{WORKLOAD['D']} "
+            f"problem scaled x{outer} outer iterations")
+    return total, desc
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    X, m0 = make_inputs()
+    oracle_sample(X, m0, n_rows=2, inner_per_outer=2)   # warm the caches / build
+    for _ in range(max(0, args.warmup - 1)):
+        oracle_sample(X, m0, n_rows=2, inner_per_outer=2)
+    times = []
+    desc = ""
+    for _ in range(args.steps):
+        t, desc = oracle_sample(X, m0, n_rows=4, inner_per_outer=20, outer=2)
+        times.append(t)
+    sec = statistics.median(times)
+    value = 1.0 / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD["name"], **{k: WORKLOAD[k] for k in
+                                                                          ("N", "D", "L", "k")}},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_slk(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1810_13044_gb300 import slk
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    X, m0 = make_inputs()
+    N, D, L, k, lam = (WORKLOAD[x] for x in ("N", "D", "L", "k", "lam"))
+    dev = torch.device("cuda", local)
+    Xd = torch.from_numpy(X).to(dev)
+    m0d = torch.from_numpy(m0).to(dev)
+    params = slk.default_params(knn_precision=args.precision)
+    ctx = slk.context(local)
+    out = (torch.empty(N, L, device=dev), torch.empty(N, dtype=torch.int32, device=dev),
+           torch.empty(L, dtype=torch.int32, device=dev))
+
+    def step():
+        return slk.solve(Xd, L, k, lam, m0d, params=params, ctx=ctx, out=out)
+
+    for _ in range(args.warmup):
+        _, _, _, stats = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, _, _, stats = step()
+        ev1.record(stream)
+        barrier()
+    ms_phase, calls, launches = ctx.profile_read()
+    ctx.profile(False)
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1e3)
+
+    # bound iterations alone on this solve's graph: N*L*iter/s (fixed 50 updates)
+    g = slk.knn_graph(Xd, k, ctx=ctx)
+    A, Z0 = slk.unary(Xd, out[2], stats["sigma"], ctx=ctx)
+    Zb, Zp = Z0.clone(), torch.empty_like(Z0)
+    slk.bound_iterate(A, g.row_ptr, g.col_idx, None, lam, Zb, Zp, 50, tol=-1.0, ctx=ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        Zb.copy_(Z0)
+        slk.bound_iterate(A, g.row_ptr, g.col_idx, None, lam, Zb, Zp, 50, tol=-1.0, ctx=ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bound_ms = e0.elapsed_time(e1) / reps
+    nl_iter_per_s = N * L * 50 / (bound_ms / 1e3)
+
+    # e2e through the host-buffer entry point (pinned X in, labels + modes out)
+    Xh = torch.from_numpy(X).pin_memory()
+    m0h = torch.from_numpy(m0)
+    hout = (None, torch.empty(N, dtype=torch.int32).pin_memory(),
+            torch.empty(L, dtype=torch.int32).pin_memory())
+    slk.solve_host(Xh, L, k, lam, m0h, params=params, ctx=ctx, out=hout)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        slk.solve_host(Xh, L, k, lam, m0h, params=params, ctx=ctx, out=hout)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps / float(te.item())
+
+    if rank == 0:
+        peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+        clocks = clk.summary()
+        # dominant kernel: the distance tiles of the kNN graph
+        cand_ms = ms_phase["knn_cand"] / max(1, calls["knn_cand"])
+        Dp = ((D + 15) // 16) * 16
+        if args.precision == "fp32":
+            flops = 2.0 * N * N * D
+            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+            peak = 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+            roof = {"bound": "alu", "kernel": "knn_cand_fp32_kernel",
+                    "achieved": flops / (cand_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                    "traffic": None}
+        else:
+            flops = 2.0 * N * N * D
+            peak = peaks.get("bf16_tflops", 1900.0)
+            roof = {"bound": "tensor", "kernel": "knn_cand_bf16_kernel",
+                    "achieved": flops / (cand_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": "measured bf16_tflops" if "bf16_tflops" in peaks else "fallback",
+                    "traffic": None}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["launch_ms"] = cand_ms
+        roof["algorithmic"] = f"2*N*N*D = {flops:.3e} flop per launch (Dp={Dp})"
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "N": N, "D": D, "L": L, "k": k, "lambda": lam,
+                       "sigma": "median kNN distance", "knn": args.precision,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (X is 219 MB > 129 MB)",
+                       "outer_iters": stats["outer_iters"],
+                       "inner_iters_total": stats["inner_iters_total"]},
+            "nl_iter_per_s": nl_iter_per_s, "bound_ms_per_50_updates": bound_ms,
+            "phase_ms_per_step": {k_: v / args.steps for k_, v in ms_phase.items()},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": N * D * 4 + L * 4,
+                    "d2h_bytes_per_step": N * 4 + L * 4},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "energy": stats["energy"], "knn_fallback_rows": stats["knn_fallback_rows"],
+        }
+        if not args.no_cpu_baseline:
+            sec, desc = oracle_sample(X, m0, n_rows=8,
+                                      inner_per_outer=max(1, stats["inner_iters_total"] // max(1, stats["outer_iters"])),
+                                      outer=stats["outer_iters"])
+            line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "solves/s", "cores": 1,
+                                    "kind": "oracle", "sample": desc}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_slk(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * slk.h -- C-ABI of the GB300 (sm_103a) hot path of Scalable Laplacian
+ * K-modes, SLK-BO variant (Ziko, Granger, Ben Ayed, "Scalable Laplacian
+ * K-modes", NeurIPS 2018, arXiv:1810.13044).
+ *
+ * Problem statement (Eq. 1): N points x_p in R^D, L clusters, affinities
+ * k(x_p, x_q), modes m_l that are data points, one-hot assignments z_p.
+ * Algorithm 1 alternates (i) z-updates -- the soft-max of Eq. (soft-max),
+ * z_p <- exp(a_p + lambda b_p) / 1^t exp(a_p + lambda b_p), with the unary
+ * term a_{p,l} = k(x_p, m_l) (Eq. general-second) and the pairwise term
+ * b_{p,l} = sum_q k(x_p, x_q) z_{q,l} (Eq. general-third) -- and (ii) mode
+ * updates m_l = x_p, p = argmax_q z_{q,l} (Eq. mode_byproduct).
+ *
+ * Conventions shared by every entry point
+ *   - Array arguments are DEVICE pointers (cudaMalloc / torch CUDA tensors)
+ *     owned by the caller, unless marked [host].  Dense matrices are
+ *     row-major and C-contiguous: X is N x D float32, A and Z are N x L
+ *     float32.  The graph is CSR: row_ptr[N+1] int64, col_idx[nnz] int32,
+ *     w[nnz] float32 or NULL for binary (all-one) weights.
+ *   - All work is enqueued on the context's stream.  Entry points with
+ *     [host] outputs synchronise that stream before returning; the others
+ *     return as soon as the work is enqueued.
+ *   - The library owns only the context and its scratch workspace, which it
+ *     grows with cudaMalloc on demand and frees in slk_destroy.
+ *   - Errors: arguments are checked before anything is launched; a bad one
+ *     returns SLK_ERR_INVALID_ARG and writes nothing.  CUDA failures return
+ *     SLK_ERR_CUDA, failed allocations SLK_ERR_OOM; slk_last_error() then
+ *     holds a one-line message.  There is no CPU fallback: without a usable
+ *     GPU every compute call fails.
+ *   - Sizes: 2 <= N < 2^31, 1 <= D, 1 <= L <= 256, L <= N, 1 <= k <= 24,
+ *     k <= N - 1.  Inputs must be finite.
+ */
+#ifndef SLK_H
+#define SLK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slk_ctx slk_ctx;
+
+typedef enum {
+    SLK_OK = 0,
+    SLK_NOT_CONVERGED = 1,      /* warning: max_outer reached, results valid */
+    SLK_ERR_INVALID_ARG = -1,
+    SLK_ERR_CUDA = -2,
+    SLK_ERR_OOM = -3,
+    SLK_ERR_TIMEOUT = -4,       /* a device-side wait gave up; results invalid */
+    SLK_ERR_NO_DEVICE = -5
+} slk_status;
+
+enum { SLK_AFFINITY_BINARY = 0, SLK_AFFINITY_HEAT = 1 };
+enum { SLK_KNN_FP32 = 0, SLK_KNN_BF16_RERANK = 1 };
+enum { SLK_SIGMA_MEDIAN = 0, SLK_SIGMA_MEANSQ = 1 };
+
+/* Limits checked by every entry point. */
+#define SLK_MAX_L 256
+#define SLK_MAX_K 24
+
+/* Library version string, e.g. "slk-gb300 0.1 sm_103a". */
+const char* slk_version(void);
+
+/* Create a context bound to CUDA device `device` and stream `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *ctx receives the
+ * handle.  Fails with SLK_ERR_NO_DEVICE when no such device is usable. */
+slk_status slk_create(slk_ctx** ctx, int device, void* stream);
+slk_status slk_destroy(slk_ctx* ctx);
+slk_status slk_set_stream(slk_ctx* ctx, void* stream);
+/* Message of the last failed call on this context ("" if none). */
+const char* slk_last_error(const slk_ctx* ctx);
+
+/* kNN affinity graph of Section 4.2: for each point p, the k nearest points
+ * q != p by Euclidean distance, ascending by (distance, index).
+ *   X        [N x D]   features.
+ *   row_ptr  [N+1]     out: row_ptr[p] = k p.
+ *   col_idx  [N k]     out: neighbour indices.
+ *   dist2    [N k]     out: squared distances, each the float32 sum of
+ *                      (x_pj - x_qj)^2.
+ *   w        [N k]     out (may be NULL for BINARY): weights; BINARY writes
+ *                      1, HEAT writes exp(-dist2 / (2 sigma^2)).
+ *   affinity SLK_AFFINITY_*; sigma (> 0) is used by HEAT only.
+ *   precision SLK_KNN_FP32: float32 SIMT distance tiles; SLK_KNN_BF16_RERANK:
+ *            bfloat16 tensor-core (tcgen05) distance tiles.  Both produce
+ *            candidates that are re-ranked with exact float32 distances and
+ *            certified by a rounding-error bound; rows that fail the
+ *            certificate are recomputed by an exact float32 scan, so both
+ *            precisions return the same graph.
+ *   fallback_rows [host, nullable]: receives how many rows were rescanned.
+ * Brute force, O(N^2 D) -- the paper's exact option for small sets. */
+slk_status slk_knn_graph(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int32_t k,
+                         int32_t affinity, int32_t precision, float sigma,
+                         int64_t* row_ptr, int32_t* col_idx, float* dist2, float* w,
+                         int64_t* fallback_rows);
+
+/* Kernel width of Section 4.2 from the n = N k squared kNN distances dist2.
+ *   rule SLK_SIGMA_MEDIAN: sigma = median of sqrt(dist2) (mean of the two
+ *        middle values when n is even); SLK_SIGMA_MEANSQ: the paper's
+ *        estimator sigma^2 = (1/n) sum dist2.
+ *   sigma_out [host] receives sigma. */
+slk_status slk_sigma(slk_ctx* ctx, const float* dist2, int64_t n, int32_t rule, float* sigma_out);
+
+/* Unary term, Eq. (general-second), with the Gaussian kernel of Section 4.2:
+ * A[p,l] = exp(-||x_p - x_{mode_idx[l]}||^2 / (2 sigma^2)).
+ *   mode_idx [L] int32 point indices in [0, N).
+ *   Z0 [N x L] (nullable): receives softmax(A) row by row, the
+ *   initialisation of the inner loop of Algorithm 1. */
+slk_status slk_unary(slk_ctx* ctx, const float* X, int64_t N, int32_t D,
+                     const int32_t* mode_idx, int32_t L, float sigma, float* A, float* Z0);
+
+/* Inner loop of Algorithm 1: the soft-max z-update of Eq. (soft-max),
+ * z_p <- softmax(a_p + lambda b_p), b_p = sum_{e in row p} w_e z_{col_idx[e]},
+ * applied to all rows from the same iterate, repeated until
+ * max_{p,l} |z_new - z_old| <= tol or max_iters updates (tol < 0: exactly
+ * max_iters).
+ *   Z      [N x L] in: starting iterate; out: the last iterate.
+ *   Z_prev [N x L] out: the iterate the last update started from (the mode
+ *          update needs it); its input contents are ignored.  Must not alias Z.
+ *   iters_done [host, nullable], last_delta [host, nullable].
+ * Runs as one persistent cooperative kernel with a device-wide barrier
+ * between updates; a barrier that waits more than about a second returns
+ * SLK_ERR_TIMEOUT. */
+slk_status slk_bound_iterate(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
+                             const int32_t* col_idx, const float* w, int64_t N, int32_t L,
+                             float lambda, float* Z, float* Z_prev, int32_t max_iters, float tol,
+                             int32_t* iters_done, float* last_delta);
+
+/* SLK-BO mode update, Eq. (mode_byproduct): mode_idx[l] <- argmax_q z_{q,l}
+ * (ties to the smaller q), where z_q = softmax(s_q) is the last iterate and
+ * s_q = a_q + lambda b_q its logits, recomputed from Z_prev (NULL: s = A, the
+ * initial iterate).  The comparison uses log z_{q,l} =
+ * (s_l - max s) - log1p(sum_{j != argmax} exp(s_j - max s)), which does not
+ * saturate when z is close to 1.
+ *   mode_idx [L] in: previous modes; out: new modes.
+ *   labels   [N] (nullable) out: argmax_l z_{q,l} (ties to the smaller l).
+ *   mode_key [L] (nullable) out: log z at the new modes.
+ *   changed  [host, nullable]: 1 if any mode index changed, else 0. */
+slk_status slk_mode_update(slk_ctx* ctx, const float* A, const float* Z_prev,
+                           const int64_t* row_ptr, const int32_t* col_idx, const float* w,
+                           int64_t N, int32_t L, float lambda, int32_t* mode_idx,
+                           int32_t* labels, float* mode_key, int32_t* changed);
+
+/* Discrete energy, Eq. (1), at the one-hot assignment given by labels and
+ * the modes m_l = x_{mode_idx[l]}:
+ *   E = -sum_p k(x_p, m_{labels[p]}) + (lambda/2) sum_p sum_{e in row p} w_e ||z_p - z_q||^2,
+ * with ||z_p - z_q||^2 = 2 [labels[p] != labels[q]].  Distances, kernel values
+ * and sums are computed in float64.  E [host] receives the value. */
+slk_status slk_energy(slk_ctx* ctx, const float* X, int32_t D, const int32_t* labels,
+                      const int64_t* row_ptr, const int32_t* col_idx, const float* w,
+                      int64_t N, int32_t L, const int32_t* mode_idx, float sigma, float lambda,
+                      double* E);
+
+typedef struct {
+    int32_t max_outer;      /* outer iterations of Algorithm 1 (default 50) */
+    int32_t max_inner;      /* z-updates per outer iteration (default 100), >= 1 */
+    float tol_inner;        /* stop the inner loop when max |dz| <= tol (default 1e-6) */
+    int32_t sigma_rule;     /* SLK_SIGMA_* used when sigma <= 0 (default MEDIAN) */
+    int32_t affinity;       /* SLK_AFFINITY_* (default BINARY) */
+    int32_t knn_precision;  /* SLK_KNN_* (default FP32) */
+} slk_params;
+
+typedef struct {
+    int32_t outer_iters;        /* outer iterations run */
+    int32_t inner_iters_total;  /* z-updates summed over outer iterations */
+    int32_t converged;          /* 1 if the modes stopped changing */
+    float sigma;                /* kernel width used */
+    double energy;              /* E of Eq. (1) after the last outer iteration */
+    int64_t knn_fallback_rows;  /* kNN rows recomputed by the exact scan */
+} slk_stats;
+
+/* Fill *p with the defaults listed in slk_params. */
+void slk_default_params(slk_params* p);
+
+/* Whole SLK-BO on the GPU: kNN graph, kernel width (sigma <= 0: estimated by
+ * params->sigma_rule), then Algorithm 1 from init_modes until the modes do
+ * not change or params->max_outer outer iterations.
+ *   init_modes [L] device int32 point indices (e.g. K-means++ seeds).
+ *   Z [N x L], labels [N], modes [L]: device outputs.
+ *   stats [host, nullable].
+ * Returns SLK_NOT_CONVERGED (results valid) when max_outer is reached. */
+slk_status slk_solve(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int32_t L, int32_t k,
+                     float lambda, float sigma, const int32_t* init_modes,
+                     const slk_params* params, float* Z, int32_t* labels, int32_t* modes,
+                     slk_stats* stats);
+
+/* slk_solve on HOST buffers: X [host, N x D], init_modes [host, L]; outputs
+ * labels [host, N], modes [host, L] and Z [host, N x L, nullable].  Copies in
+ * and out through the context's device workspace; for pinned host memory the
+ * copies run at full link speed. */
+slk_status slk_solve_host(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int32_t L,
+                          int32_t k, float lambda, float sigma, const int32_t* init_modes,
+                          const slk_params* params, float* Z, int32_t* labels, int32_t* modes,
+                          slk_stats* stats);
+
+/* Phase profiling.  While enabled, every call records a pair of CUDA events
+ * on the context's stream around each phase below (no synchronisation is
+ * added); slk_profile_read synchronises the stream and returns, per phase,
+ * the summed device time in milliseconds and the number of timed calls,
+ * plus the number of kernels the library launched since profiling was
+ * enabled (counted whether or not events are recorded).  Enabling clears the
+ * totals. */
+enum {
+    SLK_PHASE_KNN_PREP = 0,     /* centring, rounding, norms */
+    SLK_PHASE_KNN_CAND,         /* distance tiles + per-row candidate lists */
+    SLK_PHASE_KNN_RERANK,       /* exact float32 rerank + certificate */
+    SLK_PHASE_KNN_FALLBACK,     /* exact scan of uncertified rows */
+    SLK_PHASE_SIGMA,
+    SLK_PHASE_UNARY,
+    SLK_PHASE_BOUND,            /* z-updates (inner loop) */
+    SLK_PHASE_MODE,
+    SLK_PHASE_ENERGY,
+    SLK_PHASE_COUNT
+};
+slk_status slk_profile(slk_ctx* ctx, int32_t enable);
+slk_status slk_profile_read(slk_ctx* ctx, double* ms /* [host, SLK_PHASE_COUNT] */,
+                            int64_t* calls /* [host, SLK_PHASE_COUNT] */,
+                            int64_t* kernel_launches /* [host] */);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLK_H */

@@ -1,0 +1,462 @@
+// Bound iterations (inner loop of Algorithm 1) and the SLK-BO mode update.
+//
+// z-update, Eq. (soft-max):   z_p <- exp(a_p + lambda b_p) / 1^t exp(a_p + lambda b_p)
+// pairwise term, Eq. (general-third): b_{p,l} = sum_{e in row p} w_e z_{col(e), l}
+// mode update, Eq. (mode_byproduct):  m_l = argmax_q z_{q,l}
+//
+// Layout: a "group" of G lanes (G = 4, 8, 16 or 32) owns one row p; lane i of
+// the group owns labels i, i + G, ..., so the L floats of a Z row are read as
+// one coalesced segment.  The group loads up to G column indices of its row
+// with one coalesced load and broadcasts them by shuffle; the neighbour rows
+// of Z are then gathered label-parallel.  Row max and row sum use xor
+// shuffles inside the group.  Every update of all rows is one pass of a
+// persistent cooperative kernel; passes are separated by a device-wide
+// barrier whose waits are bounded in time (SLK_ERR_TIMEOUT instead of a hang).
+#include <math.h>
+#include <stdio.h>
+
+#include "slk_internal.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Device-wide barrier for a cooperative launch.  The last block to arrive
+// runs on_last() (before anyone is released), then bumps the generation.
+// Waits give up after kBarrierTimeoutNs, or as soon as another block has
+// reported a timeout; the return value is then false on every block.
+template <class F>
+__device__ bool grid_barrier(DevState* st, unsigned nblocks, F on_last) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = ld_acquire_gpu(&st->barrier_gen);
+        __threadfence();
+        const unsigned prev = atom_add_acq_rel_gpu(&st->barrier_arrive, 1u);
+        if (prev == nblocks - 1) {
+            st->barrier_arrive = 0;
+            on_last();
+            __threadfence();
+            st_release_gpu(&st->barrier_gen, gen + 1);
+        } else {
+            const unsigned long long t0 = globaltimer_ns();
+            while (ld_acquire_gpu(&st->barrier_gen) == gen) {
+                if (ld_acquire_gpu(&st->error) != 0u) { ok = 0; break; }
+                if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                    atomicOr(&st->error, ERR_BARRIER_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int G>
+__device__ __forceinline__ float group_max(float v, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o, G));
+    return v;
+}
+template <int G>
+__device__ __forceinline__ float group_sum(float v, unsigned mask) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return v;
+}
+
+// Logits s_{p,l} = a_{p,l} + lambda b_{p,l} of row p for this lane's labels
+// l = gl + G j (l >= L gets -inf).  b sums the row's edges in CSR order.
+template <int G, int LPL>
+__device__ __forceinline__ void row_logits(int64_t p, int gl, unsigned gmask,
+                                           const float* __restrict__ A,
+                                           const int64_t* __restrict__ row_ptr,
+                                           const int32_t* __restrict__ col_idx,
+                                           const float* __restrict__ w, const float* Zin,
+                                           int L, float lambda, bool with_pair, float (&s)[LPL]) {
+    float b[LPL];
+#pragma unroll
+    for (int j = 0; j < LPL; ++j) b[j] = 0.f;
+    if (with_pair) {
+        const int64_t e0 = __ldg(row_ptr + p), e1 = __ldg(row_ptr + p + 1);
+        for (int64_t base = e0; base < e1; base += G) {
+            const int cnt = (int)((e1 - base) < G ? (e1 - base) : G);
+            int myq = 0;
+            float myw = 1.f;
+            if (gl < cnt) {
+                myq = __ldg(col_idx + base + gl);
+                if (w) myw = __ldg(w + base + gl);
+            }
+            for (int t = 0; t < cnt; ++t) {
+                const int q = __shfl_sync(gmask, myq, t, G);
+                const float wq = __shfl_sync(gmask, myw, t, G);
+                const float* zq = Zin + (int64_t)q * L;
+#pragma unroll
+                for (int j = 0; j < LPL; ++j) {
+                    const int l = gl + G * j;
+                    if (l < L) b[j] = fmaf(wq, __ldcg(zq + l), b[j]);
+                }
+            }
+        }
+    }
+    const float* ap = A + p * (int64_t)L;
+#pragma unroll
+    for (int j = 0; j < LPL; ++j) {
+        const int l = gl + G * j;
+        s[j] = (l < L) ? fmaf(lambda, b[j], __ldg(ap + l)) : -INFINITY;
+    }
+}
+
+// One z-update of row p: Zout[p] = softmax(s_p); returns max |z_new - z_old|
+// over this lane's labels.
+template <int G, int LPL>
+__device__ __forceinline__ float row_update(int64_t p, int gl, unsigned gmask, const float* A,
+                                            const int64_t* row_ptr, const int32_t* col_idx,
+                                            const float* w, const float* Zin, float* Zout,
+                                            int L, float lambda) {
+    float s[LPL];
+    row_logits<G, LPL>(p, gl, gmask, A, row_ptr, col_idx, w, Zin, L, lambda, true, s);
+    float m = s[0];
+#pragma unroll
+    for (int j = 1; j < LPL; ++j) m = fmaxf(m, s[j]);
+    m = group_max<G>(m, gmask);
+    float e[LPL], sum = 0.f;
+#pragma unroll
+    for (int j = 0; j < LPL; ++j) {
+        e[j] = (gl + G * j < L) ? expf(s[j] - m) : 0.f;
+        sum += e[j];
+    }
+    sum = group_sum<G>(sum, gmask);
+    float d = 0.f;
+    const int64_t off = p * (int64_t)L;
+#pragma unroll
+    for (int j = 0; j < LPL; ++j) {
+        const int l = gl + G * j;
+        if (l < L) {
+            const float z = e[j] / sum;
+            d = fmaxf(d, fabsf(z - __ldcg(Zin + off + l)));
+            __stcg(Zout + off + l, z);
+        }
+    }
+    return d;
+}
+
+__device__ __forceinline__ float block_max(float v, float* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float m = 0.f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, red[i]);
+    return m;  // valid on thread 0
+}
+
+// Persistent inner loop.  Update it reads buffer it % 2 and writes the other;
+// Z0 holds the starting iterate.
+template <int G, int LPL>
+__global__ void __launch_bounds__(kThreads)
+bound_persistent_kernel(const float* __restrict__ A, const int64_t* __restrict__ row_ptr,
+                        const int32_t* __restrict__ col_idx, const float* __restrict__ w,
+                        int64_t N, int L, float lambda, float* Z0, float* Z1, int max_iters,
+                        float tol, DevState* st) {
+    constexpr int RPW = 32 / G;
+    __shared__ float red[kThreads / 32];
+    __shared__ int s_done;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane % G, grp = lane / G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t gwarp = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+    int it = 0;
+    while (it < max_iters) {
+        const float* Zin = (it & 1) ? Z1 : Z0;
+        float* Zout = (it & 1) ? Z0 : Z1;
+        float d = 0.f;
+        for (int64_t base = gwarp * RPW; base < N; base += nwarps * RPW) {
+            const int64_t p = base + grp;
+            if (p < N) d = fmaxf(d, row_update<G, LPL>(p, gl, gmask, A, row_ptr, col_idx, w,
+                                                        Zin, Zout, L, lambda));
+        }
+        const float bm = block_max(d, red);
+        if (threadIdx.x == 0) atomicMax(&st->delta_bits[it % 3], __float_as_uint(bm));
+        const int slot_next = (it + 1) % 3;
+        if (!grid_barrier(st, gridDim.x, [&] { st->delta_bits[slot_next] = 0u; })) return;
+        if (threadIdx.x == 0) {
+            const float dl = __uint_as_float(ld_acquire_gpu(&st->delta_bits[it % 3]));
+            s_done = (dl <= tol) ? 1 : 0;
+            if (blockIdx.x == 0) st->last_delta = dl;
+        }
+        __syncthreads();
+        ++it;
+        if (s_done) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->iters_done = it;
+}
+
+// One update per launch (used when cooperative launch is unavailable).  The
+// launch for update `it` first looks at the previous update's delta and, once
+// converged, does nothing.
+template <int G, int LPL>
+__global__ void __launch_bounds__(kThreads)
+bound_step_kernel(const float* __restrict__ A, const int64_t* __restrict__ row_ptr,
+                  const int32_t* __restrict__ col_idx, const float* __restrict__ w, int64_t N,
+                  int L, float lambda, float* Z0, float* Z1, int it, float tol, DevState* st) {
+    constexpr int RPW = 32 / G;
+    __shared__ float red[kThreads / 32];
+    if (it > 0) {
+        const float prev = __uint_as_float(*(volatile unsigned*)&st->delta_bits[(it - 1) % 3]);
+        if (*(volatile int*)&st->iters_done >= 0 || prev <= tol) {
+            if (blockIdx.x == 0 && threadIdx.x == 0 && st->iters_done < 0) {
+                st->iters_done = it;
+                st->last_delta = prev;
+            }
+            return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->delta_bits[(it + 1) % 3] = 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane % G, grp = lane / G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    const float* Zin = (it & 1) ? Z1 : Z0;
+    float* Zout = (it & 1) ? Z0 : Z1;
+    const int64_t p = ((int64_t)blockIdx.x * (kThreads / 32) + warp) * RPW + grp;
+    float d = 0.f;
+    if (p < N) d = row_update<G, LPL>(p, gl, gmask, A, row_ptr, col_idx, w, Zin, Zout, L, lambda);
+    const float bm = block_max(d, red);
+    if (threadIdx.x == 0) atomicMax(&st->delta_bits[it % 3], __float_as_uint(bm));
+}
+
+__global__ void bound_finish_kernel(int max_iters, DevState* st) {
+    if (st->iters_done < 0) {
+        st->iters_done = max_iters;
+        st->last_delta = max_iters > 0 ? __uint_as_float(st->delta_bits[(max_iters - 1) % 3]) : 0.f;
+    }
+}
+
+// After the loop the last iterate sits in buffer iters_done % 2; move it to Z.
+__global__ void swap_if_odd_kernel(float* Z, float* Zp, int64_t n, const DevState* st) {
+    if ((st->iters_done & 1) == 0) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float a = Z[i];
+        Z[i] = Zp[i];
+        Zp[i] = a;
+    }
+}
+
+// --------------------------------------------------------------------------- mode update
+
+// Per row q: logits s (from Z_prev, or s = a when there was no update),
+// label = argmax_l s (ties to the smaller l) and keys
+// log z_{q,l} = (s_l - m) - log1p(sum_{j != j*} exp(s_j - m)).  Each block
+// keeps the best (key, q) of every label in shared memory, packed so that one
+// 64-bit max picks the larger key and, on equal keys, the smaller q.
+template <int G, int LPL>
+__global__ void __launch_bounds__(kThreads)
+mode_rows_kernel(const float* __restrict__ A, const float* __restrict__ Zp,
+                 const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                 const float* __restrict__ w, int64_t N, int L, float lambda, int use_iters_flag,
+                 int32_t* __restrict__ labels, DevState* st) {
+    constexpr int RPW = 32 / G;
+    __shared__ unsigned long long best[SLK_MAX_L];
+    for (int l = threadIdx.x; l < L; l += kThreads) best[l] = 0ull;
+    __syncthreads();
+    const bool with_pair = (Zp != nullptr) && (!use_iters_flag || st->iters_done > 0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane % G, grp = lane / G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t gwarp = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+    for (int64_t base = gwarp * RPW; base < N; base += nwarps * RPW) {
+        const int64_t q = base + grp;
+        if (q >= N) continue;  // whole group skips together
+        float s[LPL];
+        row_logits<G, LPL>(q, gl, gmask, A, row_ptr, col_idx, w, Zp, L, lambda, with_pair, s);
+        // group argmax with ties to the smaller label
+        float m = s[0];
+        int jl = gl;
+#pragma unroll
+        for (int j = 1; j < LPL; ++j)
+            if (s[j] > m) { m = s[j]; jl = gl + G * j; }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const float om = __shfl_xor_sync(gmask, m, o, G);
+            const int ol = __shfl_xor_sync(gmask, jl, o, G);
+            if (om > m || (om == m && ol < jl)) { m = om; jl = ol; }
+        }
+        float r = 0.f;
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            const int l = gl + G * j;
+            if (l < L && l != jl) r += expf(s[j] - m);
+        }
+        r = group_sum<G>(r, gmask);
+        const float lse1 = log1pf(r);
+        if (gl == 0 && labels) labels[q] = jl;
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            const int l = gl + G * j;
+            if (l < L) {
+                const float key = (s[j] - m) - lse1;
+                const unsigned long long packed =
+                    ((unsigned long long)float_to_ordered(key) << 32) |
+                    (unsigned long long)(0xffffffffu - (unsigned)q);
+                atomicMax(&best[l], packed);
+            }
+        }
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < L; l += kThreads)
+        if (best[l]) atomicMax(&st->mode_best[l], best[l]);
+}
+
+__global__ void mode_finish_kernel(int L, int32_t* modes, float* mode_key, DevState* st) {
+    __shared__ int changed;
+    if (threadIdx.x == 0) changed = 0;
+    __syncthreads();
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        const unsigned long long b = st->mode_best[l];
+        const int q = (int)(0xffffffffu - (unsigned)(b & 0xffffffffull));
+        if (q != modes[l]) changed = 1;  // benign race: every writer stores 1
+        modes[l] = q;
+        if (mode_key) mode_key[l] = ordered_to_float((unsigned)(b >> 32));
+        st->mode_best[l] = 0ull;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st->changed = changed;
+}
+
+// ---------------------------------------------------------------- dispatch on L
+
+struct Shape {
+    int G, LPL;
+};
+Shape shape_for(int L) {
+    if (L <= 4) return {4, 1};
+    if (L <= 8) return {8, 1};
+    if (L <= 16) return {16, 1};
+    if (L <= 32) return {32, 1};
+    if (L <= 64) return {32, 2};
+    if (L <= 128) return {32, 4};
+    return {32, 8};
+}
+
+#define SLK_DISPATCH_L(L, MACRO)                 \
+    do {                                         \
+        Shape _s = shape_for(L);                 \
+        if (_s.G == 4) { MACRO(4, 1); }          \
+        else if (_s.G == 8) { MACRO(8, 1); }     \
+        else if (_s.G == 16) { MACRO(16, 1); }   \
+        else if (_s.LPL == 1) { MACRO(32, 1); }  \
+        else if (_s.LPL == 2) { MACRO(32, 2); }  \
+        else if (_s.LPL == 4) { MACRO(32, 4); }  \
+        else { MACRO(32, 8); }                   \
+    } while (0)
+
+}  // namespace
+
+slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
+                        const int32_t* col_idx, const float* w, int64_t N, int L, float lambda,
+                        float* Z, float* Z_prev, int max_iters, float tol, DevState* st) {
+    PhaseScope ps(ctx, SLK_PHASE_BOUND);
+    // reset barrier / delta state; iters_done = -1 marks "not finished"
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, offsetof(DevState, iters_done), ctx->stream));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->iters_done, 0xff, sizeof(int), ctx->stream));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->delta_bits[0], 0, sizeof(st->delta_bits), ctx->stream));
+    if (max_iters == 0) {
+        SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->iters_done, 0, sizeof(int), ctx->stream));
+        SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->last_delta, 0, sizeof(float), ctx->stream));
+        return SLK_OK;
+    }
+    const Shape sh = shape_for(L);
+    const int rows_per_block = (kThreads / 32) * (32 / sh.G);
+    const int64_t blocks_needed = (N + rows_per_block - 1) / rows_per_block;
+    cudaError_t e = cudaSuccess;
+    if (ctx->coop_supported) {
+        SLK_COUNT_LAUNCH(ctx, 1);
+#define SLK_LAUNCH_PERSISTENT(G_, LPL_)                                                        \
+    {                                                                                          \
+        auto kern = bound_persistent_kernel<G_, LPL_>;                                         \
+        int per_sm = 0;                                                                        \
+        SLK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0)); \
+        if (per_sm < 1) return set_err(ctx, SLK_ERR_CUDA, "bound kernel cannot be resident"); \
+        int64_t grid = (int64_t)per_sm * ctx->num_sms;                                         \
+        if (grid > blocks_needed) grid = blocks_needed;                                        \
+        const float* a_ = A; const int64_t* rp_ = row_ptr; const int32_t* ci_ = col_idx;       \
+        const float* w_ = w; int64_t n_ = N; int l_ = L; float lam_ = lambda;                  \
+        float* z0_ = Z; float* z1_ = Z_prev; int mi_ = max_iters; float tol_ = tol;            \
+        DevState* st_ = st;                                                                    \
+        void* args[] = {&a_, &rp_, &ci_, &w_, &n_, &l_, &lam_, &z0_, &z1_, &mi_, &tol_, &st_}; \
+        e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid), dim3(kThreads), \
+                                        args, 0, ctx->stream);                                 \
+    }
+        SLK_DISPATCH_L(L, SLK_LAUNCH_PERSISTENT);
+#undef SLK_LAUNCH_PERSISTENT
+        if (e != cudaSuccess) return cuda_err(ctx, e, "bound_persistent_kernel");
+    } else {
+        SLK_COUNT_LAUNCH(ctx, max_iters + 1);
+#define SLK_LAUNCH_STEPS(G_, LPL_)                                                             \
+    for (int it = 0; it < max_iters; ++it)                                                     \
+        bound_step_kernel<G_, LPL_><<<(unsigned)blocks_needed, kThreads, 0, ctx->stream>>>(    \
+            A, row_ptr, col_idx, w, N, L, lambda, Z, Z_prev, it, tol, st);
+        SLK_DISPATCH_L(L, SLK_LAUNCH_STEPS);
+#undef SLK_LAUNCH_STEPS
+        SLK_LAUNCH_CHECK(ctx, "bound_step_kernel");
+        bound_finish_kernel<<<1, 1, 0, ctx->stream>>>(max_iters, st);
+        SLK_LAUNCH_CHECK(ctx, "bound_finish_kernel");
+    }
+    const int64_t n = N * (int64_t)L;
+    int64_t sgrid = (n + 255) / 256;
+    if (sgrid > (int64_t)ctx->num_sms * 8) sgrid = (int64_t)ctx->num_sms * 8;
+    SLK_COUNT_LAUNCH(ctx, 1);
+    swap_if_odd_kernel<<<(unsigned)sgrid, 256, 0, ctx->stream>>>(Z, Z_prev, n, st);
+    SLK_LAUNCH_CHECK(ctx, "swap_if_odd_kernel");
+    return SLK_OK;
+}
+
+slk_status mode_launch(slk_ctx* ctx, const float* A, const float* Z_prev,
+                       const int64_t* row_ptr, const int32_t* col_idx, const float* w,
+                       int64_t N, int L, float lambda, int32_t* modes, int32_t* labels,
+                       float* mode_key, bool use_iters_flag, DevState* st) {
+    PhaseScope ps(ctx, SLK_PHASE_MODE);
+    SLK_COUNT_LAUNCH(ctx, 2);
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->mode_best[0], 0, sizeof(unsigned long long) * L,
+                                      ctx->stream));
+    const Shape sh = shape_for(L);
+    const int rows_per_block = (kThreads / 32) * (32 / sh.G);
+    int64_t grid = (N + rows_per_block - 1) / rows_per_block;
+    if (grid > (int64_t)ctx->num_sms * 8) grid = (int64_t)ctx->num_sms * 8;
+#define SLK_LAUNCH_MODE(G_, LPL_)                                                        \
+    mode_rows_kernel<G_, LPL_><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(            \
+        A, Z_prev, row_ptr, col_idx, w, N, L, lambda, use_iters_flag ? 1 : 0, labels, st);
+    SLK_DISPATCH_L(L, SLK_LAUNCH_MODE);
+#undef SLK_LAUNCH_MODE
+    SLK_LAUNCH_CHECK(ctx, "mode_rows_kernel");
+    mode_finish_kernel<<<1, 256, 0, ctx->stream>>>(L, modes, mode_key, st);
+    SLK_LAUNCH_CHECK(ctx, "mode_finish_kernel");
+    return SLK_OK;
+}

@@ -1,0 +1,590 @@
+// Exact kNN affinity graph of Section 4.2 (k nearest neighbours q != p by
+// Euclidean distance, ascending by (distance, index)), brute force.
+//
+// Pipeline
+//  1. prep: centre the features (x - mu, mu the column mean: distances are
+//     translation invariant) and round them to the candidate operand type
+//     (float32 or bfloat16).  Per point keep ||xt_p||^2 and the rounding
+//     perturbation rho_p = ||xt_p - (x_p - mu)||, both computed in float64.
+//  2. candidates: a distance-tile kernel evaluates
+//     dt(p, q) = ||xt_p||^2 + ||xt_q||^2 - 2 xt_p . xt_q for all pairs and keeps,
+//     per row and per column split, the KC smallest (KC > k).
+//  3. rerank + certificate (one warp per row): merge the splits, recompute the
+//     KC candidates' distances exactly in float32 from the original features,
+//     keep the k smallest.  With T the KC-th smallest dt, every other point q
+//     satisfies dt(p,q) >= T, hence (rounding bounds below) its true distance
+//     is at least LB = (sqrt(T - delta) - rho_p - rho_max)^2.  The row is
+//     certified when the k-th exact distance, inflated by its own rounding
+//     bound, is below LB; then the row equals a full float32 scan.
+//  4. fallback: rows that fail the certificate are rescanned exactly.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "slk_internal.cuh"
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 16, KT = 256;
+constexpr int QC = 32;      // per-row insertion queue of the candidate kernel
+constexpr int MAXE = 16;    // merge entries per lane (splits * KC <= 512)
+#define kInf __int_as_float(0x7f800000)
+constexpr int kNoIdx = 0x7fffffff;
+
+__device__ __forceinline__ bool lex_less(float d, int i, float d2, int i2) {
+    return d < d2 || (d == d2 && i < i2);
+}
+
+// -------------------------------------------------------------------- prep
+
+__global__ void col_sum_kernel(const float* __restrict__ X, int64_t N, int D,
+                               double* __restrict__ colsum) {
+    __shared__ double sm[8][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
+    const int64_t per = (N + gridDim.y - 1) / gridDim.y;
+    const int64_t r0 = (int64_t)blockIdx.y * per;
+    const int64_t r1 = (r0 + per < N) ? r0 + per : N;
+    double acc = 0.0;
+    if (c < D)
+        for (int64_t r = r0 + threadIdx.y; r < r1; r += 8) acc += (double)X[r * D + c];
+    sm[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < D) {
+        double s = 0.0;
+        for (int i = 0; i < 8; ++i) s += sm[i][threadIdx.x];
+        atomicAdd(&colsum[c], s);
+    }
+}
+
+// One warp per padded row: xt = round(x - mu), norms and rho in float64.
+__global__ void prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
+                                 int64_t Np, const double* __restrict__ colsum, int to_bf16,
+                                 float* __restrict__ xt32, __nv_bfloat16* __restrict__ xt16,
+                                 float* __restrict__ norms, float* __restrict__ rho,
+                                 DevState* st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < Np;
+         p += nw) {
+        double n2 = 0.0, r2 = 0.0;
+        for (int j = lane; j < Dp; j += 32) {
+            float v = 0.f;
+            double exact = 0.0;
+            if (p < N && j < D) {
+                const float mu = (float)(colsum[j] / (double)N);
+                const float x = X[p * D + j];
+                exact = (double)x - (double)mu;
+                v = x - mu;
+            }
+            double vv;
+            if (to_bf16) {
+                const __nv_bfloat16 b = __float2bfloat16_rn(v);
+                xt16[p * Dp + j] = b;
+                vv = (double)__bfloat162float(b);
+            } else {
+                xt32[p * Dp + j] = v;
+                vv = (double)v;
+            }
+            n2 += vv * vv;
+            r2 += (vv - exact) * (vv - exact);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+            r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+        }
+        if (lane == 0) {
+            const float nf = (float)n2;
+            const float rf = __double2float_ru(sqrt(r2));
+            norms[p] = nf;
+            rho[p] = rf;
+            if (p < N) {
+                atomicMax(&st->knn_max_norm_bits, __float_as_uint(nf));
+                atomicMax(&st->knn_max_rho_bits, __float_as_uint(rf));
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------- fp32 candidate tiles
+
+// Shared-memory layout of the candidate kernel (dynamic).
+template <int KC>
+struct CandSmem {
+    float As[2][BK][BM];
+    float Bs[2][BK][BN];
+    float list_d[BM][KC];
+    int list_i[BM][KC];
+    float q_d[BM][QC];
+    int q_i[BM][QC];
+    int q_cnt[BM];
+    float thr[BM];
+    float nrow[BM];
+    float ncol[BN];
+};
+
+// Merge the queued entries of row r (owner thread) into its sorted list.
+template <int KC>
+__device__ __forceinline__ void merge_queue(CandSmem<KC>& s, int r) {
+    const int n = min(s.q_cnt[r], QC);
+    for (int e = 0; e < n; ++e) {
+        const float d = s.q_d[r][e];
+        const int i = s.q_i[r][e];
+        if (!lex_less(d, i, s.list_d[r][KC - 1], s.list_i[r][KC - 1])) continue;
+        int pos = KC - 1;
+        while (pos > 0 && lex_less(d, i, s.list_d[r][pos - 1], s.list_i[r][pos - 1])) {
+            s.list_d[r][pos] = s.list_d[r][pos - 1];
+            s.list_i[r][pos] = s.list_i[r][pos - 1];
+            --pos;
+        }
+        s.list_d[r][pos] = d;
+        s.list_i[r][pos] = i;
+    }
+    s.q_cnt[r] = 0;
+    s.thr[r] = s.list_d[r][KC - 1];
+}
+
+// Grid: (row blocks of 128, column splits).  Thread (ty, tx) = (t / 16, t % 16)
+// owns rows {4ty..4ty+3, 64+4ty..64+4ty+3} and the same pattern of columns.
+template <int KC>
+__global__ void __launch_bounds__(KT, 2)
+knn_cand_fp32_kernel(const float* __restrict__ xt, const float* __restrict__ norms, int64_t N,
+                     int Dp, int n_tiles, int64_t Np, float* __restrict__ cand_d,
+                     int32_t* __restrict__ cand_i) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CandSmem<KC>& s = *reinterpret_cast<CandSmem<KC>*>(smem_raw);
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+    const int64_t row0 = (int64_t)blockIdx.x * BM;
+    const int sp = blockIdx.y, splits = gridDim.y;
+    const int tile0 = (int)((int64_t)sp * n_tiles / splits);
+    const int tile1 = (int)((int64_t)(sp + 1) * n_tiles / splits);
+    if (t < BM) {
+        for (int j = 0; j < KC; ++j) { s.list_d[t][j] = kInf; s.list_i[t][j] = kNoIdx; }
+        s.q_cnt[t] = 0;
+        s.thr[t] = kInf;
+        s.nrow[t] = norms[row0 + t];
+    }
+    const int nk = Dp / BK;
+    // load mapping: element idx = t + 256 i (i = 0, 1) -> row idx % 128, k-quad idx / 128
+    const int lr0 = t & 127, lq0 = t >> 7;          // i = 0: quads 0, 1
+    const int lq1 = lq0 + 2;                        // i = 1: quads 2, 3
+    for (int tile = tile0; tile < tile1; ++tile) {
+        const int64_t col0 = (int64_t)tile * BN;
+        __syncthreads();  // previous epilogue finished with ncol / buffers
+        if (t < BN) s.ncol[t] = norms[col0 + t];
+        float acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        const float* pa = xt + (row0 + lr0) * Dp;
+        const float* pb = xt + (col0 + lr0) * Dp;
+        float4 ra0 = __ldg(reinterpret_cast<const float4*>(pa + 4 * lq0));
+        float4 ra1 = __ldg(reinterpret_cast<const float4*>(pa + 4 * lq1));
+        float4 rb0 = __ldg(reinterpret_cast<const float4*>(pb + 4 * lq0));
+        float4 rb1 = __ldg(reinterpret_cast<const float4*>(pb + 4 * lq1));
+        auto stash = [&](int buf) {
+            s.As[buf][4 * lq0 + 0][lr0] = ra0.x; s.As[buf][4 * lq0 + 1][lr0] = ra0.y;
+            s.As[buf][4 * lq0 + 2][lr0] = ra0.z; s.As[buf][4 * lq0 + 3][lr0] = ra0.w;
+            s.As[buf][4 * lq1 + 0][lr0] = ra1.x; s.As[buf][4 * lq1 + 1][lr0] = ra1.y;
+            s.As[buf][4 * lq1 + 2][lr0] = ra1.z; s.As[buf][4 * lq1 + 3][lr0] = ra1.w;
+            s.Bs[buf][4 * lq0 + 0][lr0] = rb0.x; s.Bs[buf][4 * lq0 + 1][lr0] = rb0.y;
+            s.Bs[buf][4 * lq0 + 2][lr0] = rb0.z; s.Bs[buf][4 * lq0 + 3][lr0] = rb0.w;
+            s.Bs[buf][4 * lq1 + 0][lr0] = rb1.x; s.Bs[buf][4 * lq1 + 1][lr0] = rb1.y;
+            s.Bs[buf][4 * lq1 + 2][lr0] = rb1.z; s.Bs[buf][4 * lq1 + 3][lr0] = rb1.w;
+        };
+        stash(0);
+        __syncthreads();
+        for (int kt = 0; kt < nk; ++kt) {
+            const int buf = kt & 1;
+            if (kt + 1 < nk) {
+                const int k0 = (kt + 1) * BK;
+                ra0 = __ldg(reinterpret_cast<const float4*>(pa + k0 + 4 * lq0));
+                ra1 = __ldg(reinterpret_cast<const float4*>(pa + k0 + 4 * lq1));
+                rb0 = __ldg(reinterpret_cast<const float4*>(pb + k0 + 4 * lq0));
+                rb1 = __ldg(reinterpret_cast<const float4*>(pb + k0 + 4 * lq1));
+            }
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                const float4 a0 = *reinterpret_cast<const float4*>(&s.As[buf][kk][4 * ty]);
+                const float4 a1 = *reinterpret_cast<const float4*>(&s.As[buf][kk][64 + 4 * ty]);
+                const float4 b0 = *reinterpret_cast<const float4*>(&s.Bs[buf][kk][4 * tx]);
+                const float4 b1 = *reinterpret_cast<const float4*>(&s.Bs[buf][kk][64 + 4 * tx]);
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            }
+            if (kt + 1 < nk) stash(buf ^ 1);
+            __syncthreads();
+        }
+        // ---- epilogue: dt = n_p + n_q - 2 dot, filter against the row thresholds
+        unsigned long long pend = 0ull;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int r = (i < 4) ? 4 * ty + i : 64 + 4 * ty + (i - 4);
+            const int64_t p = row0 + r;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = (j < 4) ? 4 * tx + j : 64 + 4 * tx + (j - 4);
+                const int64_t q = col0 + c;
+                const float d = fmaf(-2.f, acc[i][j], s.nrow[r] + s.ncol[c]);
+                acc[i][j] = d;
+                if (p < N && q < N && q != p && d <= s.thr[r]) pend |= 1ull << (i * 8 + j);
+            }
+        }
+        while (__syncthreads_or(pend != 0ull)) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = (i < 4) ? 4 * ty + i : 64 + 4 * ty + (i - 4);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (pend & (1ull << (i * 8 + j))) {
+                        const int slot = atomicAdd(&s.q_cnt[r], 1);
+                        if (slot < QC) {
+                            const int c = (j < 4) ? 4 * tx + j : 64 + 4 * tx + (j - 4);
+                            s.q_d[r][slot] = acc[i][j];
+                            s.q_i[r][slot] = (int)(col0 + c);
+                            pend &= ~(1ull << (i * 8 + j));
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            if (t < BM) merge_queue<KC>(s, t);
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = (i < 4) ? 4 * ty + i : 64 + 4 * ty + (i - 4);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if ((pend & (1ull << (i * 8 + j))) && !(acc[i][j] <= s.thr[r]))
+                        pend &= ~(1ull << (i * 8 + j));
+            }
+        }
+    }
+    __syncthreads();
+    if (t < BM) {
+        const int64_t o = ((int64_t)sp * Np + row0 + t) * KC;
+        for (int j = 0; j < KC; ++j) {
+            cand_d[o + j] = s.list_d[t][j];
+            cand_i[o + j] = s.list_i[t][j] == kNoIdx ? -1 : s.list_i[t][j];
+        }
+    }
+}
+
+// ------------------------------------------------------ rerank + certificate
+
+// Exact float32 squared distance, lane-strided over features, xor-butterfly
+// sum: every lane gets the same bits, and the fallback scan uses the same
+// formula so both paths agree bit for bit.
+__device__ __forceinline__ float exact_d2(const float* __restrict__ xp,
+                                          const float* __restrict__ xq, int D, int lane) {
+    float part = 0.f;
+    for (int j = lane; j < D; j += 32) {
+        const float df = xp[j] - xq[j];
+        part = fmaf(df, df, part);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    return part;
+}
+
+template <int KC>
+__global__ void __launch_bounds__(256)
+knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, int splits,
+                  int64_t Np, const float* __restrict__ cand_d, const int32_t* __restrict__ cand_i,
+                  const float* __restrict__ norms, const float* __restrict__ rho, float u_acc,
+                  int64_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx,
+                  float* __restrict__ dist2, int32_t* __restrict__ fb_list, DevState* st) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const double nmax = (double)__uint_as_float(st->knn_max_norm_bits);
+    const double rmax = (double)__uint_as_float(st->knn_max_rho_bits);
+    const double u = 5.9604644775390625e-08;  // 2^-24
+    const double g = (double)Dp * (double)u_acc;
+    const double gam = g / (1.0 - g);
+    const double err_exact = 1.01 * (double)(D + 8) * u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) row_ptr[N] = N * (int64_t)k;
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < N;
+         p += nw) {
+        if (lane == 0) row_ptr[p] = p * (int64_t)k;
+        float ed[MAXE];
+        int ei[MAXE];
+        const int total = splits * KC;
+#pragma unroll
+        for (int m = 0; m < MAXE; ++m) {
+            const int e = lane + 32 * m;
+            ed[m] = kInf;
+            ei[m] = kNoIdx;
+            if (e < total) {
+                const int64_t o = ((int64_t)(e / KC) * Np + p) * KC + (e % KC);
+                const int i = cand_i[o];
+                if (i >= 0) { ed[m] = cand_d[o]; ei[m] = i; }
+            }
+        }
+        // select the KC smallest (distance, index) of the union of splits
+        float cd = kInf, T = kInf;
+        int ci = kNoIdx, nc = 0;
+        for (int c = 0; c < KC; ++c) {
+            float bd = kInf;
+            int bi = kNoIdx;
+#pragma unroll
+            for (int m = 0; m < MAXE; ++m)
+                if (lex_less(ed[m], ei[m], bd, bi)) { bd = ed[m]; bi = ei[m]; }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (lex_less(od, oi, bd, bi)) { bd = od; bi = oi; }
+            }
+            if (bi == kNoIdx) break;
+#pragma unroll
+            for (int m = 0; m < MAXE; ++m)
+                if (ei[m] == bi) { ed[m] = kInf; ei[m] = kNoIdx; }
+            if (lane == c) { cd = bd; ci = bi; }
+            ++nc;
+            T = bd;
+        }
+        if (nc < KC) T = kInf;  // every valid point of the row is a candidate
+        (void)cd;
+        // exact float32 distances of the candidates
+        const float* xp = X + p * D;
+        float myd = kInf;
+        for (int c = 0; c < nc; ++c) {
+            const int q = __shfl_sync(0xffffffffu, ci, c);
+            const float d = exact_d2(xp, X + (int64_t)q * D, D, lane);
+            if (lane == c) myd = d;
+        }
+        // rank of each candidate by (exact distance, index)
+        int rank = 0;
+        for (int c = 0; c < nc; ++c) {
+            const float od = __shfl_sync(0xffffffffu, myd, c);
+            const int oi = __shfl_sync(0xffffffffu, ci, c);
+            if (lex_less(od, oi, myd, ci)) ++rank;
+        }
+        if (lane < nc && rank < k) {
+            col_idx[p * k + rank] = ci;
+            dist2[p * k + rank] = myd;
+        }
+        const unsigned kth = __ballot_sync(0xffffffffu, lane < nc && rank == k - 1);
+        const float dk = __shfl_sync(0xffffffffu, myd, __ffs(kth) - 1);
+        if (lane == 0 && T < kInf) {
+            bool ok = false;
+            const double sn = sqrt((double)norms[p]) + sqrt(nmax);
+            const double delta = (gam + 3.0 * u) * sn * sn;
+            const double tt = (double)T - delta;
+            if (tt > 0.0) {
+                const double root = sqrt(tt) - (double)rho[p] - rmax;
+                if (root > 0.0) {
+                    const double lb = root * root * (1.0 - 1e-12);
+                    ok = (double)dk * (1.0 + 2.02 * err_exact) < lb;
+                }
+            }
+            if (!ok) {
+                const unsigned long long slot = atomicAdd((unsigned long long*)&st->fallback_count, 1ull);
+                fb_list[slot] = (int32_t)p;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ exact fallback
+
+// One block per listed row: 8 warps scan disjoint column subsets keeping a
+// register top-k (lane i holds entry i), then warp 0 merges the 8 lists.
+__global__ void __launch_bounds__(256)
+knn_fallback_kernel(const float* __restrict__ X, int64_t N, int D, int k,
+                    const int32_t* __restrict__ fb_list, const DevState* __restrict__ st,
+                    int32_t* __restrict__ col_idx, float* __restrict__ dist2) {
+    __shared__ float md[8][32];
+    __shared__ int mi[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long count = *(const volatile long long*)&st->fallback_count;
+    for (long long f = blockIdx.x; f < count; f += gridDim.x) {
+        const int64_t p = fb_list[f];
+        const float* xp = X + p * D;
+        float ld = kInf;
+        int li = kNoIdx;
+        for (int64_t q = warp; q < N; q += 8) {
+            if (q == p) continue;
+            const float d = exact_d2(xp, X + q * D, D, lane);
+            const float lastd = __shfl_sync(0xffffffffu, ld, k - 1);
+            const int lasti = __shfl_sync(0xffffffffu, li, k - 1);
+            if (!lex_less(d, (int)q, lastd, lasti)) continue;
+            const bool less = lane < k && lex_less(d, (int)q, ld, li);
+            const unsigned lm = __ballot_sync(0xffffffffu, less);
+            const int pos = __ffs(lm) - 1;
+            const float upd = __shfl_up_sync(0xffffffffu, ld, 1);
+            const int upi = __shfl_up_sync(0xffffffffu, li, 1);
+            if (lane < k) {
+                if (lane == pos) { ld = d; li = (int)q; }
+                else if (lane > pos) { ld = upd; li = upi; }
+            }
+        }
+        md[warp][lane] = ld;
+        mi[warp][lane] = li;
+        __syncthreads();
+        if (warp == 0) {
+            float ed[8];
+            int ei[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                ed[m] = lane < k ? md[m][lane] : kInf;
+                ei[m] = lane < k ? mi[m][lane] : kNoIdx;
+            }
+            for (int c = 0; c < k; ++c) {
+                float bd = kInf;
+                int bi = kNoIdx;
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    if (lex_less(ed[m], ei[m], bd, bi)) { bd = ed[m]; bi = ei[m]; }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (lex_less(od, oi, bd, bi)) { bd = od; bi = oi; }
+                }
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    if (ei[m] == bi) { ed[m] = kInf; ei[m] = kNoIdx; }
+                if (lane == 0) { col_idx[p * k + c] = bi; dist2[p * k + c] = bd; }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int choose_kc(int k) { return (k + 4 <= 16) ? 16 : 32; }
+
+struct KnnPlan {
+    int64_t Np;
+    int Dp, kc, splits, row_blocks, n_tiles;
+    bool bf16;
+};
+
+KnnPlan make_plan(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
+    KnnPlan pl{};
+    pl.bf16 = (precision == SLK_KNN_BF16_RERANK);
+    pl.kc = choose_kc(k);
+    pl.Np = (int64_t)align_up((size_t)N, 128);
+    pl.Dp = (int)align_up((size_t)D, pl.bf16 ? 64 : BK);
+    pl.row_blocks = (int)(pl.Np / BM);
+    pl.n_tiles = (int)(pl.Np / BN);
+    const int max_splits = (32 * MAXE) / pl.kc;
+    const int cap = 2 * (ctx->num_sms > 0 ? ctx->num_sms : 148);  // resident CTAs
+    // smallest split count giving >= 2 waves, then the one with the best wave fill
+    int best = 1;
+    double best_eff = -1.0;
+    for (int s = 1; s <= max_splits && s <= pl.n_tiles; ++s) {
+        const int64_t total = (int64_t)pl.row_blocks * s;
+        const int64_t waves = (total + cap - 1) / cap;
+        double eff = (double)total / (double)(waves * cap);
+        if (total < 2 * cap && s < max_splits && s < pl.n_tiles) eff *= 0.5;  // too few CTAs
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = s; }
+        if (total >= 8 * cap) break;
+    }
+    pl.splits = best;
+    return pl;
+}
+
+}  // namespace
+
+size_t knn_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
+    const KnnPlan pl = make_plan(ctx, N, D, k, precision);
+    size_t b = 0;
+    b += align_up(sizeof(double) * D, 256);
+    b += align_up((pl.bf16 ? 2 : 4) * (size_t)pl.Np * pl.Dp, 256);
+    b += 2 * align_up(sizeof(float) * pl.Np, 256);
+    b += 2 * align_up(sizeof(float) * (size_t)pl.splits * pl.Np * pl.kc, 256);
+    b += align_up(sizeof(int32_t) * (size_t)N, 256);
+    return b + 4096;
+}
+
+slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const float* norms,
+                                int64_t N, int Dp, int64_t Np, int kc, int splits,
+                                float* cand_d, int32_t* cand_i);
+
+slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int k,
+                            int precision, int64_t* row_ptr, int32_t* col_idx, float* dist2,
+                            void* ws, DevState* st) {
+    const KnnPlan pl = make_plan(ctx, N, D, k, precision);
+    WsCarver wc(ws);
+    double* colsum = wc.take<double>(D);
+    void* xt = wc.take<unsigned char>((pl.bf16 ? 2 : 4) * (size_t)pl.Np * pl.Dp);
+    float* norms = wc.take<float>(pl.Np);
+    float* rho = wc.take<float>(pl.Np);
+    float* cand_d = wc.take<float>((size_t)pl.splits * pl.Np * pl.kc);
+    int32_t* cand_i = wc.take<int32_t>((size_t)pl.splits * pl.Np * pl.kc);
+    int32_t* fb = wc.take<int32_t>(N);
+    cudaStream_t s = ctx->stream;
+
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(colsum, 0, sizeof(double) * D, s));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->fallback_count, 0, sizeof(long long), s));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_bits, 0, 2 * sizeof(unsigned int), s));
+    {
+        PhaseScope ps(ctx, SLK_PHASE_KNN_PREP);
+        SLK_COUNT_LAUNCH(ctx, 2);
+        int gy = (int)((N + 4095) / 4096);
+        if (gy > 1024) gy = 1024;
+        if (gy < 1) gy = 1;
+        dim3 grid((unsigned)((D + 31) / 32), (unsigned)gy);
+        col_sum_kernel<<<grid, dim3(32, 8), 0, s>>>(X, N, D, colsum);
+        SLK_LAUNCH_CHECK(ctx, "col_sum_kernel");
+        int64_t pg = (pl.Np + 7) / 8;
+        if (pg > (int64_t)ctx->num_sms * 16) pg = (int64_t)ctx->num_sms * 16;
+        prep_rows_kernel<<<(unsigned)pg, 256, 0, s>>>(
+            X, N, D, pl.Dp, pl.Np, colsum, pl.bf16 ? 1 : 0, pl.bf16 ? nullptr : (float*)xt,
+            pl.bf16 ? (__nv_bfloat16*)xt : nullptr, norms, rho, st);
+        SLK_LAUNCH_CHECK(ctx, "prep_rows_kernel");
+    }
+    float u_acc;
+    {
+    PhaseScope ps(ctx, SLK_PHASE_KNN_CAND);
+    SLK_COUNT_LAUNCH(ctx, 1);
+    if (pl.bf16) {
+        slk_status r = knn_cand_bf16_launch(ctx, (const __nv_bfloat16*)xt, norms, N, pl.Dp, pl.Np,
+                                            pl.kc, pl.splits, cand_d, cand_i);
+        if (r != SLK_OK) return r;
+        u_acc = 2.384185791015625e-07f;  // 2^-22: allows for a coarser tensor-core accumulation
+    } else {
+        u_acc = 5.9604644775390625e-08f;  // 2^-24
+#define SLK_CAND(KC_)                                                                         \
+    {                                                                                         \
+        auto kern = knn_cand_fp32_kernel<KC_>;                                                \
+        const int smem = (int)sizeof(CandSmem<KC_>);                                          \
+        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
+        kern<<<dim3((unsigned)pl.row_blocks, (unsigned)pl.splits), KT, smem, s>>>(            \
+            (const float*)xt, norms, N, pl.Dp, pl.n_tiles, pl.Np, cand_d, cand_i);            \
+    }
+        if (pl.kc == 16) SLK_CAND(16) else SLK_CAND(32)
+#undef SLK_CAND
+        SLK_LAUNCH_CHECK(ctx, "knn_cand_fp32_kernel");
+    }
+    }
+    {
+        PhaseScope ps(ctx, SLK_PHASE_KNN_RERANK);
+        SLK_COUNT_LAUNCH(ctx, 1);
+        int64_t grid = (N + 7) / 8;
+        if (grid > (int64_t)ctx->num_sms * 16) grid = (int64_t)ctx->num_sms * 16;
+        if (pl.kc == 16)
+            knn_rerank_kernel<16><<<(unsigned)grid, 256, 0, s>>>(
+                X, N, D, pl.Dp, k, pl.splits, pl.Np, cand_d, cand_i, norms, rho, u_acc, row_ptr,
+                col_idx, dist2, fb, st);
+        else
+            knn_rerank_kernel<32><<<(unsigned)grid, 256, 0, s>>>(
+                X, N, D, pl.Dp, k, pl.splits, pl.Np, cand_d, cand_i, norms, rho, u_acc, row_ptr,
+                col_idx, dist2, fb, st);
+        SLK_LAUNCH_CHECK(ctx, "knn_rerank_kernel");
+    }
+    {
+        PhaseScope ps(ctx, SLK_PHASE_KNN_FALLBACK);
+        SLK_COUNT_LAUNCH(ctx, 1);
+        knn_fallback_kernel<<<(unsigned)(ctx->num_sms * 2), 256, 0, s>>>(X, N, D, k, fb, st,
+                                                                         col_idx, dist2);
+        SLK_LAUNCH_CHECK(ctx, "knn_fallback_kernel");
+    }
+    return SLK_OK;
+}

@@ -1,0 +1,167 @@
+// Internal declarations shared by the CUDA translation units of the SLK
+// library (never included by anything outside csrc/).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/slk.h"
+
+// ---------------------------------------------------------------- context
+
+struct slk_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int coop_supported = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // scratch workspace, grown on demand (cudaMalloc), freed by slk_destroy
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    // small pinned host block for scalar results
+    void* host_pin = nullptr;
+    // small device block for scalar state (status words, sigma, energy)
+    void* dev_small = nullptr;
+    // phase profiling: recorded (phase, start, stop) event triples
+    bool prof = false;
+    long long launches = 0;
+    struct Rec { int phase; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[SLK_PHASE_COUNT] = {};
+    long long prof_calls[SLK_PHASE_COUNT] = {};
+};
+
+// Records start/stop events of one phase on the context stream (when
+// profiling is enabled).
+struct PhaseScope {
+    slk_ctx* ctx;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseScope(slk_ctx* c, int ph);
+    ~PhaseScope();
+};
+
+// Count kernel launches made by the library.
+#define SLK_COUNT_LAUNCH(ctx, n) ((ctx)->launches += (n))
+
+// Device-side status / scalar block (lives at ctx->dev_small).
+struct DevState {
+    unsigned int barrier_arrive;
+    unsigned int barrier_gen;
+    unsigned int error;          // bit 0: barrier timeout
+    int iters_done;
+    unsigned int delta_bits[3];  // float bits of max |dz| per update (ring of 3)
+    float last_delta;
+    int changed;
+    float sigma;
+    double energy;
+    unsigned long long mode_best[SLK_MAX_L];  // packed (ordered key, ~index) per label
+    // radix select state
+    unsigned int sel_prefix;
+    unsigned int sel_mask;
+    unsigned long long sel_rank;
+    unsigned int sel_hist[256];
+    double sum_d2;
+    long long fallback_count;
+    unsigned int knn_max_norm_bits;   // float bits of max candidate-operand norm^2
+    unsigned int knn_max_rho_bits;    // float bits of max rounding perturbation norm
+};
+
+enum : unsigned int { ERR_BARRIER_TIMEOUT = 1u };
+
+// ---------------------------------------------------------------- helpers
+
+slk_status set_err(slk_ctx* ctx, slk_status st, const char* fmt, ...);
+slk_status cuda_err(slk_ctx* ctx, cudaError_t e, const char* where);
+// Make sure ctx->ws holds at least `bytes`; returns SLK_OK or SLK_ERR_OOM.
+slk_status ensure_ws(slk_ctx* ctx, size_t bytes);
+
+#define SLK_CUDA_TRY(ctx, expr)                                                  \
+    do {                                                                         \
+        cudaError_t _e = (expr);                                                 \
+        if (_e != cudaSuccess) return cuda_err((ctx), _e, #expr);                \
+    } while (0)
+
+#define SLK_LAUNCH_CHECK(ctx, name)                                              \
+    do {                                                                         \
+        cudaError_t _e = cudaGetLastError();                                     \
+        if (_e != cudaSuccess) return cuda_err((ctx), _e, name);                 \
+    } while (0)
+
+static inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over the workspace (256-byte aligned slices).
+struct WsCarver {
+    char* base;
+    size_t off = 0;
+    explicit WsCarver(void* b) : base(static_cast<char*>(b)) {}
+    template <class T>
+    T* take(size_t count) {
+        off = align_up(off, 256);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+// Workspace needed by knn_graph_launch (bytes), and the launcher itself
+// (device outputs only; no synchronisation).
+size_t knn_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int k, int precision);
+slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int k,
+                            int precision, int64_t* row_ptr, int32_t* col_idx, float* dist2,
+                            void* ws, DevState* st);
+
+// weights w[e] = 1 (binary) or exp(-dist2[e] / (2 sigma^2)) with sigma read
+// from *sigma_dev (heat).
+slk_status weights_launch(slk_ctx* ctx, const float* dist2, int64_t nnz, int affinity,
+                          const float* sigma_dev, float* w);
+
+// sigma -> st->sigma (device); no synchronisation.
+size_t sigma_ws_bytes(int64_t n);
+slk_status sigma_launch(slk_ctx* ctx, const float* dist2, int64_t n, int rule, DevState* st);
+
+// A and (optionally) Z0 from modes; sigma taken from *sigma_dev.
+slk_status unary_launch(slk_ctx* ctx, const float* X, int64_t N, int D, const int32_t* modes,
+                        int L, const float* sigma_dev, float* A, float* Z0);
+
+// Inner loop; the final iterate ends in Z, the previous one in Z_prev.
+slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
+                        const int32_t* col_idx, const float* w, int64_t N, int L, float lambda,
+                        float* Z, float* Z_prev, int max_iters, float tol, DevState* st);
+
+// Mode update (keys from A + lambda K Z_prev; Z_prev NULL or st->iters_done == 0
+// when use_iters_flag: s = A).  Writes modes in place, labels, keys, st->changed.
+slk_status mode_launch(slk_ctx* ctx, const float* A, const float* Z_prev,
+                       const int64_t* row_ptr, const int32_t* col_idx, const float* w,
+                       int64_t N, int L, float lambda, int32_t* modes, int32_t* labels,
+                       float* mode_key, bool use_iters_flag, DevState* st);
+
+// Energy -> st->energy (device); sigma from *sigma_dev.
+slk_status energy_launch(slk_ctx* ctx, const float* X, int D, const int32_t* labels,
+                         const int64_t* row_ptr, const int32_t* col_idx, const float* w,
+                         int64_t N, int L, const int32_t* modes, const float* sigma_dev,
+                         float lambda, DevState* st);
+
+// Set st->sigma from a host value (enqueued on the stream).
+slk_status set_sigma_launch(slk_ctx* ctx, float sigma, DevState* st);
+
+// ---------------------------------------------------------------- device helpers
+
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned int float_to_ordered(float f) {
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+#endif

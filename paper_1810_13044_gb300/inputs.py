@@ -174,18 +174,25 @@ def random_graph(N: int, k: int, seed: int, weighted: bool = False):
     if k > N - 1:
         raise ValueError("k must be <= N-1")
     col = np.empty((N, k), dtype=np.int64)
+    m = 4 * k + 8
     for s in range(0, N, 1 << 16):
         n = min(1 << 16, N - s)
-        draw = g.integers(0, N - 1, size=(n, 4 * k + 8))
+        draw = g.integers(0, N - 1, size=(n, m))
         p = np.arange(s, s + n)[:, None]
-        draw = draw + (draw >= p)          # skip the row itself
-        for i in range(n):
-            _, first = np.unique(draw[i], return_index=True)
-            uniq = draw[i][np.sort(first)]
-            if len(uniq) < k:              # tiny N: fall back to a permutation
-                others = np.setdiff1d(np.arange(N), [s + i])
-                uniq = g.permutation(others)
-            col[s + i] = uniq[:k]
+        draw = draw + (draw >= p)                      # skip the row itself
+        # keep the first k distinct values of each row, in draw order
+        order = np.argsort(draw, axis=1, kind="stable")
+        sv = np.take_along_axis(draw, order, 1)
+        first = np.ones_like(sv, dtype=bool)
+        first[:, 1:] = sv[:, 1:] != sv[:, :-1]
+        key = np.where(first, order, m + 1)
+        pos = np.sort(key, axis=1)[:, :k]
+        ok = pos[:, -1] <= m
+        rows_ok = np.nonzero(ok)[0]
+        col[s + rows_ok] = np.take_along_axis(draw[rows_ok], pos[rows_ok], 1)
+        for i in np.nonzero(~ok)[0]:                   # tiny N: a permutation
+            others = np.setdiff1d(np.arange(N), [s + i])
+            col[s + i] = g.permutation(others)[:k]
     row_ptr = (np.arange(N + 1, dtype=np.int64) * k)
     w = g.uniform(0.05, 1.0, size=N * k).astype(np.float32) if weighted else None
     return row_ptr, col.reshape(-1).astype(np.int32), w

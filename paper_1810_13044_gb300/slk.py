@@ -1,0 +1,329 @@
+"""ctypes binding of the C-ABI in ``include/slk.h`` (argument marshalling only).
+
+Every function has the name of its C entry point without the ``slk_`` prefix
+and takes torch CUDA tensors for device arrays; all work runs in the CUDA
+library on the tensors' device, on torch's current stream.  There is no CPU
+fallback: if the library is missing or no GPU is usable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libslk_gb300.so")
+
+SLK_OK, SLK_NOT_CONVERGED = 0, 1
+STATUS = {0: "SLK_OK", 1: "SLK_NOT_CONVERGED", -1: "SLK_ERR_INVALID_ARG", -2: "SLK_ERR_CUDA",
+          -3: "SLK_ERR_OOM", -4: "SLK_ERR_TIMEOUT", -5: "SLK_ERR_NO_DEVICE"}
+AFFINITY = {"binary": 0, "heat": 1}
+PRECISION = {"fp32": 0, "bf16_rerank": 1}
+SIGMA_RULE = {"median": 0, "meansq": 1}
+
+# Every symbol include/slk.h declares (checked by the CPU tests).
+EXPORTS = ["slk_version", "slk_create", "slk_destroy", "slk_set_stream", "slk_last_error",
+           "slk_knn_graph", "slk_sigma", "slk_unary", "slk_bound_iterate", "slk_mode_update",
+           "slk_energy", "slk_default_params", "slk_solve", "slk_solve_host", "slk_profile",
+           "slk_profile_read"]
+PHASES = ["knn_prep", "knn_cand", "knn_rerank", "knn_fallback", "sigma", "unary", "bound", "mode",
+          "energy"]
+
+
+class SlkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
+                ("tol_inner", ctypes.c_float), ("sigma_rule", ctypes.c_int32),
+                ("affinity", ctypes.c_int32), ("knn_precision", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int32), ("inner_iters_total", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("sigma", ctypes.c_float),
+                ("energy", ctypes.c_double), ("knn_fallback_rows", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, f32, f64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
+                             ctypes.c_double)
+    sig = {
+        "slk_version": (ctypes.c_char_p, []),
+        "slk_create": (i32, [ctypes.POINTER(P), ctypes.c_int, P]),
+        "slk_destroy": (i32, [P]),
+        "slk_set_stream": (i32, [P, P]),
+        "slk_last_error": (ctypes.c_char_p, [P]),
+        "slk_knn_graph": (i32, [P, P, i64, i32, i32, i32, i32, f32, P, P, P, P, P]),
+        "slk_sigma": (i32, [P, P, i64, i32, P]),
+        "slk_unary": (i32, [P, P, i64, i32, P, i32, f32, P, P]),
+        "slk_bound_iterate": (i32, [P, P, P, P, P, i64, i32, f32, P, P, i32, f32, P, P]),
+        "slk_mode_update": (i32, [P, P, P, P, P, P, i64, i32, f32, P, P, P, P]),
+        "slk_energy": (i32, [P, P, i32, P, P, P, P, i64, i32, P, f32, f32, P]),
+        "slk_default_params": (None, [ctypes.POINTER(Params)]),
+        "slk_solve": (i32, [P, P, i64, i32, i32, i32, f32, f32, P, ctypes.POINTER(Params), P, P, P,
+                            ctypes.POINTER(Stats)]),
+        "slk_solve_host": (i32, [P, P, i64, i32, i32, i32, f32, f32, P, ctypes.POINTER(Params), P, P,
+                                 P, ctypes.POINTER(Stats)]),
+        "slk_profile": (i32, [P, i32]),
+        "slk_profile_read": (i32, [P, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def version() -> str:
+    return load().slk_version().decode()
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    load().slk_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "sigma_rule" and isinstance(v, str):
+            v = SIGMA_RULE[v]
+        if k == "affinity" and isinstance(v, str):
+            v = AFFINITY[v]
+        if k == "knn_precision" and isinstance(v, str):
+            v = PRECISION[v]
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One library context per (device, stream)."""
+
+    def __init__(self, device: int | None = None, stream: torch.cuda.Stream | None = None):
+        lib = load()
+        if device is None:
+            device = torch.cuda.current_device()
+        self.device = device
+        stream = stream or torch.cuda.current_stream(device)
+        self.handle = ctypes.c_void_p()
+        st = lib.slk_create(ctypes.byref(self.handle), device, ctypes.c_void_p(stream.cuda_stream))
+        if st != SLK_OK:
+            raise SlkError(st, f"slk_create(device={device}) failed")
+        self._lib = lib
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self._lib.slk_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream))
+
+    def profile(self, enable: bool):
+        """Start (clearing the totals) or stop phase profiling."""
+        self.check(self._lib.slk_profile(self.handle, 1 if enable else 0), "slk_profile")
+
+    def profile_read(self):
+        """-> ({phase: ms}, {phase: calls}, kernel launches since profiling was enabled)."""
+        n = len(PHASES)
+        ms = (ctypes.c_double * n)()
+        calls = (ctypes.c_int64 * n)()
+        launches = ctypes.c_int64(0)
+        self.check(self._lib.slk_profile_read(self.handle, ms, calls, ctypes.byref(launches)),
+                   "slk_profile_read")
+        return dict(zip(PHASES, list(ms))), dict(zip(PHASES, list(calls))), launches.value
+
+    def close(self):
+        if self.handle:
+            self._lib.slk_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st, what):
+        if st not in (SLK_OK, SLK_NOT_CONVERGED):
+            msg = self._lib.slk_last_error(self.handle).decode()
+            raise SlkError(st, f"{what}: {msg}")
+        return st
+
+
+_ctx_cache: dict = {}
+
+
+def context(device: int | None = None) -> Context:
+    """A cached context bound to torch's current stream of ``device``."""
+    if device is None:
+        device = torch.cuda.current_device()
+    ctx = _ctx_cache.get(device)
+    if ctx is None:
+        ctx = Context(device)
+        _ctx_cache[device] = ctx
+    ctx.set_stream(torch.cuda.current_stream(device))
+    return ctx
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, shape, name):
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+@dataclass
+class Graph:
+    row_ptr: torch.Tensor   # int64 [N+1]
+    col_idx: torch.Tensor   # int32 [N*k]
+    dist2: torch.Tensor     # float32 [N*k]
+    w: torch.Tensor | None  # float32 [N*k] or None (binary)
+    k: int
+    fallback_rows: int = -1
+
+
+def knn_graph(X: torch.Tensor, k: int, affinity="binary", precision="fp32", sigma=0.0,
+              ctx: Context | None = None) -> Graph:
+    ctx = ctx or context(X.device.index)
+    N, D = X.shape
+    _need(X, torch.float32, (N, D), "X")
+    dev = X.device
+    row_ptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(N * k, dtype=torch.int32, device=dev)
+    d2 = torch.empty(N * k, dtype=torch.float32, device=dev)
+    w = torch.empty(N * k, dtype=torch.float32, device=dev) if affinity == "heat" else None
+    fb = ctypes.c_int64(-1)
+    ctx.check(ctx._lib.slk_knn_graph(ctx.handle, _ptr(X), N, D, k, AFFINITY[affinity],
+                                     PRECISION[precision], float(sigma), _ptr(row_ptr), _ptr(col),
+                                     _ptr(d2), _ptr(w), ctypes.byref(fb)), "slk_knn_graph")
+    return Graph(row_ptr, col, d2, w, k, fb.value)
+
+
+def sigma(dist2: torch.Tensor, rule="median", ctx: Context | None = None) -> float:
+    ctx = ctx or context(dist2.device.index)
+    _need(dist2, torch.float32, (dist2.numel(),), "dist2")
+    out = ctypes.c_float(0.0)
+    ctx.check(ctx._lib.slk_sigma(ctx.handle, _ptr(dist2), dist2.numel(), SIGMA_RULE[rule],
+                                 ctypes.byref(out)), "slk_sigma")
+    return out.value
+
+
+def unary(X: torch.Tensor, modes: torch.Tensor, sig: float, with_z0=True,
+          ctx: Context | None = None):
+    ctx = ctx or context(X.device.index)
+    N, D = X.shape
+    L = modes.numel()
+    _need(X, torch.float32, (N, D), "X")
+    _need(modes, torch.int32, (L,), "modes")
+    A = torch.empty(N, L, dtype=torch.float32, device=X.device)
+    Z0 = torch.empty_like(A) if with_z0 else None
+    ctx.check(ctx._lib.slk_unary(ctx.handle, _ptr(X), N, D, _ptr(modes), L, float(sig), _ptr(A),
+                                 _ptr(Z0)), "slk_unary")
+    return A, Z0
+
+
+def bound_iterate(A, row_ptr, col_idx, w, lam, Z, Z_prev, max_iters, tol=-1.0,
+                  ctx: Context | None = None):
+    """In place on Z (last iterate) and Z_prev; returns (iters_done, last_delta)."""
+    ctx = ctx or context(A.device.index)
+    N, L = A.shape
+    for t, n in ((Z, "Z"), (Z_prev, "Z_prev")):
+        _need(t, torch.float32, (N, L), n)
+    it = ctypes.c_int32(0)
+    dl = ctypes.c_float(0.0)
+    ctx.check(ctx._lib.slk_bound_iterate(ctx.handle, _ptr(A), _ptr(row_ptr), _ptr(col_idx), _ptr(w),
+                                         N, L, float(lam), _ptr(Z), _ptr(Z_prev), int(max_iters),
+                                         float(tol), ctypes.byref(it), ctypes.byref(dl)),
+              "slk_bound_iterate")
+    return it.value, dl.value
+
+
+def mode_update(A, Z_prev, row_ptr, col_idx, w, lam, modes, want_labels=True,
+                ctx: Context | None = None):
+    """In place on modes; returns (changed, labels, mode_key)."""
+    ctx = ctx or context(A.device.index)
+    N, L = A.shape
+    _need(modes, torch.int32, (L,), "modes")
+    labels = torch.empty(N, dtype=torch.int32, device=A.device) if want_labels else None
+    key = torch.empty(L, dtype=torch.float32, device=A.device)
+    ch = ctypes.c_int32(0)
+    ctx.check(ctx._lib.slk_mode_update(ctx.handle, _ptr(A), _ptr(Z_prev), _ptr(row_ptr),
+                                       _ptr(col_idx), _ptr(w), N, L, float(lam), _ptr(modes),
+                                       _ptr(labels), _ptr(key), ctypes.byref(ch)), "slk_mode_update")
+    return ch.value, labels, key
+
+
+def energy(X, labels, row_ptr, col_idx, w, L, modes, sig, lam, ctx: Context | None = None) -> float:
+    ctx = ctx or context(X.device.index)
+    N, D = X.shape
+    E = ctypes.c_double(0.0)
+    ctx.check(ctx._lib.slk_energy(ctx.handle, _ptr(X), D, _ptr(labels), _ptr(row_ptr), _ptr(col_idx),
+                                  _ptr(w), N, int(L), _ptr(modes), float(sig), float(lam),
+                                  ctypes.byref(E)), "slk_energy")
+    return E.value
+
+
+def solve(X: torch.Tensor, L: int, k: int, lam: float, init_modes: torch.Tensor, sigma=0.0,
+          params: Params | None = None, ctx: Context | None = None, out=None):
+    """Whole SLK-BO on device tensors -> (Z, labels, modes, stats dict)."""
+    ctx = ctx or context(X.device.index)
+    N, D = X.shape
+    _need(X, torch.float32, (N, D), "X")
+    _need(init_modes, torch.int32, (L,), "init_modes")
+    if out is None:
+        Z = torch.empty(N, L, dtype=torch.float32, device=X.device)
+        labels = torch.empty(N, dtype=torch.int32, device=X.device)
+        modes = torch.empty(L, dtype=torch.int32, device=X.device)
+    else:
+        Z, labels, modes = out
+    st = Stats()
+    p = params or default_params()
+    ctx.check(ctx._lib.slk_solve(ctx.handle, _ptr(X), N, D, L, k, float(lam), float(sigma),
+                                 _ptr(init_modes), ctypes.byref(p), _ptr(Z), _ptr(labels),
+                                 _ptr(modes), ctypes.byref(st)), "slk_solve")
+    return Z, labels, modes, st.as_dict()
+
+
+def solve_host(X, L: int, k: int, lam: float, init_modes, sigma=0.0, params: Params | None = None,
+               ctx: Context | None = None, want_z=False, out=None):
+    """slk_solve_host on host (CPU, ideally pinned) tensors -> (Z, labels, modes, stats)."""
+    ctx = ctx or context()
+    N, D = X.shape
+    if X.is_cuda or X.dtype != torch.float32 or not X.is_contiguous():
+        raise ValueError("X must be a contiguous float32 CPU tensor")
+    init = init_modes.to(torch.int32).contiguous()
+    if out is None:
+        labels = torch.empty(N, dtype=torch.int32)
+        modes = torch.empty(L, dtype=torch.int32)
+        Z = torch.empty(N, L, dtype=torch.float32) if want_z else None
+    else:
+        Z, labels, modes = out
+    st = Stats()
+    p = params or default_params()
+    hp = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    ctx.check(ctx._lib.slk_solve_host(ctx.handle, hp(X), N, D, L, k, float(lam), float(sigma),
+                                      hp(init), ctypes.byref(p), hp(Z), hp(labels), hp(modes),
+                                      ctypes.byref(st)), "slk_solve_host")
+    return Z, labels, modes, st.as_dict()

@@ -1,0 +1,379 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (float results): Z within 1e-5 max-abs, E within 1e-6 relative,
+unary and sigma within 1e-6 (relative for sigma).  Integer results (kNN
+indices, labels, mode indices) must be identical; where float rounding can
+decide them, a difference is accepted only between near-equal candidates
+(kNN: the oracle's float64 distances of the two points agree within the
+float32 rounding bound of a D-term sum; labels/modes: the oracle's logits /
+log z agree within 1e-5), and such near-ties are counted and bounded.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1810_13044_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+Z_TOL = 1e-5
+E_RTOL = 1e-6
+KEY_TIE = 1e-5
+
+
+@pytest.fixture(scope="module")
+def slk():
+    from paper_1810_13044_gb300 import build, slk as _slk
+    build.build()
+    return _slk
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def exact_d2(X, p, qs):
+    diff = X[qs].astype(np.float64) - X[p].astype(np.float64)
+    return (diff * diff).sum(-1)
+
+
+def check_knn(X, k, g_idx, g_d2, o_idx, o_d2, rows=None, max_tie_rows=0.01):
+    """GPU rows vs oracle rows, identical up to near-equal distances."""
+    N, D = X.shape
+    rows = np.arange(N) if rows is None else rows
+    rtol = 2.0 * (D + 8) * 2.0 ** -24
+    tie_rows = 0
+    for r, p in enumerate(rows):
+        gi, oi = g_idx[r], o_idx[r]
+        assert len(set(gi.tolist())) == k and p not in gi
+        # float32 distances of the GPU are the float32 sums of the exact terms
+        ex = exact_d2(X, p, gi)
+        np.testing.assert_allclose(g_d2[r], ex, rtol=rtol, atol=1e-30)
+        if np.array_equal(gi, oi):
+            continue
+        tie_rows += 1
+        # only swaps among near-equal distances: the sorted exact distances agree
+        np.testing.assert_allclose(np.sort(ex), o_d2[r], rtol=rtol, atol=1e-12)
+    assert tie_rows <= max(1, int(max_tie_rows * len(rows))), tie_rows
+    return tie_rows
+
+
+# ------------------------------------------------------------------------ kNN
+
+@pytest.mark.parametrize("N,D,k,seed", [
+    (2000, 16, 5, 1810),      # the 2000 x 16 blobs workload
+    (2, 3, 1, 1), (3, 1, 2, 2), (17, 5, 16, 3), (129, 37, 5, 4),
+    (777, 130, 24, 5), (300, 1, 5, 6), (1000, 64, 10, 7),
+])
+def test_knn_matches_oracle(slk, N, D, k, seed):
+    if (N, D) == (2000, 16):
+        X, _ = inputs.blobs(seed=seed)
+    else:
+        X = inputs.rng(seed).normal(size=(N, D)).astype(np.float32)
+        if N > 10:
+            X[N // 2] = X[1]          # an exact duplicate point
+    o_idx, o_d2 = oracle.knn(X, k)
+    g = slk.knn_graph(dev(X), k)
+    g_idx = host(g.col_idx).reshape(N, k)
+    g_d2 = host(g.dist2).reshape(N, k)
+    np.testing.assert_array_equal(host(g.row_ptr), np.arange(N + 1) * k)
+    check_knn(X, k, g_idx, g_d2, o_idx, o_d2)
+    assert 0 <= g.fallback_rows <= N
+
+
+def test_knn_heat_weights(slk):
+    X, _ = inputs.blobs(N=500, D=6, n_blobs=3, seed=9)
+    o_idx, o_d2 = oracle.knn(X, 5)
+    sig = 1.7
+    g = slk.knn_graph(dev(X), 5, affinity="heat", sigma=sig)
+    w = host(g.w)
+    np.testing.assert_allclose(w, np.exp(-host(g.dist2).astype(np.float64) / (2 * sig * sig)),
+                               rtol=2e-6)
+    np.testing.assert_allclose(np.sort(w.reshape(500, 5), 1),
+                               np.sort(oracle.heat_weights(o_d2, sig).reshape(500, 5), 1), rtol=1e-5)
+
+
+def test_knn_mnist_like_full_size_sampled(slk):
+    """70000 x 784, k = 5 (the scale workload), sampled rows vs the oracle."""
+    X, _ = inputs.mnist_like()
+    k = 5
+    g = slk.knn_graph(dev(X), k)
+    g_idx = host(g.col_idx).reshape(-1, k)
+    g_d2 = host(g.dist2).reshape(-1, k)
+    rows = inputs.rng(99).choice(X.shape[0], size=24, replace=False)
+    rows = np.concatenate([rows, [0, X.shape[0] - 1]])
+    o_idx, o_d2 = oracle.knn(X, k, rows=rows)
+    check_knn(X, k, g_idx[rows], g_d2[rows], o_idx, o_d2, rows=rows, max_tie_rows=0.1)
+    assert g.fallback_rows < X.shape[0] * 0.05
+
+
+# ---------------------------------------------------------------------- sigma
+
+@pytest.mark.parametrize("n", [1, 2, 5, 10000, 10001])
+@pytest.mark.parametrize("rule", ["median", "meansq"])
+def test_sigma_matches_oracle(slk, n, rule):
+    d2 = inputs.rng(n).uniform(0.01, 30.0, size=n).astype(np.float32)
+    if n > 4:
+        d2[: n // 3] = d2[0]           # many exact ties
+    got = slk.sigma(dev(d2), rule)
+    want = oracle.sigma(d2.astype(np.float64), rule)
+    assert got == pytest.approx(want, rel=1e-6)
+
+
+# ---------------------------------------------------------------------- unary
+
+@pytest.mark.parametrize("N,D,L", [(2000, 16, 5), (70, 1, 1), (333, 31, 33), (500, 784, 10),
+                                   (257, 128, 100), (300, 7, 256)])
+def test_unary_matches_oracle(slk, N, D, L):
+    g = inputs.rng(N + D + L)
+    X = g.normal(size=(N, D)).astype(np.float32)
+    modes = g.choice(N, size=L, replace=False).astype(np.int32)
+    d2 = oracle.knn(X[:50], 3)[1]
+    sig = float(np.sqrt(np.median(d2)) * 1.5)
+    A, Z0 = slk.unary(dev(X), dev(modes), sig)
+    Ao = oracle.unary(X, modes, sig)
+    assert np.abs(host(A) - Ao).max() <= 1e-6
+    assert np.abs(host(Z0) - oracle.softmax_rows(Ao)).max() <= 1e-6
+
+
+# --------------------------------------------------------------- bound iterate
+
+BOUND_CASES = [(1000, 5, 5, False), (1000, 1, 3, False), (1001, 2, 5, True), (2000, 10, 5, False),
+               (777, 17, 7, True), (500, 33, 4, False), (400, 100, 10, True), (300, 256, 5, False),
+               (5, 3, 4, False), (2, 2, 1, True)]
+
+
+def _bound_inputs(N, L, k, weighted, seed):
+    rp, ci, w = inputs.random_graph(N, k, seed=seed, weighted=weighted)
+    A = inputs.random_unary(N, L, seed=seed + 1)
+    Z0 = inputs.random_simplex_rows(N, L, seed=seed + 2)
+    return rp, ci, w, A, Z0
+
+
+@pytest.mark.parametrize("N,L,k,weighted", BOUND_CASES)
+def test_bound_iterate_fixed_iterations(slk, N, L, k, weighted):
+    rp, ci, w, A, Z0 = _bound_inputs(N, L, k, weighted, seed=N * 7 + L)
+    lam = 1.3
+    for iters in (1, 2, 7):
+        Z, Zp = dev(Z0), torch.empty_like(dev(Z0))
+        it, dl = slk.bound_iterate(dev(A), dev(rp), dev(ci), None if w is None else dev(w), lam,
+                                   Z, Zp, iters, tol=-1.0)
+        Zo, Zpo, ito, dlo = oracle.bound_iterate(A, rp, ci, w, lam, Z0, iters)
+        assert it == ito == iters
+        assert np.abs(host(Z) - Zo).max() <= Z_TOL
+        assert np.abs(host(Zp) - Zpo).max() <= Z_TOL
+        assert dl == pytest.approx(dlo, abs=2 * Z_TOL)
+        np.testing.assert_allclose(host(Z).sum(1), 1.0, atol=1e-5)
+
+
+@pytest.mark.parametrize("N,L,k", [(3000, 5, 5), (2000, 12, 6)])
+def test_bound_iterate_until_converged(slk, N, L, k):
+    rp, ci, w, A, Z0 = _bound_inputs(N, L, k, False, seed=5)
+    lam, tol = 1.0, 1e-6
+    Z, Zp = dev(Z0), torch.empty_like(dev(Z0))
+    it, dl = slk.bound_iterate(dev(A), dev(rp), dev(ci), None, lam, Z, Zp, 100, tol=tol)
+    Zo, _, ito, _ = oracle.bound_iterate(A, rp, ci, None, lam, Z0, 100, tol=tol)
+    assert abs(it - ito) <= 1 and it < 100
+    assert dl <= tol
+    assert np.abs(host(Z) - Zo).max() <= Z_TOL
+
+
+@pytest.mark.parametrize("N,L,k,iters", [(70000, 10, 5, 3), (200000, 100, 10, 2)])
+def test_bound_iterate_full_size(slk, N, L, k, iters):
+    """The bound-iteration shapes of the 70000 x 784 (L=10, k=5) and
+    1e6 x 128 (L=100, k=10; 2e5 rows here) workloads."""
+    rp, ci, w, A, Z0 = _bound_inputs(N, L, k, L == 100, seed=11)
+    Z, Zp = dev(Z0), torch.empty_like(dev(Z0))
+    it, _ = slk.bound_iterate(dev(A), dev(rp), dev(ci), None if w is None else dev(w), 1.0, Z, Zp,
+                              iters, tol=-1.0)
+    Zo, _, _, _ = oracle.bound_iterate(A, rp, ci, w, 1.0, Z0, iters)
+    assert it == iters
+    assert np.abs(host(Z) - Zo).max() <= Z_TOL
+
+
+# ----------------------------------------------------------------- mode update
+
+def _near_tie_modes(g_modes, o_modes, logZ):
+    bad = []
+    for l, (gq, oq) in enumerate(zip(g_modes, o_modes)):
+        if gq != oq and abs(logZ[gq, l] - logZ[oq, l]) > KEY_TIE:
+            bad.append((l, gq, oq, logZ[gq, l], logZ[oq, l]))
+    return bad
+
+
+@pytest.mark.parametrize("N,L,k,weighted", BOUND_CASES[:8])
+def test_mode_update_matches_oracle(slk, N, L, k, weighted):
+    rp, ci, w, A, Z0 = _bound_inputs(N, L, k, weighted, seed=N + 3 * L)
+    lam = 2.0
+    Zp_in = dev(Z0)
+    modes = dev(np.zeros(L, np.int32))
+    changed, labels, key = slk.mode_update(dev(A), Zp_in, dev(rp), dev(ci),
+                                           None if w is None else dev(w), lam, modes)
+    S = oracle.logits(A, rp, ci, w, lam, Z0)
+    om, okey = oracle.mode_update(S)
+    logZ = oracle.log_z(S)
+    assert not _near_tie_modes(host(modes), om, logZ)
+    assert np.abs(host(key) - okey).max() <= KEY_TIE
+    ol = oracle.labels(S)
+    gl = host(labels)
+    diff = np.nonzero(gl != ol)[0]
+    for p in diff:
+        assert abs(S[p, gl[p]] - S[p, ol[p]]) <= KEY_TIE
+    assert changed == int(not np.array_equal(om, np.zeros(L)))
+    # without Z_prev the logits are A itself
+    modes2 = dev(np.zeros(L, np.int32))
+    slk.mode_update(dev(A), None, dev(rp), dev(ci), None, lam, modes2)
+    om2, _ = oracle.mode_update(A.astype(np.float64))
+    assert not _near_tie_modes(host(modes2), om2, oracle.log_z(A.astype(np.float64)))
+
+
+def test_mode_update_saturated_logits(slk):
+    """Logit gaps of 40: float32 z rounds to 1.0, the log1p key still orders points."""
+    N, L = 64, 3
+    A = np.zeros((N, L), np.float32)
+    A[:, 0] = 20.0 + np.arange(N, dtype=np.float32) * 0.25   # later points more confident
+    A[:, 1] = -20.0
+    rp, ci, _ = inputs.random_graph(N, 2, seed=1)
+    modes = dev(np.zeros(L, np.int32))
+    slk.mode_update(dev(A), None, dev(rp), dev(ci), None, 1.0, modes)
+    om, _ = oracle.mode_update(A.astype(np.float64))
+    assert host(modes)[0] == om[0] == N - 1
+
+
+# ---------------------------------------------------------------------- energy
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_energy_matches_oracle(slk, weighted):
+    X, _ = inputs.blobs(N=2000, D=16, seed=4)
+    N, L = X.shape[0], 5
+    rp, ci, w = inputs.random_graph(N, 5, seed=8, weighted=weighted)
+    lab = inputs.rng(3).integers(0, L, size=N).astype(np.int32)
+    modes = np.array([1, 100, 200, 300, 1999], np.int32)
+    sig, lam = 2.5, 1.5
+    E = slk.energy(dev(X), dev(lab), dev(rp), dev(ci), None if w is None else dev(w), L, dev(modes),
+                   sig, lam)
+    Eo = oracle.energy(X, lab, rp, ci, w, L, modes, np.float64(np.float32(sig)), np.float32(lam))
+    assert E == pytest.approx(Eo, rel=E_RTOL)
+
+
+# ----------------------------------------------------------------- whole solve
+
+def _compare_solve(out_gpu, ref, X):
+    Z, labels, modes, stats = out_gpu
+    assert stats["outer_iters"] == ref["outer"]
+    np.testing.assert_array_equal(host(modes), ref["modes"])
+    np.testing.assert_array_equal(host(labels), ref["labels"])
+    assert np.abs(host(Z) - ref["Z"]).max() <= Z_TOL
+    assert stats["energy"] == pytest.approx(ref["E"], rel=E_RTOL)
+
+
+def test_solve_blobs_matches_oracle(slk):
+    """2000 x 16 blobs, L=5, k=5, lambda=1, sigma = median kNN distance."""
+    X, _ = inputs.blobs()
+    L, k, lam = 5, 5, 1.0
+    m0 = inputs.kmeanspp(X, L, seed=1810)
+    ref = oracle.solve(X, L, k, lam, m0)
+    out = slk.solve(dev(X), L, k, lam, dev(m0))
+    assert out[3]["sigma"] == pytest.approx(ref["sigma"], rel=1e-6)
+    # the run is then repeated with the oracle's sigma so that both start equal
+    out = slk.solve(dev(X), L, k, lam, dev(m0), sigma=ref["sigma"])
+    _compare_solve(out, ref, X)
+    assert out[3]["converged"] == 1
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_solve_multi_outer_matches_oracle(slk, seed):
+    """Overlapping blobs and a bad seed so that the modes move over several
+    outer iterations."""
+    X, _ = inputs.blobs(N=1500, D=4, n_blobs=6, centre_var=6.0, seed=seed)
+    L, k, lam = 6, 5, 2.0
+    m0 = np.arange(L, dtype=np.int32)
+    ref = oracle.solve(X, L, k, lam, m0)
+    out = slk.solve(dev(X), L, k, lam, dev(m0), sigma=ref["sigma"])
+    _compare_solve(out, ref, X)
+
+
+def test_solve_heat_affinity_and_meansq_sigma(slk):
+    X, _ = inputs.manifolds(N=3000, D=32, n_clusters=6, seed=5)
+    L, k, lam = 6, 10, 1.0
+    m0 = inputs.kmeanspp(X, L, seed=5)
+    idx, d2 = oracle.knn(X, k)
+    sig = oracle.sigma(d2, "meansq")
+    rp = np.arange(X.shape[0] + 1, dtype=np.int64) * k
+    w = oracle.heat_weights(d2.reshape(-1), sig)
+    ref = oracle.solve_graph(X, L, rp, idx.reshape(-1), w, sig, lam, m0)
+    p = slk.default_params(affinity="heat", sigma_rule="meansq")
+    out = slk.solve(dev(X), L, k, lam, dev(m0), params=p)
+    assert out[3]["sigma"] == pytest.approx(sig, rel=1e-6)
+    # weights come from float32 distances: compare within the Z tolerance
+    out = slk.solve(dev(X), L, k, lam, dev(m0), sigma=sig, params=p)
+    Z, labels, modes, stats = out
+    np.testing.assert_array_equal(host(modes), ref["modes"])
+    np.testing.assert_array_equal(host(labels), ref["labels"])
+    assert np.abs(host(Z) - ref["Z"]).max() <= Z_TOL
+    assert stats["energy"] == pytest.approx(ref["E"], rel=E_RTOL)
+
+
+def test_solve_mnist_like_full_size(slk):
+    """The 70000 x 784, L=10, k=5 workload in the launch configuration the
+    benchmark times.  The oracle checks sampled kNN rows; the rest is checked
+    through properties that hold at any size."""
+    X, _ = inputs.mnist_like()
+    L, k, lam = 10, 5, 1.0
+    m0 = inputs.kmeanspp(X, L, seed=1810)
+    Xd = dev(X)
+    Z, labels, modes, st = slk.solve(Xd, L, k, lam, dev(m0))
+    Zh = host(Z).astype(np.float64)
+    np.testing.assert_allclose(Zh.sum(1), 1.0, atol=1e-5)
+    assert np.all(Zh > 0)
+    m = host(modes)
+    assert np.all((m >= 0) & (m < X.shape[0]))
+    lab = host(labels)
+    srt = np.sort(Zh, 1)
+    clear = srt[:, -1] - srt[:, -2] > 1e-6          # rows without a float32 near-tie
+    np.testing.assert_array_equal(lab[clear], np.argmax(Zh, 1)[clear])
+    # each mode holds the largest z of its column (up to float32 near-ties)
+    for l in range(L):
+        assert Zh[m[l], l] >= Zh[:, l].max() - 1e-6
+    # the energy is the library's own Eq. (1) on the returned labels/modes
+    g = slk.knn_graph(Xd, k)
+    E = slk.energy(Xd, labels, g.row_ptr, g.col_idx, None, L, modes, st["sigma"], lam)
+    assert E == pytest.approx(st["energy"], rel=1e-12)
+    # sampled kNN rows of this graph vs the oracle
+    rows = inputs.rng(5).choice(X.shape[0], size=8, replace=False)
+    o_idx, o_d2 = oracle.knn(X, k, rows=rows)
+    check_knn(X, k, host(g.col_idx).reshape(-1, k)[rows], host(g.dist2).reshape(-1, k)[rows],
+              o_idx, o_d2, rows=rows, max_tie_rows=0.25)
+    # the host-buffer entry point gives the same result
+    Zh2, lab2, m2, st2 = slk.solve_host(torch.from_numpy(X).pin_memory(), L, k, lam,
+                                        torch.from_numpy(m0), want_z=True)
+    np.testing.assert_array_equal(lab2.numpy(), lab)
+    np.testing.assert_array_equal(m2.numpy(), m)
+    assert np.abs(Zh2.numpy() - host(Z)).max() == 0.0
+    assert st2["energy"] == pytest.approx(st["energy"], rel=1e-12)
+
+
+# --------------------------------------------------------------- bad arguments
+
+def test_invalid_arguments_are_rejected(slk):
+    X = dev(inputs.rng(0).normal(size=(10, 3)).astype(np.float32))
+    with pytest.raises(slk.SlkError, match="INVALID_ARG"):
+        slk.knn_graph(X, 10)                      # k > N - 1
+    with pytest.raises(slk.SlkError, match="INVALID_ARG"):
+        slk.unary(X, dev(np.arange(11, dtype=np.int32)), 1.0)   # L > N
+    with pytest.raises(slk.SlkError, match="INVALID_ARG"):
+        slk.unary(X, dev(np.arange(3, dtype=np.int32)), -1.0)   # sigma <= 0
+    A = dev(np.ones((10, 3), np.float32))
+    Z = dev(np.full((10, 3), 1 / 3, np.float32))
+    rp, ci, _ = inputs.random_graph(10, 2, seed=0)
+    with pytest.raises(slk.SlkError, match="INVALID_ARG"):
+        slk.bound_iterate(A, dev(rp), dev(ci), None, 1.0, Z, Z, 3)  # aliasing buffers
+    with pytest.raises(slk.SlkError, match="INVALID_ARG"):
+        slk.solve(X, 3, 2, 1.0, dev(np.arange(3, dtype=np.int32)),
+                  params=slk.default_params(max_inner=0))
