@@ -43,7 +43,13 @@ def parse():
     ap.add_argument("--impl", choices=["slk", "reference"], default="slk")
     ap.add_argument("--precision", choices=["fp32", "bf16_rerank"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--rows", type=int, default=None,
+                    help="generate the workload with this many points (profiling captures)")
+    args = ap.parse_args()
+    if args.rows:
+        WORKLOAD["N"] = args.rows
+        WORKLOAD["name"] = f"mnist_like_{args.rows}x784_L10"
+    return args
 
 
 def dist_env():
@@ -292,7 +298,7 @@ def run_slk(args, rank, world, local):
             "config": {"workload": WORKLOAD["name"], "N": N, "D": D, "L": L, "k": k, "lambda": lam,
                        "sigma": "median kNN distance", "knn": args.precision,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (X is 219 MB > 129 MB)",
+                       "l2": f"inputs larger than L2 (X is {N * D * 4 / 1e6:.0f} MB, L2 129 MB)",
                        "outer_iters": stats["outer_iters"],
                        "inner_iters_total": stats["inner_iters_total"]},
             "nl_iter_per_s": nl_iter_per_s, "bound_ms_per_50_updates": bound_ms,
