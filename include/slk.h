@@ -48,7 +48,8 @@ typedef enum {
     SLK_ERR_CUDA = -2,
     SLK_ERR_OOM = -3,
     SLK_ERR_TIMEOUT = -4,       /* a device-side wait gave up; results invalid */
-    SLK_ERR_NO_DEVICE = -5
+    SLK_ERR_NO_DEVICE = -5,
+    SLK_ERR_SCRATCH_LIMIT = -6  /* problem larger than a fixed scratch area (see below) */
 } slk_status;
 
 enum { SLK_AFFINITY_BINARY = 0, SLK_AFFINITY_HEAT = 1 };
@@ -192,6 +193,35 @@ slk_status slk_solve_host(slk_ctx* ctx, const float* X, int64_t N, int32_t D, in
                           int32_t k, float lambda, float sigma, const int32_t* init_modes,
                           const slk_params* params, float* Z, int32_t* labels, int32_t* modes,
                           slk_stats* stats);
+
+/* slk_bound_iterate for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is a deployment variant.  It serves code
+ * that may not call cudaMalloc -- for example a plug-in running inside a
+ * host framework that has already reserved the device memory for its own
+ * pool, or a latency-critical serving loop where an allocation (which can
+ * synchronise the whole device) is not allowed after start-up.  It needs
+ * no context and allocates nothing: the ping-pong iterate and the barrier /
+ * convergence words live in one file-scope static device array of
+ * SLK_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads this library
+ * holds until the process exits.
+ *   stream   cudaStream_t to run on; the work runs on the calling thread's
+ *            current device.
+ *   A, row_ptr, col_idx, w, N, L, lambda, Z, max_iters, tol, iters_done,
+ *   last_delta: as in slk_bound_iterate (Z in: starting iterate, out: the
+ *            last iterate); the previous iterate is not returned.
+ * N * L must not exceed SLK_NOALLOC_MAX_ELEMS, else SLK_ERR_SCRATCH_LIMIT is
+ * returned before anything runs.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call reuses the same array and re-initialises
+ * the words that must start at zero; calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * The call synchronises `stream` before returning. */
+#define SLK_NOALLOC_MAX_ELEMS (4u << 20)   /* 4,194,304 floats = 16 MiB */
+#define SLK_NOALLOC_SCRATCH_BYTES (4096u + 4u * SLK_NOALLOC_MAX_ELEMS)
+slk_status slk_bound_iterate_noalloc(void* stream, const float* A, const int64_t* row_ptr,
+                                     const int32_t* col_idx, const float* w, int64_t N,
+                                     int32_t L, float lambda, float* Z, int32_t max_iters,
+                                     float tol, int32_t* iters_done, float* last_delta);
 
 /* Phase profiling.  While enabled, every call records a pair of CUDA events
  * on the context's stream around each phase below (no synchronisation is

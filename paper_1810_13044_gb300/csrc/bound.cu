@@ -15,6 +15,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <mutex>
+
 #include "slk_internal.cuh"
 
 namespace {
@@ -458,5 +460,122 @@ slk_status mode_launch(slk_ctx* ctx, const float* A, const float* Z_prev,
     SLK_LAUNCH_CHECK(ctx, "mode_rows_kernel");
     mode_finish_kernel<<<1, 256, 0, ctx->stream>>>(L, modes, mode_key, st);
     SLK_LAUNCH_CHECK(ctx, "mode_finish_kernel");
+    return SLK_OK;
+}
+
+// ------------------------------------------------- allocation-free variant
+//
+// Scratch of slk_bound_iterate_noalloc: a 4 KiB status block followed by the
+// ping-pong iterate.  Host code must not pass this symbol to a kernel (on
+// the host it names a stand-in, not device memory); its device address is
+// looked up once per device with cudaGetSymbolAddress.
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SLK_NOALLOC_SCRATCH_BYTES];
+static_assert(sizeof(DevState) <= 4096, "status block must fit the reserved 4 KiB");
+
+namespace {
+constexpr int kMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" slk_status slk_bound_iterate_noalloc(void* stream, const float* A, const int64_t* row_ptr,
+                                                const int32_t* col_idx, const float* w, int64_t N,
+                                                int32_t L, float lambda, float* Z, int32_t max_iters,
+                                                float tol, int32_t* iters_done, float* last_delta) {
+    if (!A || !row_ptr || !col_idx || !Z) return SLK_ERR_INVALID_ARG;
+    if (N < 1 || N >= (int64_t)0x7fffffff || L < 1 || L > SLK_MAX_L || max_iters < 0)
+        return SLK_ERR_INVALID_ARG;
+    if (N * (int64_t)L > (int64_t)SLK_NOALLOC_MAX_ELEMS) return SLK_ERR_SCRATCH_LIMIT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return SLK_ERR_NO_DEVICE;
+    }
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return SLK_ERR_CUDA;
+            }
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    DevState* st = static_cast<DevState*>(base);
+    float* Zs = reinterpret_cast<float*>(static_cast<unsigned char*>(base) + 4096);
+
+    // the status words this call relies on start at zero; iters_done = -1
+    if (cudaMemsetAsync(st, 0, sizeof(DevState), s) != cudaSuccess ||
+        cudaMemsetAsync(&st->iters_done, 0xff, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return SLK_ERR_CUDA;
+    }
+    int num_sms = 0, coop = 0;
+    if (cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+        cudaGetLastError();
+        return SLK_ERR_CUDA;
+    }
+    cudaError_t e = cudaSuccess;
+    if (max_iters == 0) {
+        e = cudaMemsetAsync(&st->iters_done, 0, sizeof(int), s);
+    } else {
+        const Shape sh = shape_for(L);
+        const int rows_per_block = (kThreads / 32) * (32 / sh.G);
+        const int64_t blocks_needed = (N + rows_per_block - 1) / rows_per_block;
+#define SLK_NOALLOC_LAUNCH(G_, LPL_)                                                           \
+    {                                                                                          \
+        auto kern = bound_persistent_kernel<G_, LPL_>;                                         \
+        int per_sm = 0;                                                                        \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);         \
+        if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;                 \
+        if (e == cudaSuccess) {                                                                \
+            int64_t grid = (int64_t)per_sm * num_sms;                                          \
+            if (grid > blocks_needed) grid = blocks_needed;                                    \
+            const float* a_ = A; const int64_t* rp_ = row_ptr; const int32_t* ci_ = col_idx;   \
+            const float* w_ = w; int64_t n_ = N; int l_ = L; float lam_ = lambda;              \
+            float* z0_ = Z; float* z1_ = Zs; int mi_ = max_iters; float tol_ = tol;            \
+            DevState* st_ = st;                                                                \
+            void* args[] = {&a_, &rp_, &ci_, &w_, &n_, &l_, &lam_, &z0_, &z1_, &mi_, &tol_, &st_}; \
+            e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid),           \
+                                            dim3(kThreads), args, 0, s);                       \
+        }                                                                                      \
+    }
+        SLK_DISPATCH_L(L, SLK_NOALLOC_LAUNCH);
+#undef SLK_NOALLOC_LAUNCH
+        if (e == cudaSuccess) {
+            const int64_t n = N * (int64_t)L;
+            int64_t sgrid = (n + 255) / 256;
+            if (sgrid > (int64_t)num_sms * 8) sgrid = (int64_t)num_sms * 8;
+            swap_if_odd_kernel<<<(unsigned)sgrid, 256, 0, s>>>(Z, Zs, n, st);
+            e = cudaGetLastError();
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SLK_ERR_CUDA;
+    }
+    // read the status words (iters_done, delta, error) into host variables
+    struct {
+        unsigned int arrive, gen, error;
+        int iters;
+        unsigned int delta[3];
+        float last;
+    } hs;
+    static_assert(offsetof(DevState, last_delta) + sizeof(float) <= sizeof(hs) + 0, "layout");
+    e = cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SLK_ERR_CUDA;
+    }
+    if (hs.error & ERR_BARRIER_TIMEOUT) return SLK_ERR_TIMEOUT;
+    if (iters_done) *iters_done = hs.iters;
+    if (last_delta) *last_delta = hs.last;
     return SLK_OK;
 }

@@ -18,7 +18,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libslk_gb300.so")
 
 SLK_OK, SLK_NOT_CONVERGED = 0, 1
 STATUS = {0: "SLK_OK", 1: "SLK_NOT_CONVERGED", -1: "SLK_ERR_INVALID_ARG", -2: "SLK_ERR_CUDA",
-          -3: "SLK_ERR_OOM", -4: "SLK_ERR_TIMEOUT", -5: "SLK_ERR_NO_DEVICE"}
+          -3: "SLK_ERR_OOM", -4: "SLK_ERR_TIMEOUT", -5: "SLK_ERR_NO_DEVICE",
+          -6: "SLK_ERR_SCRATCH_LIMIT"}
+NOALLOC_MAX_ELEMS = 4 << 20   # SLK_NOALLOC_MAX_ELEMS
 AFFINITY = {"binary": 0, "heat": 1}
 PRECISION = {"fp32": 0, "bf16_rerank": 1}
 SIGMA_RULE = {"median": 0, "meansq": 1}
@@ -27,7 +29,7 @@ SIGMA_RULE = {"median": 0, "meansq": 1}
 EXPORTS = ["slk_version", "slk_create", "slk_destroy", "slk_set_stream", "slk_last_error",
            "slk_knn_graph", "slk_sigma", "slk_unary", "slk_bound_iterate", "slk_mode_update",
            "slk_energy", "slk_default_params", "slk_solve", "slk_solve_host", "slk_profile",
-           "slk_profile_read"]
+           "slk_profile_read", "slk_bound_iterate_noalloc"]
 PHASES = ["knn_prep", "knn_cand", "knn_rerank", "knn_fallback", "sigma", "unary", "bound", "mode",
           "energy"]
 
@@ -84,6 +86,7 @@ def load(path: str = LIB_PATH):
         "slk_solve_host": (i32, [P, P, i64, i32, i32, i32, f32, f32, P, ctypes.POINTER(Params), P, P,
                                  P, ctypes.POINTER(Stats)]),
         "slk_profile": (i32, [P, i32]),
+        "slk_bound_iterate_noalloc": (i32, [P, P, P, P, P, i64, i32, f32, P, i32, f32, P, P]),
         "slk_profile_read": (i32, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -327,3 +330,23 @@ def solve_host(X, L: int, k: int, lam: float, init_modes, sigma=0.0, params: Par
                                       hp(init), ctypes.byref(p), hp(Z), hp(labels), hp(modes),
                                       ctypes.byref(st)), "slk_solve_host")
     return Z, labels, modes, st.as_dict()
+
+
+def bound_iterate_noalloc(A, row_ptr, col_idx, w, lam, Z, max_iters, tol=-1.0):
+    """slk_bound_iterate_noalloc: the z-updates with the library's static
+    scratch (no allocation, no context), on torch's current stream of Z's
+    device.  In place on Z; returns (iters_done, last_delta)."""
+    lib = load()
+    N, L = A.shape
+    _need(Z, torch.float32, (N, L), "Z")
+    it = ctypes.c_int32(0)
+    dl = ctypes.c_float(0.0)
+    with torch.cuda.device(Z.device):
+        stream = torch.cuda.current_stream(Z.device)
+        st = lib.slk_bound_iterate_noalloc(ctypes.c_void_p(stream.cuda_stream), _ptr(A), _ptr(row_ptr),
+                                           _ptr(col_idx), _ptr(w), N, L, float(lam), _ptr(Z),
+                                           int(max_iters), float(tol), ctypes.byref(it),
+                                           ctypes.byref(dl))
+    if st != SLK_OK:
+        raise SlkError(st, "slk_bound_iterate_noalloc")
+    return it.value, dl.value
