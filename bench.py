@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["slk", "reference"], default="slk")
-    ap.add_argument("--precision", choices=["fp32", "bf16_rerank"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16_rerank"], default="bf16_rerank")
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="skip timing the plain float32 solve beside the main arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows", type=int, default=None,
                     help="generate the workload with this many points (profiling captures)")
@@ -232,6 +234,27 @@ def run_slk(args, rank, world, local):
     ms_max = float(t.item())
     value = world * args.steps / (ms_max / 1e3)
 
+    labels_main = out[1].clone()
+    modes_main = out[2].clone()
+    plain = None
+    if not args.no_fp32_compare and args.precision != "fp32":
+        # the plain float32 GPU solve at equal labels (same workload, own timing)
+        p32 = slk.default_params(knn_precision="fp32")
+        out32 = (torch.empty(N, L, device=dev), torch.empty(N, dtype=torch.int32, device=dev),
+                 torch.empty(L, dtype=torch.int32, device=dev))
+        slk.solve(Xd, L, k, lam, m0d, params=p32, ctx=ctx, out=out32)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            slk.solve(Xd, L, k, lam, m0d, params=p32, ctx=ctx, out=out32)
+        f1.record(stream)
+        barrier()
+        ms32 = f0.elapsed_time(f1)
+        plain = {"value": args.steps / (ms32 / 1e3), "unit": "solves/s", "knn": "fp32",
+                 "equal_labels": bool(torch.equal(out32[1], labels_main)),
+                 "equal_modes": bool(torch.equal(out32[2], modes_main))}
+
     # bound iterations alone on this solve's graph: N*L*iter/s (fixed 50 updates)
     g = slk.knn_graph(Xd, k, ctx=ctx)
     A, Z0 = slk.unary(Xd, out[2], stats["sigma"], ctx=ctx)
@@ -293,10 +316,13 @@ def run_slk(args, rank, world, local):
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
+            "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "N": N, "D": D, "L": L, "k": k, "lambda": lam,
-                       "sigma": "median kNN distance", "knn": args.precision,
+                       "sigma": "median kNN distance",
+                       "knn": ("float32 SIMT distance tiles" if args.precision == "fp32" else
+                               "bfloat16 tcgen05 distance tiles for candidates, exact float32 "
+                               "rerank with rounding certificate (same graph as float32)"),
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": f"inputs larger than L2 (X is {N * D * 4 / 1e6:.0f} MB, L2 129 MB)",
                        "outer_iters": stats["outer_iters"],
@@ -304,6 +330,7 @@ def run_slk(args, rank, world, local):
             "nl_iter_per_s": nl_iter_per_s, "bound_ms_per_50_updates": bound_ms,
             "phase_ms_per_step": {k_: v / args.steps for k_, v in ms_phase.items()},
             "roofline": roof,
+            "plain_fp32_gpu": plain,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": N * D * 4 + L * 4,
                     "d2h_bytes_per_step": N * 4 + L * 4},
             "gpu_launches": launches,

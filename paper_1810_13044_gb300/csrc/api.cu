@@ -270,12 +270,12 @@ extern "C" slk_status slk_knn_graph(slk_ctx* ctx, const float* X, int64_t N, int
         r = weights_launch(ctx, dist2, N * (int64_t)k, affinity, &st->sigma, w);
         if (r != SLK_OK) return r;
     }
-    if (fallback_rows) {
-        DevState hs;
-        r = read_state(ctx, &hs);
-        if (r != SLK_OK) return r;
-        *fallback_rows = hs.fallback_count;
-    }
+    DevState hs;
+    r = read_state(ctx, &hs);
+    if (r != SLK_OK) return r;
+    if (hs.knn_error)
+        return set_err(ctx, SLK_ERR_TIMEOUT, "a wait of the tensor-core kNN pipeline timed out");
+    if (fallback_rows) *fallback_rows = hs.fallback_count;
     return SLK_OK;
 }
 
@@ -479,6 +479,8 @@ slk_status solve_device(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int3
         if (r != SLK_OK) return r;
         if (hs.error & ERR_BARRIER_TIMEOUT)
             return set_err(ctx, SLK_ERR_TIMEOUT, "device-wide barrier of the bound kernel timed out");
+        if (hs.knn_error)
+            return set_err(ctx, SLK_ERR_TIMEOUT, "a wait of the tensor-core kNN pipeline timed out");
         ++outer;
         inner_total += hs.iters_done;
         if (!hs.changed) { converged = 1; break; }

@@ -23,6 +23,8 @@
 
 #include "slk_internal.cuh"
 
+int knn_tc_tile_cols();
+
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 16, KT = 256;
@@ -322,12 +324,17 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
             if (e < total) {
                 const int64_t o = ((int64_t)(e / KC) * Np + p) * KC + (e % KC);
                 const int i = cand_i[o];
-                if (i >= 0) { ed[m] = cand_d[o]; ei[m] = i; }
+                if (i >= 0 && i != (int)p) { ed[m] = cand_d[o]; ei[m] = i; }
             }
         }
-        // select the KC smallest (distance, index) of the union of splits
-        float cd = kInf, T = kInf;
-        int ci = kNoIdx, nc = 0;
+        // select the KC smallest (distance, index) of the union of splits;
+        // candidate c lives on lane c % 32, slot c / 32
+        constexpr int CPL = (KC + 31) / 32;
+        float T = kInf;
+        int ci[CPL];
+#pragma unroll
+        for (int h = 0; h < CPL; ++h) ci[h] = kNoIdx;
+        int nc = 0;
         for (int c = 0; c < KC; ++c) {
             float bd = kInf;
             int bi = kNoIdx;
@@ -344,33 +351,70 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
 #pragma unroll
             for (int m = 0; m < MAXE; ++m)
                 if (ei[m] == bi) { ed[m] = kInf; ei[m] = kNoIdx; }
-            if (lane == c) { cd = bd; ci = bi; }
+#pragma unroll
+            for (int h = 0; h < CPL; ++h)
+                if (lane + 32 * h == c) ci[h] = bi;
             ++nc;
             T = bd;
         }
-        if (nc < KC) T = kInf;  // every valid point of the row is a candidate
-        (void)cd;
+        // Lower bound T on dt of every point that is not a candidate: a column
+        // a split rejected has dt >= that split's last list entry (when its
+        // list is full); an entry of the union left out has dt >= the KC-th
+        // selected one.
+        if (nc < KC) T = kInf;
+        {
+            float ts = kInf;
+            if (lane < splits) {
+                const int64_t o = ((int64_t)lane * Np + p) * KC + (KC - 1);
+                if (cand_i[o] >= 0) ts = cand_d[o];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ts = fminf(ts, __shfl_xor_sync(0xffffffffu, ts, o));
+            T = fminf(T, ts);
+        }
         // exact float32 distances of the candidates
         const float* xp = X + p * D;
-        float myd = kInf;
+        float myd[CPL];
+#pragma unroll
+        for (int h = 0; h < CPL; ++h) myd[h] = kInf;
         for (int c = 0; c < nc; ++c) {
-            const int q = __shfl_sync(0xffffffffu, ci, c);
+            int q = kNoIdx;
+#pragma unroll
+            for (int h = 0; h < CPL; ++h)
+                if (c / 32 == h) q = __shfl_sync(0xffffffffu, ci[h], c % 32);
             const float d = exact_d2(xp, X + (int64_t)q * D, D, lane);
-            if (lane == c) myd = d;
+#pragma unroll
+            for (int h = 0; h < CPL; ++h)
+                if (lane + 32 * h == c) myd[h] = d;
         }
         // rank of each candidate by (exact distance, index)
-        int rank = 0;
+        int rank[CPL];
+#pragma unroll
+        for (int h = 0; h < CPL; ++h) rank[h] = 0;
         for (int c = 0; c < nc; ++c) {
-            const float od = __shfl_sync(0xffffffffu, myd, c);
-            const int oi = __shfl_sync(0xffffffffu, ci, c);
-            if (lex_less(od, oi, myd, ci)) ++rank;
+            float od = kInf;
+            int oi = kNoIdx;
+#pragma unroll
+            for (int h = 0; h < CPL; ++h)
+                if (c / 32 == h) {
+                    od = __shfl_sync(0xffffffffu, myd[h], c % 32);
+                    oi = __shfl_sync(0xffffffffu, ci[h], c % 32);
+                }
+#pragma unroll
+            for (int h = 0; h < CPL; ++h)
+                if (lex_less(od, oi, myd[h], ci[h])) ++rank[h];
         }
-        if (lane < nc && rank < k) {
-            col_idx[p * k + rank] = ci;
-            dist2[p * k + rank] = myd;
+        float dk = kInf;
+#pragma unroll
+        for (int h = 0; h < CPL; ++h) {
+            const bool mine = lane + 32 * h < nc;
+            if (mine && rank[h] < k) {
+                col_idx[p * k + rank[h]] = ci[h];
+                dist2[p * k + rank[h]] = myd[h];
+            }
+            const unsigned kth = __ballot_sync(0xffffffffu, mine && rank[h] == k - 1);
+            if (kth) dk = __shfl_sync(0xffffffffu, myd[h], __ffs(kth) - 1);
         }
-        const unsigned kth = __ballot_sync(0xffffffffu, lane < nc && rank == k - 1);
-        const float dk = __shfl_sync(0xffffffffu, myd, __ffs(kth) - 1);
         if (lane == 0 && T < kInf) {
             bool ok = false;
             const double sn = sqrt((double)norms[p]) + sqrt(nmax);
@@ -465,11 +509,31 @@ struct KnnPlan {
     bool bf16;
 };
 
+// Column splits for the persistent tensor-core kernel.  Every split restarts
+// the rows' candidate lists, so prefer few, long work items (row block x
+// split): the smallest split count whose last round is at least 95 % full,
+// else the best-filled one.
+int tc_splits(int row_blocks, int n_tiles, int num_sms, int max_splits) {
+    int best = 1;
+    double best_eff = -1.0;
+    for (int s = 1; s <= max_splits && s <= n_tiles; ++s) {
+        const int64_t items = (int64_t)row_blocks * s;
+        const int64_t rounds = (items + num_sms - 1) / num_sms;
+        const double eff = (double)items / (double)(rounds * num_sms);
+        if (eff >= 0.95) return s;
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = s; }
+    }
+    return best;
+}
+
 KnnPlan make_plan(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
     KnnPlan pl{};
     pl.bf16 = (precision == SLK_KNN_BF16_RERANK);
-    pl.kc = choose_kc(k);
-    pl.Np = (int64_t)align_up((size_t)N, 128);
+    // bfloat16 candidates carry a larger rounding error: keep a longer list
+    // (KC / k >= 5) so that the certificate still holds for most rows
+    pl.kc = pl.bf16 ? (k <= 6 ? 32 : 64) : choose_kc(k);
+    // the tensor-core tiles read 256-row column tiles: keep them inside the matrix
+    pl.Np = (int64_t)align_up((size_t)N, pl.bf16 ? 256 : 128);
     pl.Dp = (int)align_up((size_t)D, pl.bf16 ? 64 : BK);
     pl.row_blocks = (int)(pl.Np / BM);
     pl.n_tiles = (int)(pl.Np / BN);
@@ -487,6 +551,11 @@ KnnPlan make_plan(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
         if (total >= 8 * cap) break;
     }
     pl.splits = best;
+    if (pl.bf16) {
+        const int tiles_tc = (int)((pl.Np + knn_tc_tile_cols() - 1) / knn_tc_tile_cols());
+        pl.splits = tc_splits(pl.row_blocks, tiles_tc, ctx->num_sms > 0 ? ctx->num_sms : 148,
+                              max_splits);
+    }
     return pl;
 }
 
@@ -505,7 +574,7 @@ size_t knn_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int k, int precision) 
 
 slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const float* norms,
                                 int64_t N, int Dp, int64_t Np, int kc, int splits,
-                                float* cand_d, int32_t* cand_i);
+                                float* cand_d, int32_t* cand_i, unsigned int* err_flag);
 
 slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int k,
                             int precision, int64_t* row_ptr, int32_t* col_idx, float* dist2,
@@ -523,7 +592,7 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
 
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(colsum, 0, sizeof(double) * D, s));
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->fallback_count, 0, sizeof(long long), s));
-    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_bits, 0, 2 * sizeof(unsigned int), s));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_bits, 0, 3 * sizeof(unsigned int), s));
     {
         PhaseScope ps(ctx, SLK_PHASE_KNN_PREP);
         SLK_COUNT_LAUNCH(ctx, 2);
@@ -546,9 +615,11 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     SLK_COUNT_LAUNCH(ctx, 1);
     if (pl.bf16) {
         slk_status r = knn_cand_bf16_launch(ctx, (const __nv_bfloat16*)xt, norms, N, pl.Dp, pl.Np,
-                                            pl.kc, pl.splits, cand_d, cand_i);
+                                            pl.kc, pl.splits, cand_d, cand_i, &st->knn_error);
         if (r != SLK_OK) return r;
-        u_acc = 2.384185791015625e-07f;  // 2^-22: allows for a coarser tensor-core accumulation
+        // 2^-23: products exact, each accumulator add off by at most one ulp
+        // (truncating adds); an assumption about the tensor-core accumulator
+        u_acc = 1.1920928955078125e-07f;
     } else {
         u_acc = 5.9604644775390625e-08f;  // 2^-24
 #define SLK_CAND(KC_)                                                                         \
@@ -569,14 +640,14 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
         SLK_COUNT_LAUNCH(ctx, 1);
         int64_t grid = (N + 7) / 8;
         if (grid > (int64_t)ctx->num_sms * 16) grid = (int64_t)ctx->num_sms * 16;
-        if (pl.kc == 16)
-            knn_rerank_kernel<16><<<(unsigned)grid, 256, 0, s>>>(
-                X, N, D, pl.Dp, k, pl.splits, pl.Np, cand_d, cand_i, norms, rho, u_acc, row_ptr,
-                col_idx, dist2, fb, st);
-        else
-            knn_rerank_kernel<32><<<(unsigned)grid, 256, 0, s>>>(
-                X, N, D, pl.Dp, k, pl.splits, pl.Np, cand_d, cand_i, norms, rho, u_acc, row_ptr,
-                col_idx, dist2, fb, st);
+#define SLK_RERANK(KC_)                                                                       \
+    knn_rerank_kernel<KC_><<<(unsigned)grid, 256, 0, s>>>(X, N, D, pl.Dp, k, pl.splits, pl.Np,  \
+                                                          cand_d, cand_i, norms, rho, u_acc,    \
+                                                          row_ptr, col_idx, dist2, fb, st)
+        if (pl.kc == 16) SLK_RERANK(16);
+        else if (pl.kc == 32) SLK_RERANK(32);
+        else SLK_RERANK(64);
+#undef SLK_RERANK
         SLK_LAUNCH_CHECK(ctx, "knn_rerank_kernel");
     }
     {

@@ -1,9 +1,497 @@
-// bfloat16 tensor-core (tcgen05) candidate tiles for the kNN graph.
+// bfloat16 tensor-core (tcgen05) distance tiles for the kNN candidates.
+//
+// Computes dt(p, q) = ||xt_p||^2 + ||xt_q||^2 - 2 xt_p . xt_q for 128 x 256
+// tiles (p: a 128-row block, q: a 256-column tile) with the dot products on
+// the 5th-generation tensor cores, and keeps per row the KC smallest
+// (dt, q) of a column split -- the same contract as the float32 SIMT
+// candidate kernel; the exact float32 rerank and its certificate follow.
+//
+// One persistent CTA per SM, six warps:
+//   warp 0      TMA producer: 64-wide K slices of the A (128 rows) and B
+//               (256 rows) tiles, 128-byte swizzle, into a 3-stage ring;
+//   warp 1      TMEM owner (512 columns = two 128 x 256 fp32 accumulators)
+//               and MMA issuer (one thread, tcgen05.mma kind::f16, M=128,
+//               N=256, K=16 per instruction);
+//   warps 2..5  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, so each
+//               thread owns one row and filters its 256 distances against the
+//               row's running threshold (the KC-th best so far).  Survivors
+//               are appended to a per-row buffer in shared memory; whenever a
+//               lane's buffer holds 16 or more, the whole warp merges in step:
+//               each lane sorts 32 buffered entries with a bitonic network in
+//               registers and bitonic-merges them into its register-resident
+//               sorted top-KC, with no divergence.
+// The two accumulators let the epilogue of tile t overlap the MMAs of t+1.
+// Every mbarrier wait is bounded in time; on a timeout the CTA raises an
+// error bit, drains its own copies in flight, frees TMEM and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <stdint.h>
 
 #include "slk_internal.cuh"
 
-slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16*, const float*, int64_t, int,
-                                int64_t, int, int, float*, int32_t*) {
-    return set_err(ctx, SLK_ERR_INVALID_ARG, "SLK_KNN_BF16_RERANK is not available in this build");
+namespace {
+
+constexpr int TC_M = 128, TC_N = 256, TC_BK = 64;  // K slice: 64 bf16 = 128 bytes
+constexpr int TC_STAGES = 3;
+constexpr int TC_BUF = 48;   // a 32-value chunk lands on a buffer holding at most 15
+constexpr int TC_THREADS = 192;
+constexpr uint32_t A_BYTES = TC_M * TC_BK * 2;  // 16 KiB
+constexpr uint32_t B_BYTES = TC_N * TC_BK * 2;  // 32 KiB
+constexpr uint32_t TMEM_COLS = 512;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+constexpr int kNoIdx = 0x7fffffff;
+
+struct TcSmem {
+    uint8_t a[TC_STAGES][A_BYTES];   // 1024-byte aligned stages (swizzle atoms)
+    uint8_t b[TC_STAGES][B_BYTES];
+    float buf_d[TC_BUF][TC_M];       // per-row append buffer, [slot][row]
+    int buf_i[TC_BUF][TC_M];
+    float ncol[2][TC_N];             // column norms of the tile in each accumulator
+    unsigned long long full[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2];
+    uint32_t tmem_base;
+    int abort;
+};
+constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 1024;
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait for phase `parity` of barrier b.  Gives up (false) after
+// kWaitNs or once another role has raised abort.
+__device__ __noinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, volatile int* abort) {
+    if (mbar_test(b, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (true) {
+        if (mbar_test(b, parity)) return true;
+        if (*abort) return false;
+        if (globaltimer_ns() - t0 > kWaitNs) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map,
+                                            unsigned long long* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
+// 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // LBO (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;       // SBO
+    d |= (uint64_t)1 << 46;                 // version
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor: D fp32, A/B bf16, both K-major, N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                            ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                     uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            su32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Barrier 1 over the 128 epilogue threads with an AND of `ok`: every
+// epilogue warp gets the same answer, so they all leave their loops together.
+__device__ __forceinline__ bool epilogue_bar_and(bool ok) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 128, p;\n"
+        " selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r) : "r"(ok ? 1u : 0u) : "memory");
+    return r != 0;
+}
+
+// (ad, ai) <-> (bd, bi) so that the pair is ascending (up) or descending,
+// ordered by (distance, index).
+__device__ __forceinline__ void cas(float& ad, int& ai, float& bd, int& bi, bool up) {
+    const bool gt = (ad > bd) || (ad == bd && ai > bi);
+    const bool sw = up ? gt : !gt;
+    const float td = sw ? bd : ad;
+    const int ti = sw ? bi : ai;
+    bd = sw ? ad : bd;
+    bi = sw ? ai : bi;
+    ad = td;
+    ai = ti;
+}
+
+// Bitonic sort of 32 (distance, index) pairs held in registers, ascending.
+__device__ __forceinline__ void bitonic_sort32(float (&d)[32], int (&i)[32]) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int x = 0; x < 32; ++x) {
+                const int l = x ^ j;
+                if (l > x) cas(d[x], i[x], d[l], i[l], (x & k) == 0);
+            }
+}
+
+// list (KC entries, sorted ascending) <- the KC smallest of list and b (32
+// entries sorted ascending, padded with +inf to KC): the element-wise
+// minimum of list and reversed b is bitonic and holds exactly those KC; a
+// bitonic merge sorts it.  Only the last 32 slots can take an entry of b.
+template <int KC>
+__device__ __forceinline__ void merge_topk(float (&ld)[KC], int (&li)[KC], const float (&bd)[32],
+                                           const int (&bi)[32]) {
+#pragma unroll
+    for (int x = KC - 32; x < KC; ++x) {
+        const float od = bd[KC - 1 - x];
+        const int oi = bi[KC - 1 - x];
+        if (od < ld[x] || (od == ld[x] && oi < li[x])) { ld[x] = od; li[x] = oi; }
+    }
+#pragma unroll
+    for (int j = KC / 2; j > 0; j >>= 1)
+#pragma unroll
+        for (int x = 0; x < KC; ++x) {
+            const int l = x ^ j;
+            if (l > x) cas(ld[x], li[x], ld[l], li[l], true);
+        }
+}
+
+// Warp-synchronous: fold every lane's buffered entries into its top-KC.
+template <int KC>
+__device__ __forceinline__ void flush_buffer(TcSmem& s, int r, int& cnt, float (&ld)[KC],
+                                             int (&li)[KC]) {
+    for (int base = 0; __any_sync(0xffffffffu, cnt > base); base += 32) {
+        float bd[32];
+        int bi[32];
+#pragma unroll
+        for (int x = 0; x < 32; ++x) {
+            const bool have = base + x < cnt;
+            bd[x] = have ? s.buf_d[base + x][r] : __int_as_float(0x7f800000);
+            bi[x] = have ? s.buf_i[base + x][r] : kNoIdx;
+        }
+        bitonic_sort32(bd, bi);
+        merge_topk<KC>(ld, li, bd, bi);
+    }
+    cnt = 0;
+}
+
+__device__ __forceinline__ void item_range(int item, int splits, int n_tiles, int& rb, int& t0,
+                                           int& t1, int& sp) {
+    rb = item / splits;
+    sp = item % splits;
+    t0 = (int)((int64_t)sp * n_tiles / splits);
+    t1 = (int)((int64_t)(sp + 1) * n_tiles / splits);
+}
+
+template <int TC_KC>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const float* __restrict__ norms, int64_t N, int64_t Np, int Dp, int n_tiles,
+                   int splits, int row_blocks, float* __restrict__ cand_d,
+                   int32_t* __restrict__ cand_i, unsigned int* __restrict__ err_flag) {
+    extern __shared__ uint8_t smem_raw[];
+    TcSmem& s = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                           ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkb = Dp / TC_BK;
+    const int n_items = row_blocks * splits;
+    volatile int* abort = &s.abort;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < TC_STAGES; ++i) {
+            mbar_init(&s.full[i], 1);
+            mbar_init(&s.empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&s.tfull[i], 1);
+            mbar_init(&s.tempty[i], 4);
+        }
+        s.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&s.tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s.tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+            uint32_t iter = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+                int rb, t0, t1, sp;
+                item_range(item, splits, n_tiles, rb, t0, t1, sp);
+                for (int t = t0; t < t1 && ok; ++t) {
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        const uint32_t st = iter % TC_STAGES, use = iter / TC_STAGES;
+                        if (use > 0 && !(ok = mbar_wait(&s.empty[st], (use - 1) & 1, abort))) break;
+                        mbar_expect_tx(&s.full[st], A_BYTES + B_BYTES);
+                        tma_load_2d(s.a[st], &tmA, &s.full[st], kb * TC_BK, rb * TC_M);
+                        tma_load_2d(s.b[st], &tmB, &s.full[st], kb * TC_BK, t * TC_N);
+                        ++iter;
+                    }
+                }
+            }
+            // drain: every issued load must have landed before the CTA leaves
+            if (!ok || *abort) {
+                const uint32_t first = iter > TC_STAGES ? iter - TC_STAGES : 0;
+                for (uint32_t i = first; i < iter; ++i) {
+                    const unsigned long long t0 = globaltimer_ns();
+                    while (!mbar_test(&s.full[i % TC_STAGES], (i / TC_STAGES) & 1) &&
+                           globaltimer_ns() - t0 < kWaitNs) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t iter = 0, tcount = 0;
+            bool ok = true;
+            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+                int rb, t0, t1, sp;
+                item_range(item, splits, n_tiles, rb, t0, t1, sp);
+                for (int t = t0; t < t1 && ok; ++t) {
+                    const uint32_t acc = tcount & 1, use = tcount >> 1;
+                    if (use > 0 && !(ok = mbar_wait(&s.tempty[acc], (use - 1) & 1, abort))) break;
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem + acc * TC_N;
+                    for (int kb = 0; kb < nkb; ++kb) {
+                        const uint32_t st = iter % TC_STAGES;
+                        if (!(ok = mbar_wait(&s.full[st], (iter / TC_STAGES) & 1, abort))) break;
+                        tc_fence_after();
+                        const uint64_t da = sw128_desc(su32(s.a[st]));
+                        const uint64_t db = sw128_desc(su32(s.b[st]));
+#pragma unroll
+                        for (int k = 0; k < TC_BK / 16; ++k)   // 32-byte steps inside the swizzle row
+                            umma(d_tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
+                                 (kb | k) != 0 ? 1u : 0u);
+                        umma_commit(&s.empty[st]);
+                        ++iter;
+                    }
+                    if (!ok) break;
+                    umma_commit(&s.tfull[acc]);
+                    ++tcount;
+                }
+            }
+            if (!ok || *abort) {
+                // let the MMAs already issued finish before TMEM is released
+                if (iter > 0) {
+                    const uint32_t i = iter - 1;
+                    const unsigned long long t0 = globaltimer_ns();
+                    while (!mbar_test(&s.empty[i % TC_STAGES], (i / TC_STAGES) & 1) &&
+                           globaltimer_ns() - t0 < kWaitNs) {
+                    }
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int sub = warp & 3;
+        const int r = sub * 32 + lane;
+        const int et = threadIdx.x - 64;  // 0..127 among the epilogue threads
+        uint32_t tcount = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+            int rb, t0, t1, sp;
+            item_range(item, splits, n_tiles, rb, t0, t1, sp);
+            const int64_t p = (int64_t)rb * TC_M + r;
+            // padding rows / columns get an infinite norm: their distances never pass
+            const float np_ = (p < N) ? norms[p] : __int_as_float(0x7f800000);
+            float ld[TC_KC];
+            int li[TC_KC];
+#pragma unroll
+            for (int x = 0; x < TC_KC; ++x) {
+                ld[x] = __int_as_float(0x7f800000);
+                li[x] = kNoIdx;
+            }
+            int cnt = 0;
+            for (int t = t0; t < t1; ++t) {
+                const uint32_t acc = tcount & 1, use = tcount >> 1;
+                const int64_t col0 = (int64_t)t * TC_N;
+                for (int c = et; c < TC_N; c += 128)
+                    s.ncol[acc][c] = (col0 + c < N) ? norms[col0 + c] : __int_as_float(0x7f800000);
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                ok = epilogue_bar_and(mbar_wait(&s.tfull[acc], use & 1, abort));
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(sub * 32) << 16) + acc * TC_N;
+#pragma unroll 1
+                for (int ch = 0; ch < TC_N / 32; ++ch) {
+                    float v[32];
+                    tmem_ld32(tbase + ch * 32, v);
+                    if (ch == TC_N / 32 - 1) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&s.tempty[acc]);
+                    }
+                    // hot path: distances and their minimum; the row's own column
+                    // (distance ~0) is kept here and dropped by the rerank
+                    const float thr_d = ld[TC_KC - 1];
+                    float mn = __int_as_float(0x7f800000);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        v[j] = fmaf(-2.f, v[j], np_ + s.ncol[acc][ch * 32 + j]);
+                        mn = fminf(mn, v[j]);
+                    }
+                    // rare path: some row of the warp has a distance below its threshold
+                    if (__any_sync(0xffffffffu, mn < thr_d)) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (v[j] < thr_d) {
+                                s.buf_d[cnt][r] = v[j];
+                                s.buf_i[cnt][r] = (int)(col0 + ch * 32 + j);
+                                ++cnt;
+                            }
+                        }
+                        if (__any_sync(0xffffffffu, cnt >= 16)) flush_buffer<TC_KC>(s, r, cnt, ld, li);
+                    }
+                }
+                ++tcount;
+            }
+            if (!ok) break;
+            flush_buffer<TC_KC>(s, r, cnt, ld, li);
+            const int64_t o = ((int64_t)sp * Np + p) * TC_KC;
+#pragma unroll
+            for (int x = 0; x < TC_KC; ++x) {
+                cand_d[o + x] = ld[x];
+                cand_i[o + x] = (li[x] == kNoIdx) ? -1 : li[x];
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && s.abort) atomicOr(err_flag, 2u);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+}  // namespace
+
+int knn_tc_tile_cols() { return TC_N; }
+
+slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const float* norms,
+                                int64_t N, int Dp, int64_t Np, int kc, int splits, float* cand_d,
+                                int32_t* cand_i, unsigned int* err_flag) {
+    if (kc != 32 && kc != 64) return set_err(ctx, SLK_ERR_INVALID_ARG, "bf16 candidates need KC=32 or 64");
+    if (Dp % TC_BK != 0 || Np % TC_M != 0)
+        return set_err(ctx, SLK_ERR_INVALID_ARG, "bad padded shape %lld x %d", (long long)Np, Dp);
+    if ((reinterpret_cast<uintptr_t>(xt) & 15) != 0)
+        return set_err(ctx, SLK_ERR_INVALID_ARG, "bf16 operand not 16-byte aligned");
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_err(ctx, SLK_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    CUtensorMap ta, tb;
+    const cuuint64_t dims[2] = {(cuuint64_t)Dp, (cuuint64_t)Np};
+    const cuuint64_t strides[1] = {(cuuint64_t)Dp * 2};
+    const cuuint32_t box_a[2] = {TC_BK, TC_M};
+    const cuuint32_t box_b[2] = {TC_BK, TC_N};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r1 = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)xt, dims, strides, box_a, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r2 = enc(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)xt, dims, strides, box_b, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
+        return set_err(ctx, SLK_ERR_CUDA, "tensor map encoding failed (%d, %d)", (int)r1, (int)r2);
+    const int row_blocks = (int)(Np / TC_M);
+    const int n_tiles = (int)((Np + TC_N - 1) / TC_N);
+    const int n_items = row_blocks * splits;
+    int grid = ctx->num_sms;
+    if (grid > n_items) grid = n_items;
+    auto kern = (kc == 32) ? knn_cand_tc_kernel<32> : knn_cand_tc_kernel<64>;
+    SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kTcSmemBytes));
+    kern<<<grid, TC_THREADS, kTcSmemBytes, ctx->stream>>>(
+        ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
+    SLK_LAUNCH_CHECK(ctx, "knn_cand_tc_kernel");
+    return SLK_OK;
 }

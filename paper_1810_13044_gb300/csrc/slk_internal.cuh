@@ -69,6 +69,7 @@ struct DevState {
     long long fallback_count;
     unsigned int knn_max_norm_bits;   // float bits of max candidate-operand norm^2
     unsigned int knn_max_rho_bits;    // float bits of max rounding perturbation norm
+    unsigned int knn_error;           // bit 1: a tensor-core pipeline wait timed out
 };
 
 enum : unsigned int { ERR_BARRIER_TIMEOUT = 1u };

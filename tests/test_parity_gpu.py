@@ -66,12 +66,13 @@ def check_knn(X, k, g_idx, g_d2, o_idx, o_d2, rows=None, max_tie_rows=0.01):
 
 # ------------------------------------------------------------------------ kNN
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16_rerank"])
 @pytest.mark.parametrize("N,D,k,seed", [
     (2000, 16, 5, 1810),      # the 2000 x 16 blobs workload
     (2, 3, 1, 1), (3, 1, 2, 2), (17, 5, 16, 3), (129, 37, 5, 4),
-    (777, 130, 24, 5), (300, 1, 5, 6), (1000, 64, 10, 7),
+    (777, 130, 24, 5), (300, 1, 5, 6), (1000, 64, 10, 7), (3000, 200, 10, 8),
 ])
-def test_knn_matches_oracle(slk, N, D, k, seed):
+def test_knn_matches_oracle(slk, N, D, k, seed, precision):
     if (N, D) == (2000, 16):
         X, _ = inputs.blobs(seed=seed)
     else:
@@ -79,7 +80,7 @@ def test_knn_matches_oracle(slk, N, D, k, seed):
         if N > 10:
             X[N // 2] = X[1]          # an exact duplicate point
     o_idx, o_d2 = oracle.knn(X, k)
-    g = slk.knn_graph(dev(X), k)
+    g = slk.knn_graph(dev(X), k, precision=precision)
     g_idx = host(g.col_idx).reshape(N, k)
     g_d2 = host(g.dist2).reshape(N, k)
     np.testing.assert_array_equal(host(g.row_ptr), np.arange(N + 1) * k)
@@ -100,16 +101,53 @@ def test_knn_heat_weights(slk):
 
 
 def test_knn_mnist_like_full_size_sampled(slk):
-    """70000 x 784, k = 5 (the scale workload), sampled rows vs the oracle."""
+    """70000 x 784, k = 5 (the scale workload), sampled rows vs the oracle;
+    the bfloat16 tensor-core candidates give the same graph as the float32
+    ones (both equal a full float32 scan once certified or rescanned)."""
     X, _ = inputs.mnist_like()
     k = 5
-    g = slk.knn_graph(dev(X), k)
+    Xd = dev(X)
+    g = slk.knn_graph(Xd, k)
     g_idx = host(g.col_idx).reshape(-1, k)
     g_d2 = host(g.dist2).reshape(-1, k)
     rows = inputs.rng(99).choice(X.shape[0], size=24, replace=False)
     rows = np.concatenate([rows, [0, X.shape[0] - 1]])
     o_idx, o_d2 = oracle.knn(X, k, rows=rows)
     check_knn(X, k, g_idx[rows], g_d2[rows], o_idx, o_d2, rows=rows, max_tie_rows=0.1)
+    assert g.fallback_rows < X.shape[0] * 0.05
+    gb = slk.knn_graph(Xd, k, precision="bf16_rerank")
+    np.testing.assert_array_equal(host(gb.col_idx), host(g.col_idx))
+    np.testing.assert_array_equal(host(gb.dist2), host(g.dist2))
+    assert gb.fallback_rows < X.shape[0] * 0.05
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16_rerank"])
+def test_knn_single_column_split_sampled(slk, precision):
+    """N = 19456 = 152 x 128: one work item per row block on 152 SMs, so every
+    row has a single candidate list (the tensor-core list keeps the row's own
+    column, which the rerank drops)."""
+    X = inputs.rng(21).normal(size=(19456, 40)).astype(np.float32)
+    k = 10
+    g = slk.knn_graph(dev(X), k, precision=precision)
+    rows = inputs.rng(22).choice(X.shape[0], size=64, replace=False)
+    o_idx, o_d2 = oracle.knn(X, k, rows=rows)
+    check_knn(X, k, host(g.col_idx).reshape(-1, k)[rows], host(g.dist2).reshape(-1, k)[rows],
+              o_idx, o_d2, rows=rows, max_tie_rows=0.05)
+
+
+def test_knn_manifolds_full_size_sampled(slk):
+    """The precision workload: 1e6 x 128, k = 10, heat weights, bfloat16
+    tensor-core candidates with the float32 rerank; sampled rows vs the oracle."""
+    X, _ = inputs.manifolds()
+    k = 10
+    g = slk.knn_graph(dev(X), k, affinity="heat", precision="bf16_rerank", sigma=2.0)
+    rows = inputs.rng(23).choice(X.shape[0], size=12, replace=False)
+    o_idx, o_d2 = oracle.knn(X, k, rows=rows)
+    check_knn(X, k, host(g.col_idx).reshape(-1, k)[rows], host(g.dist2).reshape(-1, k)[rows],
+              o_idx, o_d2, rows=rows, max_tie_rows=0.25)
+    w = host(g.w).reshape(-1, k)[rows]
+    np.testing.assert_allclose(w, np.exp(-host(g.dist2).reshape(-1, k)[rows].astype(np.float64) / 8.0),
+                               rtol=2e-6)
     assert g.fallback_rows < X.shape[0] * 0.05
 
 
@@ -273,16 +311,18 @@ def _compare_solve(out_gpu, ref, X):
     assert stats["energy"] == pytest.approx(ref["E"], rel=E_RTOL)
 
 
-def test_solve_blobs_matches_oracle(slk):
+@pytest.mark.parametrize("precision", ["fp32", "bf16_rerank"])
+def test_solve_blobs_matches_oracle(slk, precision):
     """2000 x 16 blobs, L=5, k=5, lambda=1, sigma = median kNN distance."""
     X, _ = inputs.blobs()
     L, k, lam = 5, 5, 1.0
     m0 = inputs.kmeanspp(X, L, seed=1810)
     ref = oracle.solve(X, L, k, lam, m0)
-    out = slk.solve(dev(X), L, k, lam, dev(m0))
+    p = slk.default_params(knn_precision=precision)
+    out = slk.solve(dev(X), L, k, lam, dev(m0), params=p)
     assert out[3]["sigma"] == pytest.approx(ref["sigma"], rel=1e-6)
     # the run is then repeated with the oracle's sigma so that both start equal
-    out = slk.solve(dev(X), L, k, lam, dev(m0), sigma=ref["sigma"])
+    out = slk.solve(dev(X), L, k, lam, dev(m0), sigma=ref["sigma"], params=p)
     _compare_solve(out, ref, X)
     assert out[3]["converged"] == 1
 
