@@ -467,7 +467,7 @@ slk_status solve_device(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int3
         r = unary_launch(ctx, X, N, D, modes, L, &st->sigma, b.A, Z);
         if (r != SLK_OK) return r;
         r = bound_launch(ctx, b.A, b.row_ptr, b.col_idx, w, N, L, lambda, Z, b.Zp, p.max_inner,
-                         p.tol_inner, st);
+                         p.tol_inner, st, k);
         if (r != SLK_OK) return r;
         r = mode_launch(ctx, b.A, b.Zp, b.row_ptr, b.col_idx, w, N, L, lambda, modes, labels,
                         b.mode_key, true, st);

@@ -39,41 +39,48 @@ __device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v
     return old;
 }
 
-// Device-wide barrier for a cooperative launch.  The last block to arrive
-// runs on_last() (before anyone is released), then bumps the generation.
-// Waits give up after kBarrierTimeoutNs, or as soon as another block has
-// reported a timeout; the return value is then false on every block.
-template <class F>
-__device__ bool grid_barrier(DevState* st, unsigned nblocks, F on_last) {
-    __shared__ int s_ok;
+// Device-wide step barrier of the persistent inner loop.  Every block has
+// already folded its max |dz| into delta_bits[slot_now] (a reduction without
+// return).  The last block to arrive reads the final max, clears the slot of
+// the next update, decides convergence (delta <= tol) and publishes it with
+// the new generation (bit 31 = converged), so waiting blocks learn both from
+// one load.  Returns 1 (converged), 0 (go on) or -1 (a wait gave up after
+// kBarrierTimeoutNs, or another block's did).
+__device__ int grid_step(DevState* st, unsigned nblocks, int slot_now, int slot_next, float tol) {
+    __shared__ int s_res;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = 1;
+        int res = 0;
         const unsigned gen = ld_acquire_gpu(&st->barrier_gen);
         __threadfence();
         const unsigned prev = atom_add_acq_rel_gpu(&st->barrier_arrive, 1u);
         if (prev == nblocks - 1) {
             st->barrier_arrive = 0;
-            on_last();
-            __threadfence();
-            st_release_gpu(&st->barrier_gen, gen + 1);
+            st->delta_bits[slot_next] = 0u;
+            const float dl = __uint_as_float(ld_acquire_gpu(&st->delta_bits[slot_now]));
+            st->last_delta = dl;
+            const unsigned done = (dl <= tol) ? 0x80000000u : 0u;
+            st_release_gpu(&st->barrier_gen, ((gen + 1u) & 0x7fffffffu) | done);
+            res = done ? 1 : 0;
         } else {
             const unsigned long long t0 = globaltimer_ns();
-            while (ld_acquire_gpu(&st->barrier_gen) == gen) {
-                if (ld_acquire_gpu(&st->error) != 0u) { ok = 0; break; }
-                if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
-                    atomicOr(&st->error, ERR_BARRIER_TIMEOUT);
-                    ok = 0;
-                    break;
+            unsigned polls = 0, v;
+            while ((v = ld_acquire_gpu(&st->barrier_gen)) == gen) {
+                if ((++polls & 63u) == 0u) {
+                    if (ld_acquire_gpu(&st->error) != 0u) { res = -1; break; }
+                    if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                        atomicOr(&st->error, ERR_BARRIER_TIMEOUT);
+                        res = -1;
+                        break;
+                    }
                 }
-                __nanosleep(32);
             }
+            if (res == 0) res = (v & 0x80000000u) ? 1 : 0;
         }
-        __threadfence();
-        s_ok = ok;
+        s_res = res;
     }
     __syncthreads();
-    return s_ok != 0;
+    return s_res;
 }
 
 template <int G>
@@ -165,6 +172,129 @@ __device__ __forceinline__ float row_update(int64_t p, int gl, unsigned gmask, c
     return d;
 }
 
+// RPG z-updates per lane group at once: rows p0, p0 + stride, ...  Each
+// row's own unary term and previous z are loaded first; neighbour rows of Z
+// are then gathered in windows of W per row, RPG x W loads issued before any
+// of their FMAs, so that their L2 latencies overlap.  Per row the edges are
+// summed in CSR order.  kdeg > 0 means every row has kdeg entries
+// (row_ptr[p] = kdeg p) and skips the row_ptr loads.  Returns max
+// |z_new - z_old| over this lane's entries.
+template <int G, int LPL, int RPG, int W>
+__device__ __forceinline__ float rows_update(int64_t p0, int64_t stride, int64_t N, int gl,
+                                             unsigned gmask, const float* __restrict__ A,
+                                             const int64_t* __restrict__ row_ptr, int kdeg,
+                                             const int32_t* __restrict__ col_idx,
+                                             const float* __restrict__ w, const float* Zin,
+                                             float* Zout, int L, float lambda) {
+    int64_t p[RPG], e0[RPG];
+    int cnt[RPG];
+    int maxc = 0;
+    float av[RPG][LPL], zo[RPG][LPL], b[RPG][LPL];
+#pragma unroll
+    for (int i = 0; i < RPG; ++i) {
+        p[i] = p0 + i * stride;
+        const bool live = p[i] < N;
+        e0[i] = 0;
+        cnt[i] = 0;
+        if (live) {
+            if (kdeg > 0) {
+                e0[i] = p[i] * kdeg;
+                cnt[i] = kdeg;
+            } else {
+                e0[i] = __ldg(row_ptr + p[i]);
+                cnt[i] = (int)(__ldg(row_ptr + p[i] + 1) - e0[i]);
+            }
+        }
+        maxc = max(maxc, cnt[i]);
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            const int l = gl + G * j;
+            const bool ok = live && l < L;
+            av[i][j] = ok ? __ldg(A + p[i] * (int64_t)L + l) : 0.f;
+            zo[i][j] = ok ? __ldcg(Zin + p[i] * (int64_t)L + l) : 0.f;
+            b[i][j] = 0.f;
+        }
+    }
+    for (int c0 = 0; c0 < maxc; c0 += G) {
+        int myq[RPG];
+        float myw[RPG];
+#pragma unroll
+        for (int i = 0; i < RPG; ++i) {
+            myq[i] = 0;
+            myw[i] = 1.f;
+            if (gl < cnt[i] - c0) {
+                myq[i] = __ldg(col_idx + e0[i] + c0 + gl);
+                if (w) myw[i] = __ldg(w + e0[i] + c0 + gl);
+            }
+        }
+        const int cm = min(G, maxc - c0);
+        for (int t0 = 0; t0 < cm; t0 += W) {
+            float zz[RPG][W][LPL], ww[RPG][W];
+#pragma unroll
+            for (int i = 0; i < RPG; ++i)
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    const int t = t0 + u;   // < G: W divides G and t0 < cm <= G
+                    const int q = __shfl_sync(gmask, myq[i], t, G);
+                    ww[i][u] = __shfl_sync(gmask, myw[i], t, G);
+                    const bool ok = t < cnt[i] - c0;
+                    const float* zq = Zin + (int64_t)q * L;
+#pragma unroll
+                    for (int j = 0; j < LPL; ++j) {
+                        const int l = gl + G * j;
+                        zz[i][u][j] = (ok && l < L) ? __ldcg(zq + l) : 0.f;
+                    }
+                }
+#pragma unroll
+            for (int i = 0; i < RPG; ++i)
+#pragma unroll
+                for (int u = 0; u < W; ++u)
+                    if (t0 + u < cnt[i] - c0)
+#pragma unroll
+                        for (int j = 0; j < LPL; ++j) b[i][j] = fmaf(ww[i][u], zz[i][u][j], b[i][j]);
+        }
+    }
+    float dmax = 0.f;
+#pragma unroll
+    for (int i = 0; i < RPG; ++i) {
+        if (p[i] >= N) continue;  // uniform within the group
+        float sv[LPL];
+        float m = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            const int l = gl + G * j;
+            sv[j] = (l < L) ? fmaf(lambda, b[i][j], av[i][j]) : -INFINITY;
+            m = fmaxf(m, sv[j]);
+        }
+        m = group_max<G>(m, gmask);
+        float e[LPL], sum = 0.f;
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            e[j] = (gl + G * j < L) ? expf(sv[j] - m) : 0.f;
+            sum += e[j];
+        }
+        sum = group_sum<G>(sum, gmask);
+        const int64_t off = p[i] * (int64_t)L;
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            const int l = gl + G * j;
+            if (l < L) {
+                const float z = e[j] / sum;
+                dmax = fmaxf(dmax, fabsf(z - zo[i][j]));
+                __stcg(Zout + off + l, z);
+            }
+        }
+    }
+    return dmax;
+}
+
+// Rows per group and gather window per row: about 32 loads in flight per lane.
+template <int G, int LPL>
+struct Tiling {
+    static constexpr int rpg = (LPL == 1) ? 4 : (LPL == 2 ? 2 : 1);
+    static constexpr int w = (LPL <= 2) ? (G < 8 ? G : 8) : (LPL == 4 ? 4 : 2);
+};
+
 __device__ __forceinline__ float block_max(float v, float* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -184,10 +314,9 @@ __global__ void __launch_bounds__(kThreads)
 bound_persistent_kernel(const float* __restrict__ A, const int64_t* __restrict__ row_ptr,
                         const int32_t* __restrict__ col_idx, const float* __restrict__ w,
                         int64_t N, int L, float lambda, float* Z0, float* Z1, int max_iters,
-                        float tol, DevState* st) {
+                        float tol, int kdeg, DevState* st) {
     constexpr int RPW = 32 / G;
     __shared__ float red[kThreads / 32];
-    __shared__ int s_done;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gl = lane % G, grp = lane / G;
     const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
@@ -198,23 +327,18 @@ bound_persistent_kernel(const float* __restrict__ A, const int64_t* __restrict__
         const float* Zin = (it & 1) ? Z1 : Z0;
         float* Zout = (it & 1) ? Z0 : Z1;
         float d = 0.f;
-        for (int64_t base = gwarp * RPW; base < N; base += nwarps * RPW) {
-            const int64_t p = base + grp;
-            if (p < N) d = fmaxf(d, row_update<G, LPL>(p, gl, gmask, A, row_ptr, col_idx, w,
-                                                        Zin, Zout, L, lambda));
-        }
+        constexpr int RPG = Tiling<G, LPL>::rpg;
+        const int64_t stride = nwarps * RPW;
+        for (int64_t base = gwarp * RPW + grp; base < N; base += stride * RPG)
+            d = fmaxf(d, rows_update<G, LPL, RPG, Tiling<G, LPL>::w>(base, stride, N, gl, gmask, A,
+                                                                    row_ptr, kdeg, col_idx, w,
+                                                                    Zin, Zout, L, lambda));
         const float bm = block_max(d, red);
         if (threadIdx.x == 0) atomicMax(&st->delta_bits[it % 3], __float_as_uint(bm));
-        const int slot_next = (it + 1) % 3;
-        if (!grid_barrier(st, gridDim.x, [&] { st->delta_bits[slot_next] = 0u; })) return;
-        if (threadIdx.x == 0) {
-            const float dl = __uint_as_float(ld_acquire_gpu(&st->delta_bits[it % 3]));
-            s_done = (dl <= tol) ? 1 : 0;
-            if (blockIdx.x == 0) st->last_delta = dl;
-        }
-        __syncthreads();
+        const int r = grid_step(st, gridDim.x, it % 3, (it + 1) % 3, tol);
+        if (r < 0) return;
         ++it;
-        if (s_done) break;
+        if (r == 1) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) st->iters_done = it;
 }
@@ -360,8 +484,8 @@ struct Shape {
 Shape shape_for(int L) {
     if (L <= 4) return {4, 1};
     if (L <= 8) return {8, 1};
-    if (L <= 16) return {16, 1};
-    if (L <= 32) return {32, 1};
+    if (L <= 16) return {8, 2};
+    if (L <= 32) return {16, 2};
     if (L <= 64) return {32, 2};
     if (L <= 128) return {32, 4};
     return {32, 8};
@@ -371,9 +495,9 @@ Shape shape_for(int L) {
     do {                                         \
         Shape _s = shape_for(L);                 \
         if (_s.G == 4) { MACRO(4, 1); }          \
-        else if (_s.G == 8) { MACRO(8, 1); }     \
-        else if (_s.G == 16) { MACRO(16, 1); }   \
-        else if (_s.LPL == 1) { MACRO(32, 1); }  \
+        else if (_s.G == 8 && _s.LPL == 1) { MACRO(8, 1); }     \
+        else if (_s.G == 8) { MACRO(8, 2); }     \
+        else if (_s.G == 16) { MACRO(16, 2); }   \
         else if (_s.LPL == 2) { MACRO(32, 2); }  \
         else if (_s.LPL == 4) { MACRO(32, 4); }  \
         else { MACRO(32, 8); }                   \
@@ -383,7 +507,8 @@ Shape shape_for(int L) {
 
 slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
                         const int32_t* col_idx, const float* w, int64_t N, int L, float lambda,
-                        float* Z, float* Z_prev, int max_iters, float tol, DevState* st) {
+                        float* Z, float* Z_prev, int max_iters, float tol, DevState* st,
+                        int kdeg) {
     PhaseScope ps(ctx, SLK_PHASE_BOUND);
     // reset barrier / delta state; iters_done = -1 marks "not finished"
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, offsetof(DevState, iters_done), ctx->stream));
@@ -411,8 +536,8 @@ slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
         const float* a_ = A; const int64_t* rp_ = row_ptr; const int32_t* ci_ = col_idx;       \
         const float* w_ = w; int64_t n_ = N; int l_ = L; float lam_ = lambda;                  \
         float* z0_ = Z; float* z1_ = Z_prev; int mi_ = max_iters; float tol_ = tol;            \
-        DevState* st_ = st;                                                                    \
-        void* args[] = {&a_, &rp_, &ci_, &w_, &n_, &l_, &lam_, &z0_, &z1_, &mi_, &tol_, &st_}; \
+        int kd_ = kdeg; DevState* st_ = st;                                                    \
+        void* args[] = {&a_, &rp_, &ci_, &w_, &n_, &l_, &lam_, &z0_, &z1_, &mi_, &tol_, &kd_, &st_}; \
         e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid), dim3(kThreads), \
                                         args, 0, ctx->stream);                                 \
     }
@@ -540,8 +665,8 @@ extern "C" slk_status slk_bound_iterate_noalloc(void* stream, const float* A, co
             const float* a_ = A; const int64_t* rp_ = row_ptr; const int32_t* ci_ = col_idx;   \
             const float* w_ = w; int64_t n_ = N; int l_ = L; float lam_ = lambda;              \
             float* z0_ = Z; float* z1_ = Zs; int mi_ = max_iters; float tol_ = tol;            \
-            DevState* st_ = st;                                                                \
-            void* args[] = {&a_, &rp_, &ci_, &w_, &n_, &l_, &lam_, &z0_, &z1_, &mi_, &tol_, &st_}; \
+            int kd_ = 0; DevState* st_ = st;                                                   \
+            void* args[] = {&a_, &rp_, &ci_, &w_, &n_, &l_, &lam_, &z0_, &z1_, &mi_, &tol_, &kd_, &st_}; \
             e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid),           \
                                             dim3(kThreads), args, 0, s);                       \
         }                                                                                      \

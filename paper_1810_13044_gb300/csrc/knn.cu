@@ -501,6 +501,159 @@ knn_fallback_kernel(const float* __restrict__ X, int64_t N, int D, int k,
     }
 }
 
+// Batched exact rescan of the rows that failed the certificate.  A block
+// takes R failed rows (their features cached in registers, lane-strided like
+// exact_d2) and one column range; each of its 8 warps streams a share of the
+// columns once for all R rows, computing every distance with exact_d2's
+// arithmetic (same per-lane fmaf order, same butterfly), and keeps a
+// register top-k per row (lane i holds entry i).  The 8 warp lists are
+// merged in shared memory into one list per (row, column range), written to
+// part_d / part_i at slot cs * k of the row's scratch.
+template <int R, int DPL>
+__global__ void __launch_bounds__(256)
+knn_fallback_batch_kernel(const float* __restrict__ X, int64_t N, int D, int k,
+                          const int32_t* __restrict__ fb_list, const DevState* __restrict__ st,
+                          int col_splits, int64_t slot_stride, float* __restrict__ part_d,
+                          int32_t* __restrict__ part_i) {
+    __shared__ float md[8][R][32];
+    __shared__ int mi[8][R][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long count = *(const volatile long long*)&st->fallback_count;
+    const long long nbatch = (count + R - 1) / R;
+    const int cs = blockIdx.y;
+    const int64_t q0 = (int64_t)cs * N / col_splits, q1 = (int64_t)(cs + 1) * N / col_splits;
+    for (long long b = blockIdx.x; b < nbatch; b += gridDim.x) {
+        int64_t prow[R];
+        float xr[R][DPL];
+        float ld[R], lastd[R];
+        int li[R], lasti[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const long long f = b * R + r;
+            prow[r] = (f < count) ? (int64_t)fb_list[f] : -1;
+#pragma unroll
+            for (int t = 0; t < DPL; ++t) {
+                const int j = lane + 32 * t;
+                xr[r][t] = (prow[r] >= 0 && j < D) ? X[prow[r] * D + j] : 0.f;
+            }
+            ld[r] = kInf; li[r] = kNoIdx; lastd[r] = kInf; lasti[r] = kNoIdx;
+        }
+        for (int64_t q = q0 + warp; q < q1; q += 8) {
+            float xq[DPL];
+#pragma unroll
+            for (int t = 0; t < DPL; ++t) {
+                const int j = lane + 32 * t;
+                xq[t] = (j < D) ? X[q * D + j] : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (prow[r] < 0 || q == prow[r]) continue;
+                float part = 0.f;
+#pragma unroll
+                for (int t = 0; t < DPL; ++t) {
+                    if (lane + 32 * t < D) {
+                        const float df = xr[r][t] - xq[t];
+                        part = fmaf(df, df, part);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                if (!lex_less(part, (int)q, lastd[r], lasti[r])) continue;
+                const bool less = lane < k && lex_less(part, (int)q, ld[r], li[r]);
+                const int pos = __ffs(__ballot_sync(0xffffffffu, less)) - 1;
+                const float upd = __shfl_up_sync(0xffffffffu, ld[r], 1);
+                const int upi = __shfl_up_sync(0xffffffffu, li[r], 1);
+                if (lane < k) {
+                    if (lane == pos) { ld[r] = part; li[r] = (int)q; }
+                    else if (lane > pos) { ld[r] = upd; li[r] = upi; }
+                }
+                lastd[r] = __shfl_sync(0xffffffffu, ld[r], k - 1);
+                lasti[r] = __shfl_sync(0xffffffffu, li[r], k - 1);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            md[warp][r][lane] = lane < k ? ld[r] : kInf;
+            mi[warp][r][lane] = lane < k ? li[r] : kNoIdx;
+        }
+        __syncthreads();
+        for (int r = warp; r < R; r += 8) {
+            const long long f = b * R + r;
+            if (f >= count) continue;
+            const int64_t p = fb_list[f];
+            float ed[8];
+            int ei[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) { ed[m] = md[m][r][lane]; ei[m] = mi[m][r][lane]; }
+            for (int c = 0; c < k; ++c) {
+                float bd = kInf;
+                int bi = kNoIdx;
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    if (lex_less(ed[m], ei[m], bd, bi)) { bd = ed[m]; bi = ei[m]; }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (lex_less(od, oi, bd, bi)) { bd = od; bi = oi; }
+                }
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    if (ei[m] == bi) { ed[m] = kInf; ei[m] = kNoIdx; }
+                if (lane == 0) {
+                    part_d[p * slot_stride + (int64_t)cs * k + c] = bd;
+                    part_i[p * slot_stride + (int64_t)cs * k + c] = bi;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Merge the col_splits partial lists of every failed row into its k nearest.
+__global__ void __launch_bounds__(256)
+knn_fallback_merge_kernel(int k, const int32_t* __restrict__ fb_list, const DevState* __restrict__ st,
+                          int col_splits, int64_t slot_stride, const float* __restrict__ part_d,
+                          const int32_t* __restrict__ part_i, int32_t* __restrict__ col_idx,
+                          float* __restrict__ dist2) {
+    const int lane = threadIdx.x & 31;
+    const long long count = *(const volatile long long*)&st->fallback_count;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t f = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < count;
+         f += nw) {
+        const int64_t p = fb_list[f];
+        float ed[8];
+        int ei[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int e = lane + 32 * m;
+            ed[m] = kInf;
+            ei[m] = kNoIdx;
+            if (e < col_splits * k) {
+                ed[m] = part_d[p * slot_stride + e];
+                ei[m] = part_i[p * slot_stride + e];
+            }
+        }
+        for (int c = 0; c < k; ++c) {
+            float bd = kInf;
+            int bi = kNoIdx;
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if (lex_less(ed[m], ei[m], bd, bi)) { bd = ed[m]; bi = ei[m]; }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (lex_less(od, oi, bd, bi)) { bd = od; bi = oi; }
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if (ei[m] == bi) { ed[m] = kInf; ei[m] = kNoIdx; }
+            if (lane == 0) { col_idx[p * k + c] = bi; dist2[p * k + c] = bd; }
+        }
+    }
+}
+
 int choose_kc(int k) { return (k + 4 <= 16) ? 16 : 32; }
 
 struct KnnPlan {
@@ -652,10 +805,35 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     }
     {
         PhaseScope ps(ctx, SLK_PHASE_KNN_FALLBACK);
+        // partial lists of the batched rescan reuse the row's candidate
+        // scratch: splits * KC slots per row, of which col_splits * k are used
+        const int64_t slot_stride = (int64_t)pl.splits * pl.kc;
+        int cs = (int)(slot_stride / k);
+        if (cs > 8) cs = 8;
+        const int dpl = (D + 31) / 32;
+        if (cs >= 1 && dpl <= 32) {
+            SLK_COUNT_LAUNCH(ctx, 2);
+            // the rescan scratch is laid out per row (slot_stride entries), so
+            // it may reuse cand_d / cand_i once the rerank is done with them
+            dim3 grid((unsigned)((ctx->num_sms * 2 + cs - 1) / cs), (unsigned)cs);
+#define SLK_FB(R_, DPL_)                                                                     \
+    knn_fallback_batch_kernel<R_, DPL_><<<grid, 256, 0, s>>>(X, N, D, k, fb, st, cs, slot_stride, \
+                                                             cand_d, cand_i)
+            if (dpl <= 4) SLK_FB(16, 4);
+            else if (dpl <= 8) SLK_FB(8, 8);
+            else if (dpl <= 16) SLK_FB(4, 16);
+            else SLK_FB(2, 32);
+#undef SLK_FB
+            SLK_LAUNCH_CHECK(ctx, "knn_fallback_batch_kernel");
+            knn_fallback_merge_kernel<<<(unsigned)(ctx->num_sms * 2), 256, 0, s>>>(
+                k, fb, st, cs, slot_stride, cand_d, cand_i, col_idx, dist2);
+            SLK_LAUNCH_CHECK(ctx, "knn_fallback_merge_kernel");
+        } else {
         SLK_COUNT_LAUNCH(ctx, 1);
         knn_fallback_kernel<<<(unsigned)(ctx->num_sms * 2), 256, 0, s>>>(X, N, D, k, fb, st,
                                                                          col_idx, dist2);
         SLK_LAUNCH_CHECK(ctx, "knn_fallback_kernel");
+        }
     }
     return SLK_OK;
 }

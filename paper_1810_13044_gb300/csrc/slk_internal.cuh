@@ -132,7 +132,8 @@ slk_status unary_launch(slk_ctx* ctx, const float* X, int64_t N, int D, const in
 // Inner loop; the final iterate ends in Z, the previous one in Z_prev.
 slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
                         const int32_t* col_idx, const float* w, int64_t N, int L, float lambda,
-                        float* Z, float* Z_prev, int max_iters, float tol, DevState* st);
+                        float* Z, float* Z_prev, int max_iters, float tol, DevState* st,
+                        int kdeg = 0);   // kdeg > 0: every row has kdeg entries (row_ptr[p] = kdeg p)
 
 // Mode update (keys from A + lambda K Z_prev; Z_prev NULL or st->iters_done == 0
 // when use_iters_flag: s = A).  Writes modes in place, labels, keys, st->changed.

@@ -88,6 +88,24 @@ def test_knn_matches_oracle(slk, N, D, k, seed, precision):
     assert 0 <= g.fallback_rows <= N
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16_rerank"])
+def test_knn_all_rows_through_exact_rescan(slk, precision):
+    """Two tight clusters 2000 apart: the centred norms dwarf the neighbour
+    distances, no row can be certified, and every row goes through the
+    batched exact rescan (which must still match the oracle)."""
+    g = inputs.rng(31)
+    N, D, k = 3000, 16, 7
+    X = g.normal(0.0, 1e-2, size=(N, D))
+    X[: N // 2, 0] += 1000.0
+    X[N // 2:, 0] -= 1000.0
+    X = X.astype(np.float32)
+    o_idx, o_d2 = oracle.knn(X, k)
+    gr = slk.knn_graph(dev(X), k, precision=precision)
+    assert gr.fallback_rows > N // 2
+    check_knn(X, k, host(gr.col_idx).reshape(N, k), host(gr.dist2).reshape(N, k), o_idx, o_d2,
+              max_tie_rows=0.02)
+
+
 def test_knn_heat_weights(slk):
     X, _ = inputs.blobs(N=500, D=6, n_blobs=3, seed=9)
     o_idx, o_d2 = oracle.knn(X, 5)
