@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain float32 solve beside the main arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["mnist_like", "batched"], default="mnist_like",
+                    help="mnist_like: one 70000 x 784 solve per step; batched: 256 uneven "
+                         "problems per step (slk_solve_batched)")
+    ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--rows", type=int, default=None,
                     help="generate the workload with this many points (profiling captures)")
     args = ap.parse_args()
@@ -348,11 +352,113 @@ def run_slk(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def make_batch(count, seed=1810):
+    """The batched workload: N ~ U[500, 20000], D in {9, 64, 256}, L ~ U[5, 50],
+    imbalanced Gaussian mixtures (largest cluster 60-80 %), k = 5, K-means++ seeds."""
+    from paper_1810_13044_gb300 import inputs
+    g = inputs.rng(seed)
+    probs = []
+    for i in range(count):
+        N = int(g.integers(500, 20001))
+        D = int(g.choice([9, 64, 256]))
+        L = int(g.integers(5, 51))
+        X, _ = inputs.mixture(N, D, L, seed=seed * 7919 + i)
+        m0 = inputs.kmeanspp(X, L, seed=seed * 7919 + i)
+        probs.append(dict(X=X, m0=m0, N=N, D=D, L=L, k=5, lam=1.0))
+    return probs
+
+
+def run_batched(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1810_13044_gb300 import slk
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    probs = make_batch(args.instances)
+    for pr in probs:
+        pr["Xd"] = torch.from_numpy(pr["X"]).to(dev)
+        pr["m0d"] = torch.from_numpy(pr["m0"]).to(dev)
+    params = slk.default_params(knn_precision=args.precision)
+    ctx = slk.context(local)
+    batch = [dict(X=pr["Xd"], L=pr["L"], k=pr["k"], lam=pr["lam"], init_modes=pr["m0d"]) for pr in probs]
+    outs = [(torch.empty(pr["N"], pr["L"], device=dev), torch.empty(pr["N"], dtype=torch.int32, device=dev),
+             torch.empty(pr["L"], dtype=torch.int32, device=dev)) for pr in probs]
+
+    def step():
+        return slk.solve_batched(batch, params=params, ctx=ctx, outs=outs)
+
+    for _ in range(args.warmup):
+        res = step()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        ev1.record(stream)
+        barrier()
+    ms_phase, _, launches = ctx.profile_read()
+    ctx.profile(False)
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    n = len(probs)
+    outer = [r[3]["outer_iters"] for r in res]
+    inner = [r[3]["inner_iters_total"] for r in res]
+    value = world * n * args.steps / (ms_max / 1e3)
+    # the plain per-instance GPU solve of the same problems, and label agreement
+    single = []
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for pr in probs:
+        single.append(slk.solve(pr["Xd"], pr["L"], pr["k"], pr["lam"], pr["m0d"], params=params, ctx=ctx))
+    f1.record(stream)
+    barrier()
+    ms1 = f0.elapsed_time(f1)
+    equal = sum(int(torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])) for a, b in zip(res, single))
+    if rank == 0:
+        rows = sum(pr["N"] for pr in probs)
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched_{n}_mixtures", "instances": n, "rows_total": rows,
+                       "N": "U[500,20000]", "D": "{9,64,256}", "L": "U[5,50]", "k": 5, "lambda": 1.0,
+                       "knn": args.precision, "l2": "inputs larger than L2 (all problems' X together)"},
+            "plain_per_instance_gpu": {"value": n / (ms1 / 1e3), "unit": "solves/s",
+                                       "equal_labels_and_modes": f"{equal}/{n}"},
+            "gpu_launches": launches, "clocks": clk.summary(),
+            "phase_ms_per_step": {k_: v / args.steps for k_, v in ms_phase.items() if v},
+            "outer_iters": {"max": max(outer), "mean": sum(outer) / n},
+            "inner_iters_total": {"max": max(inner), "mean": sum(inner) / n},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batched":
+        run_batched(args, rank, world, local)
     else:
         run_slk(args, rank, world, local)
 

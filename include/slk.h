@@ -194,6 +194,42 @@ slk_status slk_solve_host(slk_ctx* ctx, const float* X, int64_t N, int32_t D, in
                           const slk_params* params, float* Z, int32_t* labels, int32_t* modes,
                           slk_stats* stats);
 
+/* One clustering problem of a batch (all pointers DEVICE, caller-owned). */
+typedef struct {
+    const float* X;             /* N x D features */
+    int64_t N;
+    int32_t D;
+    int32_t L;                  /* 1 <= L <= SLK_BATCH_MAX_L */
+    int32_t k;                  /* kNN neighbours */
+    float lambda;
+    float sigma;                /* <= 0: estimated by params->sigma_rule */
+    const int32_t* init_modes;  /* [L] initial mode indices */
+    float* Z;                   /* out [N x L] */
+    int32_t* labels;            /* out [N] */
+    int32_t* modes;             /* out [L] */
+} slk_instance;
+
+#define SLK_BATCH_MAX_L 64
+#define SLK_BATCH_MAX_COUNT 4096
+
+/* Batched SLK-BO: `count` independent problems of different N, D, L solved
+ * together.  Each gets its own kNN graph and sigma (as in slk_solve); the
+ * iterative part of Algorithm 1 then runs for all of them at once:
+ * segmented unary, mode-update and energy kernels over the concatenated
+ * rows, and one persistent segment-indexed launch for the z-updates
+ * (Eq. soft-max), with a convergence test, iteration count and outer-loop
+ * state per problem, so every result equals the one slk_solve gives for
+ * that problem alone.  The per-outer-iteration launch sequence is captured
+ * once in a CUDA graph and replayed; the launch shape of the z-update kernel
+ * (threads per block, rows per lane group) is chosen by timing the
+ * candidates on the first batch of a given shape and cached in the context.
+ *   instances [host array of count, 1 <= count <= SLK_BATCH_MAX_COUNT], params as in slk_solve (max_outer,
+ *   max_inner, tol_inner, sigma_rule, affinity, knn_precision), stats [host
+ *   array of count, nullable].
+ * Returns SLK_NOT_CONVERGED when some problem hit max_outer. */
+slk_status slk_solve_batched(slk_ctx* ctx, const slk_instance* instances, int32_t count,
+                             const slk_params* params, slk_stats* stats);
+
 /* slk_bound_iterate for callers that cannot allocate device memory.  The
  * paper has no counterpart: this is a deployment variant.  It serves code
  * that may not call cudaMalloc -- for example a plug-in running inside a

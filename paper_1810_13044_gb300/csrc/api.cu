@@ -188,6 +188,8 @@ extern "C" slk_status slk_destroy(slk_ctx* ctx) {
         cudaStreamSynchronize(ctx->stream);
         for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (auto e : ctx->pool) cudaEventDestroy(e);
+        for (auto e : ctx->aux_ev) cudaEventDestroy(e);
+        for (auto a : ctx->aux) cudaStreamDestroy(a);
         if (ctx->ws) cudaFree(ctx->ws);
         if (ctx->dev_small) cudaFree(ctx->dev_small);
         if (ctx->host_pin) cudaFreeHost(ctx->host_pin);

@@ -19,6 +19,8 @@
 //  4. fallback: rows that fail the certificate are rescanned exactly.
 #include <cuda_bf16.h>
 #include <math.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "slk_internal.cuh"
@@ -664,12 +666,13 @@ struct KnnPlan {
 
 // Column splits for the persistent tensor-core kernel.  Every split restarts
 // the rows' candidate lists, so prefer few, long work items (row block x
-// split): the smallest split count whose last round is at least 95 % full,
-// else the best-filled one.
+// split) of at least 8 column tiles: the smallest split count whose last
+// round is at least 95 % full, else the best-filled one.
 int tc_splits(int row_blocks, int n_tiles, int num_sms, int max_splits) {
     int best = 1;
     double best_eff = -1.0;
-    for (int s = 1; s <= max_splits && s <= n_tiles; ++s) {
+    const int s_max = std::max(1, std::min(max_splits, n_tiles / 8));
+    for (int s = 1; s <= s_max; ++s) {
         const int64_t items = (int64_t)row_blocks * s;
         const int64_t rounds = (items + num_sms - 1) / num_sms;
         const double eff = (double)items / (double)(rounds * num_sms);

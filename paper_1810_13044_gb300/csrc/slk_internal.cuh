@@ -33,6 +33,9 @@ struct slk_ctx {
     std::vector<cudaEvent_t> pool;
     double prof_ms[SLK_PHASE_COUNT] = {};
     long long prof_calls[SLK_PHASE_COUNT] = {};
+    // auxiliary streams (batched graph building), created on first use
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> aux_ev;
 };
 
 // Records start/stop events of one phase on the context stream (when

@@ -29,7 +29,7 @@ SIGMA_RULE = {"median": 0, "meansq": 1}
 EXPORTS = ["slk_version", "slk_create", "slk_destroy", "slk_set_stream", "slk_last_error",
            "slk_knn_graph", "slk_sigma", "slk_unary", "slk_bound_iterate", "slk_mode_update",
            "slk_energy", "slk_default_params", "slk_solve", "slk_solve_host", "slk_profile",
-           "slk_profile_read", "slk_bound_iterate_noalloc"]
+           "slk_profile_read", "slk_bound_iterate_noalloc", "slk_solve_batched"]
 PHASES = ["knn_prep", "knn_cand", "knn_rerank", "knn_fallback", "sigma", "unary", "bound", "mode",
           "energy"]
 
@@ -44,6 +44,13 @@ class Params(ctypes.Structure):
     _fields_ = [("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
                 ("tol_inner", ctypes.c_float), ("sigma_rule", ctypes.c_int32),
                 ("affinity", ctypes.c_int32), ("knn_precision", ctypes.c_int32)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("N", ctypes.c_int64), ("D", ctypes.c_int32),
+                ("L", ctypes.c_int32), ("k", ctypes.c_int32), ("lam", ctypes.c_float),
+                ("sigma", ctypes.c_float), ("init_modes", ctypes.c_void_p), ("Z", ctypes.c_void_p),
+                ("labels", ctypes.c_void_p), ("modes", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -87,6 +94,8 @@ def load(path: str = LIB_PATH):
                                  P, ctypes.POINTER(Stats)]),
         "slk_profile": (i32, [P, i32]),
         "slk_bound_iterate_noalloc": (i32, [P, P, P, P, P, i64, i32, f32, P, i32, f32, P, P]),
+        "slk_solve_batched": (i32, [P, ctypes.POINTER(Instance), i32, ctypes.POINTER(Params),
+                                    ctypes.POINTER(Stats)]),
         "slk_profile_read": (i32, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -350,3 +359,34 @@ def bound_iterate_noalloc(A, row_ptr, col_idx, w, lam, Z, max_iters, tol=-1.0):
     if st != SLK_OK:
         raise SlkError(st, "slk_bound_iterate_noalloc")
     return it.value, dl.value
+
+
+def solve_batched(problems, params: Params | None = None, ctx: Context | None = None, outs=None):
+    """slk_solve_batched.  ``problems``: list of dicts with X (CUDA float32
+    N x D), L, k, lam, init_modes (CUDA int32 [L]) and optional sigma.
+    Returns a list of (Z, labels, modes, stats dict)."""
+    if not problems:
+        return []
+    ctx = ctx or context(problems[0]["X"].device.index)
+    n = len(problems)
+    arr = (Instance * n)()
+    stats = (Stats * n)()
+    keep = []
+    for i, pr in enumerate(problems):
+        X = pr["X"]
+        N, D = X.shape
+        L = int(pr["L"])
+        _need(X, torch.float32, (N, D), "X")
+        _need(pr["init_modes"], torch.int32, (L,), "init_modes")
+        if outs is not None:
+            Z, lab, modes = outs[i]
+        else:
+            Z = torch.empty(N, L, dtype=torch.float32, device=X.device)
+            lab = torch.empty(N, dtype=torch.int32, device=X.device)
+            modes = torch.empty(L, dtype=torch.int32, device=X.device)
+        keep.append((Z, lab, modes))
+        arr[i] = Instance(X.data_ptr(), N, D, L, int(pr["k"]), float(pr["lam"]), float(pr.get("sigma", 0.0)),
+                          pr["init_modes"].data_ptr(), Z.data_ptr(), lab.data_ptr(), modes.data_ptr())
+    p = params or default_params()
+    ctx.check(ctx._lib.slk_solve_batched(ctx.handle, arr, n, ctypes.byref(p), stats), "slk_solve_batched")
+    return [(z, l, m, stats[i].as_dict()) for i, (z, l, m) in enumerate(keep)]
