@@ -260,7 +260,7 @@ def run_slk(args, rank, world, local):
                  "equal_modes": bool(torch.equal(out32[2], modes_main))}
 
     # bound iterations alone on this solve's graph: N*L*iter/s (fixed 50 updates)
-    g = slk.knn_graph(Xd, k, ctx=ctx)
+    g = slk.knn_graph(Xd, k, precision=args.precision, ctx=ctx)
     A, Z0 = slk.unary(Xd, out[2], stats["sigma"], ctx=ctx)
     Zb, Zp = Z0.clone(), torch.empty_like(Z0)
     slk.bound_iterate(A, g.row_ptr, g.col_idx, None, lam, Zb, Zp, 50, tol=-1.0, ctx=ctx)

@@ -248,6 +248,10 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = Dp / TC_BK;
     const int n_items = row_blocks * splits;
+    // each CTA takes a contiguous range of items, so consecutive items mostly
+    // continue the same row block (the epilogue then keeps its lists going)
+    const int item_begin = (int)((int64_t)blockIdx.x * n_items / gridDim.x);
+    const int item_end = (int)((int64_t)(blockIdx.x + 1) * n_items / gridDim.x);
     volatile int* abort = &s.abort;
 
     if (threadIdx.x == 0) {
@@ -281,7 +285,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
             uint32_t iter = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+            for (int item = item_begin; item < item_end && ok; ++item) {
                 int rb, t0, t1, sp;
                 item_range(item, splits, n_tiles, rb, t0, t1, sp);
                 for (int t = t0; t < t1 && ok; ++t) {
@@ -311,7 +315,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         if (lane == 0) {
             uint32_t iter = 0, tcount = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+            for (int item = item_begin; item < item_end && ok; ++item) {
                 int rb, t0, t1, sp;
                 item_range(item, splits, n_tiles, rb, t0, t1, sp);
                 for (int t = t0; t < t1 && ok; ++t) {
@@ -355,20 +359,35 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         const int et = threadIdx.x - 64;  // 0..127 among the epilogue threads
         uint32_t tcount = 0;
         bool ok = true;
-        for (int item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+        float ld[TC_KC];
+        int li[TC_KC];
+        int cnt = 0;
+        int run_rb = -1, run_sp = 0;   // the row block whose list is being built
+        for (int item = item_begin; item < item_end && ok; ++item) {
             int rb, t0, t1, sp;
             item_range(item, splits, n_tiles, rb, t0, t1, sp);
             const int64_t p = (int64_t)rb * TC_M + r;
+            if (rb != run_rb) {
+                // a new row block: the list restarts (the previous one was written)
+#pragma unroll
+                for (int x = 0; x < TC_KC; ++x) {
+                    ld[x] = __int_as_float(0x7f800000);
+                    li[x] = kNoIdx;
+                }
+                cnt = 0;
+                run_rb = rb;
+                run_sp = sp;
+            } else {
+                // this split continues the run: its own slot stays empty
+                const int64_t o = ((int64_t)sp * Np + p) * TC_KC;
+#pragma unroll
+                for (int x = 0; x < TC_KC; ++x) {
+                    cand_d[o + x] = __int_as_float(0x7f800000);
+                    cand_i[o + x] = -1;
+                }
+            }
             // padding rows / columns get an infinite norm: their distances never pass
             const float np_ = (p < N) ? norms[p] : __int_as_float(0x7f800000);
-            float ld[TC_KC];
-            int li[TC_KC];
-#pragma unroll
-            for (int x = 0; x < TC_KC; ++x) {
-                ld[x] = __int_as_float(0x7f800000);
-                li[x] = kNoIdx;
-            }
-            int cnt = 0;
             for (int t = t0; t < t1; ++t) {
                 const uint32_t acc = tcount & 1, use = tcount >> 1;
                 const int64_t col0 = (int64_t)t * TC_N;
@@ -413,12 +432,20 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 ++tcount;
             }
             if (!ok) break;
-            flush_buffer<TC_KC>(s, r, cnt, ld, li);
-            const int64_t o = ((int64_t)sp * Np + p) * TC_KC;
+            // write the run's list when the next item starts another row block
+            int next_rb = -1;
+            if (item + 1 < item_end) {
+                int t0n, t1n, spn;
+                item_range(item + 1, splits, n_tiles, next_rb, t0n, t1n, spn);
+            }
+            if (next_rb != rb) {
+                flush_buffer<TC_KC>(s, r, cnt, ld, li);
+                const int64_t o = ((int64_t)run_sp * Np + p) * TC_KC;
 #pragma unroll
-            for (int x = 0; x < TC_KC; ++x) {
-                cand_d[o + x] = ld[x];
-                cand_i[o + x] = (li[x] == kNoIdx) ? -1 : li[x];
+                for (int x = 0; x < TC_KC; ++x) {
+                    cand_d[o + x] = ld[x];
+                    cand_i[o + x] = (li[x] == kNoIdx) ? -1 : li[x];
+                }
             }
         }
     }
