@@ -45,10 +45,12 @@ def parse():
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain float32 solve beside the main arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["mnist_like", "batched"], default="mnist_like",
+    ap.add_argument("--workload", choices=["mnist_like", "batched", "serving"], default="mnist_like",
                     help="mnist_like: one 70000 x 784 solve per step; batched: 256 uneven "
                          "problems per step (slk_solve_batched)")
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=64, help="serving: requests in the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: mean Poisson arrival rate (req/s)")
     ap.add_argument("--rows", type=int, default=None,
                     help="generate the workload with this many points (profiling captures)")
     args = ap.parse_args()
@@ -452,6 +454,103 @@ def run_batched(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def make_requests(count, dev, seed=1810):
+    """Serving stream: N log-uniform in [1e3, 2e5], D in {64, 512, 4096}, L ~ U[5, 100],
+    k ~ U[5, 10].  Features like the 70000 x 784 workload's, drawn on the device
+    (seeded): per cluster a 10-dim latent Gaussian u ~ N(mu_c, I), mu_c ~ N(0, 9 I),
+    pushed through a fixed random map x = W2 ReLU(W1 u + b1) (256 hidden units),
+    so that the D-dim features have low intrinsic dimension, as image features
+    do.  Initial modes: seeded random distinct points."""
+    import torch
+    from paper_1810_13044_gb300 import inputs
+    g = inputs.rng(seed)
+    reqs = []
+    for i in range(count):
+        N = int(np.exp(g.uniform(np.log(1e3), np.log(2e5))))
+        D = int(g.choice([64, 512, 4096]))
+        L = int(g.integers(5, 101))
+        k = int(g.integers(5, 11))
+        tg = torch.Generator(device=dev).manual_seed(seed * 100003 + i)
+        mu = torch.randn(L, 10, generator=tg, device=dev) * 3.0
+        lab = torch.randint(0, L, (N,), generator=tg, device=dev)
+        U = mu[lab] + torch.randn(N, 10, generator=tg, device=dev)
+        W1 = torch.randn(256, 10, generator=tg, device=dev) / np.sqrt(10)
+        b1 = torch.randn(256, generator=tg, device=dev)
+        W2 = torch.randn(D, 256, generator=tg, device=dev) / np.sqrt(256)
+        X = (torch.relu(U @ W1.T + b1) @ W2.T).contiguous()
+        m0 = torch.randperm(N, generator=tg, device=dev)[:L].to(torch.int32).contiguous()
+        reqs.append(dict(X=X, L=L, k=k, lam=1.0, init_modes=m0, N=N, D=D))
+    return reqs
+
+
+def run_serving(args, rank, world, local):
+    import torch
+
+    from paper_1810_13044_gb300 import slk
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    reqs = make_requests(args.requests, dev)
+    g = np.random.Generator(np.random.PCG64(77))
+    arrivals = np.cumsum(g.exponential(1.0 / args.rate, size=len(reqs)))
+    params = slk.default_params(knn_precision=args.precision)
+    free = torch.cuda.mem_get_info(dev)[0]
+    budget = int(min(free * 0.5, 120 << 30))
+    ctx = slk.context(local)
+    # warm-up: one small request through a throw-away server
+    w = slk.Server(max_slots=4, quantum=10, memory_bytes=1 << 30, params=params, ctx=ctx)
+    small = make_requests(1, dev, seed=99)[0]
+    t = w.submit(small)
+    w.run_until_done([t])
+    w.close()
+    srv = slk.Server(max_slots=64, quantum=10, memory_bytes=budget, params=params, ctx=ctx)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    done_at, tickets, pending = {}, {}, set()
+    nxt = 0
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        while nxt < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and arrivals[nxt] <= now:
+                tk = srv.submit(reqs[nxt])
+                tickets[tk] = nxt
+                pending.add(tk)
+                nxt += 1
+            if not pending:
+                time.sleep(max(0.0, min(0.002, arrivals[nxt] - now)))
+                continue
+            srv.step()
+            now = time.perf_counter() - t0
+            for tk in list(pending):
+                st, res = srv.poll(tk)
+                if st == srv.DONE:
+                    done_at[tickets[tk]] = now
+                    pending.discard(tk)
+        wall = time.perf_counter() - t0
+    _, _, launches = ctx.profile_read()
+    ctx.profile(False)
+    srv.close()
+    lat = np.array([done_at[i] - arrivals[i] for i in range(len(reqs))]) * 1e3
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": len(reqs) / wall, "unit": "solves/s", "n_gpus": world,
+            "steps": len(reqs), "warmup": 1, "ms_per_step": wall * 1e3 / len(reqs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"serving_poisson{int(args.rate)}_{len(reqs)}req",
+                       "N": "log-uniform [1e3, 2e5]", "D": "{64, 512, 4096}", "L": "U[5,100]",
+                       "k": "U[5,10]", "knn": args.precision, "arrivals": f"Poisson, mean {args.rate}/s",
+                       "memory_budget_gb": round(budget / 2**30, 1), "slots": 64, "quantum": 10,
+                       "offered_rate": args.rate, "l2": "inputs larger than L2"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "requests": len(reqs), "rows_total": int(sum(r["N"] for r in reqs)),
+            "gpu_launches": launches, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -459,6 +558,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batched":
         run_batched(args, rank, world, local)
+    elif args.workload == "serving":
+        run_serving(args, rank, world, local)
     else:
         run_slk(args, rank, world, local)
 

@@ -209,7 +209,7 @@ typedef struct {
     int32_t* modes;             /* out [L] */
 } slk_instance;
 
-#define SLK_BATCH_MAX_L 64
+#define SLK_BATCH_MAX_L 128
 #define SLK_BATCH_MAX_COUNT 4096
 
 /* Batched SLK-BO: `count` independent problems of different N, D, L solved
@@ -229,6 +229,43 @@ typedef struct {
  * Returns SLK_NOT_CONVERGED when some problem hit max_outer. */
 slk_status slk_solve_batched(slk_ctx* ctx, const slk_instance* instances, int32_t count,
                              const slk_params* params, slk_stats* stats);
+
+/* Continuous-batching server.  Requests (slk_instance, device pointers that
+ * stay valid until the request is done) are queued by slk_server_submit and
+ * admitted, first come first served, when a slot is free and the request's
+ * device state fits in the server's memory arena (memory_bytes, allocated
+ * once by slk_server_create): kNN graph, unary term, scratch iterate, and the
+ * kNN scratch while the graph is being built.  An admitted request's graph
+ * and sigma are built on an auxiliary stream, overlapping the work already
+ * on the device.  slk_server_step admits what fits, then advances every
+ * request that has its graph by one step -- the start of an outer iteration
+ * when due, up to `quantum` z-updates (one persistent launch for all
+ * requests), and the mode update and energy for requests whose inner loop
+ * ended -- and releases the requests that finished.  Every request keeps its
+ * own update count, convergence test and outer-loop state on the device, so
+ * its result is the same alone and in any mix.
+ *   cfg: max_slots (1 .. SLK_BATCH_MAX_COUNT), quantum (>= 1), memory_bytes.
+ *   params: as in slk_solve; applied to every request.
+ * slk_server_step synchronises the context stream; n_running / n_queued
+ * [host, nullable] receive the counts after the step.  slk_server_poll
+ * reports a ticket's state (0 queued, 1 building its graph, 2 iterating,
+ * 3 done, with stats [host, nullable]); a done ticket is reported once and
+ * then forgotten.  A request larger than the whole arena is refused at
+ * submission with SLK_ERR_OOM. */
+typedef struct slk_server slk_server;
+typedef struct {
+    int32_t max_slots;
+    int32_t quantum;
+    int64_t memory_bytes;
+} slk_server_config;
+slk_status slk_server_create(slk_ctx* ctx, const slk_server_config* cfg, const slk_params* params,
+                             slk_server** out);
+slk_status slk_server_destroy(slk_server* srv);
+slk_status slk_server_submit(slk_server* srv, const slk_instance* req, int64_t* ticket);
+slk_status slk_server_step(slk_server* srv, int32_t* n_running, int32_t* n_queued);
+slk_status slk_server_poll(slk_server* srv, int64_t ticket, int32_t* state, slk_stats* stats);
+/* Arena bytes a request needs while its graph is built (its peak) [host out]. */
+slk_status slk_server_request_bytes(slk_server* srv, const slk_instance* req, int64_t* bytes);
 
 /* slk_bound_iterate for callers that cannot allocate device memory.  The
  * paper has no counterpart: this is a deployment variant.  It serves code

@@ -29,7 +29,9 @@ SIGMA_RULE = {"median": 0, "meansq": 1}
 EXPORTS = ["slk_version", "slk_create", "slk_destroy", "slk_set_stream", "slk_last_error",
            "slk_knn_graph", "slk_sigma", "slk_unary", "slk_bound_iterate", "slk_mode_update",
            "slk_energy", "slk_default_params", "slk_solve", "slk_solve_host", "slk_profile",
-           "slk_profile_read", "slk_bound_iterate_noalloc", "slk_solve_batched"]
+           "slk_profile_read", "slk_bound_iterate_noalloc", "slk_solve_batched", "slk_server_create",
+           "slk_server_destroy", "slk_server_submit", "slk_server_step", "slk_server_poll",
+           "slk_server_request_bytes"]
 PHASES = ["knn_prep", "knn_cand", "knn_rerank", "knn_fallback", "sigma", "unary", "bound", "mode",
           "energy"]
 
@@ -51,6 +53,11 @@ class Instance(ctypes.Structure):
                 ("L", ctypes.c_int32), ("k", ctypes.c_int32), ("lam", ctypes.c_float),
                 ("sigma", ctypes.c_float), ("init_modes", ctypes.c_void_p), ("Z", ctypes.c_void_p),
                 ("labels", ctypes.c_void_p), ("modes", ctypes.c_void_p)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("quantum", ctypes.c_int32),
+                ("memory_bytes", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -96,6 +103,13 @@ def load(path: str = LIB_PATH):
         "slk_bound_iterate_noalloc": (i32, [P, P, P, P, P, i64, i32, f32, P, i32, f32, P, P]),
         "slk_solve_batched": (i32, [P, ctypes.POINTER(Instance), i32, ctypes.POINTER(Params),
                                     ctypes.POINTER(Stats)]),
+        "slk_server_create": (i32, [P, ctypes.POINTER(ServerConfig), ctypes.POINTER(Params),
+                                    ctypes.POINTER(P)]),
+        "slk_server_destroy": (i32, [P]),
+        "slk_server_submit": (i32, [P, ctypes.POINTER(Instance), ctypes.POINTER(i64)]),
+        "slk_server_step": (i32, [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "slk_server_poll": (i32, [P, i64, ctypes.POINTER(i32), ctypes.POINTER(Stats)]),
+        "slk_server_request_bytes": (i32, [P, ctypes.POINTER(Instance), ctypes.POINTER(i64)]),
         "slk_profile_read": (i32, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -390,3 +404,95 @@ def solve_batched(problems, params: Params | None = None, ctx: Context | None = 
     p = params or default_params()
     ctx.check(ctx._lib.slk_solve_batched(ctx.handle, arr, n, ctypes.byref(p), stats), "slk_solve_batched")
     return [(z, l, m, stats[i].as_dict()) for i, (z, l, m) in enumerate(keep)]
+
+
+class Server:
+    """Continuous-batching server (slk_server_*).  ``submit`` takes a problem
+    dict like :func:`solve_batched`'s and returns a ticket; ``step`` admits and
+    advances; ``poll`` returns (state, result) with result = (Z, labels, modes,
+    stats) once done (state 3)."""
+
+    QUEUED, BUILDING, ITERATING, DONE = 0, 1, 2, 3
+
+    def __init__(self, max_slots=64, quantum=10, memory_bytes=8 << 30, params: Params | None = None,
+                 ctx: Context | None = None):
+        self.ctx = ctx or context()
+        self._lib = self.ctx._lib
+        cfg = ServerConfig(int(max_slots), int(quantum), int(memory_bytes))
+        self.params = params or default_params()
+        self.handle = ctypes.c_void_p()
+        self.ctx.check(self._lib.slk_server_create(self.ctx.handle, ctypes.byref(cfg), ctypes.byref(self.params),
+                                                   ctypes.byref(self.handle)), "slk_server_create")
+        self._live = {}
+
+    def submit(self, pr, out=None) -> int:
+        X = pr["X"]
+        N, D = X.shape
+        L = int(pr["L"])
+        _need(X, torch.float32, (N, D), "X")
+        _need(pr["init_modes"], torch.int32, (L,), "init_modes")
+        if out is None:
+            out = (torch.empty(N, L, dtype=torch.float32, device=X.device),
+                   torch.empty(N, dtype=torch.int32, device=X.device),
+                   torch.empty(L, dtype=torch.int32, device=X.device))
+        Z, lab, modes = out
+        inst = Instance(X.data_ptr(), N, D, L, int(pr["k"]), float(pr["lam"]), float(pr.get("sigma", 0.0)),
+                        pr["init_modes"].data_ptr(), Z.data_ptr(), lab.data_ptr(), modes.data_ptr())
+        t = ctypes.c_int64(0)
+        self.ctx.check(self._lib.slk_server_submit(self.handle, ctypes.byref(inst), ctypes.byref(t)),
+                       "slk_server_submit")
+        self._live[t.value] = (pr, out)
+        return t.value
+
+    def request_bytes(self, pr) -> int:
+        X = pr["X"]
+        N, D = X.shape
+        inst = Instance(X.data_ptr(), N, D, int(pr["L"]), int(pr["k"]), float(pr["lam"]), 0.0,
+                        pr["init_modes"].data_ptr(), 0, 0, 0)
+        b = ctypes.c_int64(0)
+        self.ctx.check(self._lib.slk_server_request_bytes(self.handle, ctypes.byref(inst), ctypes.byref(b)),
+                       "slk_server_request_bytes")
+        return b.value
+
+    def step(self):
+        r, q = ctypes.c_int32(0), ctypes.c_int32(0)
+        self.ctx.check(self._lib.slk_server_step(self.handle, ctypes.byref(r), ctypes.byref(q)),
+                       "slk_server_step")
+        return r.value, q.value
+
+    def poll(self, ticket):
+        st = ctypes.c_int32(0)
+        stats = Stats()
+        self.ctx.check(self._lib.slk_server_poll(self.handle, int(ticket), ctypes.byref(st), ctypes.byref(stats)),
+                       "slk_server_poll")
+        if st.value != self.DONE:
+            return st.value, None
+        _, out = self._live.pop(ticket)
+        return st.value, (*out, stats.as_dict())
+
+    def run_until_done(self, tickets, max_steps=100000):
+        """Step until every ticket is done; returns {ticket: result}."""
+        results, pending = {}, set(tickets)
+        for _ in range(max_steps):
+            if not pending:
+                break
+            self.step()
+            for t in list(pending):
+                st, res = self.poll(t)
+                if st == self.DONE:
+                    results[t] = res
+                    pending.discard(t)
+        if pending:
+            raise RuntimeError(f"{len(pending)} requests not done after {max_steps} steps")
+        return results
+
+    def close(self):
+        if self.handle:
+            self._lib.slk_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -80,7 +80,7 @@ def test_batched_heat_affinity_and_single_problem(slk):
 
 def test_batched_rejects_large_L(slk):
     probs = _problems(1, seed=11, n_range=(500, 501), Ds=(9,), L_range=(5, 5))
-    probs[0]["L"] = 65
-    probs[0]["init_modes"] = torch.arange(65, dtype=torch.int32, device="cuda")
+    probs[0]["L"] = 129
+    probs[0]["init_modes"] = torch.arange(129, dtype=torch.int32, device="cuda")
     with pytest.raises(slk.SlkError, match="INVALID_ARG"):
         slk.solve_batched(probs)

@@ -1,0 +1,95 @@
+"""Serving form: continuous batching.  A request's result is the same alone
+and in a mix (bit for bit), whatever the step granularity, and equals the
+result slk_solve gives; admission waits for memory."""
+import numpy as np
+import pytest
+
+from paper_1810_13044_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def slk():
+    from paper_1810_13044_gb300 import build, slk as _slk
+    build.build()
+    return _slk
+
+
+def _problem(N, D, L, k, seed):
+    X, _ = inputs.mixture(N, D, L, seed=seed)
+    m0 = inputs.kmeanspp(X, L, seed=seed)
+    return dict(X=torch.from_numpy(X).cuda(), L=L, k=k, lam=1.0, init_modes=torch.from_numpy(m0).cuda())
+
+
+def _same(a, b):
+    return torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+
+
+def test_alone_equals_in_mix(slk):
+    target = _problem(3000, 64, 12, 6, seed=1)
+    others = [_problem(N, D, L, k, seed=10 + i) for i, (N, D, L, k) in
+              enumerate([(5000, 9, 30, 5), (800, 256, 7, 10), (12000, 64, 100, 5), (2500, 16, 50, 8)])]
+    srv = slk.Server(max_slots=8, quantum=7)
+    t = srv.submit(target)
+    alone = srv.run_until_done([t])[t]
+    srv.close()
+    srv = slk.Server(max_slots=8, quantum=7)
+    ts = [srv.submit(others[0]), srv.submit(others[1])]
+    srv.step()
+    srv.step()
+    tt = srv.submit(target)           # arrives while others iterate
+    ts += [srv.submit(others[2])]
+    srv.step()
+    ts += [srv.submit(others[3])]
+    res = srv.run_until_done(ts + [tt])
+    srv.close()
+    assert _same(alone, res[tt])
+    assert alone[3]["outer_iters"] == res[tt][3]["outer_iters"]
+    # energies are float64 sums accumulated with atomics (order-dependent last bits)
+    assert alone[3]["energy"] == pytest.approx(res[tt][3]["energy"], rel=1e-12)
+    # and every request equals slk_solve on its own
+    for pr, key in zip(others + [target], ts + [tt]):
+        Z, lab, modes, st = slk.solve(pr["X"], pr["L"], pr["k"], pr["lam"], pr["init_modes"])
+        r = res[key]
+        assert torch.equal(lab, r[1]) and torch.equal(modes, r[2])
+        assert (Z - r[0]).abs().max().item() <= 1e-6
+        assert st["outer_iters"] == r[3]["outer_iters"]
+        assert st["inner_iters_total"] == r[3]["inner_iters_total"]
+        assert r[3]["energy"] == pytest.approx(st["energy"], rel=1e-9)
+
+
+def test_quantum_does_not_change_results(slk):
+    pr = _problem(4000, 32, 20, 5, seed=3)
+    outs = []
+    for q in (1, 50):
+        srv = slk.Server(max_slots=2, quantum=q)
+        t = srv.submit(pr)
+        outs.append(srv.run_until_done([t])[t])
+        srv.close()
+    assert _same(outs[0], outs[1])
+
+
+def test_admission_waits_for_memory(slk):
+    prs = [_problem(20000, 64, 10, 5, seed=20 + i) for i in range(3)]
+    probe = slk.Server(max_slots=1, quantum=1, memory_bytes=1 << 20)
+    need = probe.request_bytes(prs[0])
+    probe.close()
+    # room for one request at its peak (graph being built), not two
+    srv = slk.Server(max_slots=8, quantum=10, memory_bytes=int(need * 1.5))
+    ts = [srv.submit(p) for p in prs]
+    running, queued = srv.step()
+    assert queued >= 1 and running >= 1
+    res = srv.run_until_done(ts)
+    srv.close()
+    for p, t in zip(prs, ts):
+        _, lab, modes, _ = slk.solve(p["X"], p["L"], p["k"], p["lam"], p["init_modes"])
+        assert torch.equal(lab, res[t][1]) and torch.equal(modes, res[t][2])
+
+
+def test_request_larger_than_arena_is_refused(slk):
+    srv = slk.Server(max_slots=2, quantum=4, memory_bytes=2 << 20)
+    with pytest.raises(slk.SlkError, match="OOM"):
+        srv.submit(_problem(20000, 64, 10, 5, seed=30))
+    srv.close()
