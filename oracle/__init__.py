@@ -1,4 +1,4 @@
-"""FP64 CPU oracle for Scalable Laplacian K-modes (SLK-BO) -- ctypes front end.
+"""FP64 CPU oracle for Scalable Laplacian K-modes (SLK-BO, SLK-MS) -- ctypes front end.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 ``bench.py``'s CPU-baseline / reference legs may import this package.  It is
@@ -66,6 +66,11 @@ def _load():
         "oracle_relaxed": (f64, [P, P, P, P, P, i64, i32, f64]),
         "oracle_solve_graph": (i32, [P, i64, i32, i32, P, P, P, f64, f64, P, i32, i32, f64,
                                      P, P, P, P, P]),
+        "oracle_unary_vec": (i32, [P, i64, i32, P, i32, f64, P]),
+        "oracle_mean_shift": (i32, [P, i64, i32, P, i32, f64, P, i32, f64, P, P]),
+        "oracle_energy_vec": (f64, [P, i32, P, P, P, P, i64, i32, P, f64, f64]),
+        "oracle_solve_ms_graph": (i32, [P, i64, i32, i32, P, P, P, f64, f64, P, i32, i32, f64,
+                                        i32, f64, f64, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -269,6 +274,86 @@ def solve(X, L, k, lam, init_modes, sigma_rule="median", affinity="binary", sig=
     w = heat_weights(d2.reshape(-1), sig) if affinity == "heat" else None
     out = solve_graph(X, L, row_ptr, idx.reshape(-1), w, sig, lam, init_modes,
                       max_outer, max_inner, tol)
+    out.update(knn_idx=idx, knn_d2=d2, sigma=sig, row_ptr=row_ptr, w=w,
+               seconds=time.perf_counter() - t0)
+    return out
+
+
+# ---------------------------------------------------------------- SLK-MS
+
+def unary_vec(X, M, sig):
+    """a_{p,l} = k(x_p, m_l) with vector modes M [L, D] -> float64 [N, L]."""
+    lib = _load()
+    X = _c(X, np.float32)
+    M = _c(M, np.float64)
+    N, D = X.shape
+    A = np.empty((N, M.shape[0]), np.float64)
+    _check(lib.oracle_unary_vec(_p(X), N, D, _p(M), M.shape[0], float(sig), _p(A)), "unary_vec")
+    return A
+
+
+def mean_shift(X, logZ, M0, sig, max_iters, tol=-1.0):
+    """Eq. (mean-shift) with z fixed (given as log z) -> (M, iters, last_shift)."""
+    lib = _load()
+    X = _c(X, np.float32)
+    logZ = _c(logZ, np.float64)
+    M = np.array(M0, dtype=np.float64, order="C", copy=True)
+    N, D = X.shape
+    it = ctypes.c_int(0)
+    sh = ctypes.c_double(0.0)
+    _check(lib.oracle_mean_shift(_p(X), N, D, _p(logZ), M.shape[0], float(sig), _p(M),
+                                 int(max_iters), float(tol), ctypes.byref(it), ctypes.byref(sh)),
+           "mean_shift")
+    return M, it.value, sh.value
+
+
+def energy_vec(X, labels_, row_ptr, col_idx, w, M, sig, lam):
+    """Discrete energy, Eq. (1), at one-hot labels and vector modes M [L, D]."""
+    lib = _load()
+    X = _c(X, np.float32)
+    rp, ci, ww = _graph(row_ptr, col_idx, w)
+    lab = _c(labels_, np.int32)
+    M = _c(M, np.float64)
+    return float(lib.oracle_energy_vec(_p(X), X.shape[1], _p(lab), _p(rp), _p(ci), _p(ww),
+                                       X.shape[0], M.shape[0], _p(M), float(sig), float(lam)))
+
+
+def solve_ms_graph(X, L, row_ptr, col_idx, w, sig, lam, init_M, max_outer=50, max_inner=100,
+                   tol=1e-6, max_ms=100, tol_ms=1e-5, tol_outer=1e-3):
+    """Algorithm 1 (SLK-MS) on a given graph -> dict of results (modes as vectors)."""
+    lib = _load()
+    X = _c(X, np.float32)
+    N, D = X.shape
+    rp, ci, ww = _graph(row_ptr, col_idx, w)
+    M = np.array(init_M, dtype=np.float64, order="C", copy=True).reshape(L, D)
+    Z = np.empty((N, L), np.float64)
+    lab = np.empty(N, np.int32)
+    E = ctypes.c_double(0.0)
+    od, it, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    rc = lib.oracle_solve_ms_graph(_p(X), N, D, int(L), _p(rp), _p(ci), _p(ww), float(sig),
+                                   float(lam), _p(M), int(max_outer), int(max_inner), float(tol),
+                                   int(max_ms), float(tol_ms), float(tol_outer), _p(Z), _p(lab),
+                                   ctypes.byref(E), ctypes.byref(od), ctypes.byref(it),
+                                   ctypes.byref(ms))
+    _check(rc, "solve_ms_graph")
+    return dict(Z=Z, labels=lab, M=M, E=E.value, outer=od.value, inner_total=it.value,
+                ms_total=ms.value, converged=(rc == 0))
+
+
+def solve_ms(X, L, k, lam, init_modes, sigma_rule="median", affinity="binary", sig=None,
+             max_outer=50, max_inner=100, tol=1e-6, max_ms=100, tol_ms=1e-5, tol_outer=1e-3):
+    """Whole SLK-MS: exact kNN graph, kernel width, Algorithm 1 with mean-shift modes
+    starting from the points x_{init_modes[l]}."""
+    t0 = time.perf_counter()
+    idx, d2 = knn(X, k)
+    if sig is None:
+        sig = sigma(d2, sigma_rule)
+    N = X.shape[0]
+    row_ptr = np.arange(N + 1, dtype=np.int64) * k
+    w = heat_weights(d2.reshape(-1), sig) if affinity == "heat" else None
+    M0 = np.asarray(X, np.float64)[np.asarray(init_modes)]
+    out = solve_ms_graph(X, L, row_ptr, idx.reshape(-1), w, sig, lam, M0, max_outer, max_inner,
+                         tol, max_ms, tol_ms, tol_outer)
     out.update(knn_idx=idx, knn_d2=d2, sigma=sig, row_ptr=row_ptr, w=w,
                seconds=time.perf_counter() - t0)
     return out

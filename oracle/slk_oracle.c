@@ -338,3 +338,160 @@ int oracle_solve_graph(const float* X, int64_t N, int D, int L,
     free(A); free(Zp); free(S); free(newm);
     return converged ? 0 : 1;
 }
+
+/* ------------------------------------------------------------------ SLK-MS */
+
+/* ||x_p - m||^2 with x_p a float32 row and m a double vector. */
+static double sqdist_vec(const float* X, int D, int64_t p, const double* m)
+{
+    double s = 0.0;
+    for (int j = 0; j < D; ++j) {
+        double d = (double)X[p * D + j] - m[j];
+        s += d * d;
+    }
+    return s;
+}
+
+/* Eq. (general-second) with m_l a vector: a_{p,l} = k(x_p, m_l). */
+int oracle_unary_vec(const float* X, int64_t N, int D, const double* M, int L,
+                     double sigma, double* A)
+{
+    if (!X || N < 1 || D < 1 || !M || L < 1 || !(sigma > 0.0) || !A) return -1;
+    for (int64_t p = 0; p < N; ++p)
+        for (int l = 0; l < L; ++l)
+            A[p * L + l] = oracle_gauss(sqdist_vec(X, D, p, M + (size_t)l * D), sigma);
+    return 0;
+}
+
+/* Eq. (mean-shift).  The weight of point p for mode l is
+ * z_{p,l} k(x_p, m_l) = exp(log z_{p,l} - ||x_p - m_l||^2 / (2 sigma^2)); every
+ * weight of label l is multiplied by exp(-c_l), c_l the largest exponent of
+ * that label, which cancels in the ratio and keeps the sums away from
+ * underflow when a mode is far from every point. */
+int oracle_mean_shift(const float* X, int64_t N, int D, const double* logZ, int L,
+                      double sigma, double* M, int max_iters, double tol,
+                      int* iters_done, double* last_shift)
+{
+    if (!X || N < 1 || D < 1 || !logZ || L < 1 || !(sigma > 0.0) || !M || max_iters < 0)
+        return -1;
+    double* Mn = (double*)malloc(sizeof(double) * (size_t)L * (size_t)D);
+    double* ex = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!Mn || !ex) { free(Mn); free(ex); return -2; }
+    int it = 0;
+    double shift = 0.0;
+    while (it < max_iters) {
+        shift = 0.0;
+        for (int l = 0; l < L; ++l) {
+            const double* m = M + (size_t)l * D;
+            double c = -INFINITY;
+            for (int64_t p = 0; p < N; ++p) {
+                ex[p] = logZ[p * L + l] - sqdist_vec(X, D, p, m) / (2.0 * sigma * sigma);
+                if (ex[p] > c) c = ex[p];
+            }
+            double den = 0.0;
+            double* mn = Mn + (size_t)l * D;
+            for (int j = 0; j < D; ++j) mn[j] = 0.0;
+            for (int64_t p = 0; p < N; ++p) {
+                double wp = exp(ex[p] - c);
+                den += wp;
+                for (int j = 0; j < D; ++j) mn[j] += wp * (double)X[p * D + j];
+            }
+            double s2 = 0.0;
+            for (int j = 0; j < D; ++j) {
+                mn[j] /= den;
+                s2 += (mn[j] - m[j]) * (mn[j] - m[j]);
+            }
+            if (sqrt(s2) > shift) shift = sqrt(s2);
+        }
+        memcpy(M, Mn, sizeof(double) * (size_t)L * (size_t)D);
+        ++it;
+        if (tol >= 0.0 && shift <= tol * sigma) break;
+    }
+    if (iters_done) *iters_done = it;
+    if (last_shift) *last_shift = shift;
+    free(Mn);
+    free(ex);
+    return 0;
+}
+
+/* Eq. (1) at one-hot labels, modes given as vectors. */
+double oracle_energy_vec(const float* X, int D, const int32_t* labels,
+                         const int64_t* row_ptr, const int32_t* col_idx, const double* w,
+                         int64_t N, int L, const double* M, double sigma, double lambda)
+{
+    double unary = 0.0, pair = 0.0;
+    for (int64_t p = 0; p < N; ++p) {
+        for (int l = 0; l < L; ++l)
+            if (labels[p] == l) unary += oracle_gauss(sqdist_vec(X, D, p, M + (size_t)l * D), sigma);
+        for (int64_t e = row_ptr[p]; e < row_ptr[p + 1]; ++e) {
+            int64_t q = col_idx[e];
+            double kpq = w ? w[e] : 1.0;
+            double n2 = 0.0;
+            for (int l = 0; l < L; ++l) {
+                double d = ((labels[p] == l) ? 1.0 : 0.0) - ((labels[q] == l) ? 1.0 : 0.0);
+                n2 += d * d;
+            }
+            pair += kpq * n2;
+        }
+    }
+    return -unary + 0.5 * lambda * pair;
+}
+
+/* Algorithm 1 with the SLK-MS branch: modes from Eq. (mean-shift) run to
+ * convergence with Z fixed after the inner z-updates. */
+int oracle_solve_ms_graph(const float* X, int64_t N, int D, int L,
+                          const int64_t* row_ptr, const int32_t* col_idx, const double* w,
+                          double sigma, double lambda, double* M,
+                          int max_outer, int max_inner, double tol,
+                          int max_ms, double tol_ms, double tol_outer,
+                          double* Z, int32_t* labels, double* energy,
+                          int* outer_done, int* inner_total, int* ms_total)
+{
+    if (!X || N < 1 || D < 1 || L < 1 || L > N || !row_ptr || !col_idx || !(sigma > 0.0) ||
+        !M || max_outer < 1 || max_inner < 0 || max_ms < 0 || !Z || !labels || !energy)
+        return -1;
+    size_t n = (size_t)N * (size_t)L;
+    double* A = (double*)malloc(sizeof(double) * n);
+    double* Zp = (double*)malloc(sizeof(double) * n);
+    double* S = (double*)malloc(sizeof(double) * n);
+    double* LZ = (double*)malloc(sizeof(double) * n);
+    double* M0 = (double*)malloc(sizeof(double) * (size_t)L * (size_t)D);
+    if (!A || !Zp || !S || !LZ || !M0) {
+        free(A); free(Zp); free(S); free(LZ); free(M0);
+        return -2;
+    }
+    int converged = 0, t = 0, total = 0, mstotal = 0;
+    for (t = 0; t < max_outer && !converged; ++t) {
+        oracle_unary_vec(X, N, D, M, L, sigma, A);
+        oracle_softmax_rows(A, N, L, Z);
+        int it = 0;
+        double dl = 0.0;
+        oracle_bound_iterate(A, row_ptr, col_idx, w, N, L, lambda, Z, max_inner, tol, Zp, &it, &dl);
+        total += it;
+        if (it > 0) oracle_logits(A, row_ptr, col_idx, w, N, L, lambda, Zp, S);
+        else memcpy(S, A, sizeof(double) * n);
+        oracle_log_z(S, N, L, LZ);
+        oracle_labels(S, N, L, labels);
+        memcpy(M0, M, sizeof(double) * (size_t)L * (size_t)D);
+        int ms = 0;
+        double sh = 0.0;
+        oracle_mean_shift(X, N, D, LZ, L, sigma, M, max_ms, tol_ms, &ms, &sh);
+        mstotal += ms;
+        *energy = oracle_energy_vec(X, D, labels, row_ptr, col_idx, w, N, L, M, sigma, lambda);
+        double moved = 0.0;
+        for (int l = 0; l < L; ++l) {
+            double s2 = 0.0;
+            for (int j = 0; j < D; ++j) {
+                double d = M[(size_t)l * D + j] - M0[(size_t)l * D + j];
+                s2 += d * d;
+            }
+            if (sqrt(s2) > moved) moved = sqrt(s2);
+        }
+        converged = (moved <= tol_outer * sigma);
+    }
+    if (outer_done) *outer_done = t;
+    if (inner_total) *inner_total = total;
+    if (ms_total) *ms_total = mstotal;
+    free(A); free(Zp); free(S); free(LZ); free(M0);
+    return converged ? 0 : 1;
+}

@@ -1,5 +1,5 @@
 /*
- * FP64 CPU oracle for Scalable Laplacian K-modes, SLK-BO variant
+ * FP64 CPU oracle for Scalable Laplacian K-modes, SLK-BO and SLK-MS variants
  * (Ziko, Granger, Ben Ayed, NeurIPS 2018, arXiv:1810.13044).
  *
  * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA path.
@@ -100,6 +100,41 @@ int oracle_solve_graph(const float* X, int64_t N, int D, int L,
                        int max_outer, int max_inner, double tol,
                        double* Z, int32_t* labels, double* energy,
                        int* outer_done, int* inner_total);
+
+/* ---- SLK-MS (modes via mean-shift, Section 3.1 "Mode updates", Algorithm 1) ----
+ * Modes are vectors m_l in R^D (M: L x D row-major, double). */
+
+/* Unary term with vector modes: a_{p,l} = k(x_p, m_l). */
+int oracle_unary_vec(const float* X, int64_t N, int D, const double* M, int L,
+                     double sigma, double* A);
+
+/* Eq. (mean-shift) with the assignments fixed: every iteration replaces, for
+ * every l, m_l by  sum_p z_{p,l} k(x_p, m_l) x_p / sum_p z_{p,l} k(x_p, m_l),
+ * all labels from the same previous M.  z is given as logZ = log z_{p,l}
+ * (N x L).  Stops when max_l ||m_l^new - m_l^old||_2 <= tol * sigma, or after
+ * max_iters iterations; tol < 0 runs exactly max_iters.  M is in/out. */
+int oracle_mean_shift(const float* X, int64_t N, int D, const double* logZ, int L,
+                      double sigma, double* M, int max_iters, double tol,
+                      int* iters_done, double* last_shift);
+
+/* Eq. (1) at one-hot labels with vector modes:
+ * -sum_p k(x_p, m_{labels[p]}) + lambda/2 sum_p sum_{q in row p} w_pq ||z_p - z_q||^2. */
+double oracle_energy_vec(const float* X, int D, const int32_t* labels,
+                         const int64_t* row_ptr, const int32_t* col_idx, const double* w,
+                         int64_t N, int L, const double* M, double sigma, double lambda);
+
+/* Algorithm 1 (SLK-MS) on a given graph and kernel width.  Outer loop: a from
+ * the modes, z = softmax(a), inner z-updates, mean-shift mode update, labels,
+ * energy; stop when max_l ||m_l^new - m_l^old||_2 <= tol_outer * sigma or after
+ * max_outer steps.  M (L x D) in: initial modes, out: final.  Returns 1 if
+ * max_outer was hit without convergence. */
+int oracle_solve_ms_graph(const float* X, int64_t N, int D, int L,
+                          const int64_t* row_ptr, const int32_t* col_idx, const double* w,
+                          double sigma, double lambda, double* M,
+                          int max_outer, int max_inner, double tol,
+                          int max_ms, double tol_ms, double tol_outer,
+                          double* Z, int32_t* labels, double* energy,
+                          int* outer_done, int* inner_total, int* ms_total);
 
 #ifdef __cplusplus
 }
