@@ -71,6 +71,8 @@ def _load():
         "oracle_energy_vec": (f64, [P, i32, P, P, P, P, i64, i32, P, f64, f64]),
         "oracle_solve_ms_graph": (i32, [P, i64, i32, i32, P, P, P, f64, f64, P, i32, i32, f64,
                                         i32, f64, f64, P, P, P, P, P, P]),
+        "oracle_initial_modes": (i32, [P, i64, i32, P, i32, f64, P, P, P]),
+        "oracle_cluster_density": (i32, [P, i64, i32, P, i32, f64, P, i64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -356,4 +358,34 @@ def solve_ms(X, L, k, lam, init_modes, sigma_rule="median", affinity="binary", s
                          tol, max_ms, tol_ms, tol_outer)
     out.update(knn_idx=idx, knn_d2=d2, sigma=sig, row_ptr=row_ptr, w=w,
                seconds=time.perf_counter() - t0)
+    return out
+
+
+# ---------------------------------------------------------------- starting modes
+
+def initial_modes(X, seeds, sig):
+    """Section 4.2 starting modes: nearest-seed assignment, then the mode
+    definition of Eq. (1) -> (modes int32 [L], assign int32 [N], density [L])."""
+    lib = _load()
+    X = _c(X, np.float32)
+    seeds = _c(seeds, np.int32)
+    N, D = X.shape
+    L = len(seeds)
+    modes = np.empty(L, np.int32)
+    assign = np.empty(N, np.int32)
+    dens = np.empty(L, np.float64)
+    _check(lib.oracle_initial_modes(_p(X), N, D, _p(seeds), L, float(sig), _p(modes), _p(assign),
+                                    _p(dens)), "initial_modes")
+    return modes, assign, dens
+
+
+def cluster_density(X, assign, l, sig, ys):
+    """sum_{p: assign[p] = l} k(x_p, x_y) for each y in ys."""
+    lib = _load()
+    X = _c(X, np.float32)
+    assign = _c(assign, np.int32)
+    ys = _c(ys, np.int64)
+    out = np.empty(len(ys), np.float64)
+    _check(lib.oracle_cluster_density(_p(X), X.shape[0], X.shape[1], _p(assign), int(l), float(sig),
+                                      _p(ys), len(ys), _p(out)), "cluster_density")
     return out

@@ -495,3 +495,61 @@ int oracle_solve_ms_graph(const float* X, int64_t N, int D, int L,
     free(A); free(Zp); free(S); free(LZ); free(M0);
     return converged ? 0 : 1;
 }
+
+/* ------------------------------------------------------------------ starting modes */
+
+/* Initial assignment to the nearest seed, then the mode definition of
+ * Eq. (1) with that one-hot z: the data point of largest cluster density. */
+int oracle_initial_modes(const float* X, int64_t N, int D, const int32_t* seeds, int L,
+                         double sigma, int32_t* modes_out, int32_t* assign_out,
+                         double* density_out)
+{
+    if (!X || N < 1 || D < 1 || !seeds || L < 1 || !(sigma > 0.0) || !modes_out) return -1;
+    for (int l = 0; l < L; ++l)
+        if (seeds[l] < 0 || seeds[l] >= N) return -1;
+    int32_t* assign = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    double* dens = (double*)malloc(sizeof(double) * (size_t)L);
+    if (!assign || !dens) { free(assign); free(dens); return -2; }
+    for (int64_t p = 0; p < N; ++p) {
+        int best = 0;
+        double bd = sqdist(X, D, p, seeds[0]);
+        for (int l = 1; l < L; ++l) {
+            double d = sqdist(X, D, p, seeds[l]);
+            if (d < bd) { bd = d; best = l; }
+        }
+        assign[p] = best;
+    }
+    for (int l = 0; l < L; ++l) { modes_out[l] = seeds[l]; dens[l] = 0.0; }
+    for (int l = 0; l < L; ++l) {
+        int any = 0;
+        for (int64_t p = 0; p < N && !any; ++p) any = (assign[p] == l);
+        if (!any) continue;
+        double best = -1.0;
+        for (int64_t y = 0; y < N; ++y) {
+            double f = 0.0;
+            for (int64_t p = 0; p < N; ++p)
+                if (assign[p] == l) f += oracle_gauss(sqdist(X, D, p, y), sigma);
+            if (f > best) { best = f; modes_out[l] = (int32_t)y; }
+        }
+        dens[l] = best;
+    }
+    if (assign_out) memcpy(assign_out, assign, sizeof(int32_t) * (size_t)N);
+    if (density_out) memcpy(density_out, dens, sizeof(double) * (size_t)L);
+    free(assign);
+    free(dens);
+    return 0;
+}
+
+int oracle_cluster_density(const float* X, int64_t N, int D, const int32_t* assign, int l,
+                           double sigma, const int64_t* ys, int64_t ny, double* out)
+{
+    if (!X || N < 1 || D < 1 || !assign || !(sigma > 0.0) || !ys || !out) return -1;
+    for (int64_t i = 0; i < ny; ++i) {
+        if (ys[i] < 0 || ys[i] >= N) return -1;
+        double f = 0.0;
+        for (int64_t p = 0; p < N; ++p)
+            if (assign[p] == l) f += oracle_gauss(sqdist(X, D, p, ys[i]), sigma);
+        out[i] = f;
+    }
+    return 0;
+}

@@ -136,6 +136,20 @@ int oracle_solve_ms_graph(const float* X, int64_t N, int D, int L,
                           double* Z, int32_t* labels, double* energy,
                           int* outer_done, int* inner_total, int* ms_total);
 
+/* ---- Starting modes (Section 4.2: the starting mode of each cluster follows
+ * the mode definition of Eq. (1) from the initial assignments) ----
+ * assign[p] = argmin_l ||x_p - x_{seeds[l]}||^2 (ties to the smaller l); then
+ * m_l = argmax_{y in X} sum_{p: assign[p] = l} k(x_p, y), ties to the smaller
+ * index.  density_out [L, nullable] receives the maximum of each cluster's sum;
+ * a cluster with no point keeps its seed (density 0). */
+int oracle_initial_modes(const float* X, int64_t N, int D, const int32_t* seeds, int L,
+                         double sigma, int32_t* modes_out, int32_t* assign_out,
+                         double* density_out);
+
+/* The cluster density sum_{p: assign[p] = l} k(x_p, x_y) at the given points y. */
+int oracle_cluster_density(const float* X, int64_t N, int D, const int32_t* assign, int l,
+                           double sigma, const int64_t* ys, int64_t ny, double* out);
+
 #ifdef __cplusplus
 }
 #endif
