@@ -30,7 +30,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SLK N·L·iter/s and solves/s vs plain FP32 GPU at equal labels; p50/p99 latency"
-WORKLOAD = dict(name="mnist_like_70000x784_L10", N=70000, D=784, L=10, k=5, lam=1.0)
+WORKLOAD = dict(name="mnist_like_70000x784_L10", N=70000, D=784, L=10, k=5, lam=1.0,
+                affinity="binary", gen="mnist_like")
+# the precision form: curved 8-dim manifolds, Zipf(1.1) cluster sizes, heat affinity
+MANIFOLDS = dict(name="manifolds_1000000x128_L100", N=1_000_000, D=128, L=100, k=10, lam=1.0,
+                 affinity="heat", gen="manifolds")
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP32_LANES_PER_SM = 128      # FP32 FMA units per SM (4 sub-partitions x 32)
 
@@ -45,18 +49,23 @@ def parse():
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain float32 solve beside the main arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["mnist_like", "batched", "serving"], default="mnist_like",
-                    help="mnist_like: one 70000 x 784 solve per step; batched: 256 uneven "
-                         "problems per step (slk_solve_batched)")
+    ap.add_argument("--workload", choices=["mnist_like", "manifolds", "batched", "serving", "ms"],
+                    default="mnist_like",
+                    help="mnist_like: one 70000 x 784 SLK-BO solve per step; manifolds: one "
+                         "1e6 x 128, L=100, k=10 heat-affinity solve per step; ms: the 70000 x 784 "
+                         "problem solved by SLK-MS (mean-shift modes); batched: 256 uneven problems "
+                         "per step (slk_solve_batched); serving: a Poisson request stream")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--requests", type=int, default=64, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean Poisson arrival rate (req/s)")
     ap.add_argument("--rows", type=int, default=None,
                     help="generate the workload with this many points (profiling captures)")
     args = ap.parse_args()
+    if args.workload == "manifolds":
+        WORKLOAD.update(MANIFOLDS)
     if args.rows:
         WORKLOAD["N"] = args.rows
-        WORKLOAD["name"] = f"mnist_like_{args.rows}x784_L10"
+        WORKLOAD["name"] = f"{WORKLOAD['gen']}_{args.rows}x{WORKLOAD['D']}_L{WORKLOAD['L']}"
     return args
 
 
@@ -82,7 +91,10 @@ def dist_env():
 
 def make_inputs():
     from paper_1810_13044_gb300 import inputs
-    X, y = inputs.mnist_like(N=WORKLOAD["N"], D=WORKLOAD["D"])
+    if WORKLOAD["gen"] == "manifolds":
+        X, y = inputs.manifolds(N=WORKLOAD["N"], D=WORKLOAD["D"], n_clusters=WORKLOAD["L"])
+    else:
+        X, y = inputs.mnist_like(N=WORKLOAD["N"], D=WORKLOAD["D"])
     m0 = inputs.kmeanspp(X, WORKLOAD["L"], seed=1810)
     return X, m0
 
@@ -159,19 +171,25 @@ def oracle_sample(X, m0, n_rows=8, inner_per_outer=None, outer=None):
     t0 = time.perf_counter()
     idx, d2 = oracle.knn(X, k, rows=rows)
     t_knn = (time.perf_counter() - t0) * N / n_rows
-    # a kNN-shaped graph for the iteration leg (the exact graph is what costs hours)
+    # a kNN-shaped graph for the iteration leg (the exact graph is what costs hours);
+    # above 70000 rows the leg runs on the first 70000 rows and is scaled by N
     from paper_1810_13044_gb300 import inputs
-    rp, ci, _ = inputs.random_graph(N, k, seed=3)
+    n_it = min(N, 70000)
+    rp, ci, _ = inputs.random_graph(n_it, k, seed=3)
+    w = np.full(n_it * k, 0.5) if WORKLOAD.get("affinity") == "heat" else None
     sig = float(np.sqrt(np.median(d2)))
     inner = int(inner_per_outer or 20)
     outer = int(outer or 1)
+    m_it = m0 if n_it == N else (np.arange(L, dtype=np.int32) * (n_it // L)).astype(np.int32)
     t0 = time.perf_counter()
-    oracle.solve_graph(X, L, rp, ci, None, sig, lam, m0, max_outer=1, max_inner=inner, tol=-1.0)
-    t_outer = time.perf_counter() - t0
+    oracle.solve_graph(X[:n_it], L, rp, ci, w, sig, lam, m_it, max_outer=1, max_inner=inner, tol=-1.0)
+    t_outer = (time.perf_counter() - t0) * N / n_it
     total = t_knn + t_outer * outer
+    scope = (f"the full {N}x{WORKLOAD['D']} problem" if n_it == N else
+             f"{n_it} of the {N} rows scaled x{N / n_it:.1f}")
     desc = (f"FP64 oracle, 1 thread: exact kNN of {n_rows} rows scaled x{N // n_rows}, plus one outer "
-            f"iteration ({inner} z-updates, unary, modes, energy) on the full {N}x{WORKLOAD['D']} "
-            f"problem scaled x{outer} outer iterations")
+            f"iteration ({inner} z-updates, unary, modes, energy) on {scope}, "
+            f"scaled x{outer} outer iterations")
     return total, desc
 
 
@@ -217,7 +235,8 @@ def run_slk(args, rank, world, local):
     dev = torch.device("cuda", local)
     Xd = torch.from_numpy(X).to(dev)
     m0d = torch.from_numpy(m0).to(dev)
-    params = slk.default_params(knn_precision=args.precision)
+    heat = WORKLOAD["affinity"] == "heat"
+    params = slk.default_params(knn_precision=args.precision, affinity=WORKLOAD["affinity"])
     ctx = slk.context(local)
     out = (torch.empty(N, L, device=dev), torch.empty(N, dtype=torch.int32, device=dev),
            torch.empty(L, dtype=torch.int32, device=dev))
@@ -253,37 +272,52 @@ def run_slk(args, rank, world, local):
     plain = None
     if not args.no_fp32_compare and args.precision != "fp32":
         # the plain float32 GPU solve at equal labels (same workload, own timing)
-        p32 = slk.default_params(knn_precision="fp32")
+        p32 = slk.default_params(knn_precision="fp32", affinity=WORKLOAD["affinity"])
         out32 = (torch.empty(N, L, device=dev), torch.empty(N, dtype=torch.int32, device=dev),
-                 torch.empty(L, dtype=torch.int32, device=dev))
+               torch.empty(L, dtype=torch.int32, device=dev))
         slk.solve(Xd, L, k, lam, m0d, params=p32, ctx=ctx, out=out32)
         barrier()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps32 = args.steps if N <= 100000 else 1   # float32 tiles at 1e6 rows take seconds
         f0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps32):
             slk.solve(Xd, L, k, lam, m0d, params=p32, ctx=ctx, out=out32)
         f1.record(stream)
         barrier()
         ms32 = f0.elapsed_time(f1)
-        plain = {"value": args.steps / (ms32 / 1e3), "unit": "solves/s", "knn": "fp32",
+        plain = {"value": steps32 / (ms32 / 1e3), "unit": "solves/s", "knn": "fp32",
                  "equal_labels": bool(torch.equal(out32[1], labels_main)),
                  "equal_modes": bool(torch.equal(out32[2], modes_main))}
 
     # bound iterations alone on this solve's graph: N*L*iter/s (fixed 50 updates)
-    g = slk.knn_graph(Xd, k, precision=args.precision, ctx=ctx)
+    g = slk.knn_graph(Xd, k, precision=args.precision, ctx=ctx,
+                      affinity=WORKLOAD["affinity"], sigma=stats["sigma"])
+    gw = g.w if heat else None
     A, Z0 = slk.unary(Xd, out[2], stats["sigma"], ctx=ctx)
     Zb, Zp = Z0.clone(), torch.empty_like(Z0)
-    slk.bound_iterate(A, g.row_ptr, g.col_idx, None, lam, Zb, Zp, 50, tol=-1.0, ctx=ctx)
+    slk.bound_iterate(A, g.row_ptr, g.col_idx, gw, lam, Zb, Zp, 50, tol=-1.0, ctx=ctx)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 5
     e0.record(stream)
     for _ in range(reps):
         Zb.copy_(Z0)
-        slk.bound_iterate(A, g.row_ptr, g.col_idx, None, lam, Zb, Zp, 50, tol=-1.0, ctx=ctx)
+        slk.bound_iterate(A, g.row_ptr, g.col_idx, gw, lam, Zb, Zp, 50, tol=-1.0, ctx=ctx)
     e1.record(stream)
     torch.cuda.synchronize()
     bound_ms = e0.elapsed_time(e1) / reps
     nl_iter_per_s = N * L * 50 / (bound_ms / 1e3)
+
+    # starting modes (Section 4.2) on the same data, timed alone: N x N float32
+    # distance tiles with the kernel-density epilogue
+    init_ms = None
+    if N <= 200000:
+        slk.initial_modes(Xd, m0d, stats["sigma"], ctx=ctx)
+        i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        i0.record(stream)
+        slk.initial_modes(Xd, m0d, stats["sigma"], ctx=ctx)
+        i1.record(stream)
+        torch.cuda.synchronize()
+        init_ms = i0.elapsed_time(i1)
 
     # e2e through the host-buffer entry point (pinned X in, labels + modes out)
     Xh = torch.from_numpy(X).pin_memory()
@@ -323,6 +357,36 @@ def run_slk(args, rank, world, local):
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["launch_ms"] = cand_ms
         roof["algorithmic"] = f"2*N*N*D = {flops:.3e} flop per launch (Dp={Dp})"
+        # bound iterations: per row and update row_ptr 8 + col 4k (+ w 4k) + a, z_old, z_new 12L
+        # bytes (each neighbour row of Z counted once, the ideal reuse)
+        b_row = 8 + 4 * k + (4 * k if heat else 0) + 12 * L
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        gbs = N * b_row * 50 / (bound_ms / 1e3) / 1e9
+        roof_bound = {"bound": "hbm", "kernel": "bound_persistent_kernel", "achieved": gbs,
+                      "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                      "peak_source": "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback",
+                      "traffic": None,
+                      "algorithmic": f"N*(8+4k{'+4k' if heat else ''}+12L) = {N * b_row / 1e6:.1f} MB "
+                                     f"per update, 50 updates per launch",
+                      "l2_resident": N * b_row < 100e6}
+        # the reported roofline is the kernel that takes the most device time in the step
+        fb_ms = ms_phase["knn_fallback"] / max(1, calls["knn_fallback"])
+        fb_rows = stats["knn_fallback_rows"]
+        bound_step_ms = ms_phase["bound"] / max(1, calls["bound"])
+        if ms_phase["knn_fallback"] > max(ms_phase["knn_cand"], ms_phase["bound"]) and fb_rows > 0:
+            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+            fflops = 2.0 * fb_rows * N * D
+            roof = {"bound": "alu", "kernel": "knn_fallback_batch_kernel",
+                    "achieved": fflops / (fb_ms / 1e3) / 1e12,
+                    "peak": 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12, "unit": "TFLOP/s",
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                    "traffic": None, "launch_ms": fb_ms,
+                    "algorithmic": f"2*rows*N*D = {fflops:.3e} flop per launch ({fb_rows} rows)"}
+            roof["frac"] = roof["achieved"] / roof["peak"]
+        elif ms_phase["bound"] > ms_phase["knn_cand"]:
+            roof = dict(roof_bound, launch_ms=bound_step_ms,
+                        note="solve launches run to the inner tolerance; achieved is from the "
+                             "fixed 50-update launches timed beside")
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -330,7 +394,7 @@ def run_slk(args, rank, world, local):
             "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "N": N, "D": D, "L": L, "k": k, "lambda": lam,
-                       "sigma": "median kNN distance",
+                       "sigma": "median kNN distance", "affinity": WORKLOAD["affinity"],
                        "knn": ("float32 SIMT distance tiles" if args.precision == "fp32" else
                                "bfloat16 tcgen05 distance tiles for candidates, exact float32 "
                                "rerank with rounding certificate (same graph as float32)"),
@@ -339,8 +403,14 @@ def run_slk(args, rank, world, local):
                        "outer_iters": stats["outer_iters"],
                        "inner_iters_total": stats["inner_iters_total"]},
             "nl_iter_per_s": nl_iter_per_s, "bound_ms_per_50_updates": bound_ms,
+            "initial_modes": None if init_ms is None else {
+                "ms": init_ms, "bound": "alu",
+                "achieved_tflops": 2.0 * N * N * D / (init_ms / 1e3) / 1e12,
+                "peak_tflops": 152 * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12,
+                "algorithmic": "2*N*N*D flop (float32 distance tiles) + N*N exp"},
             "phase_ms_per_step": {k_: v / args.steps for k_, v in ms_phase.items()},
             "roofline": roof,
+            "roofline_bound": roof_bound,
             "plain_fp32_gpu": plain,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": N * D * 4 + L * 4,
                     "d2h_bytes_per_step": N * 4 + L * 4},
@@ -354,6 +424,149 @@ def run_slk(args, rank, world, local):
                                       outer=stats["outer_iters"])
             line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "solves/s", "cores": 1,
                                     "kind": "oracle", "sample": desc}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def oracle_ms_sample(X, m0, sig, rows=2000, ms_iters=1):
+    """Seconds of one Eq. (mean-shift) iteration of the FP64 oracle on the
+    full problem, from one iteration on `rows` rows scaled to N rows."""
+    import oracle
+    N, L = WORKLOAD["N"], WORKLOAD["L"]
+    Xs = X[:rows]
+    M0 = X[m0].astype(np.float64)
+    A = oracle.unary_vec(Xs, M0, sig)
+    t0 = time.perf_counter()
+    oracle.mean_shift(Xs, oracle.log_z(A), M0, sig, ms_iters, -1.0)
+    return (time.perf_counter() - t0) / ms_iters * N / rows
+
+
+def run_ms(args, rank, world, local):
+    """SLK-MS (modes by Eq. mean-shift) on the 70000 x 784, L=10, k=5 problem."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1810_13044_gb300 import slk
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    X, m0 = make_inputs()
+    N, D, L, k, lam = (WORKLOAD[x] for x in ("N", "D", "L", "k", "lam"))
+    dev = torch.device("cuda", local)
+    Xd = torch.from_numpy(X).to(dev)
+    m0d = torch.from_numpy(m0).to(dev)
+    params = slk.default_params(knn_precision=args.precision)
+    ctx = slk.context(local)
+    out = (torch.empty(N, L, device=dev), torch.empty(N, dtype=torch.int32, device=dev),
+           torch.empty(L, D, device=dev))
+
+    def step():
+        return slk.solve_ms(Xd, L, k, lam, m0d, params=params, ctx=ctx, out=out)
+
+    for _ in range(args.warmup):
+        _, _, _, stats = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, _, _, stats = step()
+        ev1.record(stream)
+        barrier()
+    ms_phase, calls, launches = ctx.profile_read()
+    ctx.profile(False)
+    ms_max, value = whole_job(ev0.elapsed_time(ev1), args.steps, world, dev)
+
+    # e2e through the public API: pinned host X in, labels + modes out, every step
+    Xh = torch.from_numpy(X).pin_memory()
+    lab_h = torch.empty(N, dtype=torch.int32).pin_memory()
+    M_h = torch.empty(L, D, dtype=torch.float32).pin_memory()
+    Xe = torch.empty_like(Xd)
+
+    def e2e_step():
+        Xe.copy_(Xh, non_blocking=True)
+        slk.solve_ms(Xe, L, k, lam, m0d, params=params, ctx=ctx, out=out)
+        lab_h.copy_(out[1], non_blocking=True)
+        M_h.copy_(out[2], non_blocking=True)
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    _, e2e_value = whole_job((time.perf_counter() - t0) * 1e3, args.steps, world, dev)
+
+    if rank == 0:
+        peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        fp32_peak = 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        ms_iters = stats["ms_iters_total"]
+        ms_launch_ms = ms_phase["mean_shift"] / max(1, calls["mean_shift"])
+        # Eq. (mean-shift): per (point, label, feature) a difference, a square-add
+        # (distance) and a multiply-add (weighted sum) = 5 flop
+        ms_flops = 5.0 * N * L * D * ms_iters / max(1, stats["outer_iters"])
+        roof_ms = {"bound": "alu", "kernel": "ms_persistent_kernel",
+                   "achieved": ms_flops / (ms_launch_ms / 1e3) / 1e12, "peak": fp32_peak,
+                   "unit": "TFLOP/s",
+                   "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                   "traffic": None, "launch_ms": ms_launch_ms,
+                   "algorithmic": f"5*N*L*D flop per mean-shift iteration x "
+                                  f"{ms_iters / max(1, stats['outer_iters']):.1f} iterations per launch"}
+        roof_ms["frac"] = roof_ms["achieved"] / roof_ms["peak"]
+        cand_ms = ms_phase["knn_cand"] / max(1, calls["knn_cand"])
+        flops = 2.0 * N * N * D
+        peak = peaks.get("bf16_tflops", 1900.0)
+        roof_knn = {"bound": "tensor", "kernel": "knn_cand_bf16_kernel",
+                    "achieved": flops / (cand_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "peak_source": "measured bf16_tflops" if "bf16_tflops" in peaks else "fallback",
+                    "traffic": None, "launch_ms": cand_ms,
+                    "algorithmic": f"2*N*N*D = {flops:.3e} flop per launch"}
+        roof_knn["frac"] = roof_knn["achieved"] / roof_knn["peak"]
+        # the dominant kernel of the step by device time
+        dominant = roof_ms if ms_phase["mean_shift"] >= ms_phase["knn_cand"] else roof_knn
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"] + "_slk_ms", "N": N, "D": D, "L": L, "k": k,
+                       "lambda": lam, "sigma": "median kNN distance", "modes": "mean-shift (SLK-MS)",
+                       "knn": args.precision, "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": f"inputs larger than L2 (X is {N * D * 4 / 1e6:.0f} MB, L2 129 MB)",
+                       "outer_iters": stats["outer_iters"],
+                       "inner_iters_total": stats["inner_iters_total"],
+                       "ms_iters_total": ms_iters,
+                       "max_ms": params.max_ms, "tol_ms": params.tol_ms, "tol_modes": params.tol_modes},
+            "phase_ms_per_step": {k_: v / args.steps for k_, v in ms_phase.items()},
+            "roofline": dominant,
+            "roofline_mean_shift": roof_ms,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": N * D * 4,
+                    "d2h_bytes_per_step": N * 4 + L * D * 4},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "energy": stats["energy"],
+        }
+        if not args.no_cpu_baseline:
+            sec, desc = oracle_sample(X, m0, n_rows=8,
+                                      inner_per_outer=max(1, stats["inner_iters_total"] // max(1, stats["outer_iters"])),
+                                      outer=stats["outer_iters"])
+            t_ms = oracle_ms_sample(X, m0, stats["sigma"])
+            line["cpu_baseline"] = {"value": 1.0 / (sec + t_ms * ms_iters), "unit": "solves/s",
+                                    "cores": 1, "kind": "oracle",
+                                    "sample": desc + f"; mean-shift: one iteration on 2000 rows scaled "
+                                                     f"x{N // 2000} rows and x{ms_iters} iterations"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -562,6 +775,8 @@ def main():
         run_batched(args, rank, world, local)
     elif args.workload == "serving":
         run_serving(args, rank, world, local)
+    elif args.workload == "ms":
+        run_ms(args, rank, world, local)
     else:
         run_slk(args, rank, world, local)
 

@@ -159,6 +159,12 @@ typedef struct {
     int32_t sigma_rule;     /* SLK_SIGMA_* used when sigma <= 0 (default MEDIAN) */
     int32_t affinity;       /* SLK_AFFINITY_* (default BINARY) */
     int32_t knn_precision;  /* SLK_KNN_* (default FP32) */
+    int32_t refine_init;    /* slk_solve, slk_solve_host, slk_solve_ms: 1 = start from
+                               slk_initial_modes(init_modes) instead of init_modes (default 0) */
+    /* SLK-MS only (slk_solve_ms): */
+    int32_t max_ms;         /* mean-shift iterations per outer iteration (default 100) */
+    float tol_ms;           /* stop them when max_l ||m_l move||_2 <= tol_ms * sigma (default 1e-5) */
+    float tol_modes;        /* stop the outer loop when the modes moved <= tol_modes * sigma (default 1e-3) */
 } slk_params;
 
 typedef struct {
@@ -168,6 +174,7 @@ typedef struct {
     float sigma;                /* kernel width used */
     double energy;              /* E of Eq. (1) after the last outer iteration */
     int64_t knn_fallback_rows;  /* kNN rows recomputed by the exact scan */
+    int32_t ms_iters_total;     /* SLK-MS: mean-shift iterations summed over outer iterations */
 } slk_stats;
 
 /* Fill *p with the defaults listed in slk_params. */
@@ -193,6 +200,77 @@ slk_status slk_solve_host(slk_ctx* ctx, const float* X, int64_t N, int32_t D, in
                           int32_t k, float lambda, float sigma, const int32_t* init_modes,
                           const slk_params* params, float* Z, int32_t* labels, int32_t* modes,
                           slk_stats* stats);
+
+/* Starting modes (Section 4.2: the starting mode of each cluster follows the
+ * mode definition of Eq. (1) from the initial assignments): every point is
+ * assigned to its nearest seed (squared Euclidean distance, ties to the
+ * smaller l), then
+ *   modes[l] = argmax_{y in X} sum_{p: assign[p] = l} k(x_p, y),
+ * k the Gaussian kernel of width sigma, ties to the smaller index; a cluster
+ * with no point keeps its seed.  The dense N x N kernel sums run as float32
+ * distance tiles of the centred data (norm expansion) with float64 row sums;
+ * their rounding bound selects the points that can still be the maximiser,
+ * whose sums are then recomputed from float32 differences (float64 sums).
+ *   seeds [L] device int32 (e.g. K-means++ indices); modes [L] device out;
+ *   assign [N] device out (nullable); density [L] host out (nullable): the
+ *   maximum of each cluster's sum (0 for an empty cluster); candidates [host,
+ *   nullable]: the number of (point, cluster) sums recomputed exactly. */
+slk_status slk_initial_modes(slk_ctx* ctx, const float* X, int64_t N, int32_t D,
+                             const int32_t* seeds, int32_t L, float sigma, int32_t* modes,
+                             int32_t* assign, double* density, int64_t* candidates);
+
+/* ---------------------------------------------------------------- SLK-MS
+ * The mean-shift variant of Algorithm 1 (Section 3.1, "Modes via
+ * mean-shift"; Algorithm 1, SLK-MS branch): the modes are vectors m_l in R^D
+ * instead of data points.  M is L x D float32 row-major on the DEVICE. */
+
+#define SLK_MS_MAX_D 4096
+
+/* a_{p,l} = exp(-||x_p - m_l||^2 / (2 sigma^2)) with vector modes M
+ * (Eq. general-second); Z0 [nullable] = softmax rows as in slk_unary. */
+slk_status slk_unary_vec(slk_ctx* ctx, const float* X, int64_t N, int32_t D, const float* M,
+                         int32_t L, float sigma, float* A, float* Z0);
+
+/* SLK-MS mode update, Eq. (mean-shift), iterated with the assignments fixed:
+ *   m_l <- sum_p z_{p,l} k(x_p, m_l) x_p / sum_p z_{p,l} k(x_p, m_l)
+ * for every l from the same previous modes, until max_l ||m_l^new - m_l^old||_2
+ * <= tol * sigma (tol < 0: exactly max_iters iterations) or max_iters.  z is
+ * the final iterate of the inner loop; it enters through the logits of its
+ * last update (A, Z_prev, graph and lambda as in slk_mode_update; Z_prev NULL:
+ * no update ran and s = a) as log z = log softmax(s), so float32 z that round
+ * to 0 or 1 keep their weights.  Sums are taken relative to the largest
+ * exponent per label, combined across the grid in float64; the iteration state
+ * is float64 inside one call.
+ *   X [N x D], A [N x L], Z_prev [N x L, nullable]: device inputs;
+ *   M [L x D] device, in: starting modes, out: modes after the last iteration;
+ *   labels [N, device, nullable] out: argmax_l z_{p,l}, ties to the smaller l;
+ *   iters_done, last_shift [host, nullable]: iterations run and the largest
+ *   move of the last one.
+ * 1 <= D <= SLK_MS_MAX_D.  Returns SLK_ERR_TIMEOUT if a bounded wait gave up. */
+slk_status slk_mean_shift(slk_ctx* ctx, const float* X, int32_t D, const float* A,
+                          const float* Z_prev, const int64_t* row_ptr, const int32_t* col_idx,
+                          const float* w, int64_t N, int32_t L, float lambda, float sigma,
+                          float* M, int32_t max_iters, float tol, int32_t* labels,
+                          int32_t* iters_done, float* last_shift);
+
+/* Eq. (1) at one-hot labels with vector modes M (otherwise as slk_energy). */
+slk_status slk_energy_vec(slk_ctx* ctx, const float* X, int32_t D, const int32_t* labels,
+                          const int64_t* row_ptr, const int32_t* col_idx, const float* w,
+                          int64_t N, int32_t L, const float* M, float sigma, float lambda,
+                          double* E);
+
+/* Whole SLK-MS on the GPU: kNN graph and sigma as in slk_solve, modes
+ * m_l^0 = x_{init_modes[l]}, then per outer iteration: unary term from M,
+ * z = softmax(a), z-updates (Eq. soft-max), labels, mean-shift modes
+ * (slk_mean_shift with params->max_ms, params->tol_ms), energy.  Stops when
+ * no mode moved more than params->tol_modes * sigma in an outer iteration, or
+ * after params->max_outer.
+ *   init_modes [L] device int32; Z [N x L], labels [N], M [L x D]: device outputs.
+ * Returns SLK_NOT_CONVERGED (results valid) when max_outer is reached. */
+slk_status slk_solve_ms(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int32_t L, int32_t k,
+                        float lambda, float sigma, const int32_t* init_modes,
+                        const slk_params* params, float* Z, int32_t* labels, float* M,
+                        slk_stats* stats);
 
 /* One clustering problem of a batch (all pointers DEVICE, caller-owned). */
 typedef struct {
@@ -313,6 +391,7 @@ enum {
     SLK_PHASE_BOUND,            /* z-updates (inner loop) */
     SLK_PHASE_MODE,
     SLK_PHASE_ENERGY,
+    SLK_PHASE_MEANSHIFT,        /* SLK-MS mode iterations */
     SLK_PHASE_COUNT
 };
 slk_status slk_profile(slk_ctx* ctx, int32_t enable);

@@ -300,7 +300,7 @@ double oracle_relaxed(const double* A, const double* Z, const int64_t* row_ptr,
 
 /* Algorithm 1 (SLK-BO), outer loop: modes fixed -> a; z = softmax(a); inner
  * z-updates; modes as by-products (Eq. mode_byproduct); repeat until the modes
- * do not change (Section 3: "until the modes do not change"). */
+ * do not change (Section 3's stopping rule). */
 int oracle_solve_graph(const float* X, int64_t N, int D, int L,
                        const int64_t* row_ptr, const int32_t* col_idx, const double* w,
                        double sigma, double lambda, int32_t* modes,

@@ -1,5 +1,5 @@
 // C-ABI entry points of include/slk.h: context management, argument checks,
-// and the host driver of Algorithm 1 (SLK-BO).
+// and the host drivers of Algorithm 1 (SLK-BO and SLK-MS).
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -243,6 +243,10 @@ extern "C" void slk_default_params(slk_params* p) {
     p->sigma_rule = SLK_SIGMA_MEDIAN;
     p->affinity = SLK_AFFINITY_BINARY;
     p->knn_precision = SLK_KNN_FP32;
+    p->refine_init = 0;
+    p->max_ms = 100;
+    p->tol_ms = 1e-5f;
+    p->tol_modes = 1e-3f;
 }
 
 // ---------------------------------------------------------------- steps
@@ -391,6 +395,7 @@ extern "C" slk_status slk_energy(slk_ctx* ctx, const float* X, int32_t D, const 
 namespace {
 
 struct SolveBufs {
+    void* init_ws;   // starting-mode scratch (refine_init), else NULL
     float* A;
     float* Zp;
     float* dist2;
@@ -408,6 +413,7 @@ size_t solve_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int L, int k, const 
     b += align_up(sizeof(int64_t) * (size_t)(N + 1), 256);
     b += align_up(sizeof(float) * (size_t)L, 256);
     b += knn_ws_bytes(ctx, N, D, k, p.knn_precision) + 512;
+    if (p.refine_init) b += init_modes_ws_bytes(ctx, N, D, L) + 512;
     return b;
 }
 
@@ -422,6 +428,7 @@ SolveBufs carve_solve(WsCarver& wc, const slk_ctx* ctx, int64_t N, int D, int L,
     b.row_ptr = wc.take<int64_t>((size_t)N + 1);
     b.mode_key = wc.take<float>((size_t)L);
     b.knn_ws = wc.take<unsigned char>(knn_ws_bytes(ctx, N, D, k, p.knn_precision));
+    b.init_ws = p.refine_init ? wc.take<unsigned char>(init_modes_ws_bytes(ctx, N, D, L)) : nullptr;
     return b;
 }
 
@@ -460,9 +467,14 @@ slk_status solve_device(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int3
         if (r != SLK_OK) return r;
         w = b.w;
     }
-    if (modes != init_modes)
+    if (p.refine_init) {
+        r = init_modes_launch(ctx, X, N, D, init_modes, L, &st->sigma, modes, nullptr, nullptr,
+                              b.init_ws, st);
+        if (r != SLK_OK) return r;
+    } else if (modes != init_modes) {
         SLK_CUDA_TRY(ctx, cudaMemcpyAsync(modes, init_modes, sizeof(int32_t) * L,
                                           cudaMemcpyDeviceToDevice, s));
+    }
     DevState hs;
     int outer = 0, inner_total = 0, converged = 0;
     for (outer = 0; outer < p.max_outer;) {
@@ -550,4 +562,265 @@ extern "C" slk_status slk_solve_host(slk_ctx* ctx, const float* X, int64_t N, in
     r = sync_and_check(ctx);
     if (r != SLK_OK) return r;
     return rs;
+}
+
+// ---------------------------------------------------------------- SLK-MS
+
+namespace {
+
+// Scratch of the mean-shift mode update: status words, float64 modes (the
+// iteration state and its value at the start of a call), log z.
+struct MsBufs {
+    MsStatus* ms;
+    double* M64;
+    double* M64_start;
+    float* Mhi;     // M64 split into two floats for the unary term and the energy
+    float* Mlo;
+    float* LZ;
+    void* ms_ws;
+};
+
+size_t ms_bufs_bytes(const slk_ctx* ctx, int64_t N, int D, int L) {
+    return align_up(sizeof(MsStatus), 256) + 2 * align_up(sizeof(double) * (size_t)L * D, 256) +
+           2 * align_up(sizeof(float) * (size_t)L * D, 256) +
+           align_up(sizeof(float) * (size_t)N * L, 256) + ms_ws_bytes(ctx, N, D, L) + 1024;
+}
+
+MsBufs carve_ms(WsCarver& wc, const slk_ctx* ctx, int64_t N, int D, int L) {
+    MsBufs b{};
+    b.ms = wc.take<MsStatus>(1);
+    b.M64 = wc.take<double>((size_t)L * D);
+    b.M64_start = wc.take<double>((size_t)L * D);
+    b.Mhi = wc.take<float>((size_t)L * D);
+    b.Mlo = wc.take<float>((size_t)L * D);
+    b.LZ = wc.take<float>((size_t)N * L);
+    b.ms_ws = wc.take<unsigned char>(ms_ws_bytes(ctx, N, D, L));
+    return b;
+}
+
+// Head of MsStatus (barrier words, counters, moves) next to the DevState copy.
+struct MsHead {
+    unsigned arrive, gen, error, stop;
+    int iters_done;
+    float last_shift;
+    float moved;
+};
+
+slk_status read_state_ms(slk_ctx* ctx, DevState* out, const MsStatus* ms, MsHead* head) {
+    char* hp = static_cast<char*>(ctx->host_pin);
+    SLK_CUDA_TRY(ctx, cudaMemcpyAsync(hp, ctx->dev_small, sizeof(DevState), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    SLK_CUDA_TRY(ctx, cudaMemcpyAsync(hp + sizeof(DevState), ms, sizeof(MsHead),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    slk_status r = sync_and_check(ctx);
+    if (r != SLK_OK) return r;
+    memcpy(out, hp, sizeof(DevState));
+    memcpy(head, hp + sizeof(DevState), sizeof(MsHead));
+    return SLK_OK;
+}
+
+slk_status ms_errors(slk_ctx* ctx, const DevState& hs, const MsHead& mh) {
+    if (hs.error & ERR_BARRIER_TIMEOUT)
+        return set_err(ctx, SLK_ERR_TIMEOUT, "device-wide barrier of the bound kernel timed out");
+    if (hs.knn_error)
+        return set_err(ctx, SLK_ERR_TIMEOUT, "a wait of the tensor-core kNN pipeline timed out");
+    if (mh.error)
+        return set_err(ctx, SLK_ERR_TIMEOUT, "a wait of the mean-shift kernel timed out (%u)", mh.error);
+    return SLK_OK;
+}
+
+}  // namespace
+
+extern "C" slk_status slk_unary_vec(slk_ctx* ctx, const float* X, int64_t N, int32_t D,
+                                    const float* M, int32_t L, float sigma, float* A, float* Z0) {
+    BEGIN_CALL(ctx);
+    CHECK_ARG(X && M && A, "X, M and A must not be NULL");
+    CHECK_ARG(N >= 1 && N < (int64_t)0x7fffffff, "N=%lld out of range", (long long)N);
+    CHECK_ARG(D >= 1, "D=%d must be >= 1", D);
+    CHECK_ARG(L >= 1 && L <= SLK_MAX_L, "L=%d must be in [1, %d]", L, SLK_MAX_L);
+    CHECK_ARG(sigma > 0.f, "sigma must be > 0");
+    DevState* st = dstate(ctx);
+    slk_status r = set_sigma_launch(ctx, sigma, st);
+    if (r != SLK_OK) return r;
+    return unary_launch(ctx, X, N, D, nullptr, L, &st->sigma, A, Z0, M);
+}
+
+extern "C" slk_status slk_mean_shift(slk_ctx* ctx, const float* X, int32_t D, const float* A,
+                                     const float* Z_prev, const int64_t* row_ptr,
+                                     const int32_t* col_idx, const float* w, int64_t N, int32_t L,
+                                     float lambda, float sigma, float* M, int32_t max_iters,
+                                     float tol, int32_t* labels, int32_t* iters_done,
+                                     float* last_shift) {
+    BEGIN_CALL(ctx);
+    CHECK_ARG(X && A && M, "X, A and M must not be NULL");
+    if (Z_prev) {
+        slk_status r = check_graph(ctx, row_ptr, col_idx, N);
+        if (r != SLK_OK) return r;
+    }
+    CHECK_ARG(N >= 1 && N < (int64_t)0x7fffffff, "N=%lld out of range", (long long)N);
+    CHECK_ARG(D >= 1 && D <= SLK_MS_MAX_D, "D=%d must be in [1, %d]", D, SLK_MS_MAX_D);
+    CHECK_ARG(L >= 1 && L <= SLK_MAX_L, "L=%d must be in [1, %d]", L, SLK_MAX_L);
+    CHECK_ARG(sigma > 0.f, "sigma must be > 0");
+    CHECK_ARG(max_iters >= 0, "max_iters must be >= 0");
+    slk_status r = ensure_ws(ctx, ms_bufs_bytes(ctx, N, D, L));
+    if (r != SLK_OK) return r;
+    WsCarver wc(ctx->ws);
+    const MsBufs b = carve_ms(wc, ctx, N, D, L);
+    DevState* st = dstate(ctx);
+    r = set_sigma_launch(ctx, sigma, st);
+    if (r != SLK_OK) return r;
+    r = ms_widen_launch(ctx, M, (int64_t)L * D, b.M64);
+    if (r != SLK_OK) return r;
+    r = logz_launch(ctx, A, Z_prev, row_ptr, col_idx, w, N, L, lambda, labels, b.LZ, false, st);
+    if (r != SLK_OK) return r;
+    r = ms_launch(ctx, X, N, D, b.LZ, L, &st->sigma, b.M64, M, max_iters, tol, b.ms, b.ms_ws);
+    if (r != SLK_OK) return r;
+    DevState hs;
+    MsHead mh;
+    r = read_state_ms(ctx, &hs, b.ms, &mh);
+    if (r != SLK_OK) return r;
+    r = ms_errors(ctx, hs, mh);
+    if (r != SLK_OK) return r;
+    if (iters_done) *iters_done = mh.iters_done;
+    if (last_shift) *last_shift = mh.last_shift;
+    return SLK_OK;
+}
+
+extern "C" slk_status slk_energy_vec(slk_ctx* ctx, const float* X, int32_t D, const int32_t* labels,
+                                     const int64_t* row_ptr, const int32_t* col_idx, const float* w,
+                                     int64_t N, int32_t L, const float* M, float sigma, float lambda,
+                                     double* E) {
+    BEGIN_CALL(ctx);
+    CHECK_ARG(X && labels && M && E, "X, labels, M and E must not be NULL");
+    slk_status r = check_graph(ctx, row_ptr, col_idx, N);
+    if (r != SLK_OK) return r;
+    CHECK_ARG(D >= 1, "D must be >= 1");
+    CHECK_ARG(L >= 1 && L <= SLK_MAX_L, "L=%d must be in [1, %d]", L, SLK_MAX_L);
+    CHECK_ARG(sigma > 0.f, "sigma must be > 0");
+    DevState* st = dstate(ctx);
+    r = set_sigma_launch(ctx, sigma, st);
+    if (r != SLK_OK) return r;
+    r = energy_launch(ctx, X, D, labels, row_ptr, col_idx, w, N, L, nullptr, &st->sigma, lambda, st, M);
+    if (r != SLK_OK) return r;
+    DevState hs;
+    r = read_state(ctx, &hs);
+    if (r != SLK_OK) return r;
+    *E = hs.energy;
+    return SLK_OK;
+}
+
+extern "C" slk_status slk_solve_ms(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int32_t L,
+                                   int32_t k, float lambda, float sigma, const int32_t* init_modes,
+                                   const slk_params* params, float* Z, int32_t* labels, float* M,
+                                   slk_stats* stats) {
+    BEGIN_CALL(ctx);
+    slk_params p;
+    if (params) p = *params; else slk_default_params(&p);
+    CHECK_ARG(M, "M must not be NULL");
+    slk_status r = check_solve_args(ctx, X, N, D, L, k, init_modes, p, Z, labels, init_modes, false);
+    if (r != SLK_OK) return r;
+    CHECK_ARG(D <= SLK_MS_MAX_D, "D=%d must be <= %d", D, SLK_MS_MAX_D);
+    CHECK_ARG(p.max_ms >= 1, "max_ms must be >= 1");
+    r = ensure_ws(ctx, solve_ws_bytes(ctx, N, D, L, k, p) + ms_bufs_bytes(ctx, N, D, L) + 1024);
+    if (r != SLK_OK) return r;
+    WsCarver wc(ctx->ws);
+    const SolveBufs b = carve_solve(wc, ctx, N, D, L, k, p);
+    const MsBufs mb = carve_ms(wc, ctx, N, D, L);
+    DevState* st = dstate(ctx);
+    cudaStream_t s = ctx->stream;
+    r = knn_graph_launch(ctx, X, N, D, k, p.knn_precision, b.row_ptr, b.col_idx, b.dist2, b.knn_ws, st);
+    if (r != SLK_OK) return r;
+    r = (sigma > 0.f) ? set_sigma_launch(ctx, sigma, st)
+                      : sigma_launch(ctx, b.dist2, N * (int64_t)k, p.sigma_rule, st);
+    if (r != SLK_OK) return r;
+    const float* w = nullptr;
+    if (p.affinity == SLK_AFFINITY_HEAT) {
+        r = weights_launch(ctx, b.dist2, N * (int64_t)k, SLK_AFFINITY_HEAT, &st->sigma, b.w);
+        if (r != SLK_OK) return r;
+        w = b.w;
+    }
+    const int32_t* start = init_modes;
+    if (p.refine_init) {
+        int32_t* refined = wc.take<int32_t>(L);
+        r = init_modes_launch(ctx, X, N, D, init_modes, L, &st->sigma, refined, nullptr, nullptr,
+                              b.init_ws, st);
+        if (r != SLK_OK) return r;
+        start = refined;
+    }
+    r = ms_gather_launch(ctx, X, D, start, L, M, mb.M64);
+    if (r != SLK_OK) return r;
+    DevState hs;
+    MsHead mh{};
+    int outer = 0, inner_total = 0, ms_total = 0, converged = 0;
+    for (outer = 0; outer < p.max_outer;) {
+        r = ms_split_launch(ctx, mb.M64, (int64_t)L * D, mb.Mhi, mb.Mlo);
+        if (r != SLK_OK) return r;
+        r = unary_launch(ctx, X, N, D, nullptr, L, &st->sigma, b.A, Z, mb.Mhi, mb.Mlo);
+        if (r != SLK_OK) return r;
+        r = bound_launch(ctx, b.A, b.row_ptr, b.col_idx, w, N, L, lambda, Z, b.Zp, p.max_inner,
+                         p.tol_inner, st, k);
+        if (r != SLK_OK) return r;
+        r = logz_launch(ctx, b.A, b.Zp, b.row_ptr, b.col_idx, w, N, L, lambda, labels, mb.LZ, true, st);
+        if (r != SLK_OK) return r;
+        SLK_CUDA_TRY(ctx, cudaMemcpyAsync(mb.M64_start, mb.M64, sizeof(double) * (size_t)L * D,
+                                          cudaMemcpyDeviceToDevice, s));
+        r = ms_launch(ctx, X, N, D, mb.LZ, L, &st->sigma, mb.M64, M, p.max_ms, p.tol_ms, mb.ms,
+                      mb.ms_ws);
+        if (r != SLK_OK) return r;
+        r = ms_moved_launch(ctx, mb.M64, mb.M64_start, D, L, mb.ms);
+        if (r != SLK_OK) return r;
+        r = ms_split_launch(ctx, mb.M64, (int64_t)L * D, mb.Mhi, mb.Mlo);
+        if (r != SLK_OK) return r;
+        r = energy_launch(ctx, X, D, labels, b.row_ptr, b.col_idx, w, N, L, nullptr, &st->sigma,
+                          lambda, st, mb.Mhi, mb.Mlo);
+        if (r != SLK_OK) return r;
+        r = read_state_ms(ctx, &hs, mb.ms, &mh);
+        if (r != SLK_OK) return r;
+        r = ms_errors(ctx, hs, mh);
+        if (r != SLK_OK) return r;
+        ++outer;
+        inner_total += hs.iters_done;
+        ms_total += mh.iters_done;
+        if (mh.moved <= p.tol_modes * hs.sigma) { converged = 1; break; }
+    }
+    if (stats) {
+        stats->outer_iters = outer;
+        stats->inner_iters_total = inner_total;
+        stats->converged = converged;
+        stats->sigma = hs.sigma;
+        stats->energy = hs.energy;
+        stats->knn_fallback_rows = hs.fallback_count;
+        stats->ms_iters_total = ms_total;
+    }
+    return converged ? SLK_OK : SLK_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------- starting modes
+
+extern "C" slk_status slk_initial_modes(slk_ctx* ctx, const float* X, int64_t N, int32_t D,
+                                        const int32_t* seeds, int32_t L, float sigma,
+                                        int32_t* modes, int32_t* assign, double* density,
+                                        int64_t* candidates) {
+    BEGIN_CALL(ctx);
+    CHECK_ARG(X && seeds && modes, "X, seeds and modes must not be NULL");
+    CHECK_ARG(N >= 1 && N < (int64_t)0x7fffffff, "N=%lld out of range", (long long)N);
+    CHECK_ARG(D >= 1, "D=%d must be >= 1", D);
+    CHECK_ARG(L >= 1 && L <= SLK_MAX_L && L <= N, "L=%d must be in [1, min(%d, N)]", L, SLK_MAX_L);
+    CHECK_ARG(sigma > 0.f, "sigma must be > 0");
+    const size_t need = init_modes_ws_bytes(ctx, N, D, L) + align_up(sizeof(double) * L, 256) + 512;
+    slk_status r = ensure_ws(ctx, need);
+    if (r != SLK_OK) return r;
+    WsCarver wc(ctx->ws);
+    double* ddens = wc.take<double>(L);
+    void* iws = wc.take<unsigned char>(init_modes_ws_bytes(ctx, N, D, L));
+    DevState* st = dstate(ctx);
+    r = set_sigma_launch(ctx, sigma, st);
+    if (r != SLK_OK) return r;
+    r = init_modes_launch(ctx, X, N, D, seeds, L, &st->sigma, modes, assign, ddens, iws, st);
+    if (r != SLK_OK) return r;
+    if (density)
+        SLK_CUDA_TRY(ctx, cudaMemcpyAsync(density, ddens, sizeof(double) * L, cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+    if (candidates) *candidates = ctx->init_candidates;
+    return sync_and_check(ctx);
 }

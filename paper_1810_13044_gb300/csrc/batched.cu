@@ -353,12 +353,7 @@ seg_energy_kernel(const SegInfo* __restrict__ seg, const SegTile* __restrict__ t
             const int lp = si.labels[p];
             const float* xp = si.X + p * si.D;
             const float* xm = si.X + (int64_t)si.modes[lp] * si.D;
-            double d2 = 0.0;
-            for (int j = lane; j < si.D; j += 32) {
-                const double df = (double)xp[j] - (double)xm[j];
-                d2 = fma(df, df, d2);
-            }
-            for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+            const double d2 = warp_sq_dist(xp, xm, nullptr, si.D, lane);
             int64_t e0, e1;
             if (si.kdeg > 0) { e0 = p * si.kdeg; e1 = e0 + si.kdeg; }
             else { e0 = si.row_ptr[p]; e1 = si.row_ptr[p + 1]; }
@@ -754,6 +749,7 @@ extern "C" slk_status slk_solve_batched(slk_ctx* ctx, const slk_instance* inst, 
             stats[b].sigma = h_sigma[b];
             stats[b].energy = h_energy[b];
             stats[b].knn_fallback_rows = -1;
+            stats[b].ms_iters_total = 0;
         }
     }
     (void)use_graph;

@@ -460,6 +460,55 @@ mode_rows_kernel(const float* __restrict__ A, const float* __restrict__ Zp,
         if (best[l]) atomicMax(&st->mode_best[l], best[l]);
 }
 
+// log z of every row and label (SLK-MS weights, Eq. mean-shift) and labels:
+// logits from the previous iterate as in mode_rows_kernel, then
+// log z_{q,l} = (s_l - max s) - log1p(sum_{j != argmax} exp(s_j - max s)).
+template <int G, int LPL>
+__global__ void __launch_bounds__(kThreads)
+logz_rows_kernel(const float* __restrict__ A, const float* __restrict__ Zp,
+                 const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                 const float* __restrict__ w, int64_t N, int L, float lambda, int use_iters_flag,
+                 int32_t* __restrict__ labels, float* __restrict__ LZ, const DevState* st) {
+    constexpr int RPW = 32 / G;
+    const bool with_pair = (Zp != nullptr) && (!use_iters_flag || st->iters_done > 0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane % G, grp = lane / G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t gwarp = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+    for (int64_t base = gwarp * RPW; base < N; base += nwarps * RPW) {
+        const int64_t q = base + grp;
+        if (q >= N) continue;  // whole group skips together
+        float s[LPL];
+        row_logits<G, LPL>(q, gl, gmask, A, row_ptr, col_idx, w, Zp, L, lambda, with_pair, s);
+        float m = s[0];
+        int jl = gl;
+#pragma unroll
+        for (int j = 1; j < LPL; ++j)
+            if (s[j] > m) { m = s[j]; jl = gl + G * j; }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            const float om = __shfl_xor_sync(gmask, m, o, G);
+            const int ol = __shfl_xor_sync(gmask, jl, o, G);
+            if (om > m || (om == m && ol < jl)) { m = om; jl = ol; }
+        }
+        float r = 0.f;
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            const int l = gl + G * j;
+            if (l < L && l != jl) r += expf(s[j] - m);
+        }
+        r = group_sum<G>(r, gmask);
+        const float lse1 = log1pf(r);
+        if (gl == 0 && labels) labels[q] = jl;
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            const int l = gl + G * j;
+            if (l < L) LZ[q * L + l] = (s[j] - m) - lse1;
+        }
+    }
+}
+
 __global__ void mode_finish_kernel(int L, int32_t* modes, float* mode_key, DevState* st) {
     __shared__ int changed;
     if (threadIdx.x == 0) changed = 0;
@@ -585,6 +634,24 @@ slk_status mode_launch(slk_ctx* ctx, const float* A, const float* Z_prev,
     SLK_LAUNCH_CHECK(ctx, "mode_rows_kernel");
     mode_finish_kernel<<<1, 256, 0, ctx->stream>>>(L, modes, mode_key, st);
     SLK_LAUNCH_CHECK(ctx, "mode_finish_kernel");
+    return SLK_OK;
+}
+
+slk_status logz_launch(slk_ctx* ctx, const float* A, const float* Z_prev,
+                       const int64_t* row_ptr, const int32_t* col_idx, const float* w,
+                       int64_t N, int L, float lambda, int32_t* labels, float* LZ,
+                       bool use_iters_flag, const DevState* st) {
+    SLK_COUNT_LAUNCH(ctx, 1);
+    const Shape sh = shape_for(L);
+    const int rows_per_block = (kThreads / 32) * (32 / sh.G);
+    int64_t grid = (N + rows_per_block - 1) / rows_per_block;
+    if (grid > (int64_t)ctx->num_sms * 8) grid = (int64_t)ctx->num_sms * 8;
+#define SLK_LAUNCH_LOGZ(G_, LPL_)                                                        \
+    logz_rows_kernel<G_, LPL_><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(            \
+        A, Z_prev, row_ptr, col_idx, w, N, L, lambda, use_iters_flag ? 1 : 0, labels, LZ, st);
+    SLK_DISPATCH_L(L, SLK_LAUNCH_LOGZ);
+#undef SLK_LAUNCH_LOGZ
+    SLK_LAUNCH_CHECK(ctx, "logz_rows_kernel");
     return SLK_OK;
 }
 

@@ -5,7 +5,8 @@
 //  1. prep: centre the features (x - mu, mu the column mean: distances are
 //     translation invariant) and round them to the candidate operand type
 //     (float32 or bfloat16).  Per point keep ||xt_p||^2 and the rounding
-//     perturbation rho_p = ||xt_p - (x_p - mu)||, both computed in float64.
+//     perturbation rho_p >= ||xt_p - (x_p - mu)|| (float32 lane sums with
+//     their rounding bounds, lanes added in float64).
 //  2. candidates: a distance-tile kernel evaluates
 //     dt(p, q) = ||xt_p||^2 + ||xt_q||^2 - 2 xt_p . xt_q for all pairs and keeps,
 //     per row and per column split, the KC smallest (KC > k).
@@ -41,6 +42,9 @@ __device__ __forceinline__ bool lex_less(float d, int i, float d2, int i2) {
 
 // -------------------------------------------------------------------- prep
 
+// Column sums (the centring mean mu only has to be some float vector:
+// distances are translation invariant): float32 sums of 64 rows, added in
+// float64.
 __global__ void col_sum_kernel(const float* __restrict__ X, int64_t N, int D,
                                double* __restrict__ colsum) {
     __shared__ double sm[8][33];
@@ -49,8 +53,15 @@ __global__ void col_sum_kernel(const float* __restrict__ X, int64_t N, int D,
     const int64_t r0 = (int64_t)blockIdx.y * per;
     const int64_t r1 = (r0 + per < N) ? r0 + per : N;
     double acc = 0.0;
-    if (c < D)
-        for (int64_t r = r0 + threadIdx.y; r < r1; r += 8) acc += (double)X[r * D + c];
+    if (c < D) {
+        int n = 0;
+        float part = 0.f;
+        for (int64_t r = r0 + threadIdx.y; r < r1; r += 8) {
+            part += X[r * D + c];
+            if (++n == 64) { acc += (double)part; part = 0.f; n = 0; }
+        }
+        acc += (double)part;
+    }
     sm[threadIdx.y][threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.y == 0 && c < D) {
@@ -60,53 +71,76 @@ __global__ void col_sum_kernel(const float* __restrict__ X, int64_t N, int D,
     }
 }
 
-// One warp per padded row: xt = round(x - mu), norms and rho in float64.
-__global__ void prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
-                                 int64_t Np, const double* __restrict__ colsum, int to_bf16,
-                                 float* __restrict__ xt32, __nv_bfloat16* __restrict__ xt16,
-                                 float* __restrict__ norms, float* __restrict__ rho,
-                                 DevState* st) {
+// One warp per padded row: xt = round(v), v = fl(x - mu), with
+//   norms[p] = ||xt_p||^2: lane sums of xt^2 in float32 (at most Dp/32 terms,
+//     relative error <= (Dp/32) u, u = 2^-24; each bfloat16 square is exact),
+//     lanes added in float64;
+//   rho[p] >= ||xt_p - (x_p - mu)||: with e = xt - v (exact in float32) and
+//     |v - (x - mu)| <= u |v|, rho <= ||e|| + u ||v||, both norms from float32
+//     lane sums inflated by their summation bound and rounded up.
+// The row maxima go to st with one atomic per block.
+__global__ void __launch_bounds__(256)
+prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
+                 int64_t Np, const double* __restrict__ colsum, int to_bf16,
+                 float* __restrict__ xt32, __nv_bfloat16* __restrict__ xt16,
+                 float* __restrict__ norms, float* __restrict__ rho, DevState* st) {
+    __shared__ unsigned bmax_n, bmax_r;
+    if (threadIdx.x == 0) { bmax_n = 0u; bmax_r = 0u; }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const double inv_n = 1.0 / (double)N;
+    const double bound = 1.0 + (double)(Dp / 32 + 2) * 5.9604644775390625e-08;
+    unsigned my_n = 0u, my_r = 0u;
     for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < Np;
          p += nw) {
-        double n2 = 0.0, r2 = 0.0;
+        float n2 = 0.f, e2 = 0.f, v2 = 0.f;
         for (int j = lane; j < Dp; j += 32) {
-            float v = 0.f;
-            double exact = 0.0;
+            float v = 0.f, vv = 0.f;
             if (p < N && j < D) {
-                const float mu = (float)(colsum[j] / (double)N);
-                const float x = X[p * D + j];
-                exact = (double)x - (double)mu;
-                v = x - mu;
+                const float mu = (float)(colsum[j] * inv_n);
+                v = X[p * D + j] - mu;
             }
-            double vv;
             if (to_bf16) {
                 const __nv_bfloat16 b = __float2bfloat16_rn(v);
                 xt16[p * Dp + j] = b;
-                vv = (double)__bfloat162float(b);
+                vv = __bfloat162float(b);
             } else {
                 xt32[p * Dp + j] = v;
-                vv = (double)v;
+                vv = v;
             }
-            n2 += vv * vv;
-            r2 += (vv - exact) * (vv - exact);
+            n2 = fmaf(vv, vv, n2);
+            const float e = vv - v;
+            e2 = fmaf(e, e, e2);
+            v2 = fmaf(v, v, v2);
         }
+        double dn = n2, de = e2, dv = v2;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-            r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+            dn += __shfl_xor_sync(0xffffffffu, dn, o);
+            de += __shfl_xor_sync(0xffffffffu, de, o);
+            dv += __shfl_xor_sync(0xffffffffu, dv, o);
         }
         if (lane == 0) {
-            const float nf = (float)n2;
-            const float rf = __double2float_ru(sqrt(r2));
+            const float nf = (float)dn;
+            const double r = sqrt(de * bound) + 5.9604644775390625e-08 * sqrt(dv * bound);
+            const float rf = __double2float_ru(r * (1.0 + 1e-12));
             norms[p] = nf;
             rho[p] = rf;
             if (p < N) {
-                atomicMax(&st->knn_max_norm_bits, __float_as_uint(nf));
-                atomicMax(&st->knn_max_rho_bits, __float_as_uint(rf));
+                my_n = max(my_n, __float_as_uint(nf));
+                my_r = max(my_r, __float_as_uint(rf));
             }
         }
+    }
+    if (lane == 0) {
+        atomicMax(&bmax_n, my_n);
+        atomicMax(&bmax_r, my_r);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicMax(&st->knn_max_norm_bits, bmax_n);
+        atomicMax(&st->knn_max_rho_bits, bmax_r);
     }
 }
 
@@ -420,7 +454,8 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
         if (lane == 0 && T < kInf) {
             bool ok = false;
             const double sn = sqrt((double)norms[p]) + sqrt(nmax);
-            const double delta = (gam + 3.0 * u) * sn * sn;
+            // tile arithmetic (gam), the norms' float32 lane sums and roundings
+            const double delta = (gam + (double)(Dp / 32 + 5) * u) * sn * sn;
             const double tt = (double)T - delta;
             if (tt > 0.0) {
                 const double root = sqrt(tt) - (double)rho[p] - rmax;
@@ -731,6 +766,25 @@ size_t knn_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int k, int precision) 
 slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const float* norms,
                                 int64_t N, int Dp, int64_t Np, int kc, int splits,
                                 float* cand_d, int32_t* cand_i, unsigned int* err_flag);
+
+slk_status knn_prep_fp32_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int Dp, int64_t Np,
+                                double* colsum, float* xt, float* norms, float* rho, DevState* st) {
+    cudaStream_t s = ctx->stream;
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(colsum, 0, sizeof(double) * D, s));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_bits, 0, 2 * sizeof(unsigned int), s));
+    SLK_COUNT_LAUNCH(ctx, 2);
+    int gy = (int)((N + 4095) / 4096);
+    if (gy > 1024) gy = 1024;
+    if (gy < 1) gy = 1;
+    col_sum_kernel<<<dim3((unsigned)((D + 31) / 32), (unsigned)gy), dim3(32, 8), 0, s>>>(X, N, D, colsum);
+    SLK_LAUNCH_CHECK(ctx, "col_sum_kernel");
+    int64_t pg = (Np + 7) / 8;
+    if (pg > (int64_t)ctx->num_sms * 16) pg = (int64_t)ctx->num_sms * 16;
+    prep_rows_kernel<<<(unsigned)pg, 256, 0, s>>>(X, N, D, Dp, Np, colsum, 0, xt, nullptr, norms,
+                                                   rho, st);
+    SLK_LAUNCH_CHECK(ctx, "prep_rows_kernel");
+    return SLK_OK;
+}
 
 slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int k,
                             int precision, int64_t* row_ptr, int32_t* col_idx, float* dist2,

@@ -6,11 +6,12 @@
 #include <math.h>
 
 #include "slk_internal.cuh"
+#include "sync.cuh"
 
 namespace {
 
 constexpr int kLPL = 4;  // labels per lane: L <= 128 with 32 lanes
-constexpr unsigned long long kTimeoutNs = 2000000000ull;
+constexpr unsigned long long kTimeoutNs = kSyncTimeoutNs;
 
 struct SegInfo {
     const float* X;
@@ -39,25 +40,6 @@ struct SegState {
     int active_inner;  // instances still iterating in the current inner loop
     int active_outer;  // instances whose outer loop still runs
 };
-
-__device__ __forceinline__ unsigned ld_acq(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ int ld_acq_i(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_rel(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned atom_add_ar(unsigned* p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
 
 // Device-wide step barrier; the last block to arrive publishes "every
 // instance has converged" (active_inner == 0) with the new generation.

@@ -408,12 +408,7 @@ srv_energy_kernel(const SegInfo* __restrict__ seg, int S, SlotDev sd) {
             const int lp = si.labels[p];
             const float* xp = si.X + p * si.D;
             const float* xm = si.X + (int64_t)si.modes[lp] * si.D;
-            double d2 = 0.0;
-            for (int j = lane; j < si.D; j += 32) {
-                const double df = (double)xp[j] - (double)xm[j];
-                d2 = fma(df, df, d2);
-            }
-            for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+            const double d2 = warp_sq_dist(xp, xm, nullptr, si.D, lane);
             const int64_t e0 = p * si.kdeg, e1 = e0 + si.kdeg;
             double cut = 0.0;
             for (int64_t e = e0 + lane; e < e1; e += 32)

@@ -33,6 +33,8 @@ struct slk_ctx {
     std::vector<cudaEvent_t> pool;
     double prof_ms[SLK_PHASE_COUNT] = {};
     long long prof_calls[SLK_PHASE_COUNT] = {};
+    // candidates recomputed exactly by the last starting-mode call
+    long long init_candidates = 0;
     // auxiliary streams (batched graph building), created on first use
     std::vector<cudaStream_t> aux;
     std::vector<cudaEvent_t> aux_ev;
@@ -119,6 +121,19 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
                             int precision, int64_t* row_ptr, int32_t* col_idx, float* dist2,
                             void* ws, DevState* st);
 
+// Centred float32 operand of the distance tiles: xt[p][j] = x_pj - mean_j
+// (Np x Dp, zero padding), norms[p] = ||xt_p||^2, rho[p] = rounding norm.
+slk_status knn_prep_fp32_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int Dp, int64_t Np,
+                                double* colsum, float* xt, float* norms, float* rho, DevState* st);
+
+// Starting modes of Section 4.2 (nearest-seed assignment, then the mode
+// definition of Eq. (1)): modes [L] device out, assign [N] device out
+// (nullable), density [L] device float64 out (nullable); sigma from *sigma_dev.
+size_t init_modes_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int L);
+slk_status init_modes_launch(slk_ctx* ctx, const float* X, int64_t N, int D, const int32_t* seeds,
+                             int L, const float* sigma_dev, int32_t* modes, int32_t* assign,
+                             double* density, void* ws, DevState* st);
+
 // weights w[e] = 1 (binary) or exp(-dist2[e] / (2 sigma^2)) with sigma read
 // from *sigma_dev (heat).
 slk_status weights_launch(slk_ctx* ctx, const float* dist2, int64_t nnz, int affinity,
@@ -128,9 +143,13 @@ slk_status weights_launch(slk_ctx* ctx, const float* dist2, int64_t nnz, int aff
 size_t sigma_ws_bytes(int64_t n);
 slk_status sigma_launch(slk_ctx* ctx, const float* dist2, int64_t n, int rule, DevState* st);
 
-// A and (optionally) Z0 from modes; sigma taken from *sigma_dev.
+// A and (optionally) Z0 from modes; sigma taken from *sigma_dev.  With M
+// (L x D float32) the modes are those vectors and `modes` is ignored
+// (SLK-MS); with Mlo as well, the modes are M + Mlo (a float64 state split
+// into two floats by ms_split_launch).
 slk_status unary_launch(slk_ctx* ctx, const float* X, int64_t N, int D, const int32_t* modes,
-                        int L, const float* sigma_dev, float* A, float* Z0);
+                        int L, const float* sigma_dev, float* A, float* Z0,
+                        const float* M = nullptr, const float* Mlo = nullptr);
 
 // Inner loop; the final iterate ends in Z, the previous one in Z_prev.
 slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
@@ -145,11 +164,46 @@ slk_status mode_launch(slk_ctx* ctx, const float* A, const float* Z_prev,
                        int64_t N, int L, float lambda, int32_t* modes, int32_t* labels,
                        float* mode_key, bool use_iters_flag, DevState* st);
 
-// Energy -> st->energy (device); sigma from *sigma_dev.
+// log z keys (N x L) and labels for the SLK-MS weights (logits as in mode_launch).
+slk_status logz_launch(slk_ctx* ctx, const float* A, const float* Z_prev,
+                       const int64_t* row_ptr, const int32_t* col_idx, const float* w,
+                       int64_t N, int L, float lambda, int32_t* labels, float* LZ,
+                       bool use_iters_flag, const DevState* st);
+
+// SLK-MS mode update, Eq. (mean-shift), with the assignments fixed (given as
+// log z).  M64 (L x D float64, workspace) is the iteration state, in/out;
+// M (L x D float32) receives the modes after every iteration.  Counters go
+// to *ms (device).  Workspace: ms_ws_bytes.
+struct MsStatus {
+    unsigned arrive, gen, error;  // device-wide barrier words (error: bit 0 barrier, bit 1 copy timeout)
+    unsigned stop;                // launch-per-phase path: the loop has stopped
+    int iters_done;
+    float last_shift;
+    float moved;                  // max_l ||m_l after - m_l before|| of one call (ms_moved_launch)
+    double shift2[3][SLK_MAX_L];
+};
+size_t ms_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int L);
+slk_status ms_launch(slk_ctx* ctx, const float* X, int64_t N, int D, const float* LZ, int L,
+                     const float* sigma_dev, double* M64, float* M, int max_iters, float tol,
+                     MsStatus* ms, void* ws);
+// M[l] = X[idx[l]] (float32) and M64 = the same in float64.
+slk_status ms_gather_launch(slk_ctx* ctx, const float* X, int D, const int32_t* idx, int L,
+                            float* M, double* M64);
+// M64 = (double) M.
+slk_status ms_widen_launch(slk_ctx* ctx, const float* M, int64_t n, double* M64);
+// Mhi = (float) M64, Mlo = (float) (M64 - Mhi).
+slk_status ms_split_launch(slk_ctx* ctx, const double* M64, int64_t n, float* Mhi, float* Mlo);
+// ms->moved = max_l ||M64[l] - M64_start[l]||_2.
+slk_status ms_moved_launch(slk_ctx* ctx, const double* M64, const double* M64_start, int D, int L,
+                           MsStatus* ms);
+
+// Energy -> st->energy (device); sigma from *sigma_dev.  M / Mlo as in
+// unary_launch.
 slk_status energy_launch(slk_ctx* ctx, const float* X, int D, const int32_t* labels,
                          const int64_t* row_ptr, const int32_t* col_idx, const float* w,
                          int64_t N, int L, const int32_t* modes, const float* sigma_dev,
-                         float lambda, DevState* st);
+                         float lambda, DevState* st, const float* M = nullptr,
+                         const float* Mlo = nullptr);
 
 // Set st->sigma from a host value (enqueued on the stream).
 slk_status set_sigma_launch(slk_ctx* ctx, float sigma, DevState* st);
@@ -163,6 +217,27 @@ __device__ __forceinline__ unsigned int float_to_ordered(float f) {
 }
 __device__ __forceinline__ float ordered_to_float(unsigned int u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+// Squared distance of two rows by the 32 lanes of a warp (lane-strided
+// features; every lane returns the total): float32 differences, squares
+// summed in float32 chunks of 8 per lane, chunks and lanes added in float64.
+// xl (nullable): low part of a float64 row split into xm + xl.
+__device__ __forceinline__ double warp_sq_dist(const float* __restrict__ xp,
+                                               const float* __restrict__ xm,
+                                               const float* __restrict__ xl, int D, int lane) {
+    double d2 = 0.0;
+    float part = 0.f;
+    int n = 0;
+    for (int j = lane; j < D; j += 32) {
+        float df = xp[j] - xm[j];
+        if (xl) df -= xl[j];
+        part = fmaf(df, df, part);
+        if (++n == 8) { d2 += (double)part; part = 0.f; n = 0; }
+    }
+    d2 += (double)part;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+    return d2;
 }
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;

@@ -1,7 +1,8 @@
 // Unary term, kNN-edge weights and the discrete energy.
 //
 // Unary, Eq. (general-second) with the Gaussian kernel of Section 4.2:
-//   a_{p,l} = exp(-||x_p - x_{m_l}||^2 / (2 sigma^2)),  z_p^0 = softmax(a_p) (Algorithm 1).
+//   a_{p,l} = exp(-||x_p - m_l||^2 / (2 sigma^2)),  z_p^0 = softmax(a_p) (Algorithm 1),
+// m_l = x_{modes[l]} (SLK-BO) or a row of the mode vectors M (SLK-MS).
 // Energy, Eq. (1) at one-hot z:
 //   E = -sum_p k(x_p, m_{l_p}) + (lambda/2) sum_p sum_{e in row p} w_e ||z_p - z_q||^2.
 #include <math.h>
@@ -17,20 +18,25 @@ constexpr int kUThreads = 256;
 // Block: 32 points x all L labels.  Thread t owns point t % 32 and labels
 // t / 32 + 8 j.  X and mode rows are staged 32 features at a time; each
 // chunk's squared differences are summed in float32, chunk sums in float64.
+// Vector modes (SLK-MS) come as M (float32) or as a float64 state split into
+// Mhi + Mlo (two floats): (x - m_hi) - m_lo keeps the difference accurate to
+// float32 relative to itself, not to |m|.
 template <int LPT>
 __global__ void __launch_bounds__(kUThreads)
 unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __restrict__ modes,
-             int L, const float* __restrict__ sigma_dev, float* __restrict__ A,
-             float* __restrict__ Z0) {
+             const float* __restrict__ M, const float* __restrict__ Mlo, int L,
+             const float* __restrict__ sigma_dev, float* __restrict__ A, float* __restrict__ Z0) {
     extern __shared__ float sm[];
-    float* xs = sm;                            // [kUTP][kUDC + 1]
-    float* ms = xs + kUTP * (kUDC + 1);        // [L][kUDC + 1]
-    float* at = ms + (size_t)L * (kUDC + 1);   // [kUTP][L]
+    float* xs = sm;                                  // [kUTP][kUDC + 1]
+    float* ms = xs + kUTP * (kUDC + 1);              // [L][kUDC + 1]
+    float* ml = ms + (size_t)L * (kUDC + 1);         // [L][kUDC + 1] (Mlo only)
+    float* at = ml + (Mlo ? (size_t)L * (kUDC + 1) : 0);   // [kUTP][L]
     __shared__ int mrow[SLK_MAX_L];
     const int t = threadIdx.x;
     const int pl = t % kUTP, lb = t / kUTP;
     const int64_t p0 = (int64_t)blockIdx.x * kUTP;
-    for (int l = t; l < L; l += kUThreads) mrow[l] = modes[l];
+    if (M == nullptr)
+        for (int l = t; l < L; l += kUThreads) mrow[l] = modes[l];
     double acc[LPT];
 #pragma unroll
     for (int j = 0; j < LPT; ++j) acc[j] = 0.0;
@@ -44,7 +50,12 @@ unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __res
         }
         for (int i = t; i < L * kUDC; i += kUThreads) {
             const int r = i / kUDC, c = i % kUDC;
-            ms[r * (kUDC + 1) + c] = (c < dc) ? X[(int64_t)mrow[r] * D + d0 + c] : 0.f;
+            if (M) {
+                ms[r * (kUDC + 1) + c] = (c < dc) ? M[(int64_t)r * D + d0 + c] : 0.f;
+                if (Mlo) ml[r * (kUDC + 1) + c] = (c < dc) ? Mlo[(int64_t)r * D + d0 + c] : 0.f;
+            } else {
+                ms[r * (kUDC + 1) + c] = (c < dc) ? X[(int64_t)mrow[r] * D + d0 + c] : 0.f;
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -52,9 +63,17 @@ unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __res
             const int l = lb + 8 * j;
             if (l < L) {
                 float part = 0.f;
-                for (int c = 0; c < dc; ++c) {
-                    const float df = xs[pl * (kUDC + 1) + c] - ms[l * (kUDC + 1) + c];
-                    part = fmaf(df, df, part);
+                if (Mlo) {
+                    for (int c = 0; c < dc; ++c) {
+                        const float df = (xs[pl * (kUDC + 1) + c] - ms[l * (kUDC + 1) + c]) -
+                                         ml[l * (kUDC + 1) + c];
+                        part = fmaf(df, df, part);
+                    }
+                } else {
+                    for (int c = 0; c < dc; ++c) {
+                        const float df = xs[pl * (kUDC + 1) + c] - ms[l * (kUDC + 1) + c];
+                        part = fmaf(df, df, part);
+                    }
                 }
                 acc[j] += (double)part;
             }
@@ -97,12 +116,14 @@ __global__ void weights_kernel(const float* __restrict__ dist2, int64_t nnz, int
 
 __global__ void set_sigma_kernel(float sigma, DevState* st) { st->sigma = sigma; }
 
-// One warp per point: float64 squared distance to its mode (lanes over
-// features), float64 kernel value, and the cut edges of its row.
+// One warp per point: squared distance to its mode (lanes over features,
+// float32 differences, squares summed in float32 chunks of 8 and the chunks
+// in float64), float64 kernel value, and the cut edges of its row.
 __global__ void __launch_bounds__(256)
 energy_kernel(const float* __restrict__ X, int D, const int32_t* __restrict__ labels,
               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
               const float* __restrict__ w, int64_t N, const int32_t* __restrict__ modes,
+              const float* __restrict__ M, const float* __restrict__ Mlo,
               const float* __restrict__ sigma_dev, float lambda, DevState* st) {
     __shared__ double red[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -113,14 +134,8 @@ energy_kernel(const float* __restrict__ X, int D, const int32_t* __restrict__ la
     for (int64_t p = (int64_t)blockIdx.x * 8 + warp; p < N; p += nwarps) {
         const int lp = labels[p];
         const float* xp = X + p * D;
-        const float* xm = X + (int64_t)modes[lp] * D;
-        double d2 = 0.0;
-        for (int j = lane; j < D; j += 32) {
-            const double df = (double)xp[j] - (double)xm[j];
-            d2 = fma(df, df, d2);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        const float* xm = M ? M + (int64_t)lp * D : X + (int64_t)modes[lp] * D;
+        const double d2 = warp_sq_dist(xp, xm, Mlo ? Mlo + (int64_t)lp * D : nullptr, D, lane);
         double cut = 0.0;
         for (int64_t e = row_ptr[p] + lane; e < row_ptr[p + 1]; e += 32) {
             const int q = col_idx[e];
@@ -143,11 +158,12 @@ energy_kernel(const float* __restrict__ X, int D, const int32_t* __restrict__ la
 }  // namespace
 
 slk_status unary_launch(slk_ctx* ctx, const float* X, int64_t N, int D, const int32_t* modes,
-                        int L, const float* sigma_dev, float* A, float* Z0) {
+                        int L, const float* sigma_dev, float* A, float* Z0, const float* M,
+                        const float* Mlo) {
     PhaseScope ps(ctx, SLK_PHASE_UNARY);
     SLK_COUNT_LAUNCH(ctx, 1);
-    const size_t smem = sizeof(float) * ((size_t)kUTP * (kUDC + 1) + (size_t)L * (kUDC + 1) +
-                                         (size_t)kUTP * L);
+    const size_t smem = sizeof(float) * ((size_t)kUTP * (kUDC + 1) +
+                                         (Mlo ? 2 : 1) * (size_t)L * (kUDC + 1) + (size_t)kUTP * L);
     const unsigned grid = (unsigned)((N + kUTP - 1) / kUTP);
     const int lpt = (L + 7) / 8;
 #define SLK_UNARY(LPT_)                                                                     \
@@ -155,14 +171,14 @@ slk_status unary_launch(slk_ctx* ctx, const float* X, int64_t N, int D, const in
         auto kern = unary_kernel<LPT_>;                                                     \
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                (int)smem));                                 \
-        kern<<<grid, kUThreads, smem, ctx->stream>>>(X, N, D, modes, L, sigma_dev, A, Z0);  \
+        kern<<<grid, kUThreads, smem, ctx->stream>>>(X, N, D, modes, M, Mlo, L, sigma_dev, A, Z0); \
     }
-    if (lpt <= 1) SLK_UNARY(1)
-    else if (lpt <= 2) SLK_UNARY(2)
-    else if (lpt <= 4) SLK_UNARY(4)
-    else if (lpt <= 8) SLK_UNARY(8)
-    else if (lpt <= 16) SLK_UNARY(16)
-    else SLK_UNARY(32)
+    if (lpt <= 1) { SLK_UNARY(1) }
+    else if (lpt <= 2) { SLK_UNARY(2) }
+    else if (lpt <= 4) { SLK_UNARY(4) }
+    else if (lpt <= 8) { SLK_UNARY(8) }
+    else if (lpt <= 16) { SLK_UNARY(16) }
+    else { SLK_UNARY(32) }
 #undef SLK_UNARY
     SLK_LAUNCH_CHECK(ctx, "unary_kernel");
     return SLK_OK;
@@ -190,7 +206,7 @@ slk_status set_sigma_launch(slk_ctx* ctx, float sigma, DevState* st) {
 slk_status energy_launch(slk_ctx* ctx, const float* X, int D, const int32_t* labels,
                          const int64_t* row_ptr, const int32_t* col_idx, const float* w,
                          int64_t N, int L, const int32_t* modes, const float* sigma_dev,
-                         float lambda, DevState* st) {
+                         float lambda, DevState* st, const float* M, const float* Mlo) {
     (void)L;
     PhaseScope ps(ctx, SLK_PHASE_ENERGY);
     SLK_COUNT_LAUNCH(ctx, 1);
@@ -198,7 +214,7 @@ slk_status energy_launch(slk_ctx* ctx, const float* X, int D, const int32_t* lab
     int64_t grid = (N + 7) / 8;
     if (grid > (int64_t)ctx->num_sms * 8) grid = (int64_t)ctx->num_sms * 8;
     energy_kernel<<<(unsigned)grid, 256, 0, ctx->stream>>>(X, D, labels, row_ptr, col_idx, w, N,
-                                                          modes, sigma_dev, lambda, st);
+                                                          modes, M, Mlo, sigma_dev, lambda, st);
     SLK_LAUNCH_CHECK(ctx, "energy_kernel");
     return SLK_OK;
 }

@@ -31,9 +31,10 @@ EXPORTS = ["slk_version", "slk_create", "slk_destroy", "slk_set_stream", "slk_la
            "slk_energy", "slk_default_params", "slk_solve", "slk_solve_host", "slk_profile",
            "slk_profile_read", "slk_bound_iterate_noalloc", "slk_solve_batched", "slk_server_create",
            "slk_server_destroy", "slk_server_submit", "slk_server_step", "slk_server_poll",
-           "slk_server_request_bytes"]
+           "slk_server_request_bytes", "slk_unary_vec", "slk_mean_shift", "slk_energy_vec",
+           "slk_solve_ms", "slk_initial_modes"]
 PHASES = ["knn_prep", "knn_cand", "knn_rerank", "knn_fallback", "sigma", "unary", "bound", "mode",
-          "energy"]
+          "energy", "mean_shift"]
 
 
 class SlkError(RuntimeError):
@@ -45,7 +46,9 @@ class SlkError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
                 ("tol_inner", ctypes.c_float), ("sigma_rule", ctypes.c_int32),
-                ("affinity", ctypes.c_int32), ("knn_precision", ctypes.c_int32)]
+                ("affinity", ctypes.c_int32), ("knn_precision", ctypes.c_int32),
+                ("refine_init", ctypes.c_int32),
+                ("max_ms", ctypes.c_int32), ("tol_ms", ctypes.c_float), ("tol_modes", ctypes.c_float)]
 
 
 class Instance(ctypes.Structure):
@@ -63,7 +66,8 @@ class ServerConfig(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int32), ("inner_iters_total", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("sigma", ctypes.c_float),
-                ("energy", ctypes.c_double), ("knn_fallback_rows", ctypes.c_int64)]
+                ("energy", ctypes.c_double), ("knn_fallback_rows", ctypes.c_int64),
+                ("ms_iters_total", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -111,6 +115,12 @@ def load(path: str = LIB_PATH):
         "slk_server_poll": (i32, [P, i64, ctypes.POINTER(i32), ctypes.POINTER(Stats)]),
         "slk_server_request_bytes": (i32, [P, ctypes.POINTER(Instance), ctypes.POINTER(i64)]),
         "slk_profile_read": (i32, [P, P, P, P]),
+        "slk_unary_vec": (i32, [P, P, i64, i32, P, i32, f32, P, P]),
+        "slk_mean_shift": (i32, [P, P, i32, P, P, P, P, P, i64, i32, f32, f32, P, i32, f32, P, P, P]),
+        "slk_energy_vec": (i32, [P, P, i32, P, P, P, P, i64, i32, P, f32, f32, P]),
+        "slk_solve_ms": (i32, [P, P, i64, i32, i32, i32, f32, f32, P, ctypes.POINTER(Params), P, P, P,
+                               ctypes.POINTER(Stats)]),
+        "slk_initial_modes": (i32, [P, P, i64, i32, P, i32, f32, P, P, P, ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -353,6 +363,97 @@ def solve_host(X, L: int, k: int, lam: float, init_modes, sigma=0.0, params: Par
                                       hp(init), ctypes.byref(p), hp(Z), hp(labels), hp(modes),
                                       ctypes.byref(st)), "slk_solve_host")
     return Z, labels, modes, st.as_dict()
+
+
+def initial_modes(X: torch.Tensor, seeds: torch.Tensor, sig: float, want_assign=True,
+                  ctx: Context | None = None, stats: dict | None = None):
+    """slk_initial_modes -> (modes int32 [L], assign int32 [N] or None, density list [L]).
+    stats (optional dict) receives the number of exactly recomputed sums."""
+    ctx = ctx or context(X.device.index)
+    N, D = X.shape
+    L = seeds.numel()
+    _need(X, torch.float32, (N, D), "X")
+    _need(seeds, torch.int32, (L,), "seeds")
+    modes = torch.empty(L, dtype=torch.int32, device=X.device)
+    assign = torch.empty(N, dtype=torch.int32, device=X.device) if want_assign else None
+    dens = (ctypes.c_double * L)()
+    ncand = ctypes.c_int64(0)
+    ctx.check(ctx._lib.slk_initial_modes(ctx.handle, _ptr(X), N, D, _ptr(seeds), L, float(sig),
+                                         _ptr(modes), _ptr(assign), dens, ctypes.byref(ncand)),
+              "slk_initial_modes")
+    if stats is not None:
+        stats["candidates"] = ncand.value
+    return modes, assign, list(dens)
+
+
+# ---------------------------------------------------------------- SLK-MS
+
+def unary_vec(X: torch.Tensor, M: torch.Tensor, sig: float, with_z0=True,
+              ctx: Context | None = None):
+    """slk_unary_vec: unary term with vector modes M [L, D] -> (A, Z0)."""
+    ctx = ctx or context(X.device.index)
+    N, D = X.shape
+    L = M.shape[0]
+    _need(X, torch.float32, (N, D), "X")
+    _need(M, torch.float32, (L, D), "M")
+    A = torch.empty(N, L, dtype=torch.float32, device=X.device)
+    Z0 = torch.empty_like(A) if with_z0 else None
+    ctx.check(ctx._lib.slk_unary_vec(ctx.handle, _ptr(X), N, D, _ptr(M), L, float(sig), _ptr(A),
+                                     _ptr(Z0)), "slk_unary_vec")
+    return A, Z0
+
+
+def mean_shift(X, A, Z_prev, row_ptr, col_idx, w, lam, sig, M, max_iters, tol=-1.0,
+               want_labels=True, ctx: Context | None = None):
+    """slk_mean_shift, in place on M [L, D]; returns (iters_done, last_shift, labels)."""
+    ctx = ctx or context(X.device.index)
+    N, D = X.shape
+    L = A.shape[1]
+    _need(X, torch.float32, (N, D), "X")
+    _need(A, torch.float32, (N, L), "A")
+    _need(M, torch.float32, (L, D), "M")
+    if Z_prev is not None:
+        _need(Z_prev, torch.float32, (N, L), "Z_prev")
+    labels = torch.empty(N, dtype=torch.int32, device=X.device) if want_labels else None
+    it = ctypes.c_int32(0)
+    sh = ctypes.c_float(0.0)
+    ctx.check(ctx._lib.slk_mean_shift(ctx.handle, _ptr(X), D, _ptr(A), _ptr(Z_prev), _ptr(row_ptr),
+                                      _ptr(col_idx), _ptr(w), N, L, float(lam), float(sig), _ptr(M),
+                                      int(max_iters), float(tol), _ptr(labels), ctypes.byref(it),
+                                      ctypes.byref(sh)), "slk_mean_shift")
+    return it.value, sh.value, labels
+
+
+def energy_vec(X, labels, row_ptr, col_idx, w, M, sig, lam, ctx: Context | None = None) -> float:
+    """slk_energy_vec: Eq. (1) with vector modes M [L, D]."""
+    ctx = ctx or context(X.device.index)
+    N, D = X.shape
+    E = ctypes.c_double(0.0)
+    ctx.check(ctx._lib.slk_energy_vec(ctx.handle, _ptr(X), D, _ptr(labels), _ptr(row_ptr),
+                                      _ptr(col_idx), _ptr(w), N, M.shape[0], _ptr(M), float(sig),
+                                      float(lam), ctypes.byref(E)), "slk_energy_vec")
+    return E.value
+
+
+def solve_ms(X: torch.Tensor, L: int, k: int, lam: float, init_modes: torch.Tensor, sigma=0.0,
+             params: Params | None = None, ctx: Context | None = None, out=None):
+    """Whole SLK-MS on device tensors -> (Z, labels, M [L, D], stats dict)."""
+    ctx = ctx or context(X.device.index)
+    N, D = X.shape
+    _need(X, torch.float32, (N, D), "X")
+    _need(init_modes, torch.int32, (L,), "init_modes")
+    if out is None:
+        Z = torch.empty(N, L, dtype=torch.float32, device=X.device)
+        labels = torch.empty(N, dtype=torch.int32, device=X.device)
+        M = torch.empty(L, D, dtype=torch.float32, device=X.device)
+    else:
+        Z, labels, M = out
+    st = Stats()
+    p = params or default_params()
+    ctx.check(ctx._lib.slk_solve_ms(ctx.handle, _ptr(X), N, D, L, k, float(lam), float(sigma),
+                                    _ptr(init_modes), ctypes.byref(p), _ptr(Z), _ptr(labels),
+                                    _ptr(M), ctypes.byref(st)), "slk_solve_ms")
+    return Z, labels, M, st.as_dict()
 
 
 def bound_iterate_noalloc(A, row_ptr, col_idx, w, lam, Z, max_iters, tol=-1.0):
