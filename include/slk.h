@@ -161,6 +161,9 @@ typedef struct {
     int32_t knn_precision;  /* SLK_KNN_* (default FP32) */
     int32_t refine_init;    /* slk_solve, slk_solve_host, slk_solve_ms: 1 = start from
                                slk_initial_modes(init_modes) instead of init_modes (default 0) */
+    int32_t reorder;        /* slk_solve, slk_solve_host: iterate on rows sorted by their nearest
+                               initial mode, for cache locality of the z-updates (results are
+                               identical): -1 = when Z exceeds 64 MB (default), 0 = never, 1 = always */
     /* SLK-MS only (slk_solve_ms): */
     int32_t max_ms;         /* mean-shift iterations per outer iteration (default 100) */
     float tol_ms;           /* stop them when max_l ||m_l move||_2 <= tol_ms * sigma (default 1e-5) */

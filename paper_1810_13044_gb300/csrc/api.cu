@@ -244,6 +244,7 @@ extern "C" void slk_default_params(slk_params* p) {
     p->affinity = SLK_AFFINITY_BINARY;
     p->knn_precision = SLK_KNN_FP32;
     p->refine_init = 0;
+    p->reorder = -1;
     p->max_ms = 100;
     p->tol_ms = 1e-5f;
     p->tol_modes = 1e-3f;
@@ -394,8 +395,25 @@ extern "C" slk_status slk_energy(slk_ctx* ctx, const float* X, int32_t D, const 
 
 namespace {
 
+constexpr int64_t kReorderBytes = 64ll << 20;   // Z above this: sorted row order
+
+bool use_reorder(const slk_params& p, int64_t N, int L) {
+    return p.reorder > 0 || (p.reorder < 0 && N * (int64_t)L * 4 > kReorderBytes);
+}
+
 struct SolveBufs {
     void* init_ws;   // starting-mode scratch (refine_init), else NULL
+    // sorted row order (reorder): permutation, problem copies, sort scratch
+    int32_t* perm;
+    int32_t* inv;
+    float* Xp;
+    float* Ap;
+    float* Zc;
+    int32_t* colp;
+    float* wp;
+    int32_t* labp;
+    int32_t* modp;
+    void* loc_ws;
     float* A;
     float* Zp;
     float* dist2;
@@ -414,6 +432,10 @@ size_t solve_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int L, int k, const 
     b += align_up(sizeof(float) * (size_t)L, 256);
     b += knn_ws_bytes(ctx, N, D, k, p.knn_precision) + 512;
     if (p.refine_init) b += init_modes_ws_bytes(ctx, N, D, L) + 512;
+    if (use_reorder(p, N, L))
+        b += 3 * align_up(sizeof(int32_t) * (size_t)N, 256) + align_up(sizeof(float) * (size_t)N * D, 256) +
+             2 * align_up(sizeof(float) * (size_t)N * L, 256) + 2 * align_up(sizeof(float) * (size_t)N * k, 256) +
+             align_up(sizeof(int32_t) * L, 256) + locality_ws_bytes(N, L) + 2048;
     return b;
 }
 
@@ -429,6 +451,18 @@ SolveBufs carve_solve(WsCarver& wc, const slk_ctx* ctx, int64_t N, int D, int L,
     b.mode_key = wc.take<float>((size_t)L);
     b.knn_ws = wc.take<unsigned char>(knn_ws_bytes(ctx, N, D, k, p.knn_precision));
     b.init_ws = p.refine_init ? wc.take<unsigned char>(init_modes_ws_bytes(ctx, N, D, L)) : nullptr;
+    if (use_reorder(p, N, L)) {
+        b.perm = wc.take<int32_t>(N);
+        b.inv = wc.take<int32_t>(N);
+        b.Xp = wc.take<float>((size_t)N * D);
+        b.Ap = wc.take<float>((size_t)N * L);
+        b.Zc = wc.take<float>((size_t)N * L);
+        b.colp = wc.take<int32_t>((size_t)N * k);
+        b.wp = wc.take<float>((size_t)N * k);
+        b.labp = wc.take<int32_t>(N);
+        b.modp = wc.take<int32_t>(L);
+        b.loc_ws = wc.take<unsigned char>(locality_ws_bytes(N, L));
+    }
     return b;
 }
 
@@ -475,19 +509,45 @@ slk_status solve_device(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int3
         SLK_CUDA_TRY(ctx, cudaMemcpyAsync(modes, init_modes, sizeof(int32_t) * L,
                                           cudaMemcpyDeviceToDevice, s));
     }
+    // The iteration may run on the rows sorted by their nearest initial mode
+    // (neighbours then sit close in memory and the z-update gathers hit L2).
+    // Every row keeps its edge order and mode ties go to the smaller original
+    // index, so the results are the same bits as in the given order.
+    const bool reorder = use_reorder(p, N, L);
+    const float* Xc = X;
+    float* Ac = b.A;
+    float* Zc = Z;
+    const int32_t* colc = b.col_idx;
+    int32_t* labc = labels;
+    int32_t* modc = modes;
     DevState hs;
     int outer = 0, inner_total = 0, converged = 0;
     for (outer = 0; outer < p.max_outer;) {
-        r = unary_launch(ctx, X, N, D, modes, L, &st->sigma, b.A, Z);
+        r = unary_launch(ctx, Xc, N, D, modc, L, &st->sigma, Ac, Zc);
         if (r != SLK_OK) return r;
-        r = bound_launch(ctx, b.A, b.row_ptr, b.col_idx, w, N, L, lambda, Z, b.Zp, p.max_inner,
+        if (reorder && outer == 0) {
+            r = locality_perm_launch(ctx, b.A, N, L, b.perm, b.inv, b.loc_ws);
+            if (r != SLK_OK) return r;
+            r = permute_problem_launch(ctx, b.perm, b.inv, N, D, L, k, X, b.A, Z, b.col_idx, w, b.Xp,
+                                       b.Ap, b.Zc, b.colp, b.wp);
+            if (r != SLK_OK) return r;
+            r = map_modes_launch(ctx, b.inv, modes, L, b.modp);
+            if (r != SLK_OK) return r;
+            Xc = b.Xp;
+            Ac = b.Ap;
+            Zc = b.Zc;
+            colc = b.colp;
+            if (w) w = b.wp;
+            labc = b.labp;
+            modc = b.modp;
+        }
+        r = bound_launch(ctx, Ac, b.row_ptr, colc, w, N, L, lambda, Zc, b.Zp, p.max_inner,
                          p.tol_inner, st, k);
         if (r != SLK_OK) return r;
-        r = mode_launch(ctx, b.A, b.Zp, b.row_ptr, b.col_idx, w, N, L, lambda, modes, labels,
-                        b.mode_key, true, st);
+        r = mode_launch(ctx, Ac, b.Zp, b.row_ptr, colc, w, N, L, lambda, modc, labc, b.mode_key,
+                        true, st, reorder ? b.perm : nullptr, reorder ? b.inv : nullptr);
         if (r != SLK_OK) return r;
-        r = energy_launch(ctx, X, D, labels, b.row_ptr, b.col_idx, w, N, L, modes, &st->sigma,
-                          lambda, st);
+        r = energy_launch(ctx, Xc, D, labc, b.row_ptr, colc, w, N, L, modc, &st->sigma, lambda, st);
         if (r != SLK_OK) return r;
         r = read_state(ctx, &hs);
         if (r != SLK_OK) return r;
@@ -498,6 +558,12 @@ slk_status solve_device(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int3
         ++outer;
         inner_total += hs.iters_done;
         if (!hs.changed) { converged = 1; break; }
+    }
+    if (reorder && outer > 0) {
+        r = unpermute_launch(ctx, b.perm, N, L, Zc, labc, modc, Z, labels, modes);
+        if (r != SLK_OK) return r;
+        r = sync_and_check(ctx);
+        if (r != SLK_OK) return r;
     }
     if (stats) {
         stats->outer_iters = outer;

@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kThreads)
 mode_rows_kernel(const float* __restrict__ A, const float* __restrict__ Zp,
                  const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                  const float* __restrict__ w, int64_t N, int L, float lambda, int use_iters_flag,
-                 int32_t* __restrict__ labels, DevState* st) {
+                 int32_t* __restrict__ labels, const int32_t* __restrict__ orig, DevState* st) {
     constexpr int RPW = 32 / G;
     __shared__ unsigned long long best[SLK_MAX_L];
     for (int l = threadIdx.x; l < L; l += kThreads) best[l] = 0ull;
@@ -448,9 +448,11 @@ mode_rows_kernel(const float* __restrict__ A, const float* __restrict__ Zp,
             const int l = gl + G * j;
             if (l < L) {
                 const float key = (s[j] - m) - lse1;
+                // ties go to the smaller original point index
+                const unsigned qo = orig ? (unsigned)orig[q] : (unsigned)q;
                 const unsigned long long packed =
                     ((unsigned long long)float_to_ordered(key) << 32) |
-                    (unsigned long long)(0xffffffffu - (unsigned)q);
+                    (unsigned long long)(0xffffffffu - qo);
                 atomicMax(&best[l], packed);
             }
         }
@@ -509,13 +511,15 @@ logz_rows_kernel(const float* __restrict__ A, const float* __restrict__ Zp,
     }
 }
 
-__global__ void mode_finish_kernel(int L, int32_t* modes, float* mode_key, DevState* st) {
+__global__ void mode_finish_kernel(int L, int32_t* modes, float* mode_key, const int32_t* inv,
+                                   DevState* st) {
     __shared__ int changed;
     if (threadIdx.x == 0) changed = 0;
     __syncthreads();
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
         const unsigned long long b = st->mode_best[l];
-        const int q = (int)(0xffffffffu - (unsigned)(b & 0xffffffffull));
+        const int qo = (int)(0xffffffffu - (unsigned)(b & 0xffffffffull));
+        const int q = inv ? inv[qo] : qo;   // back to the rows' (permuted) order
         if (q != modes[l]) changed = 1;  // benign race: every writer stores 1
         modes[l] = q;
         if (mode_key) mode_key[l] = ordered_to_float((unsigned)(b >> 32));
@@ -617,7 +621,8 @@ slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
 slk_status mode_launch(slk_ctx* ctx, const float* A, const float* Z_prev,
                        const int64_t* row_ptr, const int32_t* col_idx, const float* w,
                        int64_t N, int L, float lambda, int32_t* modes, int32_t* labels,
-                       float* mode_key, bool use_iters_flag, DevState* st) {
+                       float* mode_key, bool use_iters_flag, DevState* st, const int32_t* orig,
+                       const int32_t* inv) {
     PhaseScope ps(ctx, SLK_PHASE_MODE);
     SLK_COUNT_LAUNCH(ctx, 2);
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->mode_best[0], 0, sizeof(unsigned long long) * L,
@@ -628,11 +633,11 @@ slk_status mode_launch(slk_ctx* ctx, const float* A, const float* Z_prev,
     if (grid > (int64_t)ctx->num_sms * 8) grid = (int64_t)ctx->num_sms * 8;
 #define SLK_LAUNCH_MODE(G_, LPL_)                                                        \
     mode_rows_kernel<G_, LPL_><<<(unsigned)grid, kThreads, 0, ctx->stream>>>(            \
-        A, Z_prev, row_ptr, col_idx, w, N, L, lambda, use_iters_flag ? 1 : 0, labels, st);
+        A, Z_prev, row_ptr, col_idx, w, N, L, lambda, use_iters_flag ? 1 : 0, labels, orig, st);
     SLK_DISPATCH_L(L, SLK_LAUNCH_MODE);
 #undef SLK_LAUNCH_MODE
     SLK_LAUNCH_CHECK(ctx, "mode_rows_kernel");
-    mode_finish_kernel<<<1, 256, 0, ctx->stream>>>(L, modes, mode_key, st);
+    mode_finish_kernel<<<1, 256, 0, ctx->stream>>>(L, modes, mode_key, inv, st);
     SLK_LAUNCH_CHECK(ctx, "mode_finish_kernel");
     return SLK_OK;
 }

@@ -598,3 +598,153 @@ slk_status init_modes_launch(slk_ctx* ctx, const float* X, int64_t N, int D, con
                                           cudaMemcpyDeviceToDevice, s));
     return SLK_OK;
 }
+
+// ---------------------------------------------------------------- row order for locality
+
+namespace {
+
+__global__ void row_argmax_kernel(const float* __restrict__ A, int64_t N, int L,
+                                  int32_t* __restrict__ lab) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const float* a = A + p * L;
+        int best = 0;
+        float bv = a[0];
+        for (int l = 1; l < L; ++l)
+            if (a[l] > bv) { bv = a[l]; best = l; }
+        lab[p] = best;
+    }
+}
+
+__global__ void inverse_perm_kernel(const int32_t* __restrict__ perm, int64_t N,
+                                    int32_t* __restrict__ inv) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        inv[perm[i]] = (int32_t)i;
+}
+
+// dst row i = src row perm[i] (rows of W floats), one warp per row.
+__global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t* __restrict__ perm,
+                                   int64_t N, int W, float* __restrict__ dst) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += nw) {
+        const float* s = src + (int64_t)perm[i] * W;
+        float* d = dst + i * W;
+        for (int j = lane; j < W; j += 32) d[j] = s[j];
+    }
+}
+
+// dst row perm[i] = src row i.
+__global__ void scatter_rows_kernel(const float* __restrict__ src, const int32_t* __restrict__ perm,
+                                    int64_t N, int W, float* __restrict__ dst) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < N; i += nw) {
+        const float* s = src + i * W;
+        float* d = dst + (int64_t)perm[i] * W;
+        for (int j = lane; j < W; j += 32) d[j] = s[j];
+    }
+}
+
+// Uniform-degree CSR in the new row order: row i = old row perm[i], every
+// neighbour renamed by inv, edge order kept (so each row sums alike).
+__global__ void permute_graph_kernel(const int32_t* __restrict__ perm, const int32_t* __restrict__ inv,
+                                     int64_t N, int k, const int32_t* __restrict__ col,
+                                     const float* __restrict__ w, int32_t* __restrict__ colp,
+                                     float* __restrict__ wp) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * k;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / k, j = e % k;
+        const int64_t o = (int64_t)perm[i] * k + j;
+        colp[e] = inv[col[o]];
+        if (w) wp[e] = w[o];
+    }
+}
+
+__global__ void map_modes_kernel(const int32_t* __restrict__ inv, const int32_t* __restrict__ modes,
+                                 int L, int32_t* __restrict__ out) {
+    for (int l = threadIdx.x; l < L; l += blockDim.x) out[l] = inv[modes[l]];
+}
+
+__global__ void unpermute_small_kernel(const int32_t* __restrict__ perm, int64_t N, int L,
+                                       const int32_t* __restrict__ labels_p,
+                                       const int32_t* __restrict__ modes_p,
+                                       int32_t* __restrict__ labels, int32_t* __restrict__ modes) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        labels[perm[i]] = labels_p[i];
+        if (i < L) modes[i] = perm[modes_p[i]];
+    }
+}
+
+unsigned grid_for(const slk_ctx* ctx, int64_t work, int per_block) {
+    int64_t g = (work + per_block - 1) / per_block;
+    const int64_t cap = (int64_t)ctx->num_sms * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+}  // namespace
+
+size_t locality_ws_bytes(int64_t N, int L) {
+    const int nb = (int)((N + kSortChunk - 1) / kSortChunk);
+    return align_up(sizeof(int32_t) * N, 256) + align_up(sizeof(int32_t) * (size_t)nb * L, 256) +
+           align_up(sizeof(int64_t) * (size_t)nb * L, 256) + align_up(sizeof(int64_t) * (L + 1), 256) +
+           1024;
+}
+
+slk_status locality_perm_launch(slk_ctx* ctx, const float* A, int64_t N, int L, int32_t* perm,
+                                int32_t* inv, void* ws) {
+    cudaStream_t s = ctx->stream;
+    const int nb = (int)((N + kSortChunk - 1) / kSortChunk);
+    WsCarver wc(ws);
+    int32_t* lab = wc.take<int32_t>(N);
+    int32_t* counts = wc.take<int32_t>((size_t)nb * L);
+    int64_t* base = wc.take<int64_t>((size_t)nb * L);
+    int64_t* off = wc.take<int64_t>(L + 1);
+    SLK_COUNT_LAUNCH(ctx, 5);
+    row_argmax_kernel<<<grid_for(ctx, N, 256), 256, 0, s>>>(A, N, L, lab);
+    label_count_kernel<<<nb, 256, sizeof(int) * L, s>>>(lab, N, L, counts);
+    label_scan_kernel<<<1, 256, 0, s>>>(counts, nb, L, base, off);
+    label_scatter_kernel<<<nb, 256, sizeof(int) * 9 * L, s>>>(lab, N, L, base, perm);
+    inverse_perm_kernel<<<grid_for(ctx, N, 256), 256, 0, s>>>(perm, N, inv);
+    SLK_LAUNCH_CHECK(ctx, "locality order");
+    return SLK_OK;
+}
+
+slk_status permute_problem_launch(slk_ctx* ctx, const int32_t* perm, const int32_t* inv,
+                                  int64_t N, int D, int L, int k, const float* X, const float* A,
+                                  const float* Z0, const int32_t* col_idx, const float* w,
+                                  float* Xp, float* Ap, float* Z0p, int32_t* colp, float* wp) {
+    cudaStream_t s = ctx->stream;
+    const unsigned rg = grid_for(ctx, N, 8);
+    SLK_COUNT_LAUNCH(ctx, 4);
+    gather_rows_kernel<<<rg, 256, 0, s>>>(X, perm, N, D, Xp);
+    gather_rows_kernel<<<rg, 256, 0, s>>>(A, perm, N, L, Ap);
+    gather_rows_kernel<<<rg, 256, 0, s>>>(Z0, perm, N, L, Z0p);
+    permute_graph_kernel<<<grid_for(ctx, N * k, 256), 256, 0, s>>>(perm, inv, N, k, col_idx, w, colp, wp);
+    SLK_LAUNCH_CHECK(ctx, "permute problem");
+    return SLK_OK;
+}
+
+slk_status unpermute_launch(slk_ctx* ctx, const int32_t* perm, int64_t N, int L, const float* Zp,
+                            const int32_t* labels_p, const int32_t* modes_p, float* Z,
+                            int32_t* labels, int32_t* modes) {
+    cudaStream_t s = ctx->stream;
+    SLK_COUNT_LAUNCH(ctx, 2);
+    scatter_rows_kernel<<<grid_for(ctx, N, 8), 256, 0, s>>>(Zp, perm, N, L, Z);
+    unpermute_small_kernel<<<grid_for(ctx, N, 256), 256, 0, s>>>(perm, N, L, labels_p, modes_p,
+                                                                 labels, modes);
+    SLK_LAUNCH_CHECK(ctx, "unpermute");
+    return SLK_OK;
+}
+
+slk_status map_modes_launch(slk_ctx* ctx, const int32_t* inv, const int32_t* modes, int L,
+                            int32_t* out) {
+    SLK_COUNT_LAUNCH(ctx, 1);
+    map_modes_kernel<<<1, 256, 0, ctx->stream>>>(inv, modes, L, out);
+    SLK_LAUNCH_CHECK(ctx, "map_modes_kernel");
+    return SLK_OK;
+}

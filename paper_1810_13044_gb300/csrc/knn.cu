@@ -27,6 +27,7 @@
 #include "slk_internal.cuh"
 
 int knn_tc_tile_cols();
+int knn_tc_lists_per_split(int kc);
 
 namespace {
 
@@ -83,15 +84,16 @@ __global__ void __launch_bounds__(256)
 prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
                  int64_t Np, const double* __restrict__ colsum, int to_bf16,
                  float* __restrict__ xt32, __nv_bfloat16* __restrict__ xt16,
-                 float* __restrict__ norms, float* __restrict__ rho, DevState* st) {
-    __shared__ unsigned bmax_n, bmax_r;
-    if (threadIdx.x == 0) { bmax_n = 0u; bmax_r = 0u; }
+                 float* __restrict__ norms, float* __restrict__ rho,
+                 float* __restrict__ norms32, DevState* st) {
+    __shared__ unsigned bmax_n, bmax_r, bmax_n32;
+    if (threadIdx.x == 0) { bmax_n = 0u; bmax_r = 0u; bmax_n32 = 0u; }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     const double inv_n = 1.0 / (double)N;
     const double bound = 1.0 + (double)(Dp / 32 + 2) * 5.9604644775390625e-08;
-    unsigned my_n = 0u, my_r = 0u;
+    unsigned my_n = 0u, my_r = 0u, my_n32 = 0u;
     for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < Np;
          p += nw) {
         float n2 = 0.f, e2 = 0.f, v2 = 0.f;
@@ -125,22 +127,28 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
             const float nf = (float)dn;
             const double r = sqrt(de * bound) + 5.9604644775390625e-08 * sqrt(dv * bound);
             const float rf = __double2float_ru(r * (1.0 + 1e-12));
-            norms[p] = nf;
+            // padding rows get an infinite norm: no distance to them can pass a filter
+            norms[p] = (p < N) ? nf : __int_as_float(0x7f800000);
             rho[p] = rf;
+            const float n32 = (float)dv;   // ||v||^2 of the float32 operand v
+            if (norms32) norms32[p] = (p < N) ? n32 : __int_as_float(0x7f800000);
             if (p < N) {
                 my_n = max(my_n, __float_as_uint(nf));
                 my_r = max(my_r, __float_as_uint(rf));
+                my_n32 = max(my_n32, __float_as_uint(n32));
             }
         }
     }
     if (lane == 0) {
         atomicMax(&bmax_n, my_n);
         atomicMax(&bmax_r, my_r);
+        atomicMax(&bmax_n32, my_n32);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         atomicMax(&st->knn_max_norm_bits, bmax_n);
         atomicMax(&st->knn_max_rho_bits, bmax_r);
+        atomicMax(&st->knn_max_norm32_bits, bmax_n32);
     }
 }
 
@@ -313,6 +321,159 @@ knn_cand_fp32_kernel(const float* __restrict__ xt, const float* __restrict__ nor
     }
 }
 
+// Column means as the prep uses them: mu_j = (float)(colsum_j / N).
+__global__ void mu_kernel(const double* __restrict__ colsum, int64_t N, int D, float* __restrict__ mu) {
+    const double inv_n = 1.0 / (double)N;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D; j += gridDim.x * blockDim.x)
+        mu[j] = (float)(colsum[j] * inv_n);
+}
+
+// Float32 distance tiles for listed query rows (the rows the bfloat16
+// certificate left open): rows fb_list[f], f < *count, against every point.
+// Both operands are centred on the fly, v = fl(x - mu) -- the float32
+// operand the float32 path would hold -- and the norms are its norms.  Work
+// items (query row block, column split) are taken persistently, so the
+// grid does not depend on the count; lists go to ((split N + f) KC).
+template <int KC>
+__global__ void __launch_bounds__(KT, 2)
+knn_cand_query_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
+                      const float* __restrict__ mu, const float* __restrict__ norms32,
+                      const int32_t* __restrict__ fb_list, const long long* count_ptr, int splits,
+                      int n_tiles, float* __restrict__ cand_d, int32_t* __restrict__ cand_i) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CandSmem<KC>& s = *reinterpret_cast<CandSmem<KC>*>(smem_raw);
+    __shared__ int64_t prow[BM];
+    const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
+    const long long F = *(const volatile long long*)count_ptr;
+    const int64_t items = (F + BM - 1) / BM * splits;
+    const int nk = Dp / BK;
+    const int lr0 = t & 127, lq0 = t >> 7, lq1 = lq0 + 2;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t rb = item / splits;
+        const int sp = (int)(item % splits);
+        const int tile0 = (int)((int64_t)sp * n_tiles / splits);
+        const int tile1 = (int)((int64_t)(sp + 1) * n_tiles / splits);
+        __syncthreads();   // the previous item is done with the lists
+        if (t < BM) {
+            const int64_t f = rb * BM + t;
+            const int64_t p = (f < F) ? (int64_t)fb_list[f] : -1;
+            prow[t] = p;
+            for (int j = 0; j < KC; ++j) { s.list_d[t][j] = kInf; s.list_i[t][j] = kNoIdx; }
+            s.q_cnt[t] = 0;
+            s.thr[t] = kInf;
+            s.nrow[t] = (p >= 0) ? norms32[p] : kInf;
+        }
+        __syncthreads();
+        const int64_t pa_row = prow[lr0];
+        for (int tile = tile0; tile < tile1; ++tile) {
+            const int64_t col0 = (int64_t)tile * BN;
+            __syncthreads();  // previous epilogue finished with ncol / buffers
+            if (t < BN) s.ncol[t] = (col0 + t < N) ? norms32[col0 + t] : kInf;
+            const int64_t qb_row = (col0 + lr0 < N) ? col0 + lr0 : -1;
+            float acc[8][8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+            float ra[8], rbv[8];
+            auto fetch = [&](int k0) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int d = k0 + 4 * (c < 4 ? lq0 : lq1) + (c & 3);
+                    const float m = (d < D) ? mu[d] : 0.f;
+                    ra[c] = (pa_row >= 0 && d < D) ? X[pa_row * D + d] - m : 0.f;
+                    rbv[c] = (qb_row >= 0 && d < D) ? X[qb_row * D + d] - m : 0.f;
+                }
+            };
+            auto stash = [&](int buf) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int kk = 4 * (c < 4 ? lq0 : lq1) + (c & 3);
+                    s.As[buf][kk][lr0] = ra[c];
+                    s.Bs[buf][kk][lr0] = rbv[c];
+                }
+            };
+            fetch(0);
+            stash(0);
+            __syncthreads();
+            for (int kt = 0; kt < nk; ++kt) {
+                const int buf = kt & 1;
+                if (kt + 1 < nk) fetch((kt + 1) * BK);
+#pragma unroll
+                for (int kk = 0; kk < BK; ++kk) {
+                    const float4 a0 = *reinterpret_cast<const float4*>(&s.As[buf][kk][4 * ty]);
+                    const float4 a1 = *reinterpret_cast<const float4*>(&s.As[buf][kk][64 + 4 * ty]);
+                    const float4 b0 = *reinterpret_cast<const float4*>(&s.Bs[buf][kk][4 * tx]);
+                    const float4 b1 = *reinterpret_cast<const float4*>(&s.Bs[buf][kk][64 + 4 * tx]);
+                    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                }
+                if (kt + 1 < nk) stash(buf ^ 1);
+                __syncthreads();
+            }
+            // ---- epilogue: dt = n_p + n_q - 2 dot, filter against the row thresholds
+            unsigned long long pend = 0ull;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = (i < 4) ? 4 * ty + i : 64 + 4 * ty + (i - 4);
+                const int64_t p = prow[r];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int c = (j < 4) ? 4 * tx + j : 64 + 4 * tx + (j - 4);
+                    const int64_t q = col0 + c;
+                    const float d = fmaf(-2.f, acc[i][j], s.nrow[r] + s.ncol[c]);
+                    acc[i][j] = d;
+                    if (p >= 0 && q < N && q != p && d <= s.thr[r]) pend |= 1ull << (i * 8 + j);
+                }
+            }
+            while (__syncthreads_or(pend != 0ull)) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int r = (i < 4) ? 4 * ty + i : 64 + 4 * ty + (i - 4);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (pend & (1ull << (i * 8 + j))) {
+                            const int slot = atomicAdd(&s.q_cnt[r], 1);
+                            if (slot < QC) {
+                                const int c = (j < 4) ? 4 * tx + j : 64 + 4 * tx + (j - 4);
+                                s.q_d[r][slot] = acc[i][j];
+                                s.q_i[r][slot] = (int)(col0 + c);
+                                pend &= ~(1ull << (i * 8 + j));
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                if (t < BM) merge_queue<KC>(s, t);
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int r = (i < 4) ? 4 * ty + i : 64 + 4 * ty + (i - 4);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if ((pend & (1ull << (i * 8 + j))) && !(acc[i][j] <= s.thr[r]))
+                            pend &= ~(1ull << (i * 8 + j));
+                }
+            }
+        }
+        __syncthreads();
+        if (t < BM) {
+            const int64_t f = rb * BM + t;
+            if (f < F) {
+                const int64_t o = ((int64_t)sp * N + f) * KC;
+                for (int j = 0; j < KC; ++j) {
+                    cand_d[o + j] = s.list_d[t][j];
+                    cand_i[o + j] = s.list_i[t][j] == kNoIdx ? -1 : s.list_i[t][j];
+                }
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------ rerank + certificate
 
 // Exact float32 squared distance, lane-strided over features, xor-butterfly
@@ -330,25 +491,37 @@ __device__ __forceinline__ float exact_d2(const float* __restrict__ xp,
     return part;
 }
 
-template <int KC>
+// Rerank + certificate, one warp per row.  Q = false: every row p < N, the
+// lists of the candidate kernels at ((split Np + p) KC), failures appended to
+// fb_list.  Q = true: the rows fb_in[f], f < *count_in, left open by the
+// bfloat16 stage, their float32 query lists at ((split N + f) KC), norms of
+// the float32 operand (rho <= u ||v||), failures appended to fb_list /
+// *count_out.
+template <int KC, bool Q>
 __global__ void __launch_bounds__(256)
 knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, int splits,
                   int64_t Np, const float* __restrict__ cand_d, const int32_t* __restrict__ cand_i,
                   const float* __restrict__ norms, const float* __restrict__ rho, float u_acc,
                   int64_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx,
-                  float* __restrict__ dist2, int32_t* __restrict__ fb_list, DevState* st) {
+                  float* __restrict__ dist2, int32_t* __restrict__ fb_list, DevState* st,
+                  const int32_t* __restrict__ fb_in = nullptr, const long long* count_in = nullptr,
+                  long long* count_out = nullptr) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const double nmax = (double)__uint_as_float(st->knn_max_norm_bits);
-    const double rmax = (double)__uint_as_float(st->knn_max_rho_bits);
     const double u = 5.9604644775390625e-08;  // 2^-24
+    const double nmax = (double)__uint_as_float(Q ? st->knn_max_norm32_bits : st->knn_max_norm_bits);
+    const double rmax = Q ? u * sqrt(nmax) * (1.0 + 1e-6)
+                          : (double)__uint_as_float(st->knn_max_rho_bits);
     const double g = (double)Dp * (double)u_acc;
     const double gam = g / (1.0 - g);
     const double err_exact = 1.01 * (double)(D + 8) * u;
-    if (blockIdx.x == 0 && threadIdx.x == 0) row_ptr[N] = N * (int64_t)k;
-    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < N;
-         p += nw) {
-        if (lane == 0) row_ptr[p] = p * (int64_t)k;
+    const int64_t rows = Q ? (int64_t)(*(const volatile long long*)count_in) : N;
+    const int64_t stride = Q ? N : Np;
+    if (!Q && blockIdx.x == 0 && threadIdx.x == 0) row_ptr[N] = N * (int64_t)k;
+    for (int64_t f = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < rows;
+         f += nw) {
+        const int64_t p = Q ? (int64_t)fb_in[f] : f;
+        if (!Q && lane == 0) row_ptr[p] = p * (int64_t)k;
         float ed[MAXE];
         int ei[MAXE];
         const int total = splits * KC;
@@ -358,7 +531,7 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
             ed[m] = kInf;
             ei[m] = kNoIdx;
             if (e < total) {
-                const int64_t o = ((int64_t)(e / KC) * Np + p) * KC + (e % KC);
+                const int64_t o = ((int64_t)(e / KC) * stride + f) * KC + (e % KC);
                 const int i = cand_i[o];
                 if (i >= 0 && i != (int)p) { ed[m] = cand_d[o]; ei[m] = i; }
             }
@@ -401,7 +574,7 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
         {
             float ts = kInf;
             if (lane < splits) {
-                const int64_t o = ((int64_t)lane * Np + p) * KC + (KC - 1);
+                const int64_t o = ((int64_t)lane * stride + f) * KC + (KC - 1);
                 if (cand_i[o] >= 0) ts = cand_d[o];
             }
 #pragma unroll
@@ -453,19 +626,22 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
         }
         if (lane == 0 && T < kInf) {
             bool ok = false;
-            const double sn = sqrt((double)norms[p]) + sqrt(nmax);
+            const double np_ = (double)norms[p];
+            const double rp = Q ? u * sqrt(np_) * (1.0 + 1e-6) : (double)rho[p];
+            const double sn = sqrt(np_) + sqrt(nmax);
             // tile arithmetic (gam), the norms' float32 lane sums and roundings
             const double delta = (gam + (double)(Dp / 32 + 5) * u) * sn * sn;
             const double tt = (double)T - delta;
             if (tt > 0.0) {
-                const double root = sqrt(tt) - (double)rho[p] - rmax;
+                const double root = sqrt(tt) - rp - rmax;
                 if (root > 0.0) {
                     const double lb = root * root * (1.0 - 1e-12);
                     ok = (double)dk * (1.0 + 2.02 * err_exact) < lb;
                 }
             }
             if (!ok) {
-                const unsigned long long slot = atomicAdd((unsigned long long*)&st->fallback_count, 1ull);
+                long long* cnt = Q ? count_out : &st->fallback_count;
+                const unsigned long long slot = atomicAdd((unsigned long long*)cnt, 1ull);
                 fb_list[slot] = (int32_t)p;
             }
         }
@@ -478,12 +654,12 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
 // register top-k (lane i holds entry i), then warp 0 merges the 8 lists.
 __global__ void __launch_bounds__(256)
 knn_fallback_kernel(const float* __restrict__ X, int64_t N, int D, int k,
-                    const int32_t* __restrict__ fb_list, const DevState* __restrict__ st,
+                    const int32_t* __restrict__ fb_list, const long long* count_ptr,
                     int32_t* __restrict__ col_idx, float* __restrict__ dist2) {
     __shared__ float md[8][32];
     __shared__ int mi[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long count = *(const volatile long long*)&st->fallback_count;
+    const long long count = *(const volatile long long*)count_ptr;
     for (long long f = blockIdx.x; f < count; f += gridDim.x) {
         const int64_t p = fb_list[f];
         const float* xp = X + p * D;
@@ -549,13 +725,13 @@ knn_fallback_kernel(const float* __restrict__ X, int64_t N, int D, int k,
 template <int R, int DPL>
 __global__ void __launch_bounds__(256)
 knn_fallback_batch_kernel(const float* __restrict__ X, int64_t N, int D, int k,
-                          const int32_t* __restrict__ fb_list, const DevState* __restrict__ st,
+                          const int32_t* __restrict__ fb_list, const long long* count_ptr,
                           int col_splits, int64_t slot_stride, float* __restrict__ part_d,
                           int32_t* __restrict__ part_i) {
     __shared__ float md[8][R][32];
     __shared__ int mi[8][R][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long count = *(const volatile long long*)&st->fallback_count;
+    const long long count = *(const volatile long long*)count_ptr;
     const long long nbatch = (count + R - 1) / R;
     const int cs = blockIdx.y;
     const int64_t q0 = (int64_t)cs * N / col_splits, q1 = (int64_t)(cs + 1) * N / col_splits;
@@ -649,12 +825,12 @@ knn_fallback_batch_kernel(const float* __restrict__ X, int64_t N, int D, int k,
 
 // Merge the col_splits partial lists of every failed row into its k nearest.
 __global__ void __launch_bounds__(256)
-knn_fallback_merge_kernel(int k, const int32_t* __restrict__ fb_list, const DevState* __restrict__ st,
+knn_fallback_merge_kernel(int k, const int32_t* __restrict__ fb_list, const long long* count_ptr,
                           int col_splits, int64_t slot_stride, const float* __restrict__ part_d,
                           const int32_t* __restrict__ part_i, int32_t* __restrict__ col_idx,
                           float* __restrict__ dist2) {
     const int lane = threadIdx.x & 31;
-    const long long count = *(const volatile long long*)&st->fallback_count;
+    const long long count = *(const volatile long long*)count_ptr;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t f = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < count;
          f += nw) {
@@ -696,6 +872,7 @@ int choose_kc(int k) { return (k + 4 <= 16) ? 16 : 32; }
 struct KnnPlan {
     int64_t Np;
     int Dp, kc, splits, row_blocks, n_tiles;
+    int lists;   // candidate lists per row: splits x lists per split
     bool bf16;
 };
 
@@ -742,10 +919,13 @@ KnnPlan make_plan(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
         if (total >= 8 * cap) break;
     }
     pl.splits = best;
+    pl.lists = pl.splits;
     if (pl.bf16) {
+        const int per = knn_tc_lists_per_split(pl.kc);
         const int tiles_tc = (int)((pl.Np + knn_tc_tile_cols() - 1) / knn_tc_tile_cols());
         pl.splits = tc_splits(pl.row_blocks, tiles_tc, ctx->num_sms > 0 ? ctx->num_sms : 148,
-                              max_splits);
+                              max_splits / per);
+        pl.lists = pl.splits * per;
     }
     return pl;
 }
@@ -758,7 +938,9 @@ size_t knn_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int k, int precision) 
     b += align_up(sizeof(double) * D, 256);
     b += align_up((pl.bf16 ? 2 : 4) * (size_t)pl.Np * pl.Dp, 256);
     b += 2 * align_up(sizeof(float) * pl.Np, 256);
-    b += 2 * align_up(sizeof(float) * (size_t)pl.splits * pl.Np * pl.kc, 256);
+    b += 2 * align_up(sizeof(float) * (size_t)pl.lists * pl.Np * pl.kc, 256);
+    b += align_up(sizeof(float) * pl.Np, 256) + align_up(sizeof(float) * D, 256);   // norms32, mu
+    b += align_up(sizeof(int32_t) * N, 256);                                         // second list
     b += align_up(sizeof(int32_t) * (size_t)N, 256);
     return b + 4096;
 }
@@ -781,7 +963,7 @@ slk_status knn_prep_fp32_launch(slk_ctx* ctx, const float* X, int64_t N, int D, 
     int64_t pg = (Np + 7) / 8;
     if (pg > (int64_t)ctx->num_sms * 16) pg = (int64_t)ctx->num_sms * 16;
     prep_rows_kernel<<<(unsigned)pg, 256, 0, s>>>(X, N, D, Dp, Np, colsum, 0, xt, nullptr, norms,
-                                                   rho, st);
+                                                   rho, nullptr, st);
     SLK_LAUNCH_CHECK(ctx, "prep_rows_kernel");
     return SLK_OK;
 }
@@ -795,14 +977,19 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     void* xt = wc.take<unsigned char>((pl.bf16 ? 2 : 4) * (size_t)pl.Np * pl.Dp);
     float* norms = wc.take<float>(pl.Np);
     float* rho = wc.take<float>(pl.Np);
-    float* cand_d = wc.take<float>((size_t)pl.splits * pl.Np * pl.kc);
-    int32_t* cand_i = wc.take<int32_t>((size_t)pl.splits * pl.Np * pl.kc);
+    float* cand_d = wc.take<float>((size_t)pl.lists * pl.Np * pl.kc);
+    int32_t* cand_i = wc.take<int32_t>((size_t)pl.lists * pl.Np * pl.kc);
     int32_t* fb = wc.take<int32_t>(N);
+    float* norms32 = wc.take<float>(pl.Np);
+    float* mu = wc.take<float>(D);
+    int32_t* fb2 = wc.take<int32_t>(N);
     cudaStream_t s = ctx->stream;
 
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(colsum, 0, sizeof(double) * D, s));
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->fallback_count, 0, sizeof(long long), s));
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_bits, 0, 3 * sizeof(unsigned int), s));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm32_bits, 0, sizeof(unsigned int), s));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->fallback2_count, 0, sizeof(long long), s));
     {
         PhaseScope ps(ctx, SLK_PHASE_KNN_PREP);
         SLK_COUNT_LAUNCH(ctx, 2);
@@ -816,7 +1003,7 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
         if (pg > (int64_t)ctx->num_sms * 16) pg = (int64_t)ctx->num_sms * 16;
         prep_rows_kernel<<<(unsigned)pg, 256, 0, s>>>(
             X, N, D, pl.Dp, pl.Np, colsum, pl.bf16 ? 1 : 0, pl.bf16 ? nullptr : (float*)xt,
-            pl.bf16 ? (__nv_bfloat16*)xt : nullptr, norms, rho, st);
+            pl.bf16 ? (__nv_bfloat16*)xt : nullptr, norms, rho, pl.bf16 ? norms32 : nullptr, st);
         SLK_LAUNCH_CHECK(ctx, "prep_rows_kernel");
     }
     float u_acc;
@@ -851,9 +1038,10 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
         int64_t grid = (N + 7) / 8;
         if (grid > (int64_t)ctx->num_sms * 16) grid = (int64_t)ctx->num_sms * 16;
 #define SLK_RERANK(KC_)                                                                       \
-    knn_rerank_kernel<KC_><<<(unsigned)grid, 256, 0, s>>>(X, N, D, pl.Dp, k, pl.splits, pl.Np,  \
-                                                          cand_d, cand_i, norms, rho, u_acc,    \
-                                                          row_ptr, col_idx, dist2, fb, st)
+    knn_rerank_kernel<KC_, false><<<(unsigned)grid, 256, 0, s>>>(X, N, D, pl.Dp, k, pl.lists,   \
+                                                                 pl.Np, cand_d, cand_i, norms,  \
+                                                                 rho, u_acc, row_ptr, col_idx,  \
+                                                                 dist2, fb, st)
         if (pl.kc == 16) SLK_RERANK(16);
         else if (pl.kc == 32) SLK_RERANK(32);
         else SLK_RERANK(64);
@@ -862,9 +1050,48 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     }
     {
         PhaseScope ps(ctx, SLK_PHASE_KNN_FALLBACK);
+        // rows still open after this stage: the exact scan reads them from
+        // (list, count); with bfloat16 candidates a float32 stage comes first
+        const int32_t* exact_list = fb;
+        const long long* exact_count = &st->fallback_count;
+        if (pl.bf16) {
+            // float32 distance tiles of the open rows against every point, then
+            // the rerank under the float32 certificate; its failures go on
+            const int kcq = (k + 4 <= 16) ? 16 : 32;
+            int qsplits = (int)std::min<int64_t>(8, (int64_t)pl.lists * pl.kc / kcq);
+            if (qsplits < 1) qsplits = 1;
+            const int n_tiles = (int)((N + BN - 1) / BN);
+            SLK_COUNT_LAUNCH(ctx, 3);
+            mu_kernel<<<(D + 255) / 256, 256, 0, s>>>(colsum, N, D, mu);
+            const unsigned qgrid = (unsigned)(ctx->num_sms * 2);
+#define SLK_QCAND(KC_)                                                                        \
+    {                                                                                         \
+        auto kern = knn_cand_query_kernel<KC_>;                                               \
+        const int smem = (int)sizeof(CandSmem<KC_>);                                          \
+        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
+        kern<<<qgrid, KT, smem, s>>>(X, N, D, pl.Dp, mu, norms32, fb, &st->fallback_count,    \
+                                     qsplits, n_tiles, cand_d, cand_i);                       \
+    }
+            if (kcq == 16) SLK_QCAND(16) else SLK_QCAND(32)
+#undef SLK_QCAND
+            SLK_LAUNCH_CHECK(ctx, "knn_cand_query_kernel");
+            const unsigned rgrid = (unsigned)(ctx->num_sms * 16);
+            const float u32 = 5.9604644775390625e-08f;
+            if (kcq == 16)
+                knn_rerank_kernel<16, true><<<rgrid, 256, 0, s>>>(
+                    X, N, D, pl.Dp, k, qsplits, N, cand_d, cand_i, norms32, nullptr, u32, row_ptr,
+                    col_idx, dist2, fb2, st, fb, &st->fallback_count, &st->fallback2_count);
+            else
+                knn_rerank_kernel<32, true><<<rgrid, 256, 0, s>>>(
+                    X, N, D, pl.Dp, k, qsplits, N, cand_d, cand_i, norms32, nullptr, u32, row_ptr,
+                    col_idx, dist2, fb2, st, fb, &st->fallback_count, &st->fallback2_count);
+            SLK_LAUNCH_CHECK(ctx, "knn_rerank_kernel (float32 stage)");
+            exact_list = fb2;
+            exact_count = &st->fallback2_count;
+        }
         // partial lists of the batched rescan reuse the row's candidate
-        // scratch: splits * KC slots per row, of which col_splits * k are used
-        const int64_t slot_stride = (int64_t)pl.splits * pl.kc;
+        // scratch: lists * KC slots per row, of which col_splits * k are used
+        const int64_t slot_stride = (int64_t)pl.lists * pl.kc;
         int cs = (int)(slot_stride / k);
         if (cs > 8) cs = 8;
         const int dpl = (D + 31) / 32;
@@ -874,8 +1101,8 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
             // it may reuse cand_d / cand_i once the rerank is done with them
             dim3 grid((unsigned)((ctx->num_sms * 2 + cs - 1) / cs), (unsigned)cs);
 #define SLK_FB(R_, DPL_)                                                                     \
-    knn_fallback_batch_kernel<R_, DPL_><<<grid, 256, 0, s>>>(X, N, D, k, fb, st, cs, slot_stride, \
-                                                             cand_d, cand_i)
+    knn_fallback_batch_kernel<R_, DPL_><<<grid, 256, 0, s>>>(X, N, D, k, exact_list, exact_count, \
+                                                             cs, slot_stride, cand_d, cand_i)
             if (dpl <= 4) SLK_FB(16, 4);
             else if (dpl <= 8) SLK_FB(8, 8);
             else if (dpl <= 16) SLK_FB(4, 16);
@@ -883,12 +1110,12 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
 #undef SLK_FB
             SLK_LAUNCH_CHECK(ctx, "knn_fallback_batch_kernel");
             knn_fallback_merge_kernel<<<(unsigned)(ctx->num_sms * 2), 256, 0, s>>>(
-                k, fb, st, cs, slot_stride, cand_d, cand_i, col_idx, dist2);
+                k, exact_list, exact_count, cs, slot_stride, cand_d, cand_i, col_idx, dist2);
             SLK_LAUNCH_CHECK(ctx, "knn_fallback_merge_kernel");
         } else {
         SLK_COUNT_LAUNCH(ctx, 1);
-        knn_fallback_kernel<<<(unsigned)(ctx->num_sms * 2), 256, 0, s>>>(X, N, D, k, fb, st,
-                                                                         col_idx, dist2);
+        knn_fallback_kernel<<<(unsigned)(ctx->num_sms * 2), 256, 0, s>>>(X, N, D, k, exact_list,
+                                                                         exact_count, col_idx, dist2);
         SLK_LAUNCH_CHECK(ctx, "knn_fallback_kernel");
         }
     }

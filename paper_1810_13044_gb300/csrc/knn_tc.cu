@@ -6,20 +6,23 @@
 // (dt, q) of a column split -- the same contract as the float32 SIMT
 // candidate kernel; the exact float32 rerank and its certificate follow.
 //
-// One persistent CTA per SM, six warps:
+// One persistent CTA per SM:
 //   warp 0      TMA producer: 64-wide K slices of the A (128 rows) and B
 //               (256 rows) tiles, 128-byte swizzle, into a 3-stage ring;
 //   warp 1      TMEM owner (512 columns = two 128 x 256 fp32 accumulators)
 //               and MMA issuer (one thread, tcgen05.mma kind::f16, M=128,
 //               N=256, K=16 per instruction);
-//   warps 2..5  epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, so each
-//               thread owns one row and filters its 256 distances against the
-//               row's running threshold (the KC-th best so far).  Survivors
-//               are appended to a per-row buffer in shared memory; whenever a
-//               lane's buffer holds 16 or more, the whole warp merges in step:
-//               each lane sorts 32 buffered entries with a bitonic network in
-//               registers and bitonic-merges them into its register-resident
-//               sorted top-KC, with no divergence.
+//   EW epilogue warps (4 or 8): warp w reads TMEM lanes 32 (w % 4) .. +31,
+//               so each thread owns one row; with 8 warps two warps share a
+//               lane quarter and take 128 columns each (one candidate list
+//               per half, written as separate lists).  Each thread filters
+//               its distances against its running threshold (the KC-th best
+//               so far).  Survivors are appended to a per-row buffer in
+//               shared memory; whenever a lane's buffer holds 16 or more, the
+//               whole warp merges in step: each lane sorts 32 buffered
+//               entries with a bitonic network in registers and
+//               bitonic-merges them into its register-resident sorted
+//               top-KC, with no divergence.
 // The two accumulators let the epilogue of tile t overlap the MMAs of t+1.
 // Every mbarrier wait is bounded in time; on a timeout the CTA raises an
 // error bit, drains its own copies in flight, frees TMEM and returns.
@@ -32,26 +35,51 @@
 namespace {
 
 constexpr int TC_M = 128, TC_N = 256, TC_BK = 64;  // K slice: 64 bf16 = 128 bytes
-constexpr int TC_STAGES = 3;
-constexpr int TC_BUF = 48;   // a 32-value chunk lands on a buffer holding at most 15
-constexpr int TC_THREADS = 192;
+#ifndef SLK_TC_STAGES
+#define SLK_TC_STAGES 3
+#endif
+constexpr int TC_STAGES = SLK_TC_STAGES;
+// Epilogue warps of the KC = 32 kernel (4 or 8) and its pipelined TMEM loads
+// (the KC = 64 kernel keeps 4 warps and single loads: its lists fill the
+// registers).
+#ifndef SLK_TC_EW32
+#define SLK_TC_EW32 4
+#endif
+#ifndef SLK_TC_PIPE
+#define SLK_TC_PIPE 0
+#endif
+// Epilogue without block barriers per tile (column norms from global memory).
+#ifndef SLK_TC_NOBAR
+#define SLK_TC_NOBAR 0
+#endif
+
+// Survivors of one vote (VOTE columns) land on a buffer holding at most 15.
+// A 4-stage operand ring leaves room only for 16-column votes.
+template <int EW> struct TcEpi {
+    static constexpr int halves = EW / 4;             // column halves of a tile
+    static constexpr int vote = (EW == 8 || TC_STAGES > 3) ? 16 : 32;  // columns per vote
+    static constexpr int buf = 15 + vote;             // buffer slots per row and half
+    static constexpr int threads = 64 + 32 * EW;
+};
 constexpr uint32_t A_BYTES = TC_M * TC_BK * 2;  // 16 KiB
 constexpr uint32_t B_BYTES = TC_N * TC_BK * 2;  // 32 KiB
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 constexpr int kNoIdx = 0x7fffffff;
 
+template <int EW>
 struct TcSmem {
     uint8_t a[TC_STAGES][A_BYTES];   // 1024-byte aligned stages (swizzle atoms)
     uint8_t b[TC_STAGES][B_BYTES];
-    float buf_d[TC_BUF][TC_M];       // per-row append buffer, [slot][row]
-    int buf_i[TC_BUF][TC_M];
+    float buf_d[TcEpi<EW>::halves][TcEpi<EW>::buf][TC_M];   // per-row append buffer
+    int buf_i[TcEpi<EW>::halves][TcEpi<EW>::buf][TC_M];
     float ncol[2][TC_N];             // column norms of the tile in each accumulator
     unsigned long long full[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2];
     uint32_t tmem_base;
     int abort;
 };
-constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 1024;
+template <int EW>
+constexpr size_t tc_smem_bytes() { return sizeof(TcSmem<EW>) + 1024; }
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -131,8 +159,10 @@ __device__ __forceinline__ void umma_commit(unsigned long long* bar) {
             su32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// tcgen05.ld of 32 columns without the wait: the registers are valid only
+// after tmem_wait_regs on the same array, which names them as in/out
+// operands so that no use can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
         "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
@@ -145,20 +175,34 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
           "=r"(r[31])
         : "r"(taddr)
         : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_regs(uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.wait::ld.sync.aligned;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+          "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+          "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]),
+          "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]),
+          "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]),
+          "+r"(r[31])
+        :
+        : "memory");
 }
 
-// Barrier 1 over the 128 epilogue threads with an AND of `ok`: every
+// Barrier 1 over the NT epilogue threads with an AND of `ok`: every
 // epilogue warp gets the same answer, so they all leave their loops together.
+template <int NT>
 __device__ __forceinline__ bool epilogue_bar_and(bool ok) {
     uint32_t r;
     asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 128, p;\n"
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n"
         " selp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r) : "r"(ok ? 1u : 0u) : "memory");
+        : "=r"(r) : "r"(ok ? 1u : 0u), "n"(NT) : "memory");
     return r != 0;
+}
+template <int NT>
+__device__ __forceinline__ void epilogue_bar() {
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
 }
 
 // (ad, ai) <-> (bd, bi) so that the pair is ascending (up) or descending,
@@ -210,17 +254,17 @@ __device__ __forceinline__ void merge_topk(float (&ld)[KC], int (&li)[KC], const
 }
 
 // Warp-synchronous: fold every lane's buffered entries into its top-KC.
-template <int KC>
-__device__ __forceinline__ void flush_buffer(TcSmem& s, int r, int& cnt, float (&ld)[KC],
-                                             int (&li)[KC]) {
+template <int KC, int EW>
+__device__ __forceinline__ void flush_buffer(TcSmem<EW>& s, int h, int r, int& cnt,
+                                             float (&ld)[KC], int (&li)[KC]) {
     for (int base = 0; __any_sync(0xffffffffu, cnt > base); base += 32) {
         float bd[32];
         int bi[32];
 #pragma unroll
         for (int x = 0; x < 32; ++x) {
             const bool have = base + x < cnt;
-            bd[x] = have ? s.buf_d[base + x][r] : __int_as_float(0x7f800000);
-            bi[x] = have ? s.buf_i[base + x][r] : kNoIdx;
+            bd[x] = have ? s.buf_d[h][base + x][r] : __int_as_float(0x7f800000);
+            bi[x] = have ? s.buf_i[h][base + x][r] : kNoIdx;
         }
         bitonic_sort32(bd, bi);
         merge_topk<KC>(ld, li, bd, bi);
@@ -236,15 +280,17 @@ __device__ __forceinline__ void item_range(int item, int splits, int n_tiles, in
     t1 = (int)((int64_t)(sp + 1) * n_tiles / splits);
 }
 
-template <int TC_KC>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <int TC_KC, int EW, bool PIPE>
+__global__ void __launch_bounds__(TcEpi<EW>::threads, 1)
 knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const float* __restrict__ norms, int64_t N, int64_t Np, int Dp, int n_tiles,
                    int splits, int row_blocks, float* __restrict__ cand_d,
                    int32_t* __restrict__ cand_i, unsigned int* __restrict__ err_flag) {
+    constexpr int H = TcEpi<EW>::halves, VOTE = TcEpi<EW>::vote, NT = 32 * EW;
+    constexpr int CH_PER_HALF = TC_N / 32 / H;   // 32-column TMEM loads per thread and tile
     extern __shared__ uint8_t smem_raw[];
-    TcSmem& s = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                           ~(uintptr_t)1023);
+    TcSmem<EW>& s = *reinterpret_cast<TcSmem<EW>*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = Dp / TC_BK;
     const int n_items = row_blocks * splits;
@@ -261,7 +307,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&s.tfull[i], 1);
-            mbar_init(&s.tempty[i], 4);
+            mbar_init(&s.tempty[i], EW);
         }
         s.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -356,7 +402,8 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         // ------------------------------------------------------------ epilogue
         const int sub = warp & 3;
         const int r = sub * 32 + lane;
-        const int et = threadIdx.x - 64;  // 0..127 among the epilogue threads
+        const int et = threadIdx.x - 64;  // 0..NT-1 among the epilogue threads
+        const int h = et / 128;           // column half of this thread (EW == 8)
         uint32_t tcount = 0;
         bool ok = true;
         float ld[TC_KC];
@@ -379,7 +426,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 run_sp = sp;
             } else {
                 // this split continues the run: its own slot stays empty
-                const int64_t o = ((int64_t)sp * Np + p) * TC_KC;
+                const int64_t o = ((int64_t)(sp * H + h) * Np + p) * TC_KC;
 #pragma unroll
                 for (int x = 0; x < TC_KC; ++x) {
                     cand_d[o + x] = __int_as_float(0x7f800000);
@@ -391,43 +438,94 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             for (int t = t0; t < t1; ++t) {
                 const uint32_t acc = tcount & 1, use = tcount >> 1;
                 const int64_t col0 = (int64_t)t * TC_N;
-                for (int c = et; c < TC_N; c += 128)
+#if SLK_TC_NOBAR
+                // column norms straight from global memory (uniform addresses,
+                // L1 hits after the first warp; norms are padded to the tile),
+                // each warp waits for the accumulator on its own
+                const float* ncol_g = norms + col0;
+                ok = mbar_wait(&s.tfull[acc], use & 1, abort);
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+#else
+                for (int c = et; c < TC_N; c += NT)
                     s.ncol[acc][c] = (col0 + c < N) ? norms[col0 + c] : __int_as_float(0x7f800000);
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                ok = epilogue_bar_and(mbar_wait(&s.tfull[acc], use & 1, abort));
+                epilogue_bar<NT>();
+                ok = epilogue_bar_and<NT>(mbar_wait(&s.tfull[acc], use & 1, abort));
                 if (!ok) break;
+#endif
                 tc_fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(sub * 32) << 16) + acc * TC_N;
-#pragma unroll 1
-                for (int ch = 0; ch < TC_N / 32; ++ch) {
+                // distances of one 32-column chunk, filtered in votes of VOTE
+                // columns against the row's threshold (the row's own column,
+                // distance ~0, is kept here and dropped by the rerank)
+                auto process = [&](const uint32_t (&rv)[32], int ch) {
                     float v[32];
-                    tmem_ld32(tbase + ch * 32, v);
-                    if (ch == TC_N / 32 - 1) {
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&s.tempty[acc]);
-                    }
-                    // hot path: distances and their minimum; the row's own column
-                    // (distance ~0) is kept here and dropped by the rerank
-                    const float thr_d = ld[TC_KC - 1];
-                    float mn = __int_as_float(0x7f800000);
+#if SLK_TC_NOBAR
+                    const float4* n4 = reinterpret_cast<const float4*>(ncol_g + ch * 32);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        v[j] = fmaf(-2.f, v[j], np_ + s.ncol[acc][ch * 32 + j]);
-                        mn = fminf(mn, v[j]);
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 c4 = __ldg(n4 + q);
+                        v[4 * q + 0] = fmaf(-2.f, __uint_as_float(rv[4 * q + 0]), np_ + c4.x);
+                        v[4 * q + 1] = fmaf(-2.f, __uint_as_float(rv[4 * q + 1]), np_ + c4.y);
+                        v[4 * q + 2] = fmaf(-2.f, __uint_as_float(rv[4 * q + 2]), np_ + c4.z);
+                        v[4 * q + 3] = fmaf(-2.f, __uint_as_float(rv[4 * q + 3]), np_ + c4.w);
                     }
-                    // rare path: some row of the warp has a distance below its threshold
-                    if (__any_sync(0xffffffffu, mn < thr_d)) {
+#else
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            if (v[j] < thr_d) {
-                                s.buf_d[cnt][r] = v[j];
-                                s.buf_i[cnt][r] = (int)(col0 + ch * 32 + j);
-                                ++cnt;
+                    for (int j = 0; j < 32; ++j)
+                        v[j] = fmaf(-2.f, __uint_as_float(rv[j]), np_ + s.ncol[acc][ch * 32 + j]);
+#endif
+#pragma unroll
+                    for (int g0 = 0; g0 < 32; g0 += VOTE) {
+                        const float thr_d = ld[TC_KC - 1];
+                        float mn = __int_as_float(0x7f800000);
+#pragma unroll
+                        for (int j = 0; j < VOTE; ++j) mn = fminf(mn, v[g0 + j]);
+                        // rare path: some row of the warp has a distance below its threshold
+                        if (__any_sync(0xffffffffu, mn < thr_d)) {
+#pragma unroll
+                            for (int j = 0; j < VOTE; ++j) {
+                                if (v[g0 + j] < thr_d) {
+                                    s.buf_d[h][cnt][r] = v[g0 + j];
+                                    s.buf_i[h][cnt][r] = (int)(col0 + ch * 32 + g0 + j);
+                                    ++cnt;
+                                }
                             }
+                            if (__any_sync(0xffffffffu, cnt >= 16))
+                                flush_buffer<TC_KC, EW>(s, h, r, cnt, ld, li);
                         }
-                        if (__any_sync(0xffffffffu, cnt >= 16)) flush_buffer<TC_KC>(s, r, cnt, ld, li);
                     }
+                };
+                auto release = [&]() {   // this warp's last TMEM read of the tile is done
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&s.tempty[acc]);
+                };
+                const int ch0 = h * CH_PER_HALF;
+                if constexpr (PIPE) {
+                // two register sets: the load of chunk c + 1 is in flight while
+                // chunk c is filtered
+                uint32_t ra[32], rb2[32];
+                tmem_ld32_issue(tbase + ch0 * 32, ra);
+                tmem_wait_regs(ra);
+#pragma unroll 1
+                for (int cc = 0; cc < CH_PER_HALF; cc += 2) {
+                    tmem_ld32_issue(tbase + (ch0 + cc + 1) * 32, rb2);
+                    process(ra, ch0 + cc);
+                    tmem_wait_regs(rb2);
+                    if (cc + 2 < CH_PER_HALF) tmem_ld32_issue(tbase + (ch0 + cc + 2) * 32, ra);
+                    else release();
+                    process(rb2, ch0 + cc + 1);
+                    if (cc + 2 < CH_PER_HALF) tmem_wait_regs(ra);
+                }
+                } else {
+#pragma unroll 1
+                for (int cc = 0; cc < CH_PER_HALF; ++cc) {
+                    uint32_t rv[32];
+                    tmem_ld32_issue(tbase + (ch0 + cc) * 32, rv);
+                    tmem_wait_regs(rv);
+                    if (cc == CH_PER_HALF - 1) release();
+                    process(rv, ch0 + cc);
+                }
                 }
                 ++tcount;
             }
@@ -439,8 +537,8 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 item_range(item + 1, splits, n_tiles, next_rb, t0n, t1n, spn);
             }
             if (next_rb != rb) {
-                flush_buffer<TC_KC>(s, r, cnt, ld, li);
-                const int64_t o = ((int64_t)run_sp * Np + p) * TC_KC;
+                flush_buffer<TC_KC, EW>(s, h, r, cnt, ld, li);
+                const int64_t o = ((int64_t)(run_sp * H + h) * Np + p) * TC_KC;
 #pragma unroll
                 for (int x = 0; x < TC_KC; ++x) {
                     cand_d[o + x] = ld[x];
@@ -485,6 +583,13 @@ EncodeTiledFn encode_fn() {
 
 int knn_tc_tile_cols() { return TC_N; }
 
+// Candidate lists one split of the tensor-core kernel writes per row: two
+// column halves with 8 epilogue warps (KC = 32), one with 4 (KC = 64, whose
+// lists need the registers of a 6-warp CTA).
+int knn_tc_lists_per_split(int kc) {
+    return kc == 32 ? TcEpi<SLK_TC_EW32>::halves : TcEpi<4>::halves;
+}
+
 slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const float* norms,
                                 int64_t N, int Dp, int64_t Np, int kc, int splits, float* cand_d,
                                 int32_t* cand_i, unsigned int* err_flag) {
@@ -514,11 +619,22 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
     const int n_items = row_blocks * splits;
     int grid = ctx->num_sms;
     if (grid > n_items) grid = n_items;
-    auto kern = (kc == 32) ? knn_cand_tc_kernel<32> : knn_cand_tc_kernel<64>;
-    SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)kTcSmemBytes));
-    kern<<<grid, TC_THREADS, kTcSmemBytes, ctx->stream>>>(
-        ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
+    if (kc == 32) {
+        constexpr int EW = SLK_TC_EW32;
+        auto kern = knn_cand_tc_kernel<32, EW, SLK_TC_PIPE != 0>;
+        const size_t smem = tc_smem_bytes<EW>();
+        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        kern<<<grid, TcEpi<EW>::threads, smem, ctx->stream>>>(
+            ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
+    } else {
+        auto kern = knn_cand_tc_kernel<64, 4, false>;
+        const size_t smem = tc_smem_bytes<4>();
+        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        kern<<<grid, TcEpi<4>::threads, smem, ctx->stream>>>(
+            ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
+    }
     SLK_LAUNCH_CHECK(ctx, "knn_cand_tc_kernel");
     return SLK_OK;
 }

@@ -36,7 +36,7 @@
 
 namespace {
 
-constexpr int kMsThreads = 512;
+constexpr int kMsThreads = 256;
 constexpr int kMsWarps = kMsThreads / 32;
 #define kNegInf __int_as_float(0xff800000)
 
@@ -63,7 +63,7 @@ struct MsArgs {
 
 template <int R, int LG>
 struct MsSmem {
-    float red[kMsWarps / (R / 4)][R][LG];  // per feature part: distances of the tile
+    float red[kMsWarps / (R / 4)][LG][R];  // per feature part: distances of the tile (label-major)
     float w[R][LG];
     float alpha[LG];
     float mu[LG];        // running maximum of s per label
@@ -189,19 +189,19 @@ __device__ bool ms_unit(const MsArgs& a, int u, const float* Mc, float* xs0, flo
             const int base = (((lane >> 4) & 1) << 5) | (((lane >> 3) & 1) << 4) |
                              (((lane >> 2) & 1) << 3) | (((lane >> 1) & 1) << 2) | ((lane & 1) << 1);
             const int i = base >> 4, l = base & 15;
-            if (l < LG) sh.red[h][4 * q + i][l] = v[0];
-            if (l + 1 < LG) sh.red[h][4 * q + i][l + 1] = v[1];
+            if (l < LG) sh.red[h][l][4 * q + i] = v[0];
+            if (l + 1 < LG) sh.red[h][l + 1][4 * q + i] = v[1];
         }
         __syncthreads();
-        // ---- B: one warp per label, lanes over the rows: s, tile maximum,
-        // rescale factor of the running sums, weights relative to the new maximum
-        if (warp < LG) {
-            const int l = warp;
+        // ---- B: a warp per label (labels warp, warp + 8, ...), lanes over the
+        // rows: s, tile maximum, rescale factor of the running sums, weights
+        // relative to the new maximum
+        for (int l = warp; l < LG; l += kMsWarps) {
             float sv = kNegInf;
             if (lane < R && lane < nrows && l < lg) {
                 float d2 = 0.f;
 #pragma unroll
-                for (int hh = 0; hh < HP; ++hh) d2 += sh.red[hh][lane][l];
+                for (int hh = 0; hh < HP; ++hh) d2 += sh.red[hh][l][lane];
                 sv = __ldg(a.LZ + (row0 + lane) * a.L + l0 + l) - d2 * inv2s2;
             }
             float tm = sv;
@@ -520,12 +520,12 @@ struct MsShape {
 };
 MsShape ms_shape(int D, int L) {
     if (D <= 1024) {
-        const int cpt = D <= 512 ? 1 : 2;
+        const int cpt = D <= 256 ? 1 : D <= 512 ? 2 : 4;
         const int lg = L <= 4 ? 4 : L <= 8 ? 8 : L <= 12 ? 12 : 16;
         return {16, lg, cpt};
     }
-    if (D <= 2048) return {8, L <= 4 ? 4 : 8, 4};
-    return {4, 4, 8};
+    if (D <= 2048) return {8, L <= 4 ? 4 : 8, 8};
+    return {4, 4, 16};
 }
 
 template <int R, int LG, int CPT>
@@ -608,8 +608,9 @@ slk_status ms_launch(slk_ctx* ctx, const float* X, int64_t N, int D, const float
     if (s.R == R_ && s.LG == LG_ && s.CPT == CPT_) return ms_run<R_, LG_, CPT_>(ctx, a);
     SLK_MS(16, 4, 1) SLK_MS(16, 8, 1) SLK_MS(16, 12, 1) SLK_MS(16, 16, 1)
     SLK_MS(16, 4, 2) SLK_MS(16, 8, 2) SLK_MS(16, 12, 2) SLK_MS(16, 16, 2)
-    SLK_MS(8, 4, 4) SLK_MS(8, 8, 4)
-    SLK_MS(4, 4, 8)
+    SLK_MS(16, 4, 4) SLK_MS(16, 8, 4) SLK_MS(16, 12, 4) SLK_MS(16, 16, 4)
+    SLK_MS(8, 4, 8) SLK_MS(8, 8, 8)
+    SLK_MS(4, 4, 16)
 #undef SLK_MS
     return set_err(ctx, SLK_ERR_INVALID_ARG, "mean-shift modes: no launch shape");
 }

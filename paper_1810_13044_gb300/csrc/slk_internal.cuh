@@ -75,6 +75,8 @@ struct DevState {
     unsigned int knn_max_norm_bits;   // float bits of max candidate-operand norm^2
     unsigned int knn_max_rho_bits;    // float bits of max rounding perturbation norm
     unsigned int knn_error;           // bit 1: a tensor-core pipeline wait timed out
+    unsigned int knn_max_norm32_bits; // float bits of max float32-operand norm^2
+    long long fallback2_count;        // rows left for the exact scan after the float32 stage
 };
 
 enum : unsigned int { ERR_BARRIER_TIMEOUT = 1u };
@@ -159,10 +161,33 @@ slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
 
 // Mode update (keys from A + lambda K Z_prev; Z_prev NULL or st->iters_done == 0
 // when use_iters_flag: s = A).  Writes modes in place, labels, keys, st->changed.
+// With orig (row -> original point index) mode ties go to the smaller
+// original index, and inv (original -> row) maps the chosen points back to
+// row indices: the result does not depend on the order of the rows.
 slk_status mode_launch(slk_ctx* ctx, const float* A, const float* Z_prev,
                        const int64_t* row_ptr, const int32_t* col_idx, const float* w,
                        int64_t N, int L, float lambda, int32_t* modes, int32_t* labels,
-                       float* mode_key, bool use_iters_flag, DevState* st);
+                       float* mode_key, bool use_iters_flag, DevState* st,
+                       const int32_t* orig = nullptr, const int32_t* inv = nullptr);
+
+// Row order for the z-updates (L2 locality): rows sorted by their argmax_l
+// A[p][l] (a stable counting sort), perm[i] = original row of row i,
+// inv[perm[i]] = i; then X, A, Z0 and the graph in that order.
+size_t locality_ws_bytes(int64_t N, int L);
+slk_status locality_perm_launch(slk_ctx* ctx, const float* A, int64_t N, int L, int32_t* perm,
+                                int32_t* inv, void* ws);
+slk_status permute_problem_launch(slk_ctx* ctx, const int32_t* perm, const int32_t* inv,
+                                  int64_t N, int D, int L, int k, const float* X, const float* A,
+                                  const float* Z0, const int32_t* col_idx, const float* w,
+                                  float* Xp, float* Ap, float* Z0p, int32_t* colp, float* wp);
+// out[l] = inv[modes[l]] (mode indices in the new row order).
+slk_status map_modes_launch(slk_ctx* ctx, const int32_t* inv, const int32_t* modes, int L,
+                            int32_t* out);
+// Outputs back in the original order: Z[perm[i]] = Zp[i], labels likewise,
+// modes[l] = perm[modes_p[l]].
+slk_status unpermute_launch(slk_ctx* ctx, const int32_t* perm, int64_t N, int L, const float* Zp,
+                            const int32_t* labels_p, const int32_t* modes_p, float* Z,
+                            int32_t* labels, int32_t* modes);
 
 // log z keys (N x L) and labels for the SLK-MS weights (logits as in mode_launch).
 slk_status logz_launch(slk_ctx* ctx, const float* A, const float* Z_prev,

@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
     _fields_ = [("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
                 ("tol_inner", ctypes.c_float), ("sigma_rule", ctypes.c_int32),
                 ("affinity", ctypes.c_int32), ("knn_precision", ctypes.c_int32),
-                ("refine_init", ctypes.c_int32),
+                ("refine_init", ctypes.c_int32), ("reorder", ctypes.c_int32),
                 ("max_ms", ctypes.c_int32), ("tol_ms", ctypes.c_float), ("tol_modes", ctypes.c_float)]
 
 

@@ -106,6 +106,23 @@ def test_knn_all_rows_through_exact_rescan(slk, precision):
               max_tie_rows=0.02)
 
 
+@pytest.mark.parametrize("D", [32, 130])
+def test_knn_float32_stage_after_bf16(slk, D):
+    """Clusters far from the data mean (centred norms ~ 900 with unit
+    neighbour distances): the bfloat16 certificate cannot hold, the float32
+    query tiles and their certificate take the rows over, and the graph
+    still matches the oracle on every row."""
+    g = inputs.rng(41 + D)
+    N, k = 1500, 7
+    c = g.normal(0.0, 30.0, size=(3, D))
+    X = (c[g.integers(0, 3, N)] + g.normal(0.0, 0.5, size=(N, D))).astype(np.float32)
+    o_idx, o_d2 = oracle.knn(X, k)
+    gr = slk.knn_graph(dev(X), k, precision="bf16_rerank")
+    assert gr.fallback_rows > N // 10
+    check_knn(X, k, host(gr.col_idx).reshape(N, k), host(gr.dist2).reshape(N, k), o_idx, o_d2,
+              max_tie_rows=0.02)
+
+
 def test_knn_heat_weights(slk):
     X, _ = inputs.blobs(N=500, D=6, n_blobs=3, seed=9)
     o_idx, o_d2 = oracle.knn(X, 5)
@@ -376,6 +393,30 @@ def test_solve_heat_affinity_and_meansq_sigma(slk):
     np.testing.assert_array_equal(host(labels), ref["labels"])
     assert np.abs(host(Z) - ref["Z"]).max() <= Z_TOL
     assert stats["energy"] == pytest.approx(ref["E"], rel=E_RTOL)
+
+
+@pytest.mark.parametrize("case", ["blobs", "multi_outer", "heat"])
+def test_solve_sorted_row_order_is_identical(slk, case):
+    """The z-updates on rows sorted by their nearest initial mode (reorder)
+    give the same bits as the given order: each row keeps its edge order and
+    mode ties go to the smaller original index."""
+    if case == "blobs":
+        X, _ = inputs.blobs()
+        L, k, lam, m0, aff = 5, 5, 1.0, inputs.kmeanspp(inputs.blobs()[0], 5, seed=1810), "binary"
+    elif case == "multi_outer":
+        X, _ = inputs.blobs(N=1500, D=4, n_blobs=6, centre_var=6.0, seed=4)
+        L, k, lam, m0, aff = 6, 5, 2.0, np.arange(6, dtype=np.int32), "binary"
+    else:
+        X, _ = inputs.manifolds(N=3000, D=32, n_clusters=6, seed=5)
+        L, k, lam, m0, aff = 6, 10, 1.0, inputs.kmeanspp(X, 6, seed=5), "heat"
+    outs = []
+    for ro in (0, 1):
+        p = slk.default_params(affinity=aff, reorder=ro)
+        outs.append(slk.solve(dev(X), L, k, lam, dev(m0), params=p))
+    (Z0, l0, m0_, s0), (Z1, l1, m1, s1) = outs
+    assert torch.equal(Z0, Z1) and torch.equal(l0, l1) and torch.equal(m0_, m1)
+    assert s0["outer_iters"] == s1["outer_iters"] and s0["inner_iters_total"] == s1["inner_iters_total"]
+    assert s1["energy"] == pytest.approx(s0["energy"], rel=1e-12)
 
 
 def test_solve_mnist_like_full_size(slk):
