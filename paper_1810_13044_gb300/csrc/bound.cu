@@ -290,9 +290,18 @@ __device__ __forceinline__ float rows_update(int64_t p0, int64_t stride, int64_t
 
 // Rows per group and gather window per row: about 32 loads in flight per lane.
 template <int G, int LPL>
+#ifndef SLK_BOUND_RPG4
+#define SLK_BOUND_RPG4 1
+#endif
+#ifndef SLK_BOUND_W4
+#define SLK_BOUND_W4 4
+#endif
+#ifndef SLK_BOUND_MINB
+#define SLK_BOUND_MINB 1
+#endif
 struct Tiling {
-    static constexpr int rpg = (LPL == 1) ? 4 : (LPL == 2 ? 2 : 1);
-    static constexpr int w = (LPL <= 2) ? (G < 8 ? G : 8) : (LPL == 4 ? 4 : 2);
+    static constexpr int rpg = (LPL == 1) ? 4 : (LPL == 2 ? 2 : (LPL == 4 ? SLK_BOUND_RPG4 : 1));
+    static constexpr int w = (LPL <= 2) ? (G < 8 ? G : 8) : (LPL == 4 ? SLK_BOUND_W4 : 2);
 };
 
 __device__ __forceinline__ float block_max(float v, float* red) {
@@ -310,7 +319,7 @@ __device__ __forceinline__ float block_max(float v, float* red) {
 // Persistent inner loop.  Update it reads buffer it % 2 and writes the other;
 // Z0 holds the starting iterate.
 template <int G, int LPL>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, SLK_BOUND_MINB)
 bound_persistent_kernel(const float* __restrict__ A, const int64_t* __restrict__ row_ptr,
                         const int32_t* __restrict__ col_idx, const float* __restrict__ w,
                         int64_t N, int L, float lambda, float* Z0, float* Z1, int max_iters,

@@ -48,9 +48,11 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 #ifndef SLK_TC_PIPE
 #define SLK_TC_PIPE 0
 #endif
-// Epilogue without block barriers per tile (column norms from global memory).
+// Epilogue of the KC = 32 kernel without block barriers per tile (column
+// norms from global memory); the KC = 64 kernel, whose epilogue dominates at
+// small D, keeps the shared-memory staging.
 #ifndef SLK_TC_NOBAR
-#define SLK_TC_NOBAR 0
+#define SLK_TC_NOBAR 1
 #endif
 
 // Survivors of one vote (VOTE columns) land on a buffer holding at most 15.
@@ -280,7 +282,7 @@ __device__ __forceinline__ void item_range(int item, int splits, int n_tiles, in
     t1 = (int)((int64_t)(sp + 1) * n_tiles / splits);
 }
 
-template <int TC_KC, int EW, bool PIPE>
+template <int TC_KC, int EW, bool PIPE, bool NOBAR>
 __global__ void __launch_bounds__(TcEpi<EW>::threads, 1)
 knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const float* __restrict__ norms, int64_t N, int64_t Np, int Dp, int n_tiles,
@@ -438,20 +440,20 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             for (int t = t0; t < t1; ++t) {
                 const uint32_t acc = tcount & 1, use = tcount >> 1;
                 const int64_t col0 = (int64_t)t * TC_N;
-#if SLK_TC_NOBAR
-                // column norms straight from global memory (uniform addresses,
-                // L1 hits after the first warp; norms are padded to the tile),
-                // each warp waits for the accumulator on its own
+                // NOBAR: column norms straight from global memory (uniform
+                // addresses, L1 hits after the first warp; padding rows hold an
+                // infinite norm), each warp waits for the accumulator on its own
                 const float* ncol_g = norms + col0;
-                ok = mbar_wait(&s.tfull[acc], use & 1, abort);
-                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
-#else
-                for (int c = et; c < TC_N; c += NT)
-                    s.ncol[acc][c] = (col0 + c < N) ? norms[col0 + c] : __int_as_float(0x7f800000);
-                epilogue_bar<NT>();
-                ok = epilogue_bar_and<NT>(mbar_wait(&s.tfull[acc], use & 1, abort));
-                if (!ok) break;
-#endif
+                if constexpr (NOBAR) {
+                    ok = mbar_wait(&s.tfull[acc], use & 1, abort);
+                    if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                } else {
+                    for (int c = et; c < TC_N; c += NT)
+                        s.ncol[acc][c] = (col0 + c < N) ? norms[col0 + c] : __int_as_float(0x7f800000);
+                    epilogue_bar<NT>();
+                    ok = epilogue_bar_and<NT>(mbar_wait(&s.tfull[acc], use & 1, abort));
+                    if (!ok) break;
+                }
                 tc_fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(sub * 32) << 16) + acc * TC_N;
                 // distances of one 32-column chunk, filtered in votes of VOTE
@@ -459,21 +461,21 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 // distance ~0, is kept here and dropped by the rerank)
                 auto process = [&](const uint32_t (&rv)[32], int ch) {
                     float v[32];
-#if SLK_TC_NOBAR
-                    const float4* n4 = reinterpret_cast<const float4*>(ncol_g + ch * 32);
+                    if constexpr (NOBAR) {
+                        const float4* n4 = reinterpret_cast<const float4*>(ncol_g + ch * 32);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 c4 = __ldg(n4 + q);
-                        v[4 * q + 0] = fmaf(-2.f, __uint_as_float(rv[4 * q + 0]), np_ + c4.x);
-                        v[4 * q + 1] = fmaf(-2.f, __uint_as_float(rv[4 * q + 1]), np_ + c4.y);
-                        v[4 * q + 2] = fmaf(-2.f, __uint_as_float(rv[4 * q + 2]), np_ + c4.z);
-                        v[4 * q + 3] = fmaf(-2.f, __uint_as_float(rv[4 * q + 3]), np_ + c4.w);
+                        for (int q = 0; q < 8; ++q) {
+                            const float4 c4 = __ldg(n4 + q);
+                            v[4 * q + 0] = fmaf(-2.f, __uint_as_float(rv[4 * q + 0]), np_ + c4.x);
+                            v[4 * q + 1] = fmaf(-2.f, __uint_as_float(rv[4 * q + 1]), np_ + c4.y);
+                            v[4 * q + 2] = fmaf(-2.f, __uint_as_float(rv[4 * q + 2]), np_ + c4.z);
+                            v[4 * q + 3] = fmaf(-2.f, __uint_as_float(rv[4 * q + 3]), np_ + c4.w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            v[j] = fmaf(-2.f, __uint_as_float(rv[j]), np_ + s.ncol[acc][ch * 32 + j]);
                     }
-#else
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        v[j] = fmaf(-2.f, __uint_as_float(rv[j]), np_ + s.ncol[acc][ch * 32 + j]);
-#endif
 #pragma unroll
                     for (int g0 = 0; g0 < 32; g0 += VOTE) {
                         const float thr_d = ld[TC_KC - 1];
@@ -621,14 +623,14 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
     if (grid > n_items) grid = n_items;
     if (kc == 32) {
         constexpr int EW = SLK_TC_EW32;
-        auto kern = knn_cand_tc_kernel<32, EW, SLK_TC_PIPE != 0>;
+        auto kern = knn_cand_tc_kernel<32, EW, SLK_TC_PIPE != 0, SLK_TC_NOBAR != 0>;
         const size_t smem = tc_smem_bytes<EW>();
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem));
         kern<<<grid, TcEpi<EW>::threads, smem, ctx->stream>>>(
             ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
     } else {
-        auto kern = knn_cand_tc_kernel<64, 4, false>;
+        auto kern = knn_cand_tc_kernel<64, 4, false, false>;
         const size_t smem = tc_smem_bytes<4>();
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem));
