@@ -455,7 +455,7 @@ size_t init_modes_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int L) {
     b += align_up(sizeof(int32_t) * (size_t)p.nb * L, 256);               // counts
     b += align_up(sizeof(int64_t) * (size_t)p.nb * L, 256);               // base
     b += align_up(sizeof(int64_t) * (L + 1), 256);                        // off
-    b += align_up(sizeof(double) * D, 256);                               // colsum
+    b += align_up(sizeof(double) * D, 256) + align_up(sizeof(float) * D, 256);   // colsum, mu
     b += align_up(sizeof(float) * (size_t)p.Np * p.Dp, 256);              // xt
     b += 2 * align_up(sizeof(float) * (size_t)p.Np, 256);                 // norms, rho
     b += align_up(sizeof(DensItem) * p.max_items, 256);
@@ -479,6 +479,7 @@ slk_status init_modes_launch(slk_ctx* ctx, const float* X, int64_t N, int D, con
     int64_t* base = wc.take<int64_t>((size_t)pl.nb * L);
     int64_t* off = wc.take<int64_t>(L + 1);
     double* colsum = wc.take<double>(D);
+    float* mu = wc.take<float>(D);
     float* xt = wc.take<float>((size_t)pl.Np * pl.Dp);
     float* norms = wc.take<float>(pl.Np);
     float* rho = wc.take<float>(pl.Np);
@@ -520,7 +521,7 @@ slk_status init_modes_launch(slk_ctx* ctx, const float* X, int64_t N, int D, con
     label_scatter_kernel<<<pl.nb, 256, sizeof(int) * 9 * L, s>>>(assign, N, L, base, perm);
     SLK_LAUNCH_CHECK(ctx, "counting sort");
     // 3. centred operand and norms
-    slk_status r = knn_prep_fp32_launch(ctx, X, N, D, pl.Dp, pl.Np, colsum, xt, norms, rho, st);
+    slk_status r = knn_prep_fp32_launch(ctx, X, N, D, pl.Dp, pl.Np, colsum, mu, xt, norms, rho, st);
     if (r != SLK_OK) return r;
     // 4. work items: every cluster's perm range cut into chunks (host, from the offsets)
     std::vector<int64_t> hoff(L + 1);

@@ -72,6 +72,13 @@ __global__ void col_sum_kernel(const float* __restrict__ X, int64_t N, int D,
     }
 }
 
+// Column means of the centring: mu_j = (float)(colsum_j / N).
+__global__ void mu_kernel(const double* __restrict__ colsum, int64_t N, int D, float* __restrict__ mu) {
+    const double inv_n = 1.0 / (double)N;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D; j += gridDim.x * blockDim.x)
+        mu[j] = (float)(colsum[j] * inv_n);
+}
+
 // One warp per padded row: xt = round(v), v = fl(x - mu), with
 //   norms[p] = ||xt_p||^2: lane sums of xt^2 in float32 (at most Dp/32 terms,
 //     relative error <= (Dp/32) u, u = 2^-24; each bfloat16 square is exact),
@@ -82,7 +89,7 @@ __global__ void col_sum_kernel(const float* __restrict__ X, int64_t N, int D,
 // The row maxima go to st with one atomic per block.
 __global__ void __launch_bounds__(256)
 prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
-                 int64_t Np, const double* __restrict__ colsum, int to_bf16,
+                 int64_t Np, const float* __restrict__ mu, int to_bf16,
                  float* __restrict__ xt32, __nv_bfloat16* __restrict__ xt16,
                  float* __restrict__ norms, float* __restrict__ rho,
                  float* __restrict__ norms32, DevState* st) {
@@ -91,7 +98,6 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const double inv_n = 1.0 / (double)N;
     const double bound = 1.0 + (double)(Dp / 32 + 2) * 5.9604644775390625e-08;
     unsigned my_n = 0u, my_r = 0u, my_n32 = 0u;
     for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < Np;
@@ -99,10 +105,7 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
         float n2 = 0.f, e2 = 0.f, v2 = 0.f;
         for (int j = lane; j < Dp; j += 32) {
             float v = 0.f, vv = 0.f;
-            if (p < N && j < D) {
-                const float mu = (float)(colsum[j] * inv_n);
-                v = X[p * D + j] - mu;
-            }
+            if (p < N && j < D) v = X[p * D + j] - __ldg(mu + j);
             if (to_bf16) {
                 const __nv_bfloat16 b = __float2bfloat16_rn(v);
                 xt16[p * Dp + j] = b;
@@ -319,13 +322,6 @@ knn_cand_fp32_kernel(const float* __restrict__ xt, const float* __restrict__ nor
             cand_i[o + j] = s.list_i[t][j] == kNoIdx ? -1 : s.list_i[t][j];
         }
     }
-}
-
-// Column means as the prep uses them: mu_j = (float)(colsum_j / N).
-__global__ void mu_kernel(const double* __restrict__ colsum, int64_t N, int D, float* __restrict__ mu) {
-    const double inv_n = 1.0 / (double)N;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < D; j += gridDim.x * blockDim.x)
-        mu[j] = (float)(colsum[j] * inv_n);
 }
 
 // Float32 distance tiles for listed query rows (the rows the bfloat16
@@ -950,7 +946,8 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                                 float* cand_d, int32_t* cand_i, unsigned int* err_flag);
 
 slk_status knn_prep_fp32_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int Dp, int64_t Np,
-                                double* colsum, float* xt, float* norms, float* rho, DevState* st) {
+                                double* colsum, float* mu, float* xt, float* norms, float* rho,
+                                DevState* st) {
     cudaStream_t s = ctx->stream;
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(colsum, 0, sizeof(double) * D, s));
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_bits, 0, 2 * sizeof(unsigned int), s));
@@ -959,10 +956,11 @@ slk_status knn_prep_fp32_launch(slk_ctx* ctx, const float* X, int64_t N, int D, 
     if (gy > 1024) gy = 1024;
     if (gy < 1) gy = 1;
     col_sum_kernel<<<dim3((unsigned)((D + 31) / 32), (unsigned)gy), dim3(32, 8), 0, s>>>(X, N, D, colsum);
+    mu_kernel<<<(D + 255) / 256, 256, 0, s>>>(colsum, N, D, mu);
     SLK_LAUNCH_CHECK(ctx, "col_sum_kernel");
     int64_t pg = (Np + 7) / 8;
     if (pg > (int64_t)ctx->num_sms * 16) pg = (int64_t)ctx->num_sms * 16;
-    prep_rows_kernel<<<(unsigned)pg, 256, 0, s>>>(X, N, D, Dp, Np, colsum, 0, xt, nullptr, norms,
+    prep_rows_kernel<<<(unsigned)pg, 256, 0, s>>>(X, N, D, Dp, Np, mu, 0, xt, nullptr, norms,
                                                    rho, nullptr, st);
     SLK_LAUNCH_CHECK(ctx, "prep_rows_kernel");
     return SLK_OK;
@@ -992,17 +990,18 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->fallback2_count, 0, sizeof(long long), s));
     {
         PhaseScope ps(ctx, SLK_PHASE_KNN_PREP);
-        SLK_COUNT_LAUNCH(ctx, 2);
+        SLK_COUNT_LAUNCH(ctx, 3);
         int gy = (int)((N + 4095) / 4096);
         if (gy > 1024) gy = 1024;
         if (gy < 1) gy = 1;
         dim3 grid((unsigned)((D + 31) / 32), (unsigned)gy);
         col_sum_kernel<<<grid, dim3(32, 8), 0, s>>>(X, N, D, colsum);
+        mu_kernel<<<(D + 255) / 256, 256, 0, s>>>(colsum, N, D, mu);
         SLK_LAUNCH_CHECK(ctx, "col_sum_kernel");
         int64_t pg = (pl.Np + 7) / 8;
         if (pg > (int64_t)ctx->num_sms * 16) pg = (int64_t)ctx->num_sms * 16;
         prep_rows_kernel<<<(unsigned)pg, 256, 0, s>>>(
-            X, N, D, pl.Dp, pl.Np, colsum, pl.bf16 ? 1 : 0, pl.bf16 ? nullptr : (float*)xt,
+            X, N, D, pl.Dp, pl.Np, mu, pl.bf16 ? 1 : 0, pl.bf16 ? nullptr : (float*)xt,
             pl.bf16 ? (__nv_bfloat16*)xt : nullptr, norms, rho, pl.bf16 ? norms32 : nullptr, st);
         SLK_LAUNCH_CHECK(ctx, "prep_rows_kernel");
     }
@@ -1061,8 +1060,7 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
             int qsplits = (int)std::min<int64_t>(8, (int64_t)pl.lists * pl.kc / kcq);
             if (qsplits < 1) qsplits = 1;
             const int n_tiles = (int)((N + BN - 1) / BN);
-            SLK_COUNT_LAUNCH(ctx, 3);
-            mu_kernel<<<(D + 255) / 256, 256, 0, s>>>(colsum, N, D, mu);
+            SLK_COUNT_LAUNCH(ctx, 2);
             const unsigned qgrid = (unsigned)(ctx->num_sms * 2);
 #define SLK_QCAND(KC_)                                                                        \
     {                                                                                         \

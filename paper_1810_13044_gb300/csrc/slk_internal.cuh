@@ -126,7 +126,8 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
 // Centred float32 operand of the distance tiles: xt[p][j] = x_pj - mean_j
 // (Np x Dp, zero padding), norms[p] = ||xt_p||^2, rho[p] = rounding norm.
 slk_status knn_prep_fp32_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int Dp, int64_t Np,
-                                double* colsum, float* xt, float* norms, float* rho, DevState* st);
+                                double* colsum, float* mu, float* xt, float* norms, float* rho,
+                                DevState* st);
 
 // Starting modes of Section 4.2 (nearest-seed assignment, then the mode
 // definition of Eq. (1)): modes [L] device out, assign [N] device out

@@ -11,9 +11,14 @@
 
 namespace {
 
-constexpr int kUTP = 32;       // points per block
-constexpr int kUDC = 32;       // feature chunk staged in shared memory
+constexpr int kUPG = 128;      // points per point group (4 per lane)
+constexpr int kUDC = 32;       // feature chunk staged in shared memory (float32 partial sums)
 constexpr int kUThreads = 256;
+
+// Row stride of the staged mode values: 4 G rounded up to 4 x odd, so that
+// 16-byte rows stay aligned and the staging stores are at most 4-way
+// bank-conflicted.
+__host__ __device__ inline int unary_mode_stride(int G) { return 4 * (G | 1); }
 
 // Block: 32 points x all L labels.  Thread t owns point t % 32 and labels
 // t / 32 + 8 j.  X and mode rows are staged 32 features at a time; each
@@ -21,86 +26,142 @@ constexpr int kUThreads = 256;
 // Vector modes (SLK-MS) come as M (float32) or as a float64 state split into
 // Mhi + Mlo (two floats): (x - m_hi) - m_lo keeps the difference accurate to
 // float32 relative to itself, not to |m|.
-template <int LPT>
-__global__ void __launch_bounds__(kUThreads)
+// 4-byte asynchronous global -> shared copy; n = 0 fills the word with zero
+// (the source is then not read).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, int n) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Thread tile: 4 points (lane + 32 i) x 4 labels.  A warp covers one point
+// group of 128 and one label group of 4; a block holds PG point groups and G
+// label groups (G PG warps), and loops over passes of 4 G labels.  Features
+// go in chunks of 32: X staged [point][33] (conflict-free per point), the
+// pass's mode values [feature][S] (S = 4 x odd: one 16-byte broadcast per
+// label group), two buffers filled by asynchronous copies so that the next
+// chunk (of this pass or the next) loads while this one is summed.  Each
+// pair's squared differences over a chunk are summed in float32 in feature
+// order, the chunk sums in float64.  Vector modes (SLK-MS) come as M
+// (float32) or as a float64 state split into M + Mlo: (x - m_hi) - m_lo keeps
+// the difference accurate to float32 relative to itself, not to |m|.  Z0's
+// softmax rows are read back from A once the block has written it.
+__global__ void __launch_bounds__(kUThreads, 2)
 unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __restrict__ modes,
-             const float* __restrict__ M, const float* __restrict__ Mlo, int L,
+             const float* __restrict__ M, const float* __restrict__ Mlo, int L, int G, int PG,
              const float* __restrict__ sigma_dev, float* __restrict__ A, float* __restrict__ Z0) {
-    extern __shared__ float sm[];
-    float* xs = sm;                                  // [kUTP][kUDC + 1]
-    float* ms = xs + kUTP * (kUDC + 1);              // [L][kUDC + 1]
-    float* ml = ms + (size_t)L * (kUDC + 1);         // [L][kUDC + 1] (Mlo only)
-    float* at = ml + (Mlo ? (size_t)L * (kUDC + 1) : 0);   // [kUTP][L]
+    extern __shared__ __align__(16) float sm[];
+    const int S = unary_mode_stride(G), npts = PG * kUPG;
+    const int nthr = blockDim.x;
+    const size_t xbuf = (size_t)npts * (kUDC + 1), mbuf = (size_t)kUDC * S;
+    float* xs = sm;                                    // 2 x [npts][kUDC + 1]
+    float* mh = xs + 2 * xbuf;                         // 2 x [kUDC][S]
+    float* mlo = mh + 2 * mbuf;                        // 2 x [kUDC][S] (Mlo only)
     __shared__ int mrow[SLK_MAX_L];
-    const int t = threadIdx.x;
-    const int pl = t % kUTP, lb = t / kUTP;
-    const int64_t p0 = (int64_t)blockIdx.x * kUTP;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int g = warp % G, pg = warp / G;
+    const int64_t p0 = (int64_t)blockIdx.x * npts;
     if (M == nullptr)
-        for (int l = t; l < L; l += kUThreads) mrow[l] = modes[l];
-    double acc[LPT];
-#pragma unroll
-    for (int j = 0; j < LPT; ++j) acc[j] = 0.0;
+        for (int l = t; l < L; l += nthr) mrow[l] = modes[l];
     __syncthreads();
-    for (int d0 = 0; d0 < D; d0 += kUDC) {
-        const int dc = min(kUDC, D - d0);
-        for (int i = t; i < kUTP * kUDC; i += kUThreads) {
-            const int r = i / kUDC, c = i % kUDC;
-            const int64_t p = p0 + r;
-            xs[r * (kUDC + 1) + c] = (p < N && c < dc) ? X[p * D + d0 + c] : 0.f;
-        }
-        for (int i = t; i < L * kUDC; i += kUThreads) {
-            const int r = i / kUDC, c = i % kUDC;
-            if (M) {
-                ms[r * (kUDC + 1) + c] = (c < dc) ? M[(int64_t)r * D + d0 + c] : 0.f;
-                if (Mlo) ml[r * (kUDC + 1) + c] = (c < dc) ? Mlo[(int64_t)r * D + d0 + c] : 0.f;
-            } else {
-                ms[r * (kUDC + 1) + c] = (c < dc) ? X[(int64_t)mrow[r] * D + d0 + c] : 0.f;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < LPT; ++j) {
-            const int l = lb + 8 * j;
-            if (l < L) {
-                float part = 0.f;
-                if (Mlo) {
-                    for (int c = 0; c < dc; ++c) {
-                        const float df = (xs[pl * (kUDC + 1) + c] - ms[l * (kUDC + 1) + c]) -
-                                         ml[l * (kUDC + 1) + c];
-                        part = fmaf(df, df, part);
-                    }
-                } else {
-                    for (int c = 0; c < dc; ++c) {
-                        const float df = xs[pl * (kUDC + 1) + c] - ms[l * (kUDC + 1) + c];
-                        part = fmaf(df, df, part);
-                    }
-                }
-                acc[j] += (double)part;
-            }
-        }
-        __syncthreads();
-    }
     const float sg = *sigma_dev;
     const float inv2s2 = 1.0f / (2.0f * sg * sg);
-    const int64_t p = p0 + pl;
-#pragma unroll
-    for (int j = 0; j < LPT; ++j) {
-        const int l = lb + 8 * j;
-        if (l < L) {
-            const float a = expf(-(float)acc[j] * inv2s2);
-            at[pl * L + l] = a;
-            if (p < N) A[p * L + l] = a;
+    const int nch = (D + kUDC - 1) / kUDC;
+    const int nsteps = ((L + 4 * G - 1) / (4 * G)) * nch;   // (pass, chunk) pairs
+    // Step s: pass s / nch (labels l0 = 4 G (s / nch) ..), chunk s % nch, buffer s & 1.
+    auto stage = [&](int s) {
+        const int d0 = (s % nch) * kUDC, l0 = (s / nch) * 4 * G, b = s & 1;
+        const int dc = min(kUDC, D - d0);
+        float* xb = xs + b * xbuf;
+        for (int i = t; i < npts * kUDC; i += nthr) {
+            const int r = i / kUDC, c = i % kUDC;
+            const int64_t p = p0 + r;
+            const bool ok = p < N && c < dc;
+            cp_async4(xb + r * (kUDC + 1) + c, ok ? X + p * D + d0 + c : X, ok ? 4 : 0);
         }
+        float* hb = mh + b * mbuf;
+        float* lb = mlo + b * mbuf;
+        for (int i = t; i < 4 * G * kUDC; i += nthr) {
+            const int r = i / kUDC, c = i % kUDC;   // label l0 + r, feature d0 + c
+            const int l = l0 + r;
+            const bool ok = l < L && c < dc;
+            const float* src = !ok ? X : M ? M + (int64_t)l * D + d0 + c
+                                          : X + (int64_t)mrow[l] * D + d0 + c;
+            cp_async4(hb + c * S + r, src, ok ? 4 : 0);
+            if (Mlo) cp_async4(lb + c * S + r, ok ? Mlo + (int64_t)l * D + d0 + c : Mlo, ok ? 4 : 0);
+        }
+        cp_async_commit();
+    };
+    stage(0);
+    double acc[4][4];
+    for (int s = 0; s < nsteps; ++s) {
+        const int k = s % nch, l0 = (s / nch) * 4 * G, b = s & 1;
+        const int dc = min(kUDC, D - k * kUDC);
+        if (k == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        }
+        if (s + 1 < nsteps) stage(s + 1);
+        else cp_async_commit();          // an empty group keeps the wait count uniform
+        cp_async_wait1();                // this thread's copies of step s have landed
+        __syncthreads();                 // ... and every thread's
+        const float* xrow = xs + b * xbuf + (size_t)(pg * kUPG + lane) * (kUDC + 1);
+        const float* hb = mh + b * mbuf + 4 * g;
+        const float* lb = mlo + b * mbuf + 4 * g;
+        float part[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
+        for (int c = 0; c < dc; ++c) {
+            float x[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[i] = xrow[32 * i * (kUDC + 1) + c];
+            const float4 h4 = *reinterpret_cast<const float4*>(hb + c * S);
+            const float m[4] = {h4.x, h4.y, h4.z, h4.w};
+            float ml[4] = {0.f, 0.f, 0.f, 0.f};
+            if (Mlo) {
+                const float4 l4 = *reinterpret_cast<const float4*>(lb + c * S);
+                ml[0] = l4.x; ml[1] = l4.y; ml[2] = l4.z; ml[3] = l4.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float df = x[i] - m[j];
+                    if (Mlo) df -= ml[j];
+                    part[i][j] = fmaf(df, df, part[i][j]);
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += (double)part[i][j];
+        if (k == nch - 1) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t p = p0 + pg * kUPG + lane + 32 * i;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int l = l0 + 4 * g + j;
+                    if (p < N && l < L) A[p * L + l] = expf(-(float)acc[i][j] * inv2s2);
+                }
+            }
+        }
+        __syncthreads();                 // buffer b is free for step s + 2
     }
     if (Z0 == nullptr) return;
-    __syncthreads();
-    if (t < kUTP && p0 + t < N) {
-        const float* ar = at + t * L;
+    for (int r = t; r < npts; r += nthr) {   // the block's rows of A are written (last barrier)
+        if (p0 + r >= N) break;
+        const float* ar = A + (p0 + r) * L;
         float m = ar[0];
         for (int l = 1; l < L; ++l) m = fmaxf(m, ar[l]);
         float s = 0.f;
         for (int l = 0; l < L; ++l) s += expf(ar[l] - m);
-        float* zr = Z0 + (p0 + t) * L;
+        float* zr = Z0 + (p0 + r) * L;
         for (int l = 0; l < L; ++l) zr[l] = expf(ar[l] - m) / s;
     }
 }
@@ -162,24 +223,19 @@ slk_status unary_launch(slk_ctx* ctx, const float* X, int64_t N, int D, const in
                         const float* Mlo) {
     PhaseScope ps(ctx, SLK_PHASE_UNARY);
     SLK_COUNT_LAUNCH(ctx, 1);
-    const size_t smem = sizeof(float) * ((size_t)kUTP * (kUDC + 1) +
-                                         (Mlo ? 2 : 1) * (size_t)L * (kUDC + 1) + (size_t)kUTP * L);
-    const unsigned grid = (unsigned)((N + kUTP - 1) / kUTP);
-    const int lpt = (L + 7) / 8;
-#define SLK_UNARY(LPT_)                                                                     \
-    {                                                                                       \
-        auto kern = unary_kernel<LPT_>;                                                     \
-        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                               (int)smem));                                 \
-        kern<<<grid, kUThreads, smem, ctx->stream>>>(X, N, D, modes, M, Mlo, L, sigma_dev, A, Z0); \
-    }
-    if (lpt <= 1) { SLK_UNARY(1) }
-    else if (lpt <= 2) { SLK_UNARY(2) }
-    else if (lpt <= 4) { SLK_UNARY(4) }
-    else if (lpt <= 8) { SLK_UNARY(8) }
-    else if (lpt <= 16) { SLK_UNARY(16) }
-    else { SLK_UNARY(32) }
-#undef SLK_UNARY
+    // label groups of 4: up to 8 warps per pass, the passes balanced
+    const int gtot = (L + 3) / 4;
+    const int passes = (gtot + 7) / 8;
+    const int G = (gtot + passes - 1) / passes;
+    const int PG = G <= 2 ? 2 : 1;
+    const size_t smem = 2 * sizeof(float) * ((size_t)PG * kUPG * (kUDC + 1) +
+                                             (Mlo ? 2 : 1) * (size_t)kUDC * unary_mode_stride(G));
+    SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(unary_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+    const int64_t npts = (int64_t)PG * kUPG;
+    const unsigned grid = (unsigned)((N + npts - 1) / npts);
+    unary_kernel<<<grid, 32 * G * PG, smem, ctx->stream>>>(X, N, D, modes, M, Mlo, L, G, PG,
+                                                            sigma_dev, A, Z0);
     SLK_LAUNCH_CHECK(ctx, "unary_kernel");
     return SLK_OK;
 }
