@@ -29,53 +29,45 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
-                 : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
+__device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Device-wide step barrier of the persistent inner loop.  Every block has
-// already folded its max |dz| into delta_bits[slot_now] (a reduction without
-// return).  The last block to arrive reads the final max, clears the slot of
-// the next update, decides convergence (delta <= tol) and publishes it with
-// the new generation (bit 31 = converged), so waiting blocks learn both from
-// one load.  Returns 1 (converged), 0 (go on) or -1 (a wait gave up after
-// kBarrierTimeoutNs, or another block's did).
-__device__ int grid_step(DevState* st, unsigned nblocks, int slot_now, int slot_next, float tol) {
+// already folded its max |dz| into delta_bits[it % 3] (a reduction without
+// return); it adds one to a monotonic arrival counter (release) and waits
+// (acquire) until the counter reaches nblocks (it + 1), compared modulo 2^32.
+// By then every block's max is in the slot, so each block reads the same
+// final delta and takes the same decision (delta <= tol) itself.  Block 0
+// clears the slot of update it + 2 (its last readers passed this barrier)
+// and records the delta.  Returns 1 (converged), 0 (go on) or -1 (a wait
+// gave up after kBarrierTimeoutNs, or another block's did).
+__device__ int grid_step(DevState* st, unsigned nblocks, int it, float tol) {
     __shared__ int s_res;
     __syncthreads();
     if (threadIdx.x == 0) {
         int res = 0;
-        const unsigned gen = ld_acquire_gpu(&st->barrier_gen);
-        __threadfence();
-        const unsigned prev = atom_add_acq_rel_gpu(&st->barrier_arrive, 1u);
-        if (prev == nblocks - 1) {
-            st->barrier_arrive = 0;
-            st->delta_bits[slot_next] = 0u;
-            const float dl = __uint_as_float(ld_acquire_gpu(&st->delta_bits[slot_now]));
-            st->last_delta = dl;
-            const unsigned done = (dl <= tol) ? 0x80000000u : 0u;
-            st_release_gpu(&st->barrier_gen, ((gen + 1u) & 0x7fffffffu) | done);
-            res = done ? 1 : 0;
-        } else {
-            const unsigned long long t0 = globaltimer_ns();
-            unsigned polls = 0, v;
-            while ((v = ld_acquire_gpu(&st->barrier_gen)) == gen) {
-                if ((++polls & 63u) == 0u) {
-                    if (ld_acquire_gpu(&st->error) != 0u) { res = -1; break; }
-                    if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
-                        atomicOr(&st->error, ERR_BARRIER_TIMEOUT);
-                        res = -1;
-                        break;
-                    }
+        const unsigned target = nblocks * (unsigned)(it + 1);
+        red_add_release_gpu(&st->barrier_arrive, 1u);
+        const unsigned long long t0 = globaltimer_ns();
+        unsigned polls = 0;
+        while ((int)(ld_acquire_gpu(&st->barrier_arrive) - target) < 0) {
+            if ((++polls & 63u) == 0u) {
+                if (ld_acquire_gpu(&st->error) != 0u) { res = -1; break; }
+                if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                    atomicOr(&st->error, ERR_BARRIER_TIMEOUT);
+                    res = -1;
+                    break;
                 }
             }
-            if (res == 0) res = (v & 0x80000000u) ? 1 : 0;
+        }
+        if (res == 0) {
+            const float dl = __uint_as_float(ld_acquire_gpu(&st->delta_bits[it % 3]));
+            if (blockIdx.x == 0) {
+                st->delta_bits[(it + 2) % 3] = 0u;
+                st->last_delta = dl;
+            }
+            res = (dl <= tol) ? 1 : 0;
         }
         s_res = res;
     }
@@ -344,7 +336,164 @@ bound_persistent_kernel(const float* __restrict__ A, const int64_t* __restrict__
                                                                     Zin, Zout, L, lambda));
         const float bm = block_max(d, red);
         if (threadIdx.x == 0) atomicMax(&st->delta_bits[it % 3], __float_as_uint(bm));
-        const int r = grid_step(st, gridDim.x, it % 3, (it + 1) % 3, tol);
+        const int r = grid_step(st, gridDim.x, it, tol);
+        if (r < 0) return;
+        ++it;
+        if (r == 1) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->iters_done = it;
+}
+
+// rows_update on operands cached in shared memory: the CTA's rows
+// [r0, r0 + nr) keep their unary terms sA[lr][L], column indices
+// sQ[lr][kdeg] and weights sW[lr][kdeg] (lr = p - r0) there for the whole
+// inner loop, so an update reads only Z from L2.  Rows lr0, lr0 + lstride,
+// ...; the arithmetic (edge order, windows, soft-max) is that of rows_update.
+template <int G, int LPL, int RPG, int W>
+__device__ __forceinline__ float rows_update_cached(int lr0, int lstride, int nr, int64_t r0, int gl,
+                                                    unsigned gmask, const float* sA, const int* sQ,
+                                                    const float* sW, int kdeg, const float* Zin,
+                                                    float* Zout, int L, float lambda) {
+    int lr[RPG], cnt[RPG];
+    int maxc = 0;
+    float av[RPG][LPL], zo[RPG][LPL], b[RPG][LPL];
+#pragma unroll
+    for (int i = 0; i < RPG; ++i) {
+        lr[i] = lr0 + i * lstride;
+        const bool live = lr[i] < nr;
+        cnt[i] = live ? kdeg : 0;
+        maxc = max(maxc, cnt[i]);
+        const int64_t p = r0 + lr[i];
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            const int l = gl + G * j;
+            const bool ok = live && l < L;
+            av[i][j] = ok ? sA[lr[i] * L + l] : 0.f;
+            zo[i][j] = ok ? __ldcg(Zin + p * (int64_t)L + l) : 0.f;
+            b[i][j] = 0.f;
+        }
+    }
+    for (int c0 = 0; c0 < maxc; c0 += G) {
+        int myq[RPG];
+        float myw[RPG];
+#pragma unroll
+        for (int i = 0; i < RPG; ++i) {
+            myq[i] = 0;
+            myw[i] = 1.f;
+            if (gl < cnt[i] - c0) {
+                myq[i] = sQ[lr[i] * kdeg + c0 + gl];
+                if (sW) myw[i] = sW[lr[i] * kdeg + c0 + gl];
+            }
+        }
+        const int cm = min(G, maxc - c0);
+        for (int t0 = 0; t0 < cm; t0 += W) {
+            float zz[RPG][W][LPL], ww[RPG][W];
+#pragma unroll
+            for (int i = 0; i < RPG; ++i)
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    const int t = t0 + u;   // < G: W divides G and t0 < cm <= G
+                    const int q = __shfl_sync(gmask, myq[i], t, G);
+                    ww[i][u] = __shfl_sync(gmask, myw[i], t, G);
+                    const bool ok = t < cnt[i] - c0;
+                    const float* zq = Zin + (int64_t)q * L;
+#pragma unroll
+                    for (int j = 0; j < LPL; ++j) {
+                        const int l = gl + G * j;
+                        zz[i][u][j] = (ok && l < L) ? __ldcg(zq + l) : 0.f;
+                    }
+                }
+#pragma unroll
+            for (int i = 0; i < RPG; ++i)
+#pragma unroll
+                for (int u = 0; u < W; ++u)
+                    if (t0 + u < cnt[i] - c0)
+#pragma unroll
+                        for (int j = 0; j < LPL; ++j) b[i][j] = fmaf(ww[i][u], zz[i][u][j], b[i][j]);
+        }
+    }
+    float dmax = 0.f;
+#pragma unroll
+    for (int i = 0; i < RPG; ++i) {
+        if (lr[i] >= nr) continue;  // uniform within the group
+        float sv[LPL];
+        float m = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            const int l = gl + G * j;
+            sv[j] = (l < L) ? fmaf(lambda, b[i][j], av[i][j]) : -INFINITY;
+            m = fmaxf(m, sv[j]);
+        }
+        m = group_max<G>(m, gmask);
+        float e[LPL], sum = 0.f;
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            e[j] = (gl + G * j < L) ? expf(sv[j] - m) : 0.f;
+            sum += e[j];
+        }
+        sum = group_sum<G>(sum, gmask);
+        const int64_t off = (r0 + lr[i]) * (int64_t)L;
+#pragma unroll
+        for (int j = 0; j < LPL; ++j) {
+            const int l = gl + G * j;
+            if (l < L) {
+                const float z = e[j] / sum;
+                dmax = fmaxf(dmax, fabsf(z - zo[i][j]));
+                __stcg(Zout + off + l, z);
+            }
+        }
+    }
+    return dmax;
+}
+
+#ifndef SLK_BOUND_CACHED_RPG2
+#define SLK_BOUND_CACHED_RPG2 2
+#endif
+template <int LPL>
+struct CachedTiling {
+    static constexpr int rpg = (LPL == 1) ? 4 : (LPL == 2 ? SLK_BOUND_CACHED_RPG2 : (LPL == 4 ? 2 : 1));
+};
+
+// Persistent inner loop over a fixed-degree graph (kdeg edges per row) with
+// each CTA's operands cached in shared memory: CTA b owns rows
+// [b rpc, (b + 1) rpc).  Same updates, barrier and results as
+// bound_persistent_kernel.
+template <int G, int LPL>
+__global__ void __launch_bounds__(kThreads, SLK_BOUND_MINB)
+bound_cached_kernel(const float* __restrict__ A, const int32_t* __restrict__ col_idx,
+                    const float* __restrict__ w, int64_t N, int L, float lambda, float* Z0,
+                    float* Z1, int max_iters, float tol, int kdeg, int rpc, DevState* st) {
+    extern __shared__ __align__(16) float csm[];
+    constexpr int RPW = 32 / G;
+    __shared__ float red[kThreads / 32];
+    const int64_t r0 = (int64_t)blockIdx.x * rpc;
+    const int nr = (int)(N - r0 < (int64_t)rpc ? (N - r0 > 0 ? N - r0 : 0) : rpc);
+    float* sA = csm;                                            // [rpc][L]
+    int* sQ = reinterpret_cast<int*>(sA + (size_t)rpc * L);     // [rpc][kdeg]
+    float* sW = w ? reinterpret_cast<float*>(sQ + (size_t)rpc * kdeg) : nullptr;   // [rpc][kdeg]
+    for (int i = threadIdx.x; i < nr * L; i += kThreads) sA[i] = __ldg(A + r0 * L + i);
+    for (int i = threadIdx.x; i < nr * kdeg; i += kThreads) {
+        sQ[i] = __ldg(col_idx + r0 * kdeg + i);
+        if (w) sW[i] = __ldg(w + r0 * kdeg + i);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane % G, grp = lane / G;
+    const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
+    const int gidx = warp * RPW + grp;
+    constexpr int ng = (kThreads / 32) * RPW;   // groups per CTA
+    constexpr int RPG = CachedTiling<LPL>::rpg;
+    int it = 0;
+    while (it < max_iters) {
+        const float* Zin = (it & 1) ? Z1 : Z0;
+        float* Zout = (it & 1) ? Z0 : Z1;
+        float d = 0.f;
+        for (int lr0 = gidx; lr0 < nr; lr0 += ng * RPG)
+            d = fmaxf(d, rows_update_cached<G, LPL, RPG, Tiling<G, LPL>::w>(
+                             lr0, ng, nr, r0, gl, gmask, sA, sQ, sW, kdeg, Zin, Zout, L, lambda));
+        const float bm = block_max(d, red);
+        if (threadIdx.x == 0) atomicMax(&st->delta_bits[it % 3], __float_as_uint(bm));
+        const int r = grid_step(st, gridDim.x, it, tol);
         if (r < 0) return;
         ++it;
         if (r == 1) break;
@@ -565,6 +714,47 @@ Shape shape_for(int L) {
         else { MACRO(32, 8); }                   \
     } while (0)
 
+constexpr size_t kCachedSmemMax = 96 * 1024;   // bytes of cached operands per CTA
+
+// Launches bound_cached_kernel when the graph has a fixed degree and every
+// CTA's share of A, col_idx and w fits kCachedSmemMax with all CTAs resident;
+// *used says whether it did.
+template <int G, int LPL>
+cudaError_t launch_cached(slk_ctx* ctx, const float* A, const int32_t* col_idx, const float* w,
+                          int64_t N, int L, float lambda, float* Z, float* Z_prev, int max_iters,
+                          float tol, int kdeg, DevState* st, bool* used) {
+    *used = false;
+    auto kern = bound_cached_kernel<G, LPL>;
+    const size_t per_row = sizeof(float) * L + sizeof(int) * kdeg + (w ? sizeof(float) * kdeg : 0);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    for (int tries = 0; tries < 4 && per_sm >= 1; ++tries) {
+        const int64_t grid = (int64_t)per_sm * ctx->num_sms;
+        const int64_t rpc = (N + grid - 1) / grid;
+        const size_t smem = per_row * (size_t)rpc;
+        if (smem > kCachedSmemMax) return cudaSuccess;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int fit = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (fit >= per_sm) {
+            const int64_t g2 = (N + rpc - 1) / rpc;   // <= grid: every CTA is resident
+            const float* a_ = A; const int32_t* ci_ = col_idx; const float* w_ = w;
+            int64_t n_ = N; int l_ = L; float lam_ = lambda; float* z0_ = Z; float* z1_ = Z_prev;
+            int mi_ = max_iters; float tol_ = tol; int kd_ = kdeg; int rpc_ = (int)rpc;
+            DevState* st_ = st;
+            void* args[] = {&a_, &ci_, &w_, &n_, &l_, &lam_, &z0_, &z1_, &mi_, &tol_, &kd_, &rpc_, &st_};
+            *used = true;
+            return cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)g2), dim3(kThreads),
+                                               args, smem, ctx->stream);
+        }
+        per_sm = fit;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
@@ -587,8 +777,15 @@ slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
     cudaError_t e = cudaSuccess;
     if (ctx->coop_supported) {
         SLK_COUNT_LAUNCH(ctx, 1);
+        bool cached = false;
+#define SLK_LAUNCH_CACHED(G_, LPL_)                                                            \
+    e = launch_cached<G_, LPL_>(ctx, A, col_idx, w, N, L, lambda, Z, Z_prev, max_iters, tol,   \
+                                kdeg, st, &cached);
+        if (kdeg > 0) SLK_DISPATCH_L(L, SLK_LAUNCH_CACHED);
+#undef SLK_LAUNCH_CACHED
+        if (e != cudaSuccess) return cuda_err(ctx, e, "bound_cached_kernel");
 #define SLK_LAUNCH_PERSISTENT(G_, LPL_)                                                        \
-    {                                                                                          \
+    if (!cached) {                                                                             \
         auto kern = bound_persistent_kernel<G_, LPL_>;                                         \
         int per_sm = 0;                                                                        \
         SLK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0)); \

@@ -511,6 +511,12 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
     const double g = (double)Dp * (double)u_acc;
     const double gam = g / (1.0 - g);
     const double err_exact = 1.01 * (double)(D + 8) * u;
+    // float32 copies of the bound's constants for the candidate pruning
+    // (margins of 1e-6 .. 1e-5 cover the float rounding of the bounds)
+    const float coef_f = (float)((gam + (double)(Dp / 32 + 5) * u) * (1.0 + 1e-6));
+    const float rmax_f = (float)(rmax * (1.0 + 1e-6));
+    const float snmax_f = (float)(sqrt(nmax) * (1.0 + 1e-6));
+    const float keep_f = (float)((1.0 + 2.02 * err_exact) / (1.0 - 2.02 * err_exact) * (1.0 + 1e-5));
     const int64_t rows = Q ? (int64_t)(*(const volatile long long*)count_in) : N;
     const int64_t stride = Q ? N : Np;
     if (!Q && blockIdx.x == 0 && threadIdx.x == 0) row_ptr[N] = N * (int64_t)k;
@@ -537,8 +543,12 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
         constexpr int CPL = (KC + 31) / 32;
         float T = kInf;
         int ci[CPL];
+        float cd[CPL];
 #pragma unroll
-        for (int h = 0; h < CPL; ++h) ci[h] = kNoIdx;
+        for (int h = 0; h < CPL; ++h) {
+            ci[h] = kNoIdx;
+            cd[h] = kInf;
+        }
         int nc = 0;
         for (int c = 0; c < KC; ++c) {
             float bd = kInf;
@@ -558,7 +568,10 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
                 if (ei[m] == bi) { ed[m] = kInf; ei[m] = kNoIdx; }
 #pragma unroll
             for (int h = 0; h < CPL; ++h)
-                if (lane + 32 * h == c) ci[h] = bi;
+                if (lane + 32 * h == c) {
+                    ci[h] = bi;
+                    cd[h] = bd;
+                }
             ++nc;
             T = bd;
         }
@@ -577,12 +590,70 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
             for (int o = 16; o > 0; o >>= 1) ts = fminf(ts, __shfl_xor_sync(0xffffffffu, ts, o));
             T = fminf(T, ts);
         }
-        // exact float32 distances of the candidates
+        // Candidates that cannot be among the k nearest need no exact
+        // distance.  With |dt - |xt_p - xt_q|^2| <= delta and
+        // |xt - (x - mu)| <= rho, the exact distance of candidate c lies in
+        // [lb_c, ub_c] = [(sqrt(dt - delta) - rho_p - rho_max)^2,
+        // (sqrt(dt + delta) + rho_p + rho_max)^2]; if lb_c exceeds the k-th
+        // smallest ub (by more than the float32 rounding of the exact sums),
+        // k candidates beat c whatever the rounding.  Skipped candidates keep
+        // an infinite distance, so they rank after every computed one and the
+        // k nearest, their distances and the certificate are unchanged.
+        unsigned need[CPL];
+        {
+            const float npf = norms[p];
+            const float rr = (Q ? 5.9604645e-08f * 1.000001f * sqrtf(npf) : rho[p] * 1.000001f) + rmax_f;
+            const float snf = sqrtf(npf) * 1.000001f + snmax_f;
+            const float dl = coef_f * snf * snf;
+            float ub[CPL], lb[CPL];
+#pragma unroll
+            for (int h = 0; h < CPL; ++h) {
+                ub[h] = kInf;
+                lb[h] = kInf;
+                if (lane + 32 * h < nc) {
+                    const float a = sqrtf(cd[h] + dl) + rr;
+                    ub[h] = a * a * 1.00001f;
+                    const float lo = cd[h] - dl;
+                    const float r = lo > 0.f ? sqrtf(lo) * 0.99999f - rr : 0.f;
+                    lb[h] = r > 0.f ? r * r * 0.99999f : 0.f;
+                }
+            }
+            float U = kInf;   // k-th smallest ub (ties by candidate slot)
+            if (nc >= k) {
+                int rk[CPL];
+#pragma unroll
+                for (int h = 0; h < CPL; ++h) rk[h] = 0;
+                for (int c = 0; c < nc; ++c) {
+                    float oc = kInf;
+#pragma unroll
+                    for (int h = 0; h < CPL; ++h)
+                        if (c / 32 == h) oc = __shfl_sync(0xffffffffu, ub[h], c % 32);
+#pragma unroll
+                    for (int h = 0; h < CPL; ++h)
+                        if (oc < ub[h] || (oc == ub[h] && c < lane + 32 * h)) ++rk[h];
+                }
+#pragma unroll
+                for (int h = 0; h < CPL; ++h) {
+                    const unsigned kth = __ballot_sync(0xffffffffu, lane + 32 * h < nc && rk[h] == k - 1);
+                    if (kth) U = __shfl_sync(0xffffffffu, ub[h], __ffs(kth) - 1);
+                }
+            }
+            const float lim = U * keep_f;
+#pragma unroll
+            for (int h = 0; h < CPL; ++h)
+                need[h] = __ballot_sync(0xffffffffu, lane + 32 * h < nc && !(lb[h] > lim));
+        }
+        // exact float32 distances of the remaining candidates
         const float* xp = X + p * D;
         float myd[CPL];
 #pragma unroll
         for (int h = 0; h < CPL; ++h) myd[h] = kInf;
         for (int c = 0; c < nc; ++c) {
+            bool skip = true;
+#pragma unroll
+            for (int h = 0; h < CPL; ++h)
+                if (c / 32 == h) skip = ((need[h] >> (c % 32)) & 1u) == 0u;
+            if (skip) continue;   // warp-uniform
             int q = kNoIdx;
 #pragma unroll
             for (int h = 0; h < CPL; ++h)

@@ -55,12 +55,14 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 #define SLK_TC_NOBAR 1
 #endif
 
-// Survivors of one vote (VOTE columns) land on a buffer holding at most 15.
-// A 4-stage operand ring leaves room only for 16-column votes.
+// A vote checks VOTE columns at once; the survivors of APP columns land on a
+// buffer holding at most 15, which is merged when some lane holds 16 or
+// more.  A 4-stage operand ring leaves room only for appends of 16 columns.
 template <int EW> struct TcEpi {
     static constexpr int halves = EW / 4;             // column halves of a tile
-    static constexpr int vote = (EW == 8 || TC_STAGES > 3) ? 16 : 32;  // columns per vote
-    static constexpr int buf = 15 + vote;             // buffer slots per row and half
+    static constexpr int vote = (EW == 8) ? 16 : 32;  // columns per vote
+    static constexpr int app = (TC_STAGES > 3) ? 16 : vote;   // columns per append
+    static constexpr int buf = 15 + app;              // buffer slots per row and half
     static constexpr int threads = 64 + 32 * EW;
 };
 constexpr uint32_t A_BYTES = TC_M * TC_BK * 2;  // 16 KiB
@@ -288,7 +290,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                    const float* __restrict__ norms, int64_t N, int64_t Np, int Dp, int n_tiles,
                    int splits, int row_blocks, float* __restrict__ cand_d,
                    int32_t* __restrict__ cand_i, unsigned int* __restrict__ err_flag) {
-    constexpr int H = TcEpi<EW>::halves, VOTE = TcEpi<EW>::vote, NT = 32 * EW;
+    constexpr int H = TcEpi<EW>::halves, VOTE = TcEpi<EW>::vote, APP = TcEpi<EW>::app, NT = 32 * EW;
     constexpr int CH_PER_HALF = TC_N / 32 / H;   // 32-column TMEM loads per thread and tile
     extern __shared__ uint8_t smem_raw[];
     TcSmem<EW>& s = *reinterpret_cast<TcSmem<EW>*>(
@@ -482,18 +484,23 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         float mn = __int_as_float(0x7f800000);
 #pragma unroll
                         for (int j = 0; j < VOTE; ++j) mn = fminf(mn, v[g0 + j]);
-                        // rare path: some row of the warp has a distance below its threshold
+                        // rare path: some row of the warp has a distance below its
+                        // threshold (after a merge the threshold only drops, so the
+                        // stale one lets through entries the next merge discards)
                         if (__any_sync(0xffffffffu, mn < thr_d)) {
 #pragma unroll
-                            for (int j = 0; j < VOTE; ++j) {
-                                if (v[g0 + j] < thr_d) {
-                                    s.buf_d[h][cnt][r] = v[g0 + j];
-                                    s.buf_i[h][cnt][r] = (int)(col0 + ch * 32 + g0 + j);
-                                    ++cnt;
+                            for (int a0 = 0; a0 < VOTE; a0 += APP) {
+#pragma unroll
+                                for (int j = a0; j < a0 + APP; ++j) {
+                                    if (v[g0 + j] < thr_d) {
+                                        s.buf_d[h][cnt][r] = v[g0 + j];
+                                        s.buf_i[h][cnt][r] = (int)(col0 + ch * 32 + g0 + j);
+                                        ++cnt;
+                                    }
                                 }
+                                if (__any_sync(0xffffffffu, cnt >= 16))
+                                    flush_buffer<TC_KC, EW>(s, h, r, cnt, ld, li);
                             }
-                            if (__any_sync(0xffffffffu, cnt >= 16))
-                                flush_buffer<TC_KC, EW>(s, h, r, cnt, ld, li);
                         }
                     }
                 };
