@@ -494,7 +494,7 @@ __device__ __forceinline__ float exact_d2(const float* __restrict__ xp,
 // the float32 operand (rho <= u ||v||), failures appended to fb_list /
 // *count_out.
 template <int KC, bool Q>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, int splits,
                   int64_t Np, const float* __restrict__ cand_d, const int32_t* __restrict__ cand_i,
                   const float* __restrict__ norms, const float* __restrict__ rho, float u_acc,
@@ -594,10 +594,12 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
         // distance.  With |dt - |xt_p - xt_q|^2| <= delta and
         // |xt - (x - mu)| <= rho, the exact distance of candidate c lies in
         // [lb_c, ub_c] = [(sqrt(dt - delta) - rho_p - rho_max)^2,
-        // (sqrt(dt + delta) + rho_p + rho_max)^2]; if lb_c exceeds the k-th
-        // smallest ub (by more than the float32 rounding of the exact sums),
-        // k candidates beat c whatever the rounding.  Skipped candidates keep
-        // an infinite distance, so they rank after every computed one and the
+        // (sqrt(dt + delta) + rho_p + rho_max)^2].  Both bounds grow with dt
+        // and the candidates come in increasing dt, so the k-th smallest ub
+        // is that of candidate k - 1; a candidate whose lb exceeds it (by
+        // more than the float32 rounding of the exact sums) is beaten by k
+        // candidates whatever the rounding.  Skipped candidates keep an
+        // infinite distance, so they rank after every computed one and the
         // k nearest, their distances and the certificate are unchanged.
         unsigned need[CPL];
         {
@@ -605,43 +607,27 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
             const float rr = (Q ? 5.9604645e-08f * 1.000001f * sqrtf(npf) : rho[p] * 1.000001f) + rmax_f;
             const float snf = sqrtf(npf) * 1.000001f + snmax_f;
             const float dl = coef_f * snf * snf;
-            float ub[CPL], lb[CPL];
-#pragma unroll
-            for (int h = 0; h < CPL; ++h) {
-                ub[h] = kInf;
-                lb[h] = kInf;
-                if (lane + 32 * h < nc) {
-                    const float a = sqrtf(cd[h] + dl) + rr;
-                    ub[h] = a * a * 1.00001f;
-                    const float lo = cd[h] - dl;
-                    const float r = lo > 0.f ? sqrtf(lo) * 0.99999f - rr : 0.f;
-                    lb[h] = r > 0.f ? r * r * 0.99999f : 0.f;
-                }
-            }
-            float U = kInf;   // k-th smallest ub (ties by candidate slot)
+            float U = kInf;
             if (nc >= k) {
-                int rk[CPL];
+                float dkt = kInf;
 #pragma unroll
-                for (int h = 0; h < CPL; ++h) rk[h] = 0;
-                for (int c = 0; c < nc; ++c) {
-                    float oc = kInf;
-#pragma unroll
-                    for (int h = 0; h < CPL; ++h)
-                        if (c / 32 == h) oc = __shfl_sync(0xffffffffu, ub[h], c % 32);
-#pragma unroll
-                    for (int h = 0; h < CPL; ++h)
-                        if (oc < ub[h] || (oc == ub[h] && c < lane + 32 * h)) ++rk[h];
-                }
-#pragma unroll
-                for (int h = 0; h < CPL; ++h) {
-                    const unsigned kth = __ballot_sync(0xffffffffu, lane + 32 * h < nc && rk[h] == k - 1);
-                    if (kth) U = __shfl_sync(0xffffffffu, ub[h], __ffs(kth) - 1);
-                }
+                for (int h = 0; h < CPL; ++h)
+                    if ((k - 1) / 32 == h) dkt = __shfl_sync(0xffffffffu, cd[h], (k - 1) % 32);
+                const float a = sqrtf(dkt + dl) + rr;
+                U = a * a * 1.00001f;
             }
             const float lim = U * keep_f;
 #pragma unroll
-            for (int h = 0; h < CPL; ++h)
-                need[h] = __ballot_sync(0xffffffffu, lane + 32 * h < nc && !(lb[h] > lim));
+            for (int h = 0; h < CPL; ++h) {
+                bool keep = false;
+                if (lane + 32 * h < nc) {
+                    const float lo = cd[h] - dl;
+                    const float r = lo > 0.f ? sqrtf(lo) * 0.99999f - rr : 0.f;
+                    const float lb = r > 0.f ? r * r * 0.99999f : 0.f;
+                    keep = !(lb > lim);
+                }
+                need[h] = __ballot_sync(0xffffffffu, keep);
+            }
         }
         // exact float32 distances of the remaining candidates
         const float* xp = X + p * D;

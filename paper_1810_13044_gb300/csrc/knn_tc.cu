@@ -5,6 +5,10 @@
 // the 5th-generation tensor cores, and keeps per row the KC smallest
 // (dt, q) of a column split -- the same contract as the float32 SIMT
 // candidate kernel; the exact float32 rerank and its certificate follow.
+// The epilogue forms w = fl(||xt_q||^2 - 2 dot) and compares it with the
+// row's threshold less ||xt_p||^2 rounded upward, so that a rejected column
+// has dt = fl(w + ||xt_p||^2) >= threshold; the survivors store that dt
+// (two roundings, as fl(-2 dot + fl(||xt_p||^2 + ||xt_q||^2)) had).
 //
 // One persistent CTA per SM:
 //   warp 0      TMA producer: 64-wide K slices of the A (128 rows) and B
@@ -55,35 +59,49 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 #define SLK_TC_NOBAR 1
 #endif
 
+// CTA pairs (cta_group::2) for the KC = 32 kernel: the two CTAs of a cluster
+// share one 256 x 256 MMA tile, each loading its own 128 A rows and half of
+// the B tile, so that an SM takes 32 KiB instead of 48 KiB from L2 per K slice.
+#ifndef SLK_TC_PAIR
+#define SLK_TC_PAIR 0
+#endif
+#ifndef SLK_TC_PAIR_STAGES
+#define SLK_TC_PAIR_STAGES 4
+#endif
+constexpr uint32_t A_BYTES = TC_M * TC_BK * 2;  // 16 KiB
+constexpr uint32_t B_BYTES = TC_N * TC_BK * 2;  // 32 KiB
+
 // A vote checks VOTE columns at once; the survivors of APP columns land on a
 // buffer holding at most 15, which is merged when some lane holds 16 or
-// more.  A 4-stage operand ring leaves room only for appends of 16 columns.
-template <int EW> struct TcEpi {
+// more.  A 4-stage ring of whole B tiles leaves room only for appends of 16
+// columns; with CTA pairs a stage holds half a B tile.
+template <int EW, bool PAIR = false> struct TcEpi {
+    static constexpr int stages = PAIR ? SLK_TC_PAIR_STAGES : TC_STAGES;
+    static constexpr uint32_t b_bytes = PAIR ? B_BYTES / 2 : B_BYTES;
     static constexpr int halves = EW / 4;             // column halves of a tile
     static constexpr int vote = (EW == 8) ? 16 : 32;  // columns per vote
-    static constexpr int app = (TC_STAGES > 3) ? 16 : vote;   // columns per append
+    static constexpr int app = (!PAIR && TC_STAGES > 3) ? 16 : vote;   // columns per append
     static constexpr int buf = 15 + app;              // buffer slots per row and half
     static constexpr int threads = 64 + 32 * EW;
 };
-constexpr uint32_t A_BYTES = TC_M * TC_BK * 2;  // 16 KiB
-constexpr uint32_t B_BYTES = TC_N * TC_BK * 2;  // 32 KiB
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 constexpr int kNoIdx = 0x7fffffff;
 
-template <int EW>
+template <int EW, bool PAIR = false>
 struct TcSmem {
-    uint8_t a[TC_STAGES][A_BYTES];   // 1024-byte aligned stages (swizzle atoms)
-    uint8_t b[TC_STAGES][B_BYTES];
-    float buf_d[TcEpi<EW>::halves][TcEpi<EW>::buf][TC_M];   // per-row append buffer
-    int buf_i[TcEpi<EW>::halves][TcEpi<EW>::buf][TC_M];
+    using E = TcEpi<EW, PAIR>;
+    uint8_t a[E::stages][A_BYTES];   // 1024-byte aligned stages (swizzle atoms)
+    uint8_t b[E::stages][E::b_bytes];
+    float buf_d[E::halves][E::buf][TC_M];   // per-row append buffer
+    int buf_i[E::halves][E::buf][TC_M];
     float ncol[2][TC_N];             // column norms of the tile in each accumulator
-    unsigned long long full[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2];
+    unsigned long long full[E::stages], empty[E::stages], tfull[2], tempty[2];
     uint32_t tmem_base;
     int abort;
 };
-template <int EW>
-constexpr size_t tc_smem_bytes() { return sizeof(TcSmem<EW>) + 1024; }
+template <int EW, bool PAIR = false>
+constexpr size_t tc_smem_bytes() { return sizeof(TcSmem<EW, PAIR>) + 1024; }
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -106,13 +124,23 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* b, uint32_t parity
         : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
     return ok != 0;
 }
+// the same with cluster-scope acquire (arrivals from the peer CTA)
+__device__ __forceinline__ bool mbar_test_cl(unsigned long long* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
 // Bounded wait for phase `parity` of barrier b.  Gives up (false) after
 // kWaitNs or once another role has raised abort.
+template <bool CL = false>
 __device__ __noinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, volatile int* abort) {
-    if (mbar_test(b, parity)) return true;
+    if (CL ? mbar_test_cl(b, parity) : mbar_test(b, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     while (true) {
-        if (mbar_test(b, parity)) return true;
+        if (CL ? mbar_test_cl(b, parity) : mbar_test(b, parity)) return true;
         if (*abort) return false;
         if (globaltimer_ns() - t0 > kWaitNs) {
             *abort = 1;
@@ -163,6 +191,55 @@ __device__ __forceinline__ void umma_commit(unsigned long long* bar) {
             su32(bar))
         : "memory");
 }
+// CTA-pair forms.  The leader (rank 0 of the cluster) issues the M = 256
+// MMAs over both CTAs' A rows and B halves (same shared-memory offsets);
+// each CTA's TMEM receives its own 128 rows.  Commits arrive on the barrier
+// at the same offset in both CTAs; the loads of both CTAs complete on the
+// leader's stage barrier.
+constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                                ((uint32_t)((2 * TC_M) >> 4) << 24);
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ uint32_t mapa_rank(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(su32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cl_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_addr)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cl,
+                                                 int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cl), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdescPair), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit_pair(unsigned long long* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(su32(bar)), "h"((unsigned short)3)
+        : "memory");
+}
+
 // tcgen05.ld of 32 columns without the wait: the registers are valid only
 // after tmem_wait_regs on the same array, which names them as in/out
 // operands so that no use can be scheduled before the wait.
@@ -258,8 +335,8 @@ __device__ __forceinline__ void merge_topk(float (&ld)[KC], int (&li)[KC], const
 }
 
 // Warp-synchronous: fold every lane's buffered entries into its top-KC.
-template <int KC, int EW>
-__device__ __forceinline__ void flush_buffer(TcSmem<EW>& s, int h, int r, int& cnt,
+template <int KC, class S>
+__device__ __forceinline__ void flush_buffer(S& s, int h, int r, int& cnt,
                                              float (&ld)[KC], int (&li)[KC]) {
     for (int base = 0; __any_sync(0xffffffffu, cnt > base); base += 32) {
         float bd[32];
@@ -284,47 +361,64 @@ __device__ __forceinline__ void item_range(int item, int splits, int n_tiles, in
     t1 = (int)((int64_t)(sp + 1) * n_tiles / splits);
 }
 
-template <int TC_KC, int EW, bool PIPE, bool NOBAR>
-__global__ void __launch_bounds__(TcEpi<EW>::threads, 1)
+// PAIR: launched in clusters of two; an item's row block is a pair of
+// 128-row blocks (rank r of the cluster takes block 2 rb + r), both CTAs walk
+// the same items, and only the leader's MMA warp issues.
+template <int TC_KC, int EW, bool PIPE, bool NOBAR, bool PAIR = false>
+__global__ void __launch_bounds__(TcEpi<EW, PAIR>::threads, 1)
 knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const float* __restrict__ norms, int64_t N, int64_t Np, int Dp, int n_tiles,
                    int splits, int row_blocks, float* __restrict__ cand_d,
                    int32_t* __restrict__ cand_i, unsigned int* __restrict__ err_flag) {
-    constexpr int H = TcEpi<EW>::halves, VOTE = TcEpi<EW>::vote, APP = TcEpi<EW>::app, NT = 32 * EW;
+    using E = TcEpi<EW, PAIR>;
+    constexpr int STAGES = E::stages;
+    constexpr int H = E::halves, VOTE = E::vote, APP = E::app, NT = 32 * EW;
     constexpr int CH_PER_HALF = TC_N / 32 / H;   // 32-column TMEM loads per thread and tile
     extern __shared__ uint8_t smem_raw[];
-    TcSmem<EW>& s = *reinterpret_cast<TcSmem<EW>*>(
+    TcSmem<EW, PAIR>& s = *reinterpret_cast<TcSmem<EW, PAIR>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = Dp / TC_BK;
-    const int n_items = row_blocks * splits;
-    // each CTA takes a contiguous range of items, so consecutive items mostly
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;
+    const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;      // CTA or cluster
+    const int n_units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    const int n_items = (PAIR ? row_blocks / 2 : row_blocks) * splits;
+    // each unit takes a contiguous range of items, so consecutive items mostly
     // continue the same row block (the epilogue then keeps its lists going)
-    const int item_begin = (int)((int64_t)blockIdx.x * n_items / gridDim.x);
-    const int item_end = (int)((int64_t)(blockIdx.x + 1) * n_items / gridDim.x);
+    const int item_begin = (int)((int64_t)unit * n_items / n_units);
+    const int item_end = (int)((int64_t)(unit + 1) * n_items / n_units);
     volatile int* abort = &s.abort;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < TC_STAGES; ++i) {
+        for (int i = 0; i < STAGES; ++i) {
             mbar_init(&s.full[i], 1);
             mbar_init(&s.empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&s.tfull[i], 1);
-            mbar_init(&s.tempty[i], EW);
+            mbar_init(&s.tempty[i], PAIR ? 2 * EW : EW);
         }
         s.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         su32(&s.tmem_base)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if constexpr (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             su32(&s.tmem_base)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             su32(&s.tmem_base)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) cluster_sync_all();   // barriers and TMEM of both CTAs are ready
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s.tmem_base;
 
@@ -338,31 +432,50 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             for (int item = item_begin; item < item_end && ok; ++item) {
                 int rb, t0, t1, sp;
                 item_range(item, splits, n_tiles, rb, t0, t1, sp);
+                const int arow = (PAIR ? 2 * rb + (int)rank : rb) * TC_M;
                 for (int t = t0; t < t1 && ok; ++t) {
+                    const int bcol = t * TC_N + (int)rank * (TC_N / 2);   // rank 0 unless PAIR
                     for (int kb = 0; kb < nkb; ++kb) {
-                        const uint32_t st = iter % TC_STAGES, use = iter / TC_STAGES;
+                        const uint32_t st = iter % STAGES, use = iter / STAGES;
                         if (use > 0 && !(ok = mbar_wait(&s.empty[st], (use - 1) & 1, abort))) break;
-                        mbar_expect_tx(&s.full[st], A_BYTES + B_BYTES);
-                        tma_load_2d(s.a[st], &tmA, &s.full[st], kb * TC_BK, rb * TC_M);
-                        tma_load_2d(s.b[st], &tmB, &s.full[st], kb * TC_BK, t * TC_N);
+                        if constexpr (PAIR) {
+                            // both CTAs' loads complete on the leader's barrier, whose
+                            // one arrival (the leader's) expects the bytes of both
+                            const uint32_t bar = mapa_rank(&s.full[st], 0);
+                            if (rank == 0) mbar_expect_tx(&s.full[st], 2 * (A_BYTES + E::b_bytes));
+                            tma_load_2d_pair(s.a[st], &tmA, bar, kb * TC_BK, arow);
+                            tma_load_2d_pair(s.b[st], &tmB, bar, kb * TC_BK, bcol);
+                        } else {
+                            mbar_expect_tx(&s.full[st], A_BYTES + B_BYTES);
+                            tma_load_2d(s.a[st], &tmA, &s.full[st], kb * TC_BK, arow);
+                            tma_load_2d(s.b[st], &tmB, &s.full[st], kb * TC_BK, bcol);
+                        }
                         ++iter;
                     }
                 }
             }
             // drain: every issued load must have landed before the CTA leaves
             if (!ok || *abort) {
-                const uint32_t first = iter > TC_STAGES ? iter - TC_STAGES : 0;
-                for (uint32_t i = first; i < iter; ++i) {
+                if (!PAIR || rank == 0) {
+                    const uint32_t first = iter > STAGES ? iter - STAGES : 0;
+                    for (uint32_t i = first; i < iter; ++i) {
+                        const unsigned long long t0 = globaltimer_ns();
+                        while (!mbar_test(&s.full[i % STAGES], (i / STAGES) & 1) &&
+                               globaltimer_ns() - t0 < kWaitNs) {
+                        }
+                    }
+                } else {
+                    // the peer's loads complete on the leader's barriers: give
+                    // them time to land (a load takes microseconds)
                     const unsigned long long t0 = globaltimer_ns();
-                    while (!mbar_test(&s.full[i % TC_STAGES], (i / TC_STAGES) & 1) &&
-                           globaltimer_ns() - t0 < kWaitNs) {
+                    while (globaltimer_ns() - t0 < 1000000ull) {
                     }
                 }
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        if (lane == 0 && rank == 0) {
             uint32_t iter = 0, tcount = 0;
             bool ok = true;
             for (int item = item_begin; item < item_end && ok; ++item) {
@@ -370,24 +483,32 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 item_range(item, splits, n_tiles, rb, t0, t1, sp);
                 for (int t = t0; t < t1 && ok; ++t) {
                     const uint32_t acc = tcount & 1, use = tcount >> 1;
-                    if (use > 0 && !(ok = mbar_wait(&s.tempty[acc], (use - 1) & 1, abort))) break;
+                    // with CTA pairs the epilogues of both CTAs release the accumulator
+                    if (use > 0 && !(ok = mbar_wait<PAIR>(&s.tempty[acc], (use - 1) & 1, abort))) break;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + acc * TC_N;
                     for (int kb = 0; kb < nkb; ++kb) {
-                        const uint32_t st = iter % TC_STAGES;
-                        if (!(ok = mbar_wait(&s.full[st], (iter / TC_STAGES) & 1, abort))) break;
+                        const uint32_t st = iter % STAGES;
+                        if (!(ok = mbar_wait(&s.full[st], (iter / STAGES) & 1, abort))) break;
                         tc_fence_after();
                         const uint64_t da = sw128_desc(su32(s.a[st]));
                         const uint64_t db = sw128_desc(su32(s.b[st]));
 #pragma unroll
-                        for (int k = 0; k < TC_BK / 16; ++k)   // 32-byte steps inside the swizzle row
-                            umma(d_tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
-                                 (kb | k) != 0 ? 1u : 0u);
-                        umma_commit(&s.empty[st]);
+                        for (int k = 0; k < TC_BK / 16; ++k) {   // 32-byte steps inside the swizzle row
+                            if constexpr (PAIR)
+                                umma_pair(d_tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
+                                          (kb | k) != 0 ? 1u : 0u);
+                            else
+                                umma(d_tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
+                                     (kb | k) != 0 ? 1u : 0u);
+                        }
+                        if constexpr (PAIR) umma_commit_pair(&s.empty[st]);
+                        else umma_commit(&s.empty[st]);
                         ++iter;
                     }
                     if (!ok) break;
-                    umma_commit(&s.tfull[acc]);
+                    if constexpr (PAIR) umma_commit_pair(&s.tfull[acc]);
+                    else umma_commit(&s.tfull[acc]);
                     ++tcount;
                 }
             }
@@ -396,7 +517,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 if (iter > 0) {
                     const uint32_t i = iter - 1;
                     const unsigned long long t0 = globaltimer_ns();
-                    while (!mbar_test(&s.empty[i % TC_STAGES], (i / TC_STAGES) & 1) &&
+                    while (!mbar_test(&s.empty[i % STAGES], (i / STAGES) & 1) &&
                            globaltimer_ns() - t0 < kWaitNs) {
                     }
                 }
@@ -417,7 +538,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         for (int item = item_begin; item < item_end && ok; ++item) {
             int rb, t0, t1, sp;
             item_range(item, splits, n_tiles, rb, t0, t1, sp);
-            const int64_t p = (int64_t)rb * TC_M + r;
+            const int64_t p = (int64_t)(PAIR ? 2 * rb + (int)rank : rb) * TC_M + r;
             if (rb != run_rb) {
                 // a new row block: the list restarts (the previous one was written)
 #pragma unroll
@@ -462,44 +583,59 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 // columns against the row's threshold (the row's own column,
                 // distance ~0, is kept here and dropped by the rerank)
                 auto process = [&](const uint32_t (&rv)[32], int ch) {
-                    float v[32];
+                    float v[32];   // w = fl(||xt_q||^2 - 2 dot)
                     if constexpr (NOBAR) {
                         const float4* n4 = reinterpret_cast<const float4*>(ncol_g + ch * 32);
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
                             const float4 c4 = __ldg(n4 + q);
-                            v[4 * q + 0] = fmaf(-2.f, __uint_as_float(rv[4 * q + 0]), np_ + c4.x);
-                            v[4 * q + 1] = fmaf(-2.f, __uint_as_float(rv[4 * q + 1]), np_ + c4.y);
-                            v[4 * q + 2] = fmaf(-2.f, __uint_as_float(rv[4 * q + 2]), np_ + c4.z);
-                            v[4 * q + 3] = fmaf(-2.f, __uint_as_float(rv[4 * q + 3]), np_ + c4.w);
+                            v[4 * q + 0] = fmaf(-2.f, __uint_as_float(rv[4 * q + 0]), c4.x);
+                            v[4 * q + 1] = fmaf(-2.f, __uint_as_float(rv[4 * q + 1]), c4.y);
+                            v[4 * q + 2] = fmaf(-2.f, __uint_as_float(rv[4 * q + 2]), c4.z);
+                            v[4 * q + 3] = fmaf(-2.f, __uint_as_float(rv[4 * q + 3]), c4.w);
                         }
                     } else {
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
-                            v[j] = fmaf(-2.f, __uint_as_float(rv[j]), np_ + s.ncol[acc][ch * 32 + j]);
+                            v[j] = fmaf(-2.f, __uint_as_float(rv[j]), s.ncol[acc][ch * 32 + j]);
                     }
 #pragma unroll
                     for (int g0 = 0; g0 < 32; g0 += VOTE) {
-                        const float thr_d = ld[TC_KC - 1];
-                        float mn = __int_as_float(0x7f800000);
+                        // w < thr - ||xt_p||^2 (rounded up) whenever dt < thr; a
+                        // padding row (infinite norm) gets NaN and never passes
+                        const float thr_w = __fsub_ru(ld[TC_KC - 1], np_);
+                        float m8[VOTE / 8];
 #pragma unroll
-                        for (int j = 0; j < VOTE; ++j) mn = fminf(mn, v[g0 + j]);
-                        // rare path: some row of the warp has a distance below its
-                        // threshold (after a merge the threshold only drops, so the
-                        // stale one lets through entries the next merge discards)
-                        if (__any_sync(0xffffffffu, mn < thr_d)) {
+                        for (int q = 0; q < VOTE / 8; ++q) {
+                            m8[q] = v[g0 + 8 * q];
+#pragma unroll
+                            for (int j = 1; j < 8; ++j) m8[q] = fminf(m8[q], v[g0 + 8 * q + j]);
+                        }
+                        float mn = m8[0];
+#pragma unroll
+                        for (int q = 1; q < VOTE / 8; ++q) mn = fminf(mn, m8[q]);
+                        // some row of the warp may have a distance below its threshold:
+                        // narrow down by groups of 8 columns (warp-uniform branches),
+                        // then append per lane
+                        if (__any_sync(0xffffffffu, mn < thr_w)) {
 #pragma unroll
                             for (int a0 = 0; a0 < VOTE; a0 += APP) {
 #pragma unroll
-                                for (int j = a0; j < a0 + APP; ++j) {
-                                    if (v[g0 + j] < thr_d) {
-                                        s.buf_d[h][cnt][r] = v[g0 + j];
-                                        s.buf_i[h][cnt][r] = (int)(col0 + ch * 32 + g0 + j);
-                                        ++cnt;
+                                for (int q = a0 / 8; q < (a0 + APP) / 8; ++q) {
+                                    if (!__any_sync(0xffffffffu, m8[q] < thr_w)) continue;
+#pragma unroll
+                                    for (int j = g0 + 8 * q; j < g0 + 8 * q + 8; ++j) {
+                                        if (v[j] < thr_w) {
+                                            s.buf_d[h][cnt][r] = __fadd_rn(v[j], np_);
+                                            s.buf_i[h][cnt][r] = (int)(col0 + ch * 32 + j);
+                                            ++cnt;
+                                        }
                                     }
                                 }
+                                // after a merge the threshold only drops: the stale one
+                                // lets through entries the next merge discards
                                 if (__any_sync(0xffffffffu, cnt >= 16))
-                                    flush_buffer<TC_KC, EW>(s, h, r, cnt, ld, li);
+                                    flush_buffer<TC_KC>(s, h, r, cnt, ld, li);
                             }
                         }
                     }
@@ -507,7 +643,10 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 auto release = [&]() {   // this warp's last TMEM read of the tile is done
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&s.tempty[acc]);
+                    if (lane == 0) {
+                        if constexpr (PAIR) mbar_arrive_remote(mapa_rank(&s.tempty[acc], 0));
+                        else mbar_arrive(&s.tempty[acc]);
+                    }
                 };
                 const int ch0 = h * CH_PER_HALF;
                 if constexpr (PIPE) {
@@ -546,7 +685,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 item_range(item + 1, splits, n_tiles, next_rb, t0n, t1n, spn);
             }
             if (next_rb != rb) {
-                flush_buffer<TC_KC, EW>(s, h, r, cnt, ld, li);
+                flush_buffer<TC_KC>(s, h, r, cnt, ld, li);
                 const int64_t o = ((int64_t)(run_sp * H + h) * Np + p) * TC_KC;
 #pragma unroll
                 for (int x = 0; x < TC_KC; ++x) {
@@ -558,12 +697,20 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     }
 
     tc_fence_before();
-    __syncthreads();
+    // with CTA pairs neither CTA leaves while the other may still reach its
+    // shared memory (remote arrivals, commits, loads) or TMEM
+    if constexpr (PAIR) cluster_sync_all();
+    else __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TMEM_COLS)
-                     : "memory");
+        if constexpr (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                         "r"(TMEM_COLS)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                         "r"(TMEM_COLS)
+                         : "memory");
     }
     if (threadIdx.x == 0 && s.abort) atomicOr(err_flag, 2u);
 }
@@ -628,7 +775,38 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
     const int n_items = row_blocks * splits;
     int grid = ctx->num_sms;
     if (grid > n_items) grid = n_items;
-    if (kc == 32) {
+    if (kc == 32 && SLK_TC_PAIR != 0 && row_blocks % 2 == 0) {
+        // CTA pairs: clusters of two over 256-row blocks, B tiles in halves
+        CUtensorMap tb2;
+        const cuuint32_t box_b2[2] = {TC_BK, TC_N / 2};
+        CUresult r3 = enc(&tb2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)xt, dims, strides, box_b2,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r3 != CUDA_SUCCESS)
+            return set_err(ctx, SLK_ERR_CUDA, "tensor map encoding failed (%d)", (int)r3);
+        auto kern = knn_cand_tc_kernel<32, 4, false, true, true>;
+        const size_t smem = tc_smem_bytes<4, true>();
+        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        const int pair_items = (row_blocks / 2) * splits;
+        int clusters = ctx->num_sms / 2;
+        if (clusters > pair_items) clusters = pair_items;
+        if (clusters < 1) clusters = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(2 * clusters));
+        cfg.blockDim = dim3(TcEpi<4, true>::threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = ctx->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        SLK_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, ta, tb2, norms, N, Np, Dp, n_tiles, splits,
+                                             row_blocks, cand_d, cand_i, err_flag));
+    } else if (kc == 32) {
         constexpr int EW = SLK_TC_EW32;
         auto kern = knn_cand_tc_kernel<32, EW, SLK_TC_PIPE != 0, SLK_TC_NOBAR != 0>;
         const size_t smem = tc_smem_bytes<EW>();
