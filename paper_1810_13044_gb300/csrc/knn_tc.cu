@@ -71,26 +71,32 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 constexpr uint32_t A_BYTES = TC_M * TC_BK * 2;  // 16 KiB
 constexpr uint32_t B_BYTES = TC_N * TC_BK * 2;  // 32 KiB
 
-// A vote checks VOTE columns at once; the survivors of APP columns land on a
-// buffer holding at most 15, which is merged when some lane holds 16 or
-// more.  A 4-stage ring of whole B tiles leaves room only for appends of 16
-// columns; with CTA pairs a stage holds half a B tile.
-template <int EW, bool PAIR = false> struct TcEpi {
+// A vote checks VOTE columns at once and the survivors of APP columns are
+// appended to a per-row buffer of BUF slots.  The buffer is merged into the
+// sorted list once the tile's accumulator has been released, when some lane
+// holds 16 or more; inside a tile only when it could otherwise overflow, so
+// that merges rarely hold TMEM while the MMA waits for it.  A 4-stage ring of
+// whole B tiles leaves room only for appends of 16 columns and 31 slots; with
+// CTA pairs a stage holds half a B tile.
+template <int EW, bool PAIR = false, int KC = 32> struct TcEpi {
     static constexpr int stages = PAIR ? SLK_TC_PAIR_STAGES : TC_STAGES;
     static constexpr uint32_t b_bytes = PAIR ? B_BYTES / 2 : B_BYTES;
     static constexpr int halves = EW / 4;             // column halves of a tile
     static constexpr int vote = (EW == 8) ? 16 : 32;  // columns per vote
-    static constexpr int app = (!PAIR && TC_STAGES > 3) ? 16 : vote;   // columns per append
-    static constexpr int buf = 15 + app;              // buffer slots per row and half
+    static constexpr bool tight = !PAIR && TC_STAGES > 3;
+    // KC = 64 (an epilogue-bound kernel at small D) merges right away instead
+    static constexpr bool defer = (KC == 32) && !tight;
+    static constexpr int app = tight ? 16 : vote;     // columns per append
+    static constexpr int buf = defer ? 31 + app : 15 + app;   // buffer slots per row and half
     static constexpr int threads = 64 + 32 * EW;
 };
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 constexpr int kNoIdx = 0x7fffffff;
 
-template <int EW, bool PAIR = false>
+template <int EW, bool PAIR = false, int KC = 32>
 struct TcSmem {
-    using E = TcEpi<EW, PAIR>;
+    using E = TcEpi<EW, PAIR, KC>;
     uint8_t a[E::stages][A_BYTES];   // 1024-byte aligned stages (swizzle atoms)
     uint8_t b[E::stages][E::b_bytes];
     float buf_d[E::halves][E::buf][TC_M];   // per-row append buffer
@@ -100,8 +106,8 @@ struct TcSmem {
     uint32_t tmem_base;
     int abort;
 };
-template <int EW, bool PAIR = false>
-constexpr size_t tc_smem_bytes() { return sizeof(TcSmem<EW, PAIR>) + 1024; }
+template <int EW, bool PAIR = false, int KC = 32>
+constexpr size_t tc_smem_bytes() { return sizeof(TcSmem<EW, PAIR, KC>) + 1024; }
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -365,17 +371,17 @@ __device__ __forceinline__ void item_range(int item, int splits, int n_tiles, in
 // 128-row blocks (rank r of the cluster takes block 2 rb + r), both CTAs walk
 // the same items, and only the leader's MMA warp issues.
 template <int TC_KC, int EW, bool PIPE, bool NOBAR, bool PAIR = false>
-__global__ void __launch_bounds__(TcEpi<EW, PAIR>::threads, 1)
+__global__ void __launch_bounds__(TcEpi<EW, PAIR, TC_KC>::threads, 1)
 knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const float* __restrict__ norms, int64_t N, int64_t Np, int Dp, int n_tiles,
                    int splits, int row_blocks, float* __restrict__ cand_d,
                    int32_t* __restrict__ cand_i, unsigned int* __restrict__ err_flag) {
-    using E = TcEpi<EW, PAIR>;
+    using E = TcEpi<EW, PAIR, TC_KC>;
     constexpr int STAGES = E::stages;
     constexpr int H = E::halves, VOTE = E::vote, APP = E::app, NT = 32 * EW;
     constexpr int CH_PER_HALF = TC_N / 32 / H;   // 32-column TMEM loads per thread and tile
     extern __shared__ uint8_t smem_raw[];
-    TcSmem<EW, PAIR>& s = *reinterpret_cast<TcSmem<EW, PAIR>*>(
+    TcSmem<EW, PAIR, TC_KC>& s = *reinterpret_cast<TcSmem<EW, PAIR, TC_KC>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = Dp / TC_BK;
@@ -620,6 +626,11 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         if (__any_sync(0xffffffffu, mn < thr_w)) {
 #pragma unroll
                             for (int a0 = 0; a0 < VOTE; a0 += APP) {
+                                // room for APP more entries
+                                if constexpr (E::defer) {
+                                    if (__any_sync(0xffffffffu, cnt > E::buf - APP))
+                                        flush_buffer<TC_KC>(s, h, r, cnt, ld, li);
+                                }
 #pragma unroll
                                 for (int q = a0 / 8; q < (a0 + APP) / 8; ++q) {
                                     if (!__any_sync(0xffffffffu, m8[q] < thr_w)) continue;
@@ -632,10 +643,12 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                                         }
                                     }
                                 }
-                                // after a merge the threshold only drops: the stale one
-                                // lets through entries the next merge discards
-                                if (__any_sync(0xffffffffu, cnt >= 16))
-                                    flush_buffer<TC_KC>(s, h, r, cnt, ld, li);
+                                if constexpr (!E::defer) {
+                                    // merge right away (the threshold only drops: the stale
+                                    // one lets through entries the next merge discards)
+                                    if (__any_sync(0xffffffffu, cnt >= 16))
+                                        flush_buffer<TC_KC>(s, h, r, cnt, ld, li);
+                                }
                             }
                         }
                     }
@@ -674,6 +687,11 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     if (cc == CH_PER_HALF - 1) release();
                     process(rv, ch0 + cc);
                 }
+                }
+                // merge with the accumulator released (the threshold only drops,
+                // so the stale one let through entries the merge discards)
+                if constexpr (E::defer) {
+                    if (__any_sync(0xffffffffu, cnt >= 16)) flush_buffer<TC_KC>(s, h, r, cnt, ld, li);
                 }
                 ++tcount;
             }
@@ -816,10 +834,10 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
             ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
     } else {
         auto kern = knn_cand_tc_kernel<64, 4, false, false>;
-        const size_t smem = tc_smem_bytes<4>();
+        const size_t smem = tc_smem_bytes<4, false, 64>();
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem));
-        kern<<<grid, TcEpi<4>::threads, smem, ctx->stream>>>(
+        kern<<<grid, TcEpi<4, false, 64>::threads, smem, ctx->stream>>>(
             ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
     }
     SLK_LAUNCH_CHECK(ctx, "knn_cand_tc_kernel");
