@@ -57,6 +57,7 @@ __global__ void col_sum_kernel(const float* __restrict__ X, int64_t N, int D,
     if (c < D) {
         int n = 0;
         float part = 0.f;
+#pragma unroll 8
         for (int64_t r = r0 + threadIdx.y; r < r1; r += 8) {
             part += X[r * D + c];
             if (++n == 64) { acc += (double)part; part = 0.f; n = 0; }
@@ -103,6 +104,7 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
     for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < Np;
          p += nw) {
         float n2 = 0.f, e2 = 0.f, v2 = 0.f;
+#pragma unroll 4
         for (int j = lane; j < Dp; j += 32) {
             float v = 0.f, vv = 0.f;
             if (p < N && j < D) v = X[p * D + j] - __ldg(mu + j);
@@ -1009,14 +1011,14 @@ slk_status knn_prep_fp32_launch(slk_ctx* ctx, const float* X, int64_t N, int D, 
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(colsum, 0, sizeof(double) * D, s));
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_bits, 0, 2 * sizeof(unsigned int), s));
     SLK_COUNT_LAUNCH(ctx, 2);
-    int gy = (int)((N + 4095) / 4096);
-    if (gy > 1024) gy = 1024;
+    int gy = (int)((N + 511) / 512);   // 64 rows per thread
+    if (gy > 8192) gy = 8192;
     if (gy < 1) gy = 1;
     col_sum_kernel<<<dim3((unsigned)((D + 31) / 32), (unsigned)gy), dim3(32, 8), 0, s>>>(X, N, D, colsum);
     mu_kernel<<<(D + 255) / 256, 256, 0, s>>>(colsum, N, D, mu);
     SLK_LAUNCH_CHECK(ctx, "col_sum_kernel");
     int64_t pg = (Np + 7) / 8;
-    if (pg > (int64_t)ctx->num_sms * 16) pg = (int64_t)ctx->num_sms * 16;
+    if (pg > (int64_t)ctx->num_sms * 64) pg = (int64_t)ctx->num_sms * 64;
     prep_rows_kernel<<<(unsigned)pg, 256, 0, s>>>(X, N, D, Dp, Np, mu, 0, xt, nullptr, norms,
                                                    rho, nullptr, st);
     SLK_LAUNCH_CHECK(ctx, "prep_rows_kernel");
@@ -1048,15 +1050,15 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     {
         PhaseScope ps(ctx, SLK_PHASE_KNN_PREP);
         SLK_COUNT_LAUNCH(ctx, 3);
-        int gy = (int)((N + 4095) / 4096);
-        if (gy > 1024) gy = 1024;
+        int gy = (int)((N + 511) / 512);   // 64 rows per thread
+        if (gy > 8192) gy = 8192;
         if (gy < 1) gy = 1;
         dim3 grid((unsigned)((D + 31) / 32), (unsigned)gy);
         col_sum_kernel<<<grid, dim3(32, 8), 0, s>>>(X, N, D, colsum);
         mu_kernel<<<(D + 255) / 256, 256, 0, s>>>(colsum, N, D, mu);
         SLK_LAUNCH_CHECK(ctx, "col_sum_kernel");
         int64_t pg = (pl.Np + 7) / 8;
-        if (pg > (int64_t)ctx->num_sms * 16) pg = (int64_t)ctx->num_sms * 16;
+        if (pg > (int64_t)ctx->num_sms * 64) pg = (int64_t)ctx->num_sms * 64;
         prep_rows_kernel<<<(unsigned)pg, 256, 0, s>>>(
             X, N, D, pl.Dp, pl.Np, mu, pl.bf16 ? 1 : 0, pl.bf16 ? nullptr : (float*)xt,
             pl.bf16 ? (__nv_bfloat16*)xt : nullptr, norms, rho, pl.bf16 ? norms32 : nullptr, st);

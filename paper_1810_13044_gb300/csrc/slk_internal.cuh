@@ -252,15 +252,28 @@ __device__ __forceinline__ double warp_sq_dist(const float* __restrict__ xp,
                                                const float* __restrict__ xm,
                                                const float* __restrict__ xl, int D, int lane) {
     double d2 = 0.0;
-    float part = 0.f;
-    int n = 0;
-    for (int j = lane; j < D; j += 32) {
-        float df = xp[j] - xm[j];
-        if (xl) df -= xl[j];
-        part = fmaf(df, df, part);
-        if (++n == 8) { d2 += (double)part; part = 0.f; n = 0; }
+    // chunks of 8 lane-iterations (features lane + 32 i), their loads issued
+    // together; each chunk's squares summed in float32, the chunks in float64
+    for (int j0 = lane; j0 < D; j0 += 256) {
+        float a[8], b[8], c[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int j = j0 + 32 * t;
+            a[t] = j < D ? xp[j] : 0.f;
+            b[t] = j < D ? xm[j] : 0.f;
+            c[t] = (xl && j < D) ? xl[j] : 0.f;
+        }
+        float part = 0.f;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (j0 + 32 * t < D) {
+                float df = a[t] - b[t];
+                if (xl) df -= c[t];
+                part = fmaf(df, df, part);
+            }
+        }
+        d2 += (double)part;
     }
-    d2 += (double)part;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
     return d2;

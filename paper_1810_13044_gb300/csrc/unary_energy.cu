@@ -20,12 +20,6 @@ constexpr int kUThreads = 256;
 // bank-conflicted.
 __host__ __device__ inline int unary_mode_stride(int G) { return 4 * (G | 1); }
 
-// Block: 32 points x all L labels.  Thread t owns point t % 32 and labels
-// t / 32 + 8 j.  X and mode rows are staged 32 features at a time; each
-// chunk's squared differences are summed in float32, chunk sums in float64.
-// Vector modes (SLK-MS) come as M (float32) or as a float64 state split into
-// Mhi + Mlo (two floats): (x - m_hi) - m_lo keeps the difference accurate to
-// float32 relative to itself, not to |m|.
 // 4-byte asynchronous global -> shared copy; n = 0 fills the word with zero
 // (the source is then not read).
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, int n) {
@@ -43,10 +37,12 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 // label group), two buffers filled by asynchronous copies so that the next
 // chunk (of this pass or the next) loads while this one is summed.  Each
 // pair's squared differences over a chunk are summed in float32 in feature
-// order, the chunk sums in float64.  Vector modes (SLK-MS) come as M
-// (float32) or as a float64 state split into M + Mlo: (x - m_hi) - m_lo keeps
-// the difference accurate to float32 relative to itself, not to |m|.  Z0's
-// softmax rows are read back from A once the block has written it.
+// order; the chunk sums are added as an unevaluated pair of floats (2Sum:
+// about as accurate as a float64 sum and off the slow float64 pipe).  Vector
+// modes (SLK-MS) come as M (float32) or as a float64 state split into
+// M + Mlo: (x - m_hi) - m_lo keeps the difference accurate to float32
+// relative to itself, not to |m|.  Z0's softmax rows are read back from A
+// once the block has written it.
 __global__ void __launch_bounds__(kUThreads, 2)
 unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __restrict__ modes,
              const float* __restrict__ M, const float* __restrict__ Mlo, int L, int G, int PG,
@@ -94,7 +90,7 @@ unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __res
         cp_async_commit();
     };
     stage(0);
-    double acc[4][4];
+    float hi[4][4], lo[4][4];   // chunk sums added as an unevaluated float pair (2Sum)
     for (int s = 0; s < nsteps; ++s) {
         const int k = s % nch, l0 = (s / nch) * 4 * G, b = s & 1;
         const int dc = min(kUDC, D - k * kUDC);
@@ -102,7 +98,10 @@ unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __res
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+                for (int j = 0; j < 4; ++j) {
+                    hi[i][j] = 0.f;
+                    lo[i][j] = 0.f;
+                }
         }
         if (s + 1 < nsteps) stage(s + 1);
         else cp_async_commit();          // an empty group keeps the wait count uniform
@@ -139,7 +138,15 @@ unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __res
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] += (double)part[i][j];
+            for (int j = 0; j < 4; ++j) {
+                // 2Sum (Knuth): s + e == hi + part exactly
+                const float sum = __fadd_rn(hi[i][j], part[i][j]);
+                const float bb = __fsub_rn(sum, hi[i][j]);
+                const float e = __fadd_rn(__fsub_rn(hi[i][j], __fsub_rn(sum, bb)),
+                                          __fsub_rn(part[i][j], bb));
+                lo[i][j] = __fadd_rn(lo[i][j], e);
+                hi[i][j] = sum;
+            }
         if (k == nch - 1) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -147,7 +154,7 @@ unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __res
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int l = l0 + 4 * g + j;
-                    if (p < N && l < L) A[p * L + l] = expf(-(float)acc[i][j] * inv2s2);
+                    if (p < N && l < L) A[p * L + l] = expf(-__fadd_rn(hi[i][j], lo[i][j]) * inv2s2);
                 }
             }
         }
