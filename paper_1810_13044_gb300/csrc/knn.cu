@@ -57,10 +57,18 @@ __global__ void col_sum_kernel(const float* __restrict__ X, int64_t N, int D,
     if (c < D) {
         int n = 0;
         float part = 0.f;
-#pragma unroll 8
-        for (int64_t r = r0 + threadIdx.y; r < r1; r += 8) {
-            part += X[r * D + c];
-            if (++n == 64) { acc += (double)part; part = 0.f; n = 0; }
+        // rows r0 + y, r0 + y + 8, ... in increasing order, 8 loads in flight
+        for (int64_t rb = r0 + threadIdx.y; rb < r1; rb += 64) {
+            float v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = (rb + 8 * t < r1) ? X[(rb + 8 * t) * D + c] : 0.f;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                if (rb + 8 * t < r1) {
+                    part += v[t];
+                    if (++n == 64) { acc += (double)part; part = 0.f; n = 0; }
+                }
+            }
         }
         acc += (double)part;
     }
@@ -80,10 +88,20 @@ __global__ void mu_kernel(const double* __restrict__ colsum, int64_t N, int D, f
         mu[j] = (float)(colsum[j] * inv_n);
 }
 
+// (h, l) += (bh, bl) for unevaluated float pairs: 2Sum of the high parts,
+// the low parts and the rounding error added to the low part.
+__device__ __forceinline__ void pair_add(float& h, float& l, float bh, float bl) {
+    const float s = __fadd_rn(h, bh);
+    const float bb = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    l = __fadd_rn(__fadd_rn(l, bl), e);
+    h = s;
+}
+
 // One warp per padded row: xt = round(v), v = fl(x - mu), with
 //   norms[p] = ||xt_p||^2: lane sums of xt^2 in float32 (at most Dp/32 terms,
 //     relative error <= (Dp/32) u, u = 2^-24; each bfloat16 square is exact),
-//     lanes added in float64;
+//     lanes added as float pairs (within a few u^2 of the exact sum);
 //   rho[p] >= ||xt_p - (x_p - mu)||: with e = xt - v (exact in float32) and
 //     |v - (x - mu)| <= u |v|, rho <= ||e|| + u ||v||, both norms from float32
 //     lane sums inflated by their summation bound and rounded up.
@@ -121,13 +139,17 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
             e2 = fmaf(e, e, e2);
             v2 = fmaf(v, v, v2);
         }
-        double dn = n2, de = e2, dv = v2;
+        // butterfly sums of the lane sums as unevaluated float pairs (2Sum):
+        // within a few u^2 of the exact sum, and off the slow float64 pipe
+        float nh = n2, nl = 0.f, eh = e2, el = 0.f, vh = v2, vl = 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            dn += __shfl_xor_sync(0xffffffffu, dn, o);
-            de += __shfl_xor_sync(0xffffffffu, de, o);
-            dv += __shfl_xor_sync(0xffffffffu, dv, o);
+            pair_add(nh, nl, __shfl_xor_sync(0xffffffffu, nh, o), __shfl_xor_sync(0xffffffffu, nl, o));
+            pair_add(eh, el, __shfl_xor_sync(0xffffffffu, eh, o), __shfl_xor_sync(0xffffffffu, el, o));
+            pair_add(vh, vl, __shfl_xor_sync(0xffffffffu, vh, o), __shfl_xor_sync(0xffffffffu, vl, o));
         }
+        const double dn = (double)nh + (double)nl, de = (double)eh + (double)el,
+                     dv = (double)vh + (double)vl;
         if (lane == 0) {
             const float nf = (float)dn;
             const double r = sqrt(de * bound) + 5.9604644775390625e-08 * sqrt(dv * bound);
