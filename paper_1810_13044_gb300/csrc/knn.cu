@@ -55,22 +55,25 @@ __global__ void col_sum_kernel(const float* __restrict__ X, int64_t N, int D,
     const int64_t r1 = (r0 + per < N) ? r0 + per : N;
     double acc = 0.0;
     if (c < D) {
-        int n = 0;
-        float part = 0.f;
-        // rows r0 + y, r0 + y + 8, ... in increasing order, 8 loads in flight
-        for (int64_t rb = r0 + threadIdx.y; rb < r1; rb += 64) {
-            float v[8];
+        // rows r0 + y, r0 + y + 8, ... in increasing order; each chunk of 64
+        // of them summed in float32 (8 loads in flight), the chunks in
+        // float64 outside the inner loops (a float64 add predicated into
+        // every iteration would occupy GB300's narrow float64 pipe)
+        for (int64_t cb = r0 + threadIdx.y; cb < r1; cb += 512) {
+            float part = 0.f;
+#pragma unroll 2
+            for (int b = 0; b < 8; ++b) {
+                float v[8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) v[t] = (rb + 8 * t < r1) ? X[(rb + 8 * t) * D + c] : 0.f;
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                if (rb + 8 * t < r1) {
-                    part += v[t];
-                    if (++n == 64) { acc += (double)part; part = 0.f; n = 0; }
+                for (int t = 0; t < 8; ++t) {
+                    const int64_t r = cb + 64 * b + 8 * t;
+                    v[t] = (r < r1) ? X[r * D + c] : 0.f;
                 }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) part += v[t];
             }
+            acc += (double)part;
         }
-        acc += (double)part;
     }
     sm[threadIdx.y][threadIdx.x] = acc;
     __syncthreads();
@@ -148,9 +151,9 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
             pair_add(eh, el, __shfl_xor_sync(0xffffffffu, eh, o), __shfl_xor_sync(0xffffffffu, el, o));
             pair_add(vh, vl, __shfl_xor_sync(0xffffffffu, vh, o), __shfl_xor_sync(0xffffffffu, vl, o));
         }
-        const double dn = (double)nh + (double)nl, de = (double)eh + (double)el,
-                     dv = (double)vh + (double)vl;
         if (lane == 0) {
+            const double dn = (double)nh + (double)nl, de = (double)eh + (double)el,
+                         dv = (double)vh + (double)vl;
             const float nf = (float)dn;
             const double r = sqrt(de * bound) + 5.9604644775390625e-08 * sqrt(dv * bound);
             const float rf = __double2float_ru(r * (1.0 + 1e-12));
