@@ -347,7 +347,9 @@ seg_energy_kernel(const SegInfo* __restrict__ seg, const SegTile* __restrict__ t
         load_seg(seg, b, si);
         const double sg = (double)*si.sigma;
         const double inv2s2 = 1.0 / (2.0 * sg * sg);
-        double acc = 0.0;
+        double acc = 0.0, my_d2 = 0.0, my_cut = 0.0;
+        bool mine = false;
+        int slot = 0;
         for (int r = 0; r < tl.nrows; ++r) {
             const int64_t p = tl.row + r;
             const int lp = si.labels[p];
@@ -357,12 +359,26 @@ seg_energy_kernel(const SegInfo* __restrict__ seg, const SegTile* __restrict__ t
             int64_t e0, e1;
             if (si.kdeg > 0) { e0 = p * si.kdeg; e1 = e0 + si.kdeg; }
             else { e0 = si.row_ptr[p]; e1 = si.row_ptr[p + 1]; }
-            double cut = 0.0;
+            float ch = 0.f, cl = 0.f;   // cut weight as a float pair
             for (int64_t e = e0 + lane; e < e1; e += 32)
-                if (si.labels[si.col[e]] != lp) cut += si.w ? (double)si.w[e] : 1.0;
-            for (int o = 16; o > 0; o >>= 1) cut += __shfl_xor_sync(0xffffffffu, cut, o);
-            if (lane == 0) acc += -exp(-d2 * inv2s2) + 0.5 * (double)si.lambda * 2.0 * cut;
+                if (si.labels[si.col[e]] != lp) fpair_add(ch, cl, si.w ? si.w[e] : 1.f, 0.f);
+            for (int o = 16; o > 0; o >>= 1)
+                fpair_add(ch, cl, __shfl_xor_sync(0xffffffffu, ch, o), __shfl_xor_sync(0xffffffffu, cl, o));
+            // lane `slot` keeps this row; the float64 kernel values of 32 rows
+            // are then one warp-wide sequence
+            if (lane == slot) {
+                my_d2 = d2;
+                my_cut = (double)ch + (double)cl;
+                mine = true;
+            }
+            if (++slot == 32) {
+                if (mine) acc += -exp(-my_d2 * inv2s2) + 0.5 * (double)si.lambda * 2.0 * my_cut;
+                mine = false;
+                slot = 0;
+            }
         }
+        if (mine) acc += -exp(-my_d2 * inv2s2) + 0.5 * (double)si.lambda * 2.0 * my_cut;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) atomicAdd(&energy[b], acc);
     }
 }

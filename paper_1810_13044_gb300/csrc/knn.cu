@@ -91,16 +91,6 @@ __global__ void mu_kernel(const double* __restrict__ colsum, int64_t N, int D, f
         mu[j] = (float)(colsum[j] * inv_n);
 }
 
-// (h, l) += (bh, bl) for unevaluated float pairs: 2Sum of the high parts,
-// the low parts and the rounding error added to the low part.
-__device__ __forceinline__ void pair_add(float& h, float& l, float bh, float bl) {
-    const float s = __fadd_rn(h, bh);
-    const float bb = __fsub_rn(s, h);
-    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
-    l = __fadd_rn(__fadd_rn(l, bl), e);
-    h = s;
-}
-
 // One warp per padded row: xt = round(v), v = fl(x - mu), with
 //   norms[p] = ||xt_p||^2: lane sums of xt^2 in float32 (at most Dp/32 terms,
 //     relative error <= (Dp/32) u, u = 2^-24; each bfloat16 square is exact),
@@ -147,9 +137,9 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
         float nh = n2, nl = 0.f, eh = e2, el = 0.f, vh = v2, vl = 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            pair_add(nh, nl, __shfl_xor_sync(0xffffffffu, nh, o), __shfl_xor_sync(0xffffffffu, nl, o));
-            pair_add(eh, el, __shfl_xor_sync(0xffffffffu, eh, o), __shfl_xor_sync(0xffffffffu, el, o));
-            pair_add(vh, vl, __shfl_xor_sync(0xffffffffu, vh, o), __shfl_xor_sync(0xffffffffu, vl, o));
+            fpair_add(nh, nl, __shfl_xor_sync(0xffffffffu, nh, o), __shfl_xor_sync(0xffffffffu, nl, o));
+            fpair_add(eh, el, __shfl_xor_sync(0xffffffffu, eh, o), __shfl_xor_sync(0xffffffffu, el, o));
+            fpair_add(vh, vl, __shfl_xor_sync(0xffffffffu, vh, o), __shfl_xor_sync(0xffffffffu, vl, o));
         }
         if (lane == 0) {
             const double dn = (double)nh + (double)nl, de = (double)eh + (double)el,

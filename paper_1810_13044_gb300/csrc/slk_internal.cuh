@@ -244,16 +244,28 @@ __device__ __forceinline__ unsigned int float_to_ordered(float f) {
 __device__ __forceinline__ float ordered_to_float(unsigned int u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
+// (h, l) += (bh, bl) for unevaluated float pairs: 2Sum of the high parts
+// (exact, and the same on both lanes of an xor-butterfly step), the low
+// parts and the rounding error added to the low part.  A butterfly of such
+// additions gives every lane the same pair, within a few u^2 of the exact sum.
+__device__ __forceinline__ void fpair_add(float& h, float& l, float bh, float bl) {
+    const float s = __fadd_rn(h, bh);
+    const float bb = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    l = __fadd_rn(__fadd_rn(l, bl), e);
+    h = s;
+}
 // Squared distance of two rows by the 32 lanes of a warp (lane-strided
 // features; every lane returns the total): float32 differences, squares
-// summed in float32 chunks of 8 per lane, chunks and lanes added in float64.
+// summed in float32 chunks of 8 per lane, chunks and lanes added as float
+// pairs (as accurate as float64 here, off GB300's narrow float64 pipe).
 // xl (nullable): low part of a float64 row split into xm + xl.
 __device__ __forceinline__ double warp_sq_dist(const float* __restrict__ xp,
                                                const float* __restrict__ xm,
                                                const float* __restrict__ xl, int D, int lane) {
-    double d2 = 0.0;
+    float h = 0.f, lo = 0.f;
     // chunks of 8 lane-iterations (features lane + 32 i), their loads issued
-    // together; each chunk's squares summed in float32, the chunks in float64
+    // together
     for (int j0 = lane; j0 < D; j0 += 256) {
         float a[8], b[8], c[8];
 #pragma unroll
@@ -272,11 +284,12 @@ __device__ __forceinline__ double warp_sq_dist(const float* __restrict__ xp,
                 part = fmaf(df, df, part);
             }
         }
-        d2 += (double)part;
+        fpair_add(h, lo, part, 0.f);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-    return d2;
+    for (int o = 16; o > 0; o >>= 1)
+        fpair_add(h, lo, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, lo, o));
+    return (double)h + (double)lo;
 }
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;

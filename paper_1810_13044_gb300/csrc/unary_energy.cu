@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(kUThreads, 2)
 unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __restrict__ modes,
              const float* __restrict__ M, const float* __restrict__ Mlo, int L, int G, int PG,
              const float* __restrict__ sigma_dev, float* __restrict__ A, float* __restrict__ Z0) {
+    constexpr int PPL = kUPG / 32;   // points per lane
     extern __shared__ __align__(16) float sm[];
     const int S = unary_mode_stride(G), npts = PG * kUPG;
     const int nthr = blockDim.x;
@@ -90,13 +91,13 @@ unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __res
         cp_async_commit();
     };
     stage(0);
-    float hi[4][4], lo[4][4];   // chunk sums added as an unevaluated float pair (2Sum)
+    float hi[PPL][4], lo[PPL][4];   // chunk sums added as an unevaluated float pair (2Sum)
     for (int s = 0; s < nsteps; ++s) {
         const int k = s % nch, l0 = (s / nch) * 4 * G, b = s & 1;
         const int dc = min(kUDC, D - k * kUDC);
         if (k == 0) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < PPL; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     hi[i][j] = 0.f;
@@ -110,15 +111,15 @@ unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __res
         const float* xrow = xs + b * xbuf + (size_t)(pg * kUPG + lane) * (kUDC + 1);
         const float* hb = mh + b * mbuf + 4 * g;
         const float* lb = mlo + b * mbuf + 4 * g;
-        float part[4][4];
+        float part[PPL][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < PPL; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
         for (int c = 0; c < dc; ++c) {
-            float x[4];
+            float x[PPL];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) x[i] = xrow[32 * i * (kUDC + 1) + c];
+            for (int i = 0; i < PPL; ++i) x[i] = xrow[32 * i * (kUDC + 1) + c];
             const float4 h4 = *reinterpret_cast<const float4*>(hb + c * S);
             const float m[4] = {h4.x, h4.y, h4.z, h4.w};
             float ml[4] = {0.f, 0.f, 0.f, 0.f};
@@ -127,7 +128,7 @@ unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __res
                 ml[0] = l4.x; ml[1] = l4.y; ml[2] = l4.z; ml[3] = l4.w;
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < PPL; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     float df = x[i] - m[j];
@@ -136,7 +137,7 @@ unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __res
                 }
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < PPL; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 // 2Sum (Knuth): s + e == hi + part exactly
@@ -149,7 +150,7 @@ unary_kernel(const float* __restrict__ X, int64_t N, int D, const int32_t* __res
             }
         if (k == nch - 1) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < PPL; ++i) {
                 const int64_t p = p0 + pg * kUPG + lane + 32 * i;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -184,9 +185,12 @@ __global__ void weights_kernel(const float* __restrict__ dist2, int64_t nnz, int
 
 __global__ void set_sigma_kernel(float sigma, DevState* st) { st->sigma = sigma; }
 
-// One warp per point: squared distance to its mode (lanes over features,
-// float32 differences, squares summed in float32 chunks of 8 and the chunks
-// in float64), float64 kernel value, and the cut edges of its row.
+// One warp per point: squared distance to its mode (warp_sq_dist) and the
+// cut edges of its row (weights summed as float pairs).  Lane i keeps the
+// distance and cut of the warp's points i, i + 32, ... until it has to add
+// them, so that the float64 kernel value exp(-d2 / (2 sigma^2)) is one
+// warp-wide instruction sequence per 32 points rather than one single-lane
+// sequence per point.
 __global__ void __launch_bounds__(256)
 energy_kernel(const float* __restrict__ X, int D, const int32_t* __restrict__ labels,
               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
@@ -199,21 +203,37 @@ energy_kernel(const float* __restrict__ X, int D, const int32_t* __restrict__ la
     const double inv2s2 = 1.0 / (2.0 * sg * sg);
     double acc = 0.0;  // per-lane partial of E
     const int64_t nwarps = (int64_t)gridDim.x * 8;
+    double my_d2 = 0.0, my_cut = 0.0;
+    bool mine = false;
+    int slot = 0;   // lane that keeps the current point
     for (int64_t p = (int64_t)blockIdx.x * 8 + warp; p < N; p += nwarps) {
         const int lp = labels[p];
         const float* xp = X + p * D;
         const float* xm = M ? M + (int64_t)lp * D : X + (int64_t)modes[lp] * D;
         const double d2 = warp_sq_dist(xp, xm, Mlo ? Mlo + (int64_t)lp * D : nullptr, D, lane);
-        double cut = 0.0;
+        float ch = 0.f, cl = 0.f;
         for (int64_t e = row_ptr[p] + lane; e < row_ptr[p + 1]; e += 32) {
             const int q = col_idx[e];
-            if (labels[q] != lp) cut += w ? (double)w[e] : 1.0;
+            if (labels[q] != lp) fpair_add(ch, cl, w ? w[e] : 1.f, 0.f);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cut += __shfl_xor_sync(0xffffffffu, cut, o);
-        // ||z_p - z_q||^2 = 2 for every cut edge
-        if (lane == 0) acc += -exp(-d2 * inv2s2) + 0.5 * (double)lambda * 2.0 * cut;
+        for (int o = 16; o > 0; o >>= 1)
+            fpair_add(ch, cl, __shfl_xor_sync(0xffffffffu, ch, o), __shfl_xor_sync(0xffffffffu, cl, o));
+        if (lane == slot) {
+            my_d2 = d2;
+            my_cut = (double)ch + (double)cl;
+            mine = true;
+        }
+        if (++slot == 32) {
+            // ||z_p - z_q||^2 = 2 for every cut edge
+            if (mine) acc += -exp(-my_d2 * inv2s2) + 0.5 * (double)lambda * 2.0 * my_cut;
+            mine = false;
+            slot = 0;
+        }
     }
+    if (mine) acc += -exp(-my_d2 * inv2s2) + 0.5 * (double)lambda * 2.0 * my_cut;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) red[warp] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
