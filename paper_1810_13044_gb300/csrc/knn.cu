@@ -1130,7 +1130,9 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
         if (pl.bf16) {
             // float32 distance tiles of the open rows against every point, then
             // the rerank under the float32 certificate; its failures go on
-            const int kcq = (k + 4 <= 16) ? 16 : 32;
+            // float32 lists of at least 2k candidates (the gap between the k-th and the
+            // last decides the certificate)
+            const int kcq = (2 * k <= 16) ? 16 : 32;
             int qsplits = (int)std::min<int64_t>(8, (int64_t)pl.lists * pl.kc / kcq);
             if (qsplits < 1) qsplits = 1;
             const int n_tiles = (int)((N + BN - 1) / BN);
