@@ -510,7 +510,7 @@ __device__ __forceinline__ float exact_d2(const float* __restrict__ xp,
 // bfloat16 stage, their float32 query lists at ((split N + f) KC), norms of
 // the float32 operand (rho <= u ||v||), failures appended to fb_list /
 // *count_out.
-template <int KC, bool Q>
+template <int KC, bool Q, int E = MAXE>
 __global__ void __launch_bounds__(256, 4)
 knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, int splits,
                   int64_t Np, const float* __restrict__ cand_d, const int32_t* __restrict__ cand_i,
@@ -541,11 +541,11 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
          f += nw) {
         const int64_t p = Q ? (int64_t)fb_in[f] : f;
         if (!Q && lane == 0) row_ptr[p] = p * (int64_t)k;
-        float ed[MAXE];
-        int ei[MAXE];
+        float ed[E];   // E >= ceil(splits KC / 32) entries per lane
+        int ei[E];
         const int total = splits * KC;
 #pragma unroll
-        for (int m = 0; m < MAXE; ++m) {
+        for (int m = 0; m < E; ++m) {
             const int e = lane + 32 * m;
             ed[m] = kInf;
             ei[m] = kNoIdx;
@@ -571,7 +571,7 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
             float bd = kInf;
             int bi = kNoIdx;
 #pragma unroll
-            for (int m = 0; m < MAXE; ++m)
+            for (int m = 0; m < E; ++m)
                 if (lex_less(ed[m], ei[m], bd, bi)) { bd = ed[m]; bi = ei[m]; }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -581,7 +581,7 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
             }
             if (bi == kNoIdx) break;
 #pragma unroll
-            for (int m = 0; m < MAXE; ++m)
+            for (int m = 0; m < E; ++m)
                 if (ei[m] == bi) { ed[m] = kInf; ei[m] = kNoIdx; }
 #pragma unroll
             for (int h = 0; h < CPL; ++h)
@@ -1110,14 +1110,21 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
         SLK_COUNT_LAUNCH(ctx, 1);
         int64_t grid = (N + 7) / 8;
         if (grid > (int64_t)ctx->num_sms * 16) grid = (int64_t)ctx->num_sms * 16;
-#define SLK_RERANK(KC_)                                                                       \
-    knn_rerank_kernel<KC_, false><<<(unsigned)grid, 256, 0, s>>>(X, N, D, pl.Dp, k, pl.lists,   \
-                                                                 pl.Np, cand_d, cand_i, norms,  \
-                                                                 rho, u_acc, row_ptr, col_idx,  \
-                                                                 dist2, fb, st)
-        if (pl.kc == 16) SLK_RERANK(16);
-        else if (pl.kc == 32) SLK_RERANK(32);
-        else SLK_RERANK(64);
+        // entries per lane: the splits' lists, KC each, over 32 lanes
+        const int per_lane = (pl.lists * pl.kc + 31) / 32;
+#define SLK_RERANK(KC_, E_)                                                                   \
+    knn_rerank_kernel<KC_, false, E_><<<(unsigned)grid, 256, 0, s>>>(X, N, D, pl.Dp, k, pl.lists, \
+                                                                     pl.Np, cand_d, cand_i, norms, \
+                                                                     rho, u_acc, row_ptr, col_idx, \
+                                                                     dist2, fb, st)
+#define SLK_RERANK_E(KC_)                                                                     \
+    if (per_lane <= 4) SLK_RERANK(KC_, 4);                                                    \
+    else if (per_lane <= 8) SLK_RERANK(KC_, 8);                                               \
+    else SLK_RERANK(KC_, 16);
+        if (pl.kc == 16) { SLK_RERANK_E(16) }
+        else if (pl.kc == 32) { SLK_RERANK_E(32) }
+        else { SLK_RERANK_E(64) }
+#undef SLK_RERANK_E
 #undef SLK_RERANK
         SLK_LAUNCH_CHECK(ctx, "knn_rerank_kernel");
     }

@@ -65,6 +65,10 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 #ifndef SLK_TC_PAIR
 #define SLK_TC_PAIR 0
 #endif
+// Buffered entries (per lane) that trigger a merge after a tile (KC = 32).
+#ifndef SLK_TC_MERGE_AT
+#define SLK_TC_MERGE_AT 24
+#endif
 #ifndef SLK_TC_PAIR_STAGES
 #define SLK_TC_PAIR_STAGES 4
 #endif
@@ -691,7 +695,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 // merge with the accumulator released (the threshold only drops,
                 // so the stale one let through entries the merge discards)
                 if constexpr (E::defer) {
-                    if (__any_sync(0xffffffffu, cnt >= 16)) flush_buffer<TC_KC>(s, h, r, cnt, ld, li);
+                    if (__any_sync(0xffffffffu, cnt >= SLK_TC_MERGE_AT)) flush_buffer<TC_KC>(s, h, r, cnt, ld, li);
                 }
                 ++tcount;
             }
