@@ -373,43 +373,35 @@ __device__ __forceinline__ float rows_update_cached(int lr0, int lstride, int nr
             b[i][j] = 0.f;
         }
     }
-    for (int c0 = 0; c0 < maxc; c0 += G) {
-        int myq[RPG];
-        float myw[RPG];
+    // neighbour names and weights straight from shared memory (every lane of
+    // a group reads the same word); windows of W edges, slots beyond the
+    // row's degree skipped with a warp-uniform test
+    for (int t0 = 0; t0 < maxc; t0 += W) {
+        float zz[RPG][W][LPL], ww[RPG][W];
 #pragma unroll
-        for (int i = 0; i < RPG; ++i) {
-            myq[i] = 0;
-            myw[i] = 1.f;
-            if (gl < cnt[i] - c0) {
-                myq[i] = sQ[lr[i] * kdeg + c0 + gl];
-                if (sW) myw[i] = sW[lr[i] * kdeg + c0 + gl];
+        for (int u = 0; u < W; ++u) {
+            if (t0 + u >= maxc) break;   // maxc = kdeg for every live row: uniform
+#pragma unroll
+            for (int i = 0; i < RPG; ++i) {
+                const bool ok = t0 + u < cnt[i];
+                const int q = ok ? sQ[lr[i] * kdeg + t0 + u] : 0;
+                ww[i][u] = (ok && sW) ? sW[lr[i] * kdeg + t0 + u] : 1.f;
+                const float* zq = Zin + (int64_t)q * L;
+#pragma unroll
+                for (int j = 0; j < LPL; ++j) {
+                    const int l = gl + G * j;
+                    zz[i][u][j] = (ok && l < L) ? __ldcg(zq + l) : 0.f;
+                }
             }
         }
-        const int cm = min(G, maxc - c0);
-        for (int t0 = 0; t0 < cm; t0 += W) {
-            float zz[RPG][W][LPL], ww[RPG][W];
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+            if (t0 + u >= maxc) break;
 #pragma unroll
             for (int i = 0; i < RPG; ++i)
+                if (t0 + u < cnt[i])
 #pragma unroll
-                for (int u = 0; u < W; ++u) {
-                    const int t = t0 + u;   // < G: W divides G and t0 < cm <= G
-                    const int q = __shfl_sync(gmask, myq[i], t, G);
-                    ww[i][u] = __shfl_sync(gmask, myw[i], t, G);
-                    const bool ok = t < cnt[i] - c0;
-                    const float* zq = Zin + (int64_t)q * L;
-#pragma unroll
-                    for (int j = 0; j < LPL; ++j) {
-                        const int l = gl + G * j;
-                        zz[i][u][j] = (ok && l < L) ? __ldcg(zq + l) : 0.f;
-                    }
-                }
-#pragma unroll
-            for (int i = 0; i < RPG; ++i)
-#pragma unroll
-                for (int u = 0; u < W; ++u)
-                    if (t0 + u < cnt[i] - c0)
-#pragma unroll
-                        for (int j = 0; j < LPL; ++j) b[i][j] = fmaf(ww[i][u], zz[i][u][j], b[i][j]);
+                    for (int j = 0; j < LPL; ++j) b[i][j] = fmaf(ww[i][u], zz[i][u][j], b[i][j]);
         }
     }
     float dmax = 0.f;
