@@ -119,6 +119,7 @@ __device__ __forceinline__ void seg_logits(const SegInfo& si, int64_t p, int gl,
 #pragma unroll
                 for (int u = 0; u < W; ++u) {
                     const int t = t0 + u;
+                    if (t >= cm) break;   // uniform within the group (one row)
                     const int src = t < G ? t : 0;
                     const int q = __shfl_sync(gm, myq, src, G);
                     ww[u] = __shfl_sync(gm, myw, src, G);
@@ -130,10 +131,11 @@ __device__ __forceinline__ void seg_logits(const SegInfo& si, int64_t p, int gl,
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < W; ++u)
-                    if (t0 + u < cm)
+                for (int u = 0; u < W; ++u) {
+                    if (t0 + u >= cm) break;
 #pragma unroll
-                        for (int j = 0; j < kLPL; ++j) b[j] = fmaf(ww[u], zz[u][j], b[j]);
+                    for (int j = 0; j < kLPL; ++j) b[j] = fmaf(ww[u], zz[u][j], b[j]);
+                }
             }
         }
     }
