@@ -38,7 +38,14 @@
 
 namespace {
 
-constexpr int TC_M = 128, TC_N = 256, TC_BK = 64;  // K slice: 64 bf16 = 128 bytes
+// K slice of a stage: 64 bf16 = 128-byte rows (128-byte swizzle), or 32 bf16 =
+// 64-byte rows (64-byte swizzle) for twice as many stages in the same bytes.
+#ifndef SLK_TC_BK
+#define SLK_TC_BK 64
+#endif
+constexpr int TC_M = 128, TC_N = 256, TC_BK = SLK_TC_BK;
+static_assert(TC_BK == 64 || TC_BK == 32, "K slice of 64 or 32 bf16");
+constexpr int TC_ROWB = TC_BK * 2;   // bytes per operand row of a stage (= the swizzle span)
 #ifndef SLK_TC_STAGES
 #define SLK_TC_STAGES 3
 #endif
@@ -72,8 +79,8 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 #ifndef SLK_TC_PAIR_STAGES
 #define SLK_TC_PAIR_STAGES 4
 #endif
-constexpr uint32_t A_BYTES = TC_M * TC_BK * 2;  // 16 KiB
-constexpr uint32_t B_BYTES = TC_N * TC_BK * 2;  // 32 KiB
+constexpr uint32_t A_BYTES = TC_M * TC_BK * 2;  // 16 KiB (BK = 64)
+constexpr uint32_t B_BYTES = TC_N * TC_BK * 2;  // 32 KiB (BK = 64)
 
 // A vote checks VOTE columns at once and the survivors of APP columns are
 // appended to a per-row buffer of BUF slots.  The buffer is merged into the
@@ -87,7 +94,8 @@ template <int EW, bool PAIR = false, int KC = 32> struct TcEpi {
     static constexpr uint32_t b_bytes = PAIR ? B_BYTES / 2 : B_BYTES;
     static constexpr int halves = EW / 4;             // column halves of a tile
     static constexpr int vote = (EW == 8) ? 16 : 32;  // columns per vote
-    static constexpr bool tight = !PAIR && TC_STAGES > 3;
+    // more than 3 x 48 KiB of operand stages leaves room only for 31 slots
+    static constexpr bool tight = !PAIR && TC_STAGES * (A_BYTES + B_BYTES) > 3u * 49152u;
     // KC = 64 (an epilogue-bound kernel at small D) merges right away instead
     static constexpr bool defer = (KC == 32) && !tight;
     static constexpr int app = tight ? 16 : vote;     // columns per append
@@ -178,9 +186,9 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;                 // LBO (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;       // SBO
+    d |= (uint64_t)((8 * TC_ROWB) >> 4) << 32;   // SBO: 8-row atoms
     d |= (uint64_t)1 << 46;                 // version
-    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    d |= (uint64_t)(TC_ROWB == 128 ? 2 : 4) << 61;   // 128- or 64-byte swizzle
     return d;
 }
 // Instruction descriptor: D fp32, A/B bf16, both K-major, N = 256, M = 128.
@@ -742,6 +750,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+constexpr CUtensorMapSwizzle kTcSwizzle =
+    TC_ROWB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+
 EncodeTiledFn encode_fn() {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
@@ -785,10 +796,10 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
     const cuuint32_t box_b[2] = {TC_BK, TC_N};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r1 = enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)xt, dims, strides, box_a, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, kTcSwizzle,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     CUresult r2 = enc(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)xt, dims, strides, box_b, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, kTcSwizzle,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
         return set_err(ctx, SLK_ERR_CUDA, "tensor map encoding failed (%d, %d)", (int)r1, (int)r2);
@@ -802,7 +813,7 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
         CUtensorMap tb2;
         const cuuint32_t box_b2[2] = {TC_BK, TC_N / 2};
         CUresult r3 = enc(&tb2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)xt, dims, strides, box_b2,
-                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, kTcSwizzle,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r3 != CUDA_SUCCESS)
             return set_err(ctx, SLK_ERR_CUDA, "tensor map encoding failed (%d)", (int)r3);
