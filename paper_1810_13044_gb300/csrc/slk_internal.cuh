@@ -77,6 +77,11 @@ struct DevState {
     unsigned int knn_error;           // bit 1: a tensor-core pipeline wait timed out
     unsigned int knn_max_norm32_bits; // float bits of max float32-operand norm^2
     long long fallback2_count;        // rows left for the exact scan after the float32 stage
+    // one-launch median: grid barrier words, count of values <= the lower
+    // middle order statistic, smallest value above it (bits)
+    unsigned int sel_bar[4];
+    unsigned long long sel_cnt;
+    unsigned int sel_min_bits;
 };
 
 enum : unsigned int { ERR_BARRIER_TIMEOUT = 1u };
