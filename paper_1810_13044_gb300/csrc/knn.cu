@@ -1156,7 +1156,7 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
             if (kcq == 16) SLK_QCAND(16) else SLK_QCAND(32)
 #undef SLK_QCAND
             SLK_LAUNCH_CHECK(ctx, "knn_cand_query_kernel");
-            const unsigned rgrid = (unsigned)(ctx->num_sms * 16);
+            const unsigned rgrid = (unsigned)(ctx->num_sms * 4);   // grid-stride over the open rows
             const float u32 = 5.9604644775390625e-08f;
             if (kcq == 16)
                 knn_rerank_kernel<16, true><<<rgrid, 256, 0, s>>>(
