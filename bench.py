@@ -43,9 +43,9 @@ FP32_LANES_PER_SM = 128      # FP32 FMA units per SM (4 sub-partitions x 32)
 # kernel's source file at capture time: a changed source reports null.
 NCU_TRAFFIC = {
     ("knn_cand_tc_kernel", "mnist_like_70000x784_L10"): {
-        "bytes": 1139794176 + 53511936,
+        "bytes": 1141291264 + 52733952,
         "source": "paper_1810_13044_gb300/csrc/knn_tc.cu",
-        "sha256": "0d09ac2e7d383c668989f01c817b91a14e6072d54c271a1559dfb97e8f2f1aaa",
+        "sha256": "f1cfb1769353c79491e3282b9cbfdc350725504ecf50738d4421afa789e2be89",
     },
 }
 
