@@ -519,6 +519,10 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
                   float* __restrict__ dist2, int32_t* __restrict__ fb_list, DevState* st,
                   const int32_t* __restrict__ fb_in = nullptr, const long long* count_in = nullptr,
                   long long* count_out = nullptr) {
+    __shared__ float s_d[8][32 * E];   // each warp's staged lists (256 threads)
+    __shared__ int s_i[8][32 * E];
+    __shared__ float s_od[8][KC];      // and its KC selected candidates
+    __shared__ int s_oi[8][KC];
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     const double u = 5.9604644775390625e-08;  // 2^-24
@@ -541,62 +545,100 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
          f += nw) {
         const int64_t p = Q ? (int64_t)fb_in[f] : f;
         if (!Q && lane == 0) row_ptr[p] = p * (int64_t)k;
-        float ed[E];   // E >= ceil(splits KC / 32) entries per lane
-        int ei[E];
+        // The splits' lists are sorted by (distance, index) and cover
+        // disjoint columns, so the position of an entry in their union is its
+        // position in its own list plus, for every other list, the number of
+        // that list's entries ordered before it (a binary search; equal keys
+        // count from earlier lists only, so positions stay distinct).  Empty
+        // slots are (+inf, no index) and follow every entry.
+        const int wib = threadIdx.x >> 5;
+        float* sd = s_d[wib];
+        int* si = s_i[wib];
         const int total = splits * KC;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int e = lane + 32 * m;
-            ed[m] = kInf;
-            ei[m] = kNoIdx;
             if (e < total) {
                 const int64_t o = ((int64_t)(e / KC) * stride + f) * KC + (e % KC);
                 const int i = cand_i[o];
-                if (i >= 0 && i != (int)p) { ed[m] = cand_d[o]; ei[m] = i; }
+                sd[e] = i >= 0 ? cand_d[o] : kInf;
+                si[e] = i >= 0 ? i : kNoIdx;
             }
         }
-        // select the KC smallest (distance, index) of the union of splits;
+        __syncwarp();
+        int rk[E];   // E >= ceil(splits KC / 32) entries per lane
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int e = lane + 32 * m;
+            rk[m] = 0x7fffffff;
+            if (e >= total) continue;
+            const float xd = sd[e];
+            const int xi = si[e];
+            if (xi == kNoIdx) continue;   // empty slots are never selected
+            const int l = e / KC;
+            int r = 0;
+            for (int l2 = 0; l2 < splits; ++l2) {
+                int c;
+                if (l2 == l) {
+                    c = e % KC;
+                } else {
+                    const float* bd = sd + l2 * KC;
+                    const int* bi = si + l2 * KC;
+                    const bool eq = l2 < l;
+                    c = 0;
+#pragma unroll
+                    for (int w = KC / 2; w > 0; w >>= 1) {
+                        const float od = bd[c + w - 1];
+                        const int oi = bi[c + w - 1];
+                        if (lex_less(od, oi, xd, xi) || (eq && od == xd && oi == xi)) c += w;
+                    }
+                    const float od = bd[c];
+                    const int oi = bi[c];
+                    if (lex_less(od, oi, xd, xi) || (eq && od == xd && oi == xi)) ++c;
+                }
+                r += c;
+            }
+            rk[m] = r;
+        }
+        // the row itself is not a neighbour: entries after it move up one
+        int self_rank = 0x7fffffff;
+#pragma unroll
+        for (int m = 0; m < E; ++m)
+            if (lane + 32 * m < total && si[lane + 32 * m] == (int)p) self_rank = rk[m];
+        self_rank = __reduce_min_sync(0xffffffffu, self_rank);
+        float* od_ = s_od[wib];
+        int* oi_ = s_oi[wib];
+        int nv = 0;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int e = lane + 32 * m;
+            const int xi = e < total ? si[e] : kNoIdx;
+            const bool valid = xi != kNoIdx && xi != (int)p;
+            nv += __popc(__ballot_sync(0xffffffffu, valid));
+            const int r = rk[m] - (rk[m] > self_rank ? 1 : 0);
+            if (valid && r < KC) {
+                od_[r] = sd[e];
+                oi_[r] = xi;
+            }
+        }
+        __syncwarp();
         // candidate c lives on lane c % 32, slot c / 32
         constexpr int CPL = (KC + 31) / 32;
-        float T = kInf;
+        const int nc = nv < KC ? nv : KC;
         int ci[CPL];
         float cd[CPL];
 #pragma unroll
         for (int h = 0; h < CPL; ++h) {
-            ci[h] = kNoIdx;
-            cd[h] = kInf;
+            const int c = lane + 32 * h;
+            ci[h] = c < nc ? oi_[c] : kNoIdx;
+            cd[h] = c < nc ? od_[c] : kInf;
         }
-        int nc = 0;
-        for (int c = 0; c < KC; ++c) {
-            float bd = kInf;
-            int bi = kNoIdx;
-#pragma unroll
-            for (int m = 0; m < E; ++m)
-                if (lex_less(ed[m], ei[m], bd, bi)) { bd = ed[m]; bi = ei[m]; }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float od = __shfl_xor_sync(0xffffffffu, bd, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (lex_less(od, oi, bd, bi)) { bd = od; bi = oi; }
-            }
-            if (bi == kNoIdx) break;
-#pragma unroll
-            for (int m = 0; m < E; ++m)
-                if (ei[m] == bi) { ed[m] = kInf; ei[m] = kNoIdx; }
-#pragma unroll
-            for (int h = 0; h < CPL; ++h)
-                if (lane + 32 * h == c) {
-                    ci[h] = bi;
-                    cd[h] = bd;
-                }
-            ++nc;
-            T = bd;
-        }
+        float T = nc == KC ? od_[KC - 1] : kInf;
+        __syncwarp();   // read before the next row's lists are staged
         // Lower bound T on dt of every point that is not a candidate: a column
         // a split rejected has dt >= that split's last list entry (when its
         // list is full); an entry of the union left out has dt >= the KC-th
         // selected one.
-        if (nc < KC) T = kInf;
         {
             float ts = kInf;
             if (lane < splits) {
@@ -651,37 +693,30 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
         float myd[CPL];
 #pragma unroll
         for (int h = 0; h < CPL; ++h) myd[h] = kInf;
-        for (int c = 0; c < nc; ++c) {
-            bool skip = true;
 #pragma unroll
-            for (int h = 0; h < CPL; ++h)
-                if (c / 32 == h) skip = ((need[h] >> (c % 32)) & 1u) == 0u;
-            if (skip) continue;   // warp-uniform
-            int q = kNoIdx;
-#pragma unroll
-            for (int h = 0; h < CPL; ++h)
-                if (c / 32 == h) q = __shfl_sync(0xffffffffu, ci[h], c % 32);
-            const float d = exact_d2(xp, X + (int64_t)q * D, D, lane);
-#pragma unroll
-            for (int h = 0; h < CPL; ++h)
-                if (lane + 32 * h == c) myd[h] = d;
+        for (int h = 0; h < CPL; ++h) {
+            for (unsigned msk = need[h]; msk != 0u; msk &= msk - 1u) {   // warp-uniform
+                const int b = __ffs(msk) - 1;
+                const int q = __shfl_sync(0xffffffffu, ci[h], b);
+                const float d = exact_d2(xp, X + (int64_t)q * D, D, lane);
+                if (lane == b) myd[h] = d;
+            }
         }
-        // rank of each candidate by (exact distance, index)
+        // rank of each candidate by (exact distance, index) among the
+        // computed ones; a skipped one (+inf) ranks after at least k of them
         int rank[CPL];
 #pragma unroll
         for (int h = 0; h < CPL; ++h) rank[h] = 0;
-        for (int c = 0; c < nc; ++c) {
-            float od = kInf;
-            int oi = kNoIdx;
 #pragma unroll
-            for (int h = 0; h < CPL; ++h)
-                if (c / 32 == h) {
-                    od = __shfl_sync(0xffffffffu, myd[h], c % 32);
-                    oi = __shfl_sync(0xffffffffu, ci[h], c % 32);
-                }
+        for (int hs = 0; hs < CPL; ++hs) {
+            for (unsigned msk = need[hs]; msk != 0u; msk &= msk - 1u) {
+                const int b = __ffs(msk) - 1;
+                const float od = __shfl_sync(0xffffffffu, myd[hs], b);
+                const int oi = __shfl_sync(0xffffffffu, ci[hs], b);
 #pragma unroll
-            for (int h = 0; h < CPL; ++h)
-                if (lex_less(od, oi, myd[h], ci[h])) ++rank[h];
+                for (int h = 0; h < CPL; ++h)
+                    if (lex_less(od, oi, myd[h], ci[h])) ++rank[h];
+            }
         }
         float dk = kInf;
 #pragma unroll
