@@ -45,42 +45,63 @@ __device__ __forceinline__ bool lex_less(float d, int i, float d2, int i2) {
 
 // Column sums (the centring mean mu only has to be some float vector:
 // distances are translation invariant): float32 sums of 64 rows, added in
-// float64.
+// float64.  Each lane sums V adjacent columns (V = 4: 16-byte loads, when D
+// is a multiple of 4 and X is 16-byte aligned); the rows and their order do
+// not depend on V.
+template <int V>
 __global__ void col_sum_kernel(const float* __restrict__ X, int64_t N, int D,
                                double* __restrict__ colsum) {
-    __shared__ double sm[8][33];
-    const int c = blockIdx.x * 32 + threadIdx.x;
+    __shared__ double sm[8][32 * V + 1];
+    const int DV = D / V;
+    const int c = blockIdx.x * 32 + threadIdx.x;   // column group
     const int64_t per = (N + gridDim.y - 1) / gridDim.y;
     const int64_t r0 = (int64_t)blockIdx.y * per;
     const int64_t r1 = (r0 + per < N) ? r0 + per : N;
-    double acc = 0.0;
-    if (c < D) {
+    double acc[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) acc[q] = 0.0;
+    if (c < DV) {
         // rows r0 + y, r0 + y + 8, ... in increasing order; each chunk of 64
         // of them summed in float32 (8 loads in flight), the chunks in
         // float64 outside the inner loops (a float64 add predicated into
         // every iteration would occupy GB300's narrow float64 pipe)
         for (int64_t cb = r0 + threadIdx.y; cb < r1; cb += 512) {
-            float part = 0.f;
+            float part[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) part[q] = 0.f;
 #pragma unroll 2
             for (int b = 0; b < 8; ++b) {
-                float v[8];
+                float v[8][V];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const int64_t r = cb + 64 * b + 8 * t;
-                    v[t] = (r < r1) ? X[r * D + c] : 0.f;
+                    if constexpr (V == 4) {
+                        const float4 w = (r < r1) ? __ldg(reinterpret_cast<const float4*>(X + r * D) + c)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                        v[t][0] = w.x; v[t][1] = w.y; v[t][2] = w.z; v[t][3] = w.w;
+                    } else {
+                        v[t][0] = (r < r1) ? X[r * D + c] : 0.f;
+                    }
                 }
 #pragma unroll
-                for (int t = 0; t < 8; ++t) part += v[t];
+                for (int t = 0; t < 8; ++t)
+#pragma unroll
+                    for (int q = 0; q < V; ++q) part[q] += v[t][q];
             }
-            acc += (double)part;
+#pragma unroll
+            for (int q = 0; q < V; ++q) acc[q] += (double)part[q];
         }
     }
-    sm[threadIdx.y][threadIdx.x] = acc;
+#pragma unroll
+    for (int q = 0; q < V; ++q) sm[threadIdx.y][threadIdx.x * V + q] = acc[q];
     __syncthreads();
-    if (threadIdx.y == 0 && c < D) {
-        double s = 0.0;
-        for (int i = 0; i < 8; ++i) s += sm[i][threadIdx.x];
-        atomicAdd(&colsum[c], s);
+    if (threadIdx.y == 0 && c < DV) {
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            double t = 0.0;
+            for (int i = 0; i < 8; ++i) t += sm[i][threadIdx.x * V + q];
+            atomicAdd(&colsum[c * V + q], t);
+        }
     }
 }
 
@@ -92,13 +113,19 @@ __global__ void mu_kernel(const double* __restrict__ colsum, int64_t N, int D, f
 }
 
 // One warp per padded row: xt = round(v), v = fl(x - mu), with
-//   norms[p] = ||xt_p||^2: lane sums of xt^2 in float32 (at most Dp/32 terms,
-//     relative error <= (Dp/32) u, u = 2^-24; each bfloat16 square is exact),
-//     lanes added as float pairs (within a few u^2 of the exact sum);
+//   norms[p] = ||xt_p||^2: lane sums of xt^2 in float32, lanes added as float
+//     pairs (within a few u^2 of the exact sum);
 //   rho[p] >= ||xt_p - (x_p - mu)||: with e = xt - v (exact in float32) and
 //     |v - (x - mu)| <= u |v|, rho <= ||e|| + u ||v||, both norms from float32
 //     lane sums inflated by their summation bound and rounded up.
+// Every square of a lane sum passes through at most Dp/32 roundings (u =
+// 2^-24): V = 1 sums the lane's Dp/32 columns in one accumulator; V = 4
+// (16-byte loads, D a multiple of 4, X 16-byte aligned, Dp >= 128) keeps one
+// accumulator per column of its 4-column groups, ceil(Dp/128) terms each,
+// added pairwise at the end: ceil(Dp/128) + 2 <= Dp/32 roundings.  Each
+// bfloat16 square is exact.
 // The row maxima go to st with one atomic per block.
+template <int V>
 __global__ void __launch_bounds__(256)
 prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
                  int64_t Np, const float* __restrict__ mu, int to_bf16,
@@ -114,23 +141,59 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
     unsigned my_n = 0u, my_r = 0u, my_n32 = 0u;
     for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < Np;
          p += nw) {
-        float n2 = 0.f, e2 = 0.f, v2 = 0.f;
+        float n2v[V], e2v[V], v2v[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) { n2v[q] = 0.f; e2v[q] = 0.f; v2v[q] = 0.f; }
 #pragma unroll 4
-        for (int j = lane; j < Dp; j += 32) {
-            float v = 0.f, vv = 0.f;
-            if (p < N && j < D) v = X[p * D + j] - __ldg(mu + j);
-            if (to_bf16) {
-                const __nv_bfloat16 b = __float2bfloat16_rn(v);
-                xt16[p * Dp + j] = b;
-                vv = __bfloat162float(b);
-            } else {
-                xt32[p * Dp + j] = v;
-                vv = v;
+        for (int j = lane * V; j < Dp; j += 32 * V) {
+            float v[V], vv[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) v[q] = 0.f;
+            if (p < N && j < D) {
+                if constexpr (V == 4) {
+                    const float4 x = __ldg(reinterpret_cast<const float4*>(X + p * D + j));
+                    const float4 m = __ldg(reinterpret_cast<const float4*>(mu + j));
+                    v[0] = x.x - m.x; v[1] = x.y - m.y; v[2] = x.z - m.z; v[3] = x.w - m.w;
+                } else {
+                    v[0] = X[p * D + j] - __ldg(mu + j);
+                }
             }
-            n2 = fmaf(vv, vv, n2);
-            const float e = vv - v;
-            e2 = fmaf(e, e, e2);
-            v2 = fmaf(v, v, v2);
+            if (to_bf16) {
+                if constexpr (V == 4) {
+                    const __nv_bfloat162 b01 = __floats2bfloat162_rn(v[0], v[1]);
+                    const __nv_bfloat162 b23 = __floats2bfloat162_rn(v[2], v[3]);
+                    uint2 w;
+                    w.x = *reinterpret_cast<const unsigned*>(&b01);
+                    w.y = *reinterpret_cast<const unsigned*>(&b23);
+                    *reinterpret_cast<uint2*>(xt16 + p * Dp + j) = w;
+                    vv[0] = __low2float(b01); vv[1] = __high2float(b01);
+                    vv[2] = __low2float(b23); vv[3] = __high2float(b23);
+                } else {
+                    const __nv_bfloat16 b = __float2bfloat16_rn(v[0]);
+                    xt16[p * Dp + j] = b;
+                    vv[0] = __bfloat162float(b);
+                }
+            } else {
+                if constexpr (V == 4)
+                    *reinterpret_cast<float4*>(xt32 + p * Dp + j) = make_float4(v[0], v[1], v[2], v[3]);
+                else
+                    xt32[p * Dp + j] = v[0];
+#pragma unroll
+                for (int q = 0; q < V; ++q) vv[q] = v[q];
+            }
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                n2v[q] = fmaf(vv[q], vv[q], n2v[q]);
+                const float e = vv[q] - v[q];
+                e2v[q] = fmaf(e, e, e2v[q]);
+                v2v[q] = fmaf(v[q], v[q], v2v[q]);
+            }
+        }
+        float n2 = n2v[0], e2 = e2v[0], v2 = v2v[0];
+        if constexpr (V == 4) {
+            n2 = (n2v[0] + n2v[1]) + (n2v[2] + n2v[3]);
+            e2 = (e2v[0] + e2v[1]) + (e2v[2] + e2v[3]);
+            v2 = (v2v[0] + v2v[1]) + (v2v[2] + v2v[3]);
         }
         // butterfly sums of the lane sums as unevaluated float pairs (2Sum):
         // within a few u^2 of the exact sum, and off the slow float64 pipe
@@ -1054,6 +1117,40 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                                 int64_t N, int Dp, int64_t Np, int kc, int splits,
                                 float* cand_d, int32_t* cand_i, unsigned int* err_flag);
 
+namespace {
+
+// Column sums, mu and the prepared rows on the context's stream; 16-byte
+// loads where the row layout and the summation bound allow them.
+slk_status launch_prep(slk_ctx* ctx, const float* X, int64_t N, int D, int Dp, int64_t Np,
+                       double* colsum, float* mu, float* xt32, __nv_bfloat16* xt16,
+                       float* norms, float* rho, float* norms32, DevState* st) {
+    cudaStream_t s = ctx->stream;
+    const bool v4 = D % 4 == 0 && Dp >= 128 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(mu) & 15) == 0;
+    int gy = (int)((N + 511) / 512);   // 64 rows per thread
+    if (gy > 8192) gy = 8192;
+    if (gy < 1) gy = 1;
+    const int groups = v4 ? D / 4 : D;
+    const dim3 cgrid((unsigned)((groups + 31) / 32), (unsigned)gy);
+    if (v4) col_sum_kernel<4><<<cgrid, dim3(32, 8), 0, s>>>(X, N, D, colsum);
+    else col_sum_kernel<1><<<cgrid, dim3(32, 8), 0, s>>>(X, N, D, colsum);
+    mu_kernel<<<(D + 255) / 256, 256, 0, s>>>(colsum, N, D, mu);
+    SLK_LAUNCH_CHECK(ctx, "col_sum_kernel");
+    int64_t pg = (Np + 7) / 8;
+    if (pg > (int64_t)ctx->num_sms * 64) pg = (int64_t)ctx->num_sms * 64;
+    const int to_bf16 = xt16 != nullptr ? 1 : 0;
+    if (v4)
+        prep_rows_kernel<4><<<(unsigned)pg, 256, 0, s>>>(X, N, D, Dp, Np, mu, to_bf16, xt32, xt16,
+                                                         norms, rho, norms32, st);
+    else
+        prep_rows_kernel<1><<<(unsigned)pg, 256, 0, s>>>(X, N, D, Dp, Np, mu, to_bf16, xt32, xt16,
+                                                         norms, rho, norms32, st);
+    SLK_LAUNCH_CHECK(ctx, "prep_rows_kernel");
+    return SLK_OK;
+}
+
+}  // namespace
+
 slk_status knn_prep_fp32_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int Dp, int64_t Np,
                                 double* colsum, float* mu, float* xt, float* norms, float* rho,
                                 DevState* st) {
@@ -1061,18 +1158,7 @@ slk_status knn_prep_fp32_launch(slk_ctx* ctx, const float* X, int64_t N, int D, 
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(colsum, 0, sizeof(double) * D, s));
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_bits, 0, 2 * sizeof(unsigned int), s));
     SLK_COUNT_LAUNCH(ctx, 2);
-    int gy = (int)((N + 511) / 512);   // 64 rows per thread
-    if (gy > 8192) gy = 8192;
-    if (gy < 1) gy = 1;
-    col_sum_kernel<<<dim3((unsigned)((D + 31) / 32), (unsigned)gy), dim3(32, 8), 0, s>>>(X, N, D, colsum);
-    mu_kernel<<<(D + 255) / 256, 256, 0, s>>>(colsum, N, D, mu);
-    SLK_LAUNCH_CHECK(ctx, "col_sum_kernel");
-    int64_t pg = (Np + 7) / 8;
-    if (pg > (int64_t)ctx->num_sms * 64) pg = (int64_t)ctx->num_sms * 64;
-    prep_rows_kernel<<<(unsigned)pg, 256, 0, s>>>(X, N, D, Dp, Np, mu, 0, xt, nullptr, norms,
-                                                   rho, nullptr, st);
-    SLK_LAUNCH_CHECK(ctx, "prep_rows_kernel");
-    return SLK_OK;
+    return launch_prep(ctx, X, N, D, Dp, Np, colsum, mu, xt, nullptr, norms, rho, nullptr, st);
 }
 
 slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int k,
@@ -1100,19 +1186,11 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     {
         PhaseScope ps(ctx, SLK_PHASE_KNN_PREP);
         SLK_COUNT_LAUNCH(ctx, 3);
-        int gy = (int)((N + 511) / 512);   // 64 rows per thread
-        if (gy > 8192) gy = 8192;
-        if (gy < 1) gy = 1;
-        dim3 grid((unsigned)((D + 31) / 32), (unsigned)gy);
-        col_sum_kernel<<<grid, dim3(32, 8), 0, s>>>(X, N, D, colsum);
-        mu_kernel<<<(D + 255) / 256, 256, 0, s>>>(colsum, N, D, mu);
-        SLK_LAUNCH_CHECK(ctx, "col_sum_kernel");
-        int64_t pg = (pl.Np + 7) / 8;
-        if (pg > (int64_t)ctx->num_sms * 64) pg = (int64_t)ctx->num_sms * 64;
-        prep_rows_kernel<<<(unsigned)pg, 256, 0, s>>>(
-            X, N, D, pl.Dp, pl.Np, mu, pl.bf16 ? 1 : 0, pl.bf16 ? nullptr : (float*)xt,
-            pl.bf16 ? (__nv_bfloat16*)xt : nullptr, norms, rho, pl.bf16 ? norms32 : nullptr, st);
-        SLK_LAUNCH_CHECK(ctx, "prep_rows_kernel");
+        const slk_status r = launch_prep(ctx, X, N, D, pl.Dp, pl.Np, colsum, mu,
+                                         pl.bf16 ? nullptr : (float*)xt,
+                                         pl.bf16 ? (__nv_bfloat16*)xt : nullptr, norms, rho,
+                                         pl.bf16 ? norms32 : nullptr, st);
+        if (r != SLK_OK) return r;
     }
     float u_acc;
     {
