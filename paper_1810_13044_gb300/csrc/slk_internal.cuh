@@ -296,6 +296,49 @@ __device__ __forceinline__ double warp_sq_dist(const float* __restrict__ xp,
         fpair_add(h, lo, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, lo, o));
     return (double)h + (double)lo;
 }
+// warp_sq_dist with 16-byte loads (D a multiple of 4, rows 16-byte aligned):
+// a chunk covers 4 float4 per lane, one float32 accumulator per column of
+// the lane's 4-column groups (at most 4 squares each, as accurate as the
+// chunks of 8 above), the accumulators added as float pairs.
+__device__ __forceinline__ double warp_sq_dist4(const float* __restrict__ xp,
+                                                const float* __restrict__ xm,
+                                                const float* __restrict__ xl, int D, int lane) {
+    const int D4 = D >> 2;
+    const float4* p4 = reinterpret_cast<const float4*>(xp);
+    const float4* m4 = reinterpret_cast<const float4*>(xm);
+    const float4* l4 = reinterpret_cast<const float4*>(xl);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float h = 0.f, lo = 0.f;
+    for (int j0 = lane; j0 < D4; j0 += 128) {
+        float4 a[4], b[4], c[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int j = j0 + 32 * t;
+            a[t] = j < D4 ? p4[j] : z4;
+            b[t] = j < D4 ? m4[j] : z4;
+            c[t] = (xl && j < D4) ? l4[j] : z4;
+        }
+        float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            float dx = a[t].x - b[t].x, dy = a[t].y - b[t].y, dz = a[t].z - b[t].z,
+                  dw = a[t].w - b[t].w;
+            if (xl) { dx -= c[t].x; dy -= c[t].y; dz -= c[t].z; dw -= c[t].w; }
+            q0 = fmaf(dx, dx, q0);
+            q1 = fmaf(dy, dy, q1);
+            q2 = fmaf(dz, dz, q2);
+            q3 = fmaf(dw, dw, q3);
+        }
+        fpair_add(h, lo, q0, 0.f);
+        fpair_add(h, lo, q1, 0.f);
+        fpair_add(h, lo, q2, 0.f);
+        fpair_add(h, lo, q3, 0.f);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        fpair_add(h, lo, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, lo, o));
+    return (double)h + (double)lo;
+}
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -190,8 +190,9 @@ __global__ void set_sigma_kernel(float sigma, DevState* st) { st->sigma = sigma;
 // distance and cut of the warp's points i, i + 32, ... until it has to add
 // them, so that the float64 kernel value exp(-d2 / (2 sigma^2)) is one
 // warp-wide instruction sequence per 32 points rather than one single-lane
-// sequence per point.
-__global__ void __launch_bounds__(256)
+// sequence per point.  V4: 16-byte row loads (warp_sq_dist4).
+template <bool V4>
+__global__ void __launch_bounds__(256, 4)
 energy_kernel(const float* __restrict__ X, int D, const int32_t* __restrict__ labels,
               const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
               const float* __restrict__ w, int64_t N, const int32_t* __restrict__ modes,
@@ -210,7 +211,8 @@ energy_kernel(const float* __restrict__ X, int D, const int32_t* __restrict__ la
         const int lp = labels[p];
         const float* xp = X + p * D;
         const float* xm = M ? M + (int64_t)lp * D : X + (int64_t)modes[lp] * D;
-        const double d2 = warp_sq_dist(xp, xm, Mlo ? Mlo + (int64_t)lp * D : nullptr, D, lane);
+        const float* xl = Mlo ? Mlo + (int64_t)lp * D : nullptr;
+        const double d2 = V4 ? warp_sq_dist4(xp, xm, xl, D, lane) : warp_sq_dist(xp, xm, xl, D, lane);
         float ch = 0.f, cl = 0.f;
         for (int64_t e = row_ptr[p] + lane; e < row_ptr[p + 1]; e += 32) {
             const int q = col_idx[e];
@@ -294,10 +296,16 @@ slk_status energy_launch(slk_ctx* ctx, const float* X, int D, const int32_t* lab
     PhaseScope ps(ctx, SLK_PHASE_ENERGY);
     SLK_COUNT_LAUNCH(ctx, 1);
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->energy, 0, sizeof(double), ctx->stream));
-    int64_t grid = (N + 7) / 8;
-    if (grid > (int64_t)ctx->num_sms * 8) grid = (int64_t)ctx->num_sms * 8;
-    energy_kernel<<<(unsigned)grid, 256, 0, ctx->stream>>>(X, D, labels, row_ptr, col_idx, w, N,
-                                                          modes, M, Mlo, sigma_dev, lambda, st);
+    int64_t grid = (N + 7) / 8;   // one wave: 4 CTAs per SM (launch bounds)
+    if (grid > (int64_t)ctx->num_sms * 4) grid = (int64_t)ctx->num_sms * 4;
+    auto al16 = [](const float* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    const bool v4 = D % 4 == 0 && al16(X) && (M == nullptr || al16(M)) && (Mlo == nullptr || al16(Mlo));
+    if (v4)
+        energy_kernel<true><<<(unsigned)grid, 256, 0, ctx->stream>>>(
+            X, D, labels, row_ptr, col_idx, w, N, modes, M, Mlo, sigma_dev, lambda, st);
+    else
+        energy_kernel<false><<<(unsigned)grid, 256, 0, ctx->stream>>>(
+            X, D, labels, row_ptr, col_idx, w, N, modes, M, Mlo, sigma_dev, lambda, st);
     SLK_LAUNCH_CHECK(ctx, "energy_kernel");
     return SLK_OK;
 }
