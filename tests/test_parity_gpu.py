@@ -89,6 +89,21 @@ def test_knn_matches_oracle(slk, N, D, k, seed, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16_rerank"])
+@pytest.mark.parametrize("N,D,k,top,seed", [(2500, 8, 10, 3, 51), (4000, 12, 16, 20, 52)])
+def test_knn_integer_lattice_exact_ties(slk, N, D, k, top, seed, precision):
+    """Integer coordinates in [0, top]: every squared distance is a small
+    integer, exact in float32 and float64, so equal distances are exact ties
+    (many of them straddle the k-th place and the candidate lists' ends).
+    Both sides order by (distance, index), so the graphs agree entry by
+    entry, with no tie allowance."""
+    X = inputs.rng(seed).integers(0, top + 1, size=(N, D)).astype(np.float32)
+    o_idx, o_d2 = oracle.knn(X, k)
+    g = slk.knn_graph(dev(X), k, precision=precision)
+    np.testing.assert_array_equal(host(g.col_idx).reshape(N, k), o_idx)
+    np.testing.assert_array_equal(host(g.dist2).reshape(N, k).astype(np.float64), o_d2)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16_rerank"])
 def test_knn_all_rows_through_exact_rescan(slk, precision):
     """Two tight clusters 2000 apart: the centred norms dwarf the neighbour
     distances, no row can be certified, and every row goes through the
