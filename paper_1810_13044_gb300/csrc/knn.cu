@@ -713,21 +713,26 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
             T = fminf(T, ts);
         }
         // Candidates that cannot be among the k nearest need no exact
-        // distance.  With |dt - |xt_p - xt_q|^2| <= delta and
-        // |xt - (x - mu)| <= rho, the exact distance of candidate c lies in
-        // [lb_c, ub_c] = [(sqrt(dt - delta) - rho_p - rho_max)^2,
-        // (sqrt(dt + delta) + rho_p + rho_max)^2].  Both bounds grow with dt
-        // and the candidates come in increasing dt, so the k-th smallest ub
-        // is that of candidate k - 1; a candidate whose lb exceeds it (by
-        // more than the float32 rounding of the exact sums) is beaten by k
-        // candidates whatever the rounding.  Skipped candidates keep an
-        // infinite distance, so they rank after every computed one and the
-        // k nearest, their distances and the certificate are unchanged.
+        // distance.  With |dt - |xt_p - xt_q|^2| <= delta_q =
+        // coef (|xt_p| + |xt_q|)^2 and |xt - (x - mu)| <= rho, the exact
+        // distance of candidate c = q lies in
+        // [lb_c, ub_c] = [(sqrt(dt - delta_q) - rho_p - rho_q)^2,
+        // (sqrt(dt + delta_q) + rho_p + rho_q)^2].  Every ub_c is at most the
+        // same bound taken with the largest norm and rho of all rows, which
+        // grows with dt, and the candidates come in increasing dt, so the
+        // k-th smallest ub is at most that bound of candidate k - 1 (U); a
+        // candidate whose own lb exceeds U (by more than the float32
+        // rounding of the exact sums) is beaten by k candidates whatever the
+        // rounding.  Skipped candidates keep an infinite distance, so they
+        // rank after every computed one and the k nearest, their distances
+        // and the certificate are unchanged.
         unsigned need[CPL];
         {
             const float npf = norms[p];
-            const float rr = (Q ? 5.9604645e-08f * 1.000001f * sqrtf(npf) : rho[p] * 1.000001f) + rmax_f;
-            const float snf = sqrtf(npf) * 1.000001f + snmax_f;
+            const float rp = Q ? 5.9604645e-08f * 1.000001f * sqrtf(npf) : rho[p] * 1.000001f;
+            const float snp = sqrtf(npf) * 1.000001f;   // the row's own terms
+            const float rr = rp + rmax_f;
+            const float snf = snp + snmax_f;
             const float dl = coef_f * snf * snf;
             float U = kInf;
             if (nc >= k) {
@@ -743,8 +748,12 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
             for (int h = 0; h < CPL; ++h) {
                 bool keep = false;
                 if (lane + 32 * h < nc) {
-                    const float lo = cd[h] - dl;
-                    const float r = lo > 0.f ? sqrtf(lo) * 0.99999f - rr : 0.f;
+                    const int q = ci[h];
+                    const float nqf = norms[q];
+                    const float rq = (Q ? 5.9604645e-08f * 1.000001f * sqrtf(nqf) : rho[q] * 1.000001f);
+                    const float snq = snp + sqrtf(nqf) * 1.000001f;
+                    const float lo = cd[h] - coef_f * snq * snq;
+                    const float r = lo > 0.f ? sqrtf(lo) * 0.99999f - (rp + rq) : 0.f;
                     const float lb = r > 0.f ? r * r * 0.99999f : 0.f;
                     keep = !(lb > lim);
                 }
