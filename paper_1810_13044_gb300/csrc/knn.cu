@@ -6,18 +6,22 @@
 //     translation invariant) and round them to the candidate operand type
 //     (float32 or bfloat16).  Per point keep ||xt_p||^2 and the rounding
 //     perturbation rho_p >= ||xt_p - (x_p - mu)|| (float32 lane sums with
-//     their rounding bounds, lanes added in float64).
+//     their rounding bounds, lanes added as 2Sum float pairs).
 //  2. candidates: a distance-tile kernel evaluates
 //     dt(p, q) = ||xt_p||^2 + ||xt_q||^2 - 2 xt_p . xt_q for all pairs and keeps,
-//     per row and per column split, the KC smallest (KC > k).
-//  3. rerank + certificate (one warp per row): merge the splits, recompute the
-//     KC candidates' distances exactly in float32 from the original features,
-//     keep the k smallest.  With T the KC-th smallest dt, every other point q
+//     per row and per column split, the KC smallest (KC > k), sorted.
+//  3. rerank + certificate (one warp per row): merge the splits' sorted lists,
+//     recompute exactly in float32, from the original features, the distances
+//     of the candidates whose lower bound can still reach the k nearest, keep
+//     the k smallest.  With T the KC-th smallest dt, every other point q
 //     satisfies dt(p,q) >= T, hence (rounding bounds below) its true distance
 //     is at least LB = (sqrt(T - delta) - rho_p - rho_max)^2.  The row is
 //     certified when the k-th exact distance, inflated by its own rounding
 //     bound, is below LB; then the row equals a full float32 scan.
-//  4. fallback: rows that fail the certificate are rescanned exactly.
+//  4. fallback: with bfloat16 candidates, the rows that fail the certificate
+//     first get float32 candidate tiles and the same rerank under the float32
+//     certificate; rows that fail that (or the float32 certificate of a
+//     float32 pass) are rescanned exactly.
 #include <cuda_bf16.h>
 #include <math.h>
 
