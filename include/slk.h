@@ -85,10 +85,13 @@ const char* slk_last_error(const slk_ctx* ctx);
  *   precision SLK_KNN_FP32: float32 SIMT distance tiles; SLK_KNN_BF16_RERANK:
  *            bfloat16 tensor-core (tcgen05) distance tiles.  Both produce
  *            candidates that are re-ranked with exact float32 distances and
- *            certified by a rounding-error bound; rows that fail the
- *            certificate are recomputed by an exact float32 scan, so both
- *            precisions return the same graph.
- *   fallback_rows [host, nullable]: receives how many rows were rescanned.
+ *            certified by a rounding-error bound.  With BF16_RERANK the rows
+ *            that fail it get float32 candidate tiles and the float32
+ *            certificate next; rows still uncertified are recomputed by an
+ *            exact float32 scan, so both precisions return the same graph.
+ *   fallback_rows [host, nullable]: receives how many rows the first
+ *            certificate left open (for BF16_RERANK: the rows sent to the
+ *            float32 stage).
  * Brute force, O(N^2 D) -- the paper's exact option for small sets. */
 slk_status slk_knn_graph(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int32_t k,
                          int32_t affinity, int32_t precision, float sigma,
