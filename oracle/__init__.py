@@ -5,8 +5,10 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 independent of the CUDA path: it shares no code with it and never takes an
 input that the CUDA path produced.
 
-The arithmetic lives in ``slk_oracle.c`` (plain C, double precision, one
-thread); this module only builds it with gcc and marshals numpy arrays.
+The arithmetic lives in ``slk_oracle.c`` (plain C, double precision); this
+module only builds it with gcc (with OpenMP where the compiler has it: rows
+that are independent run on all host cores, with results identical to one
+thread) and marshals numpy arrays.
 Parity of each function is pinned by the ``-m "not gpu"`` tests under
 ``tests/`` (brute force, closed forms, invariants, library special cases).
 """
@@ -31,12 +33,17 @@ CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (idempotent; rebuilds when the source is newer)."""
+    """Compile the oracle with gcc (idempotent; rebuilds when the source is newer).
+    OpenMP is used when gcc accepts -fopenmp, else the loops run on one thread."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    src_m = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    src_m = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR), os.path.getmtime(__file__))
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < src_m:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        try:
+            subprocess.check_call(["gcc", *CFLAGS, "-fopenmp", "-o", tmp, _SRC, "-lm"],
+                                  stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -49,6 +56,8 @@ def _load():
     P = ctypes.c_void_p
     i64, i32, f64 = ctypes.c_int64, ctypes.c_int, ctypes.c_double
     sig = {
+        "oracle_threads": (i32, [i32]),
+        "oracle_pair_d2": (i32, [P, i64, i32, P, P, i64, P]),
         "oracle_knn_rows": (i32, [P, i64, i32, i32, P, i64, P, P]),
         "oracle_knn": (i32, [P, i64, i32, i32, P, P]),
         "oracle_sigma": (f64, [P, i64, i32]),
@@ -73,6 +82,7 @@ def _load():
                                         i32, f64, f64, P, P, P, P, P, P]),
         "oracle_initial_modes": (i32, [P, i64, i32, P, i32, f64, P, P, P]),
         "oracle_cluster_density": (i32, [P, i64, i32, P, i32, f64, P, i64, P]),
+        "oracle_kmeanspp": (i32, [P, i64, i32, i32, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -93,6 +103,22 @@ def _p(a):
 def _check(rc, what):
     if rc < 0:
         raise ValueError(f"oracle {what}: invalid arguments (code {rc})")
+
+
+def threads(n: int = 0) -> int:
+    """Threads of the oracle's row-parallel loops (n > 0 sets the count first)."""
+    return int(_load().oracle_threads(int(n)))
+
+
+def pair_d2(X, p, q):
+    """||x_p - x_q||^2 (float64, the kNN scan's own sums) for the pairs (p[i], q[i])."""
+    lib = _load()
+    X = _c(X, np.float32)
+    p = _c(p, np.int64).reshape(-1)
+    q = _c(q, np.int64).reshape(-1)
+    out = np.empty(p.size, np.float64)
+    _check(lib.oracle_pair_d2(_p(X), X.shape[0], X.shape[1], _p(p), _p(q), p.size, _p(out)), "pair_d2")
+    return out
 
 
 def knn(X, k, rows=None):
@@ -389,3 +415,19 @@ def cluster_density(X, assign, l, sig, ys):
     _check(lib.oracle_cluster_density(_p(X), X.shape[0], X.shape[1], _p(assign), int(l), float(sig),
                                       _p(ys), len(ys), _p(out)), "cluster_density")
     return out
+
+
+# ---------------------------------------------------------------- K-means++ seeds
+
+def kmeanspp(X, L, first, u):
+    """K-means++ seeds from the given draws (first index, L - 1 uniforms in
+    [0, 1)) -> int32 [L]."""
+    lib = _load()
+    X = _c(X, np.float32)
+    u = _c(u, np.float64).reshape(-1)
+    if u.size != max(L - 1, 0):
+        raise ValueError("need L - 1 uniform draws")
+    seeds = np.empty(L, np.int32)
+    _check(lib.oracle_kmeanspp(_p(X), X.shape[0], X.shape[1], int(L), int(first),
+                               _p(u) if u.size else None, _p(seeds)), "kmeanspp")
+    return seeds

@@ -12,6 +12,33 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the row-parallel loops.  Only loops whose iterations are
+ * independent (one output row each, or a maximum) run in parallel, so the
+ * results are bit-identical for every thread count. */
+int oracle_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+static int thread_index(void)
+{
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
 /* ||x_p - x_q||^2 with every difference and product in double.  A float
  * difference is exact in double and so is its square (two 24-bit
  * significands), so only the running sum rounds. */
@@ -30,7 +57,29 @@ static double sqdist(const float* X, int D, int64_t p, int64_t q)
 /* Section 4.2: kNN affinity, N_p = the k nearest neighbours of x_p by
  * Euclidean distance.  The point itself is excluded; ties go to the smaller
  * index (the scan runs over increasing q and only a strictly smaller
- * distance displaces an earlier entry). */
+ * distance displaces an earlier entry).  bd / bi hold the sorted list. */
+static void knn_one_row(const float* X, int64_t N, int D, int k, int64_t p,
+                        double* bd, int32_t* bi, int32_t* idx_out, double* d2_out)
+{
+    int count = 0;
+    for (int64_t q = 0; q < N; ++q) {
+        if (q == p) continue;
+        double d = sqdist(X, D, p, q);
+        if (count == k && !(d < bd[k - 1])) continue;
+        /* insertion into the ascending list, after every entry <= d */
+        int pos = count < k ? count : k - 1;
+        while (pos > 0 && bd[pos - 1] > d) {
+            if (pos < k) { bd[pos] = bd[pos - 1]; bi[pos] = bi[pos - 1]; }
+            --pos;
+        }
+        bd[pos] = d;
+        bi[pos] = (int32_t)q;
+        if (count < k) ++count;
+    }
+    memcpy(idx_out, bi, sizeof(int32_t) * (size_t)k);
+    memcpy(d2_out, bd, sizeof(double) * (size_t)k);
+}
+
 int oracle_knn_rows(const float* X, int64_t N, int D, int k,
                     const int64_t* rows, int64_t nrows,
                     int32_t* idx_out, double* d2_out)
@@ -41,31 +90,31 @@ int oracle_knn_rows(const float* X, int64_t N, int D, int k,
         int64_t p = rows[r];
         if (p < 0 || p >= N) return -1;
     }
-    double* bd = (double*)malloc(sizeof(double) * (size_t)k);
-    int32_t* bi = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+    /* one sorted list per thread */
+    int nt = oracle_threads(0);
+    double* bd = (double*)malloc(sizeof(double) * (size_t)k * (size_t)nt);
+    int32_t* bi = (int32_t*)malloc(sizeof(int32_t) * (size_t)k * (size_t)nt);
     if (!bd || !bi) { free(bd); free(bi); return -2; }
+#pragma omp parallel for schedule(dynamic, 4)
     for (int64_t r = 0; r < nrows; ++r) {
-        int64_t p = rows[r];
-        int count = 0;
-        for (int64_t q = 0; q < N; ++q) {
-            if (q == p) continue;
-            double d = sqdist(X, D, p, q);
-            if (count == k && !(d < bd[k - 1])) continue;
-            /* insertion into the ascending list, after every entry <= d */
-            int pos = count < k ? count : k - 1;
-            while (pos > 0 && bd[pos - 1] > d) {
-                if (pos < k) { bd[pos] = bd[pos - 1]; bi[pos] = bi[pos - 1]; }
-                --pos;
-            }
-            bd[pos] = d;
-            bi[pos] = (int32_t)q;
-            if (count < k) ++count;
-        }
-        memcpy(idx_out + r * k, bi, sizeof(int32_t) * (size_t)k);
-        memcpy(d2_out + r * k, bd, sizeof(double) * (size_t)k);
+        int t = thread_index();
+        knn_one_row(X, N, D, k, rows[r], bd + (size_t)t * k, bi + (size_t)t * k,
+                    idx_out + r * k, d2_out + r * k);
     }
     free(bd);
     free(bi);
+    return 0;
+}
+
+/* ||x_p - x_q||^2 (the sum of the kNN scan) for n given pairs. */
+int oracle_pair_d2(const float* X, int64_t N, int D, const int64_t* p, const int64_t* q,
+                   int64_t n, double* out)
+{
+    if (!X || N < 1 || D < 1 || !p || !q || n < 0 || !out) return -1;
+    for (int64_t i = 0; i < n; ++i)
+        if (p[i] < 0 || p[i] >= N || q[i] < 0 || q[i] >= N) return -1;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) out[i] = sqdist(X, D, p[i], q[i]);
     return 0;
 }
 
@@ -124,6 +173,7 @@ int oracle_unary(const float* X, int64_t N, int D, const int32_t* modes, int L,
     if (!X || N < 1 || D < 1 || !modes || L < 1 || !(sigma > 0.0) || !A) return -1;
     for (int l = 0; l < L; ++l)
         if (modes[l] < 0 || modes[l] >= N) return -1;
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < N; ++p)
         for (int l = 0; l < L; ++l)
             A[p * L + l] = oracle_gauss(sqdist(X, D, p, modes[l]), sigma);
@@ -134,6 +184,7 @@ int oracle_unary(const float* X, int64_t N, int D, const int32_t* modes, int L,
  * (the same ratio; the shift only keeps exp in range). */
 void oracle_softmax_rows(const double* S, int64_t N, int L, double* Z)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < N; ++p) {
         const double* s = S + p * L;
         double m = s[0];
@@ -149,6 +200,7 @@ void oracle_softmax_rows(const double* S, int64_t N, int L, double* Z)
 void oracle_pairwise(const int64_t* row_ptr, const int32_t* col_idx, const double* w,
                      int64_t N, int L, const double* Z, double* B)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < N; ++p) {
         for (int l = 0; l < L; ++l) B[p * L + l] = 0.0;
         for (int64_t e = row_ptr[p]; e < row_ptr[p + 1]; ++e) {
@@ -165,6 +217,7 @@ void oracle_logits(const double* A, const int64_t* row_ptr, const int32_t* col_i
                    const double* Z, double* S)
 {
     oracle_pairwise(row_ptr, col_idx, w, N, L, Z, S);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N * (int64_t)L; ++i) S[i] = A[i] + lambda * S[i];
 }
 
@@ -187,6 +240,7 @@ int oracle_bound_iterate(const double* A, const int64_t* row_ptr, const int32_t*
         oracle_logits(A, row_ptr, col_idx, w, N, L, lambda, Z, S);
         oracle_softmax_rows(S, N, L, Znew);
         delta = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : delta)
         for (size_t i = 0; i < n; ++i) {
             double d = fabs(Znew[i] - Z[i]);
             if (d > delta) delta = d;
@@ -208,6 +262,7 @@ int oracle_bound_iterate(const double* A, const int64_t* row_ptr, const int32_t*
  * the log1p form keeping full precision when z_{q,l} is close to 1. */
 void oracle_log_z(const double* S, int64_t N, int L, double* logZ)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t q = 0; q < N; ++q) {
         const double* s = S + q * L;
         int jstar = 0;
@@ -240,6 +295,7 @@ void oracle_mode_update(const double* S, int64_t N, int L, int32_t* modes_out, d
  * soft-max being monotone within a row), ties to the smaller l. */
 void oracle_labels(const double* S, int64_t N, int L, int32_t* labels)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < N; ++p) {
         int best = 0;
         for (int l = 1; l < L; ++l) if (S[p * L + l] > S[p * L + best]) best = l;
@@ -551,5 +607,49 @@ int oracle_cluster_density(const float* X, int64_t N, int D, const int32_t* assi
             if (assign[p] == l) f += oracle_gauss(sqdist(X, D, p, ys[i]), sigma);
         out[i] = f;
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ K-means++ seeds */
+
+/* K-means++ seeding (Section 4.2 takes its initial seeds from Arthur and
+ * Vassilvitskii's K-means++): seed 0 is the given point `first`; seed i is
+ * drawn with probability proportional to D(x)^2, the squared distance to the
+ * closest seed so far.  The draw is made with the given uniform u[i-1] in
+ * [0, 1): r = u[i-1] * sum_p D(x_p)^2, and the seed is the first p whose
+ * running sum D(x_0)^2 + ... + D(x_p)^2 exceeds r (the last point if none
+ * does).  When every D(x)^2 is zero the seed is point floor(u[i-1] N). */
+int oracle_kmeanspp(const float* X, int64_t N, int D, int L, int32_t first, const double* u,
+                    int32_t* seeds)
+{
+    if (!X || N < 1 || D < 1 || L < 1 || L > N || first < 0 || first >= N || (L > 1 && !u) || !seeds)
+        return -1;
+    double* closest = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!closest) return -2;
+    for (int64_t p = 0; p < N; ++p) closest[p] = INFINITY;
+    seeds[0] = first;
+    for (int i = 1; i < L; ++i) {
+        int64_t c = seeds[i - 1];
+#pragma omp parallel for schedule(static)
+        for (int64_t p = 0; p < N; ++p) {
+            double d = sqdist(X, D, p, c);
+            if (d < closest[p]) closest[p] = d;
+        }
+        double total = 0.0;
+        for (int64_t p = 0; p < N; ++p) total += closest[p];
+        int64_t pick = N - 1;
+        if (total > 0.0) {
+            double r = u[i - 1] * total, run = 0.0;
+            for (int64_t p = 0; p < N; ++p) {
+                run += closest[p];
+                if (run > r) { pick = p; break; }
+            }
+        } else {
+            pick = (int64_t)(u[i - 1] * (double)N);
+            if (pick > N - 1) pick = N - 1;
+        }
+        seeds[i] = (int32_t)pick;
+    }
+    free(closest);
     return 0;
 }

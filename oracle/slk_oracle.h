@@ -8,7 +8,10 @@
  * with the CUDA library, and it never reads anything the CUDA path produced.
  *
  * Plain, slow, obviously correct: every function is the paper's definition
- * written out with scalar loops in double precision, single-threaded.
+ * written out with scalar loops in double precision.  Built with OpenMP, the
+ * loops whose iterations are independent (one output row each, or a
+ * maximum) are shared among threads; every sum keeps its sequential order,
+ * so results do not depend on the thread count.
  * Inputs X are the float32 features; every other real value is double.
  *
  * Conventions: X is N x D row-major; A, Z, S are N x L row-major; the affinity
@@ -24,12 +27,21 @@
 extern "C" {
 #endif
 
+/* Number of threads of the row-parallel loops (n > 0 sets it first);
+ * 1 when the library was built without OpenMP. */
+int oracle_threads(int n);
+
 /* Exact kNN of Section 4.2: for each requested row p, the k points q != p with
  * the smallest squared Euclidean distance, ascending by (distance, index). */
 int oracle_knn_rows(const float* X, int64_t N, int D, int k,
                     const int64_t* rows, int64_t nrows,
                     int32_t* idx_out, double* d2_out);
 int oracle_knn(const float* X, int64_t N, int D, int k, int32_t* idx_out, double* d2_out);
+
+/* Squared distances ||x_p[i] - x_q[i]||^2 of n point pairs (the sum of the
+ * kNN scan, so they equal the d2 it reports for the same pairs). */
+int oracle_pair_d2(const float* X, int64_t N, int D, const int64_t* p, const int64_t* q,
+                   int64_t n, double* out);
 
 /* Kernel width of Section 4.2.  rule 0: sigma = median of the n Euclidean
  * kNN distances sqrt(d2) (mean of the two middle values for even n);
@@ -149,6 +161,14 @@ int oracle_initial_modes(const float* X, int64_t N, int D, const int32_t* seeds,
 /* The cluster density sum_{p: assign[p] = l} k(x_p, x_y) at the given points y. */
 int oracle_cluster_density(const float* X, int64_t N, int D, const int32_t* assign, int l,
                            double sigma, const int64_t* ys, int64_t ny, double* out);
+
+/* ---- K-means++ seeds (Section 4.2 cites Arthur & Vassilvitskii 2007) ----
+ * seeds[0] = first; seeds[i] = the first p whose running sum of
+ * D(x_p)^2 (squared distance to the closest of seeds[0..i-1]) exceeds
+ * u[i-1] * sum_p D(x_p)^2, the last point if none does; if every D(x)^2 is 0,
+ * point floor(u[i-1] N).  u: L - 1 uniform draws in [0, 1). */
+int oracle_kmeanspp(const float* X, int64_t N, int D, int L, int32_t first, const double* u,
+                    int32_t* seeds);
 
 #ifdef __cplusplus
 }
