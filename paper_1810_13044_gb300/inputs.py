@@ -30,7 +30,7 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
-    "rng", "blobs", "mnist_like", "manifolds", "mixture", "kmeanspp",
+    "rng", "blobs", "mnist_like", "manifolds", "mixture", "kmeanspp", "kmeanspp_draws",
     "random_graph", "random_unary", "random_simplex_rows", "WORKLOADS",
 ]
 
@@ -80,20 +80,33 @@ def blobs(N: int = 2000, D: int = 16, n_blobs: int = 5, centre_var: float = 25.0
     return _shuffle(g, X.astype(np.float32), y)
 
 
+def _dyadic(x: np.ndarray, bits: int, lim: float) -> np.ndarray:
+    """x clipped to [-lim, lim] and rounded to a multiple of 2^-bits (float64)."""
+    return np.round(np.clip(x, -lim, lim) * 2.0 ** bits) / 2.0 ** bits
+
+
 def mnist_like(N: int = 70000, D: int = 784, n_clusters: int = 10, latent: int = 10,
                hidden: int = 256, seed: int = 1810):
     """Latent Gaussians u ~ N(mu_c, I) with mu_c ~ N(0, 9 I), a fixed random
-    map x = W2 ReLU(W1 u + b1) + b2, then per-feature min-max to [0, 1]."""
+    map x = W2 ReLU(W1 u + b1) + b2, then per-feature min-max to [0, 1].
+
+    Every random factor is rounded to a short dyadic grid (and clipped far
+    out in its tail) so that each product and every partial sum of the two
+    matrix products is exact in float64: the result does not depend on the
+    order in which a BLAS library adds, so x86 and Arm hosts produce the
+    same bits.  Grids and bounds: mu, u - mu, W1, b1, b2 on 2^-16, W2 on
+    2^-12, the hidden layer rounded to 2^-20; every sum then stays below
+    2^50 units of its grid."""
     g = rng(seed)
-    mu = g.normal(0.0, 3.0, size=(n_clusters, latent))
-    W1 = g.normal(0.0, np.sqrt(1.0 / latent), size=(hidden, latent))
-    b1 = g.normal(0.0, 1.0, size=hidden)
-    W2 = g.normal(0.0, np.sqrt(1.0 / hidden), size=(D, hidden))
-    b2 = g.normal(0.0, 0.1, size=D)
+    mu = _dyadic(g.normal(0.0, 3.0, size=(n_clusters, latent)), 16, 24.0)
+    W1 = _dyadic(g.normal(0.0, np.sqrt(1.0 / latent), size=(hidden, latent)), 16, 2.0)
+    b1 = _dyadic(g.normal(0.0, 1.0, size=hidden), 16, 8.0)
+    W2 = _dyadic(g.normal(0.0, np.sqrt(1.0 / hidden), size=(D, hidden)), 12, 0.5)
+    b2 = _dyadic(g.normal(0.0, 0.1, size=D), 16, 1.0)
     sizes = _split_sizes(N, np.ones(n_clusters))
     y = np.repeat(np.arange(n_clusters, dtype=np.int32), sizes)
-    U = mu[y] + g.normal(0.0, 1.0, size=(N, latent))
-    H = np.maximum(U @ W1.T + b1, 0.0)
+    U = mu[y] + _dyadic(g.normal(0.0, 1.0, size=(N, latent)), 16, 8.0)
+    H = _dyadic(np.maximum(U @ W1.T + b1, 0.0), 20, 1e6)
     X = H @ W2.T + b2
     lo = X.min(axis=0)
     hi = X.max(axis=0)
@@ -138,18 +151,29 @@ def mixture(N: int, D: int, n_clusters: int, seed: int, largest=(0.6, 0.8)):
     return _shuffle(g, X.astype(np.float32), y)
 
 
+def kmeanspp_draws(N: int, L: int, seed: int = 1810):
+    """The random draws of K-means++ seeding: the first seed's index (uniform
+    over the N points) and L - 1 uniforms in [0, 1), one per further seed."""
+    g = rng(seed)
+    first = int(g.integers(N))
+    u = g.random(max(L - 1, 0))
+    return first, u
+
+
 def kmeanspp(X: np.ndarray, L: int, seed: int = 1810, chunk: int = 65536) -> np.ndarray:
     """K-means++ seeding (Arthur & Vassilvitskii 2007): the first seed is a
     uniformly drawn point, each next one is drawn with probability
-    proportional to the squared distance to the closest seed so far.
-    Returns ``L`` point indices (int32)."""
-    g = rng(seed)
+    proportional to the squared distance to the closest seed so far -- the
+    point at which the running sum of those squared distances first exceeds
+    u * their total, u the next uniform of :func:`kmeanspp_draws` (when every
+    distance is zero: point floor(u N)).  Returns ``L`` point indices (int32)."""
     N = X.shape[0]
     if not 1 <= L <= N:
         raise ValueError("need 1 <= L <= N")
-    seeds = [int(g.integers(N))]
+    first, u = kmeanspp_draws(N, L, seed)
+    seeds = [first]
     closest = np.full(N, np.inf)
-    for _ in range(1, L):
+    for i in range(1, L):
         c = X[seeds[-1]].astype(np.float64)
         for s in range(0, N, chunk):
             diff = X[s:s + chunk].astype(np.float64) - c
@@ -157,11 +181,9 @@ def kmeanspp(X: np.ndarray, L: int, seed: int = 1810, chunk: int = 65536) -> np.
                        out=closest[s:s + chunk])
         total = closest.sum()
         if total <= 0.0:
-            cand = np.setdiff1d(np.arange(N), np.array(seeds))
-            seeds.append(int(cand[g.integers(len(cand))]) if len(cand) else seeds[-1])
+            seeds.append(min(int(u[i - 1] * N), N - 1))
             continue
-        r = g.uniform(0.0, total)
-        idx = int(np.searchsorted(np.cumsum(closest), r, side="right"))
+        idx = int(np.searchsorted(np.cumsum(closest), u[i - 1] * total, side="right"))
         seeds.append(min(idx, N - 1))
     return np.array(seeds, dtype=np.int32)
 
