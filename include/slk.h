@@ -123,12 +123,22 @@ slk_status slk_unary(slk_ctx* ctx, const float* X, int64_t N, int32_t D,
  *          update needs it); its input contents are ignored.  Must not alias Z.
  *   iters_done [host, nullable], last_delta [host, nullable].
  * Runs as one persistent cooperative kernel with a device-wide barrier
- * between updates; a barrier that waits more than about a second returns
- * SLK_ERR_TIMEOUT. */
+ * between updates; a barrier wait longer than 2 s gives up and the call
+ * returns SLK_ERR_TIMEOUT, with Z and Z_prev undefined (they may hold a
+ * partly written update). */
 slk_status slk_bound_iterate(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
                              const int32_t* col_idx, const float* w, int64_t N, int32_t L,
                              float lambda, float* Z, float* Z_prev, int32_t max_iters, float tol,
                              int32_t* iters_done, float* last_delta);
+
+/* Self-test of the failure path of the z-update kernels (no counterpart in
+ * the paper).  One block waits at the same bounded device-wide barrier for a
+ * second block that is never launched, so the wait must give up after
+ * timeout_ms (1 .. 2000) milliseconds.  Returns SLK_ERR_TIMEOUT -- the status
+ * slk_bound_iterate reports when its barrier gives up -- and leaves the
+ * context usable; any other status means the failure path is broken.
+ * Synchronises the context stream. */
+slk_status slk_barrier_selftest(slk_ctx* ctx, int32_t timeout_ms);
 
 /* SLK-BO mode update, Eq. (mode_byproduct): mode_idx[l] <- argmax_q z_{q,l}
  * (ties to the smaller q), where z_q = softmax(s_q) is the last iterate and
@@ -206,6 +216,20 @@ slk_status slk_solve_host(slk_ctx* ctx, const float* X, int64_t N, int32_t D, in
                           int32_t k, float lambda, float sigma, const int32_t* init_modes,
                           const slk_params* params, float* Z, int32_t* labels, int32_t* modes,
                           slk_stats* stats);
+
+/* K-means++ seeds (Section 4.2 takes the initial seeds from K-means++,
+ * Arthur & Vassilvitskii 2007), with the random draws made by the caller:
+ * seeds[0] = first; seeds[i] (i >= 1) is the first point p whose running sum
+ * D(x_0)^2 + ... + D(x_p)^2 exceeds u[i-1] * sum_q D(x_q)^2, where D(x)^2 is
+ * the squared Euclidean distance to the closest of seeds[0..i-1] (float64
+ * sums); the last point if no running sum does, and point floor(u[i-1] N) if
+ * every D(x)^2 is 0.  Two launches per seed: a float64 distance pass over X
+ * and a one-block selection.
+ *   X [N x D]; first in [0, N); u [host, L - 1] uniforms in [0, 1) (NULL
+ *   allowed when L = 1); seeds [L] device int32 out.  1 <= L <= N.
+ * Synchronises the context stream. */
+slk_status slk_kmeanspp(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int32_t L,
+                        int32_t first, const double* u, int32_t* seeds);
 
 /* Starting modes (Section 4.2: the starting mode of each cluster follows the
  * mode definition of Eq. (1) from the initial assignments): every point is
@@ -368,11 +392,13 @@ slk_status slk_server_request_bytes(slk_server* srv, const slk_instance* req, in
  *            last iterate); the previous iterate is not returned.
  * N * L must not exceed SLK_NOALLOC_MAX_ELEMS, else SLK_ERR_SCRATCH_LIMIT is
  * returned before anything runs.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call reuses the same array and re-initialises
- * the words that must start at zero; calls that overlap on the GPU (other
- * streams, other threads) race on it and must be serialised by the caller.
- * The call synchronises `stream` before returning. */
+ * array's device address (cudaGetSymbolAddress), and so does the first call
+ * after the device's context was replaced (cudaDeviceReset); make that first
+ * call before any stream capture.  Every call reuses the same array and
+ * re-initialises the words that must start at zero; calls that overlap on the
+ * GPU (other streams, other threads) race on it and must be serialised by the
+ * caller.  After SLK_ERR_TIMEOUT, Z is undefined.  The call synchronises
+ * `stream` before returning. */
 #define SLK_NOALLOC_MAX_ELEMS (4u << 20)   /* 4,194,304 floats = 16 MiB */
 #define SLK_NOALLOC_SCRATCH_BYTES (4096u + 4u * SLK_NOALLOC_MAX_ELEMS)
 slk_status slk_bound_iterate_noalloc(void* stream, const float* A, const int64_t* row_ptr,

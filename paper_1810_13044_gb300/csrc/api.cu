@@ -342,6 +342,20 @@ extern "C" slk_status slk_bound_iterate(slk_ctx* ctx, const float* A, const int6
     return SLK_OK;
 }
 
+extern "C" slk_status slk_barrier_selftest(slk_ctx* ctx, int32_t timeout_ms) {
+    BEGIN_CALL(ctx);
+    CHECK_ARG(timeout_ms >= 1 && timeout_ms <= 2000, "timeout_ms=%d must be in [1, 2000]", timeout_ms);
+    DevState* st = dstate(ctx);
+    slk_status r = barrier_probe_launch(ctx, st, (unsigned long long)timeout_ms * 1000000ull);
+    if (r != SLK_OK) return r;
+    DevState hs;
+    r = read_state(ctx, &hs);
+    if (r != SLK_OK) return r;
+    if (hs.error & ERR_BARRIER_TIMEOUT)
+        return set_err(ctx, SLK_ERR_TIMEOUT, "device-wide barrier of the bound kernel timed out");
+    return set_err(ctx, SLK_ERR_CUDA, "the barrier wait did not give up");
+}
+
 extern "C" slk_status slk_mode_update(slk_ctx* ctx, const float* A, const float* Z_prev,
                                       const int64_t* row_ptr, const int32_t* col_idx,
                                       const float* w, int64_t N, int32_t L, float lambda,
@@ -862,6 +876,25 @@ extern "C" slk_status slk_solve_ms(slk_ctx* ctx, const float* X, int64_t N, int3
 }
 
 // ---------------------------------------------------------------- starting modes
+
+extern "C" slk_status slk_kmeanspp(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int32_t L,
+                                   int32_t first, const double* u, int32_t* seeds) {
+    BEGIN_CALL(ctx);
+    CHECK_ARG(X && seeds, "X and seeds must not be NULL");
+    CHECK_ARG(N >= 1 && N < (int64_t)0x7fffffff, "N=%lld out of range", (long long)N);
+    CHECK_ARG(D >= 1, "D=%d must be >= 1", D);
+    CHECK_ARG(L >= 1 && L <= N, "L=%d must be in [1, N]", L);
+    CHECK_ARG(first >= 0 && first < N, "first=%d must be a point index", first);
+    CHECK_ARG(L == 1 || u, "u must not be NULL when L > 1");
+    for (int i = 0; i + 1 < L; ++i)
+        CHECK_ARG(u[i] >= 0.0 && u[i] < 1.0, "u[%d] must lie in [0, 1)", i);
+    slk_status r = ensure_ws(ctx, kmeanspp_ws_bytes(N, L));
+    if (r != SLK_OK) return r;
+    r = kmeanspp_launch(ctx, X, N, D, L, first, u, seeds, ctx->ws);
+    if (r != SLK_OK) return r;
+    // the draws are read from host memory by an asynchronous copy
+    return sync_and_check(ctx);
+}
 
 extern "C" slk_status slk_initial_modes(slk_ctx* ctx, const float* X, int64_t N, int32_t D,
                                         const int32_t* seeds, int32_t L, float sigma,

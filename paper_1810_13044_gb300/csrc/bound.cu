@@ -12,6 +12,7 @@
 // shuffles inside the group.  Every update of all rows is one pass of a
 // persistent cooperative kernel; passes are separated by a device-wide
 // barrier whose waits are bounded in time (SLK_ERR_TIMEOUT instead of a hang).
+#include <cuda.h>
 #include <math.h>
 #include <stdio.h>
 
@@ -41,8 +42,9 @@ __device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
 // final delta and takes the same decision (delta <= tol) itself.  Block 0
 // clears the slot of update it + 2 (its last readers passed this barrier)
 // and records the delta.  Returns 1 (converged), 0 (go on) or -1 (a wait
-// gave up after kBarrierTimeoutNs, or another block's did).
-__device__ int grid_step(DevState* st, unsigned nblocks, int it, float tol) {
+// gave up after timeout_ns, or another block's did).
+__device__ int grid_step(DevState* st, unsigned nblocks, int it, float tol,
+                         unsigned long long timeout_ns = kBarrierTimeoutNs) {
     __shared__ int s_res;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -54,7 +56,7 @@ __device__ int grid_step(DevState* st, unsigned nblocks, int it, float tol) {
         while ((int)(ld_acquire_gpu(&st->barrier_arrive) - target) < 0) {
             if ((++polls & 63u) == 0u) {
                 if (ld_acquire_gpu(&st->error) != 0u) { res = -1; break; }
-                if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                if (globaltimer_ns() - t0 > timeout_ns) {
                     atomicOr(&st->error, ERR_BARRIER_TIMEOUT);
                     res = -1;
                     break;
@@ -344,6 +346,178 @@ bound_persistent_kernel(const float* __restrict__ A, const int64_t* __restrict__
     if (blockIdx.x == 0 && threadIdx.x == 0) st->iters_done = it;
 }
 
+// ------------------------------------------------ 16-byte form for 64 < L <= 128
+//
+// For L a multiple of 4 in (64, 128] one warp owns a row and lane v owns the
+// labels 4v .. 4v + 3 (v < L/4), so every row of A and Z -- a unary row, the
+// row's previous z and each neighbour's z -- is one 16-byte load per lane,
+// and all neighbour rows of a window are in flight together.  The arithmetic
+// is that of rows_update<32, 4>, bit for bit: each label sums its edges in
+// CSR order, and the row sum of the soft-max is formed in that kernel's
+// order (lane s adds the labels s, s + 32, s + 64, s + 96 from 0, then the
+// xor butterfly over the 32 lanes), its addends fetched by shuffles.
+__device__ __forceinline__ float4 ld4_cg(const float4* p) { return __ldcg(p); }
+
+template <int W, int RPG>
+__device__ __forceinline__ float rows_update_vec4(int64_t p0, int64_t stride, int64_t N, int lane,
+                                                  const float4* __restrict__ A4,
+                                                  const int64_t* __restrict__ row_ptr, int kdeg,
+                                                  const int32_t* __restrict__ col_idx,
+                                                  const float* __restrict__ w, const float4* Zin4,
+                                                  float4* Zout4, int L4, float lambda) {
+    const bool act = lane < L4;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int64_t p[RPG], e0[RPG];
+    int cnt[RPG];
+    int maxc = 0;
+    float4 av[RPG], zo[RPG], b[RPG];
+#pragma unroll
+    for (int i = 0; i < RPG; ++i) {
+        p[i] = p0 + i * stride;
+        const bool live = p[i] < N;
+        e0[i] = 0;
+        cnt[i] = 0;
+        if (live) {
+            if (kdeg > 0) {
+                e0[i] = p[i] * kdeg;
+                cnt[i] = kdeg;
+            } else {
+                e0[i] = __ldg(row_ptr + p[i]);
+                cnt[i] = (int)(__ldg(row_ptr + p[i] + 1) - e0[i]);
+            }
+        }
+        maxc = max(maxc, cnt[i]);
+        av[i] = (live && act) ? __ldg(A4 + p[i] * L4 + lane) : z4;
+        zo[i] = (live && act) ? ld4_cg(Zin4 + p[i] * L4 + lane) : z4;
+        b[i] = z4;
+    }
+    for (int c0 = 0; c0 < maxc; c0 += 32) {
+        int myq[RPG];
+        float myw[RPG];
+#pragma unroll
+        for (int i = 0; i < RPG; ++i) {
+            myq[i] = 0;
+            myw[i] = 1.f;
+            if (lane < cnt[i] - c0) {
+                myq[i] = __ldg(col_idx + e0[i] + c0 + lane);
+                if (w) myw[i] = __ldg(w + e0[i] + c0 + lane);
+            }
+        }
+        const int cm = min(32, maxc - c0);
+        for (int t0 = 0; t0 < cm; t0 += W) {
+            float4 zz[RPG][W];
+            float ww[RPG][W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if (t0 + u >= cm) break;   // uniform over the warp
+#pragma unroll
+                for (int i = 0; i < RPG; ++i) {
+                    const int q = __shfl_sync(0xffffffffu, myq[i], t0 + u);
+                    ww[i][u] = __shfl_sync(0xffffffffu, myw[i], t0 + u);
+                    const bool ok = act && (t0 + u < cnt[i] - c0);
+                    zz[i][u] = ok ? ld4_cg(Zin4 + (int64_t)q * L4 + lane) : z4;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if (t0 + u >= cm) break;
+#pragma unroll
+                for (int i = 0; i < RPG; ++i) {
+                    if (t0 + u < cnt[i] - c0) {
+                        b[i].x = fmaf(ww[i][u], zz[i][u].x, b[i].x);
+                        b[i].y = fmaf(ww[i][u], zz[i][u].y, b[i].y);
+                        b[i].z = fmaf(ww[i][u], zz[i][u].z, b[i].z);
+                        b[i].w = fmaf(ww[i][u], zz[i][u].w, b[i].w);
+                    }
+                }
+            }
+        }
+    }
+    float dmax = 0.f;
+#pragma unroll
+    for (int i = 0; i < RPG; ++i) {
+        if (p[i] >= N) continue;  // uniform over the warp
+        float4 sv;
+        sv.x = act ? fmaf(lambda, b[i].x, av[i].x) : -INFINITY;
+        sv.y = act ? fmaf(lambda, b[i].y, av[i].y) : -INFINITY;
+        sv.z = act ? fmaf(lambda, b[i].z, av[i].z) : -INFINITY;
+        sv.w = act ? fmaf(lambda, b[i].w, av[i].w) : -INFINITY;
+        float m = fmaxf(fmaxf(sv.x, sv.y), fmaxf(sv.z, sv.w));
+        m = group_max<32>(m, 0xffffffffu);
+        float4 e;
+        e.x = act ? expf(sv.x - m) : 0.f;
+        e.y = act ? expf(sv.y - m) : 0.f;
+        e.z = act ? expf(sv.z - m) : 0.f;
+        e.w = act ? expf(sv.w - m) : 0.f;
+        // lane s adds labels s + 32 j (j = 0..3), held by lane s/4 + 8 j as
+        // component s % 4, in the order of the label-strided kernel
+        float part = 0.f;
+        const int c = lane & 3;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int src = (lane >> 2) + 8 * j;
+            const float ex = __shfl_sync(0xffffffffu, e.x, src);
+            const float ey = __shfl_sync(0xffffffffu, e.y, src);
+            const float ez = __shfl_sync(0xffffffffu, e.z, src);
+            const float ew = __shfl_sync(0xffffffffu, e.w, src);
+            part += (c == 0) ? ex : (c == 1) ? ey : (c == 2) ? ez : ew;
+        }
+        const float sum = group_sum<32>(part, 0xffffffffu);
+        if (act) {
+            float4 z;
+            z.x = e.x / sum;
+            z.y = e.y / sum;
+            z.z = e.z / sum;
+            z.w = e.w / sum;
+            dmax = fmaxf(dmax, fmaxf(fmaxf(fabsf(z.x - zo[i].x), fabsf(z.y - zo[i].y)),
+                                     fmaxf(fabsf(z.z - zo[i].z), fabsf(z.w - zo[i].w))));
+            __stcg(Zout4 + p[i] * L4 + lane, z);
+        }
+    }
+    return dmax;
+}
+
+#ifndef SLK_BOUND_VEC_W
+#define SLK_BOUND_VEC_W 12
+#endif
+#ifndef SLK_BOUND_VEC_RPG
+#define SLK_BOUND_VEC_RPG 1
+#endif
+
+// Persistent inner loop in the 16-byte form (64 < L <= 128, L % 4 == 0,
+// 16-byte aligned A, Z0, Z1); barrier, convergence and results as
+// bound_persistent_kernel<32, 4>.
+__global__ void __launch_bounds__(kThreads, SLK_BOUND_MINB)
+bound_vec4_kernel(const float* __restrict__ A, const int64_t* __restrict__ row_ptr,
+                  const int32_t* __restrict__ col_idx, const float* __restrict__ w, int64_t N,
+                  int L, float lambda, float* Z0, float* Z1, int max_iters, float tol, int kdeg,
+                  DevState* st) {
+    __shared__ float red[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t gwarp = (int64_t)blockIdx.x * (kThreads / 32) + warp;
+    const int L4 = L >> 2;
+    const float4* A4 = reinterpret_cast<const float4*>(A);
+    constexpr int RPG = SLK_BOUND_VEC_RPG;
+    int it = 0;
+    while (it < max_iters) {
+        const float4* Zin4 = reinterpret_cast<const float4*>((it & 1) ? Z1 : Z0);
+        float4* Zout4 = reinterpret_cast<float4*>((it & 1) ? Z0 : Z1);
+        float d = 0.f;
+        for (int64_t base = gwarp; base < N; base += nwarps * RPG)
+            d = fmaxf(d, rows_update_vec4<SLK_BOUND_VEC_W, RPG>(base, nwarps, N, lane, A4, row_ptr,
+                                                                 kdeg, col_idx, w, Zin4, Zout4, L4,
+                                                                 lambda));
+        const float bm = block_max(d, red);
+        if (threadIdx.x == 0) atomicMax(&st->delta_bits[it % 3], __float_as_uint(bm));
+        const int r = grid_step(st, gridDim.x, it, tol);
+        if (r < 0) return;
+        ++it;
+        if (r == 1) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->iters_done = it;
+}
+
 // rows_update on operands cached in shared memory: the CTA's rows
 // [r0, r0 + nr) keep their unary terms sA[lr][L], column indices
 // sQ[lr][kdeg] and weights sW[lr][kdeg] (lr = p - r0) there for the whole
@@ -526,6 +700,14 @@ bound_step_kernel(const float* __restrict__ A, const int64_t* __restrict__ row_p
     if (threadIdx.x == 0) atomicMax(&st->delta_bits[it % 3], __float_as_uint(bm));
 }
 
+// The device-wide barrier of the persistent kernels, waited on by one block
+// against an arrival target of nblocks_expected blocks that no other block
+// will join: its wait must give up after timeout_ns and set the error bit.
+__global__ void barrier_probe_kernel(DevState* st, unsigned nblocks_expected,
+                                     unsigned long long timeout_ns) {
+    grid_step(st, nblocks_expected, 0, -1.f, timeout_ns);
+}
+
 __global__ void bound_finish_kernel(int max_iters, DevState* st) {
     if (st->iters_done < 0) {
         st->iters_done = max_iters;
@@ -534,8 +716,9 @@ __global__ void bound_finish_kernel(int max_iters, DevState* st) {
 }
 
 // After the loop the last iterate sits in buffer iters_done % 2; move it to Z.
+// iters_done < 0 (a barrier wait gave up) leaves both buffers as they are.
 __global__ void swap_if_odd_kernel(float* Z, float* Zp, int64_t n, const DevState* st) {
-    if ((st->iters_done & 1) == 0) return;
+    if (st->iters_done < 0 || (st->iters_done & 1) == 0) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float a = Z[i];
@@ -776,6 +959,26 @@ slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
         if (kdeg > 0) SLK_DISPATCH_L(L, SLK_LAUNCH_CACHED);
 #undef SLK_LAUNCH_CACHED
         if (e != cudaSuccess) return cuda_err(ctx, e, "bound_cached_kernel");
+        const bool aligned16 = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Z) |
+                                 reinterpret_cast<uintptr_t>(Z_prev)) & 15) == 0;
+        if (!cached && L % 4 == 0 && L > 64 && L <= 128 && aligned16) {
+            auto kern = bound_vec4_kernel;
+            int per_sm = 0;
+            SLK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
+            if (per_sm < 1) return set_err(ctx, SLK_ERR_CUDA, "bound kernel cannot be resident");
+            int64_t grid = (int64_t)per_sm * ctx->num_sms;
+            const int64_t vblocks = (N + (kThreads / 32) - 1) / (kThreads / 32);
+            if (grid > vblocks) grid = vblocks;
+            const float* a_ = A; const int64_t* rp_ = row_ptr; const int32_t* ci_ = col_idx;
+            const float* w_ = w; int64_t n_ = N; int l_ = L; float lam_ = lambda;
+            float* z0_ = Z; float* z1_ = Z_prev; int mi_ = max_iters; float tol_ = tol;
+            int kd_ = kdeg; DevState* st_ = st;
+            void* args[] = {&a_, &rp_, &ci_, &w_, &n_, &l_, &lam_, &z0_, &z1_, &mi_, &tol_, &kd_, &st_};
+            e = cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid), dim3(kThreads),
+                                            args, 0, ctx->stream);
+            if (e != cudaSuccess) return cuda_err(ctx, e, "bound_vec4_kernel");
+            cached = true;   // launched: skip the label-strided kernel below
+        }
 #define SLK_LAUNCH_PERSISTENT(G_, LPL_)                                                        \
     if (!cached) {                                                                             \
         auto kern = bound_persistent_kernel<G_, LPL_>;                                         \
@@ -813,6 +1016,16 @@ slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
     SLK_COUNT_LAUNCH(ctx, 1);
     swap_if_odd_kernel<<<(unsigned)sgrid, 256, 0, ctx->stream>>>(Z, Z_prev, n, st);
     SLK_LAUNCH_CHECK(ctx, "swap_if_odd_kernel");
+    return SLK_OK;
+}
+
+slk_status barrier_probe_launch(slk_ctx* ctx, DevState* st, unsigned long long timeout_ns) {
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(st, 0, offsetof(DevState, iters_done), ctx->stream));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->delta_bits[0], 0, sizeof(st->delta_bits), ctx->stream));
+    SLK_COUNT_LAUNCH(ctx, 1);
+    // one block waits for a second one that is never launched
+    barrier_probe_kernel<<<1, 32, 0, ctx->stream>>>(st, 2u, timeout_ns);
+    SLK_LAUNCH_CHECK(ctx, "barrier_probe_kernel");
     return SLK_OK;
 }
 
@@ -872,6 +1085,37 @@ namespace {
 constexpr int kMaxDevices = 256;
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxDevices] = {};
+unsigned long long g_noalloc_ctx_id[kMaxDevices] = {};
+
+// Unique id of the calling thread's current CUDA context (0 if unknown), read
+// through the driver entry points the runtime hands out, so the library does
+// not link the driver library itself.  A device reset makes a new context
+// with a new id, and the static array's address is looked up again.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 }  // namespace
 
 extern "C" slk_status slk_bound_iterate_noalloc(void* stream, const float* A, const int64_t* row_ptr,
@@ -890,14 +1134,19 @@ extern "C" slk_status slk_bound_iterate_noalloc(void* stream, const float* A, co
     }
     void* base = nullptr;
     {
+        // set-up once per device and context: the array's device address
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
+        const unsigned long long cid = current_context_id();   // 0: no context current yet
+        if (!g_noalloc_addr[dev] || cid == 0 || cid != g_noalloc_ctx_id[dev]) {
             void* p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
                 cudaGetLastError();
+                g_noalloc_addr[dev] = nullptr;
                 return SLK_ERR_CUDA;
             }
             g_noalloc_addr[dev] = p;
+            // the lookup made the device's context current if none was
+            g_noalloc_ctx_id[dev] = current_context_id();
         }
         base = g_noalloc_addr[dev];
     }
@@ -955,22 +1204,17 @@ extern "C" slk_status slk_bound_iterate_noalloc(void* stream, const float* A, co
         cudaGetLastError();
         return SLK_ERR_CUDA;
     }
-    // read the status words (iters_done, delta, error) into host variables
-    struct {
-        unsigned int arrive, gen, error;
-        int iters;
-        unsigned int delta[3];
-        float last;
-    } hs;
-    static_assert(offsetof(DevState, last_delta) + sizeof(float) <= sizeof(hs) + 0, "layout");
-    e = cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s);
+    // read the status block (iters_done, delta, error) into a host copy of
+    // the same type (pageable memory: the copy is synchronous for the host)
+    DevState hs;
+    e = cudaMemcpyAsync(&hs, st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return SLK_ERR_CUDA;
     }
     if (hs.error & ERR_BARRIER_TIMEOUT) return SLK_ERR_TIMEOUT;
-    if (iters_done) *iters_done = hs.iters;
-    if (last_delta) *last_delta = hs.last;
+    if (iters_done) *iters_done = hs.iters_done;
+    if (last_delta) *last_delta = hs.last_delta;
     return SLK_OK;
 }

@@ -142,6 +142,12 @@ slk_status init_modes_launch(slk_ctx* ctx, const float* X, int64_t N, int D, con
                              int L, const float* sigma_dev, int32_t* modes, int32_t* assign,
                              double* density, void* ws, DevState* st);
 
+// K-means++ seeds from the caller's draws (first, u_host [L - 1] host
+// uniforms in [0, 1)) into seeds [L] (device); workspace kmeanspp_ws_bytes.
+size_t kmeanspp_ws_bytes(int64_t N, int L);
+slk_status kmeanspp_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int L, int32_t first,
+                           const double* u_host, int32_t* seeds, void* ws);
+
 // weights w[e] = 1 (binary) or exp(-dist2[e] / (2 sigma^2)) with sigma read
 // from *sigma_dev (heat).
 slk_status weights_launch(slk_ctx* ctx, const float* dist2, int64_t nnz, int affinity,
@@ -164,6 +170,11 @@ slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
                         const int32_t* col_idx, const float* w, int64_t N, int L, float lambda,
                         float* Z, float* Z_prev, int max_iters, float tol, DevState* st,
                         int kdeg = 0);   // kdeg > 0: every row has kdeg entries (row_ptr[p] = kdeg p)
+
+// One block waits at the device-wide barrier of the persistent z-update
+// kernels for a second block that is never launched; the wait gives up after
+// timeout_ns and sets ERR_BARRIER_TIMEOUT in st->error.
+slk_status barrier_probe_launch(slk_ctx* ctx, DevState* st, unsigned long long timeout_ns);
 
 // Mode update (keys from A + lambda K Z_prev; Z_prev NULL or st->iters_done == 0
 // when use_iters_flag: s = A).  Writes modes in place, labels, keys, st->changed.

@@ -32,7 +32,7 @@ EXPORTS = ["slk_version", "slk_create", "slk_destroy", "slk_set_stream", "slk_la
            "slk_profile_read", "slk_bound_iterate_noalloc", "slk_solve_batched", "slk_server_create",
            "slk_server_destroy", "slk_server_submit", "slk_server_step", "slk_server_poll",
            "slk_server_request_bytes", "slk_unary_vec", "slk_mean_shift", "slk_energy_vec",
-           "slk_solve_ms", "slk_initial_modes"]
+           "slk_solve_ms", "slk_initial_modes", "slk_barrier_selftest", "slk_kmeanspp"]
 PHASES = ["knn_prep", "knn_cand", "knn_rerank", "knn_fallback", "sigma", "unary", "bound", "mode",
           "energy", "mean_shift"]
 
@@ -121,6 +121,8 @@ def load(path: str = LIB_PATH):
         "slk_solve_ms": (i32, [P, P, i64, i32, i32, i32, f32, f32, P, ctypes.POINTER(Params), P, P, P,
                                ctypes.POINTER(Stats)]),
         "slk_initial_modes": (i32, [P, P, i64, i32, P, i32, f32, P, P, P, ctypes.POINTER(i64)]),
+        "slk_barrier_selftest": (i32, [P, i32]),
+        "slk_kmeanspp": (i32, [P, P, i64, i32, i32, i32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -454,6 +456,28 @@ def solve_ms(X: torch.Tensor, L: int, k: int, lam: float, init_modes: torch.Tens
                                     _ptr(init_modes), ctypes.byref(p), _ptr(Z), _ptr(labels),
                                     _ptr(M), ctypes.byref(st)), "slk_solve_ms")
     return Z, labels, M, st.as_dict()
+
+
+def kmeanspp(X: torch.Tensor, L: int, first: int, u, ctx: Context | None = None) -> torch.Tensor:
+    """slk_kmeanspp: K-means++ seeds of X from the draws (first index, L - 1
+    uniforms in [0, 1), e.g. inputs.kmeanspp_draws) -> int32 CUDA tensor [L]."""
+    import numpy as np
+    ctx = ctx or context(X.device.index)
+    N, D = X.shape
+    _need(X, torch.float32, (N, D), "X")
+    uh = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
+    seeds = torch.empty(L, dtype=torch.int32, device=X.device)
+    ctx.check(ctx._lib.slk_kmeanspp(ctx.handle, _ptr(X), N, D, int(L), int(first),
+                                    uh.ctypes.data_as(ctypes.c_void_p) if uh.size else None,
+                                    _ptr(seeds)), "slk_kmeanspp")
+    return seeds
+
+
+def barrier_selftest(timeout_ms=50, ctx: Context | None = None):
+    """slk_barrier_selftest: the bounded device-wide wait must give up; raises
+    SlkError (SLK_ERR_TIMEOUT when the failure path works)."""
+    ctx = ctx or context()
+    ctx.check(ctx._lib.slk_barrier_selftest(ctx.handle, int(timeout_ms)), "slk_barrier_selftest")
 
 
 def bound_iterate_noalloc(A, row_ptr, col_idx, w, lam, Z, max_iters, tol=-1.0):
