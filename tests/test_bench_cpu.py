@@ -19,13 +19,13 @@ def _json_lines(text):
     return [json.loads(s) for s in text.splitlines() if s.lstrip().startswith("{")]
 
 
-def _check_line(d, n_gpus):
+def _check_line(d, n_gpus, workload):
     for key in KEYS:
         assert key in d, key
     assert d["impl"] == "reference" and d["n_gpus"] == n_gpus
     assert d["value"] > 0 and d["unit"] == "solves/s" and d["higher_is_better"] is True
     assert abs(d["ms_per_step"] - 1e3 / d["value"]) <= 1e-6 * d["ms_per_step"]
-    assert d["config"]["workload"] == "mnist_like_70000x784_L10"
+    assert d["config"]["workload"] == workload
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
@@ -38,20 +38,19 @@ def test_reference_arm_prints_one_line():
     assert r.returncode == 0, r.stderr[-2000:]
     lines = _json_lines(r.stdout)
     assert len(lines) == 1, r.stdout[-2000:]
-    _check_line(lines[0], 1)
+    _check_line(lines[0], 1, "manifolds_1000000x128_L100")
 
 
 def test_reference_arm_two_ranks_rank0_alone_prints():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
-    env = dict(os.environ, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
                         "--nproc-per-node", "2", "--master-addr", "127.0.0.1",
                         "--master-port", str(port), "bench.py", "--impl", "reference",
-                        "--gpus", "2", "--steps", "1", "--warmup", "1"],
-                       cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+                        "--workload", "mnist_like", "--gpus", "2", "--steps", "1", "--warmup", "1"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = _json_lines(r.stdout)
     assert len(lines) == 1, r.stdout[-2000:]
-    _check_line(lines[0], 2)
+    _check_line(lines[0], 2, "mnist_like_70000x784_L10")

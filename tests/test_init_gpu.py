@@ -149,3 +149,42 @@ def test_solve_with_refined_start_matches_oracle(slk):
     np.testing.assert_array_equal(host(labels), ref["labels"])
     assert np.abs(host(Z) - ref["Z"]).max() <= 1e-5
     assert st["energy"] == pytest.approx(ref["E"], rel=1e-6)
+
+
+# ------------------------------------------------------------ K-means++ seeds
+
+@pytest.mark.parametrize("case", ["blobs", "mixture", "mnist_like", "manifolds", "duplicates"])
+def test_kmeanspp_matches_oracle(slk, case):
+    """GPU K-means++ from the same draws gives the oracle's seeds index for
+    index (and the numpy recipe's)."""
+    if case == "blobs":
+        X, _ = inputs.blobs()
+        L, seed = 5, 1810
+    elif case == "mixture":
+        X, _ = inputs.mixture(20000, 9, 50, seed=8)
+        L, seed = 50, 8
+    elif case == "mnist_like":
+        X, _ = inputs.mnist_like(N=6000)
+        L, seed = 10, 1810
+    elif case == "manifolds":
+        X, _ = inputs.manifolds(N=20000)
+        L, seed = 100, 1810
+    else:   # every point repeated: exact zero distances, and an all-zero draw
+        base = inputs.rng(3).normal(size=(7, 5)).astype(np.float32)
+        X = np.repeat(base, 40, axis=0)
+        L, seed = 12, 3
+    first, u = inputs.kmeanspp_draws(X.shape[0], L, seed)
+    want = oracle.kmeanspp(X, L, first, u)
+    got = slk.kmeanspp(torch.from_numpy(X).cuda(), L, first, u).cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    np.testing.assert_array_equal(got, inputs.kmeanspp(X, L, seed=seed))
+
+
+def test_kmeanspp_rejects_bad_draws(slk):
+    X = torch.zeros(10, 3, device="cuda")
+    with pytest.raises(slk.SlkError, match="INVALID_ARG"):
+        slk.kmeanspp(X, 3, 0, [0.5, 1.0])
+    with pytest.raises(slk.SlkError, match="INVALID_ARG"):
+        slk.kmeanspp(X, 3, 10, [0.5, 0.5])
+    with pytest.raises(slk.SlkError, match="INVALID_ARG"):
+        slk.kmeanspp(X, 11, 0, [0.5] * 10)

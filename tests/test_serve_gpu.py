@@ -4,7 +4,9 @@ result slk_solve gives; admission waits for memory."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1810_13044_gb300 import inputs
+from parity_checks import compare_solve
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -93,3 +95,31 @@ def test_request_larger_than_arena_is_refused(slk):
     with pytest.raises(slk.SlkError, match="OOM"):
         srv.submit(_problem(20000, 64, 10, 5, seed=30))
     srv.close()
+
+
+def test_served_requests_match_oracle(slk):
+    """A mix of requests of different N, D, L served together: every result
+    equals the FP64 oracle's solve of that request (each request is given
+    the oracle's sigma, as the batched test does)."""
+    shapes = [(3000, 64, 8), (1200, 9, 5), (5000, 256, 12), (800, 16, 3)]
+    reqs, refs = [], []
+    for i, (N, D, L) in enumerate(shapes):
+        X, _ = inputs.blobs(N=N, D=D, n_blobs=L, seed=90 + i)
+        m0 = inputs.kmeanspp(X, L, seed=90 + i)
+        ref = oracle.solve(X, L, 5, 1.0, m0)
+        refs.append(ref)
+        reqs.append(dict(X=torch.from_numpy(X).cuda(), L=L, k=5, lam=1.0,
+                         init_modes=torch.from_numpy(m0).cuda(), sigma=ref["sigma"]))
+    srv = slk.Server(max_slots=4, quantum=5)
+    ts = [srv.submit(reqs[0]), srv.submit(reqs[1])]
+    srv.step()
+    ts += [srv.submit(reqs[2]), srv.submit(reqs[3])]   # arrive while the first two iterate
+    res = srv.run_until_done(ts)
+    srv.close()
+    for t, ref in zip(ts, refs):
+        Z, lab, modes, st = res[t]
+        # modes and labels identical up to near-ties of the oracle's own
+        # values (a cluster whose points all sit near other modes has no
+        # clear maximiser of z)
+        compare_solve(Z.cpu().numpy(), lab.cpu().numpy(), modes.cpu().numpy(), st, ref,
+                      max_label_ties=0.01, max_mode_ties=2)

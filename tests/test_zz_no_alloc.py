@@ -11,6 +11,7 @@ failure has already run every other test.
 import numpy as np
 import pytest
 
+import oracle
 from paper_1810_13044_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -48,6 +49,29 @@ def test_noalloc_matches_allocating_entry_point_twice(slk):
         assert it_na == it_ref
         assert abs(dl_na - dl_ref) <= Z_TOL
         assert (Z_na - Z_ref).abs().max().item() <= Z_TOL
+
+
+def test_noalloc_matches_oracle(slk):
+    """The same z-updates against the FP64 oracle, within the Z tolerance."""
+    N, L, k = 4000, 17, 5
+    rp, ci, w = inputs.random_graph(N, k, seed=77, weighted=True)
+    A = inputs.random_unary(N, L, seed=78)
+    Z0 = inputs.random_simplex_rows(N, L, seed=79)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    for iters in (1, 6):
+        Z = d(Z0)
+        it, _ = slk.bound_iterate_noalloc(d(A), d(rp), d(ci), d(w), 1.3, Z, iters, tol=-1.0)
+        Zo, _, ito, _ = oracle.bound_iterate(A, rp, ci, w, 1.3, Z0, iters)
+        assert it == ito == iters
+        assert np.abs(Z.cpu().numpy() - Zo).max() <= Z_TOL
+
+
+def test_noalloc_zero_iterations_leaves_z(slk):
+    rp, ci, w, A, Z0 = _case(1000, 7, 4, False, seed=5)
+    Z = Z0.clone()
+    it, dl = slk.bound_iterate_noalloc(A, rp, ci, w, 1.0, Z, 0)
+    assert it == 0 and dl == 0.0
+    assert torch.equal(Z, Z0)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(slk):
