@@ -1,17 +1,23 @@
 #!/usr/bin/env python3
 """Benchmark of the SLK-BO hot path on one GB300 (one JSON line on stdout).
 
-A step is one whole solve of the 70000 x 784, L=10, k=5 workload (synthetic,
-MNIST-shaped; see paper_1810_13044_gb300/inputs.py): kNN graph, sigma, and
-Algorithm 1's outer loop (unary, bound iterations, mode update, energy) until
-the modes stop changing.  The metric is solves/s; the bound iterations are
-also reported as N*L*iterations/s.
+A step is one whole solve (kNN graph, sigma, and Algorithm 1's outer loop:
+unary term, bound iterations, mode update, energy, until the modes stop
+changing) of the default workload: 1e6 points x 128 features on curved
+8-dim manifolds, L = 100 clusters with Zipf(1.1) sizes, k = 10 heat-kernel
+affinity, bfloat16 tensor-core distance tiles with the exact float32 rerank
+(synthetic; see paper_1810_13044_gb300/inputs.py).  The metric is solves/s;
+the bound iterations are also reported as N*L*iterations/s.  The same line
+carries the 70000 x 784, L = 10, k = 5 MNIST-shaped workload under
+"workloads" (its own device and end-to-end figures).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl slk|reference]
+                  [--workload manifolds|mnist_like|ms|batched|serving]
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
-project) on a bounded sample of the same workload.  Under torchrun each rank
-solves its own copy of the workload (replicas: weak scaling), rank 0 prints.
+project) on a bounded sample of the same workload, the sample the main arm's
+cpu_baseline also times.  Under torchrun each rank solves its own copy of
+the workload (replicas: weak scaling), rank 0 prints.
 """
 from __future__ import annotations
 
@@ -30,13 +36,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SLK N·L·iter/s and solves/s vs plain FP32 GPU at equal labels; p50/p99 latency"
-WORKLOAD = dict(name="mnist_like_70000x784_L10", N=70000, D=784, L=10, k=5, lam=1.0,
-                affinity="binary", gen="mnist_like")
-# the precision form: curved 8-dim manifolds, Zipf(1.1) cluster sizes, heat affinity
-MANIFOLDS = dict(name="manifolds_1000000x128_L100", N=1_000_000, D=128, L=100, k=10, lam=1.0,
-                 affinity="heat", gen="manifolds")
+WORKLOADS = {
+    # the precision form: curved 8-dim manifolds, Zipf(1.1) cluster sizes, heat affinity
+    "manifolds": dict(name="manifolds_1000000x128_L100", N=1_000_000, D=128, L=100, k=10, lam=1.0,
+                      affinity="heat", gen="manifolds", sample_rows=32, sample_sub=20000),
+    # the MNIST-shaped plain form
+    "mnist_like": dict(name="mnist_like_70000x784_L10", N=70000, D=784, L=10, k=5, lam=1.0,
+                       affinity="binary", gen="mnist_like", sample_rows=16, sample_sub=7000),
+}
+WORKLOAD = dict(WORKLOADS["manifolds"])
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP32_LANES_PER_SM = 128      # FP32 FMA units per SM (4 sub-partitions x 32)
+SEED = 1810
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # a kernel on a workload, from a one-pass ncu capture, with the SHA-256 of the
@@ -65,7 +76,7 @@ def ncu_traffic(kernel, workload):
     return rec["bytes"]
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -75,23 +86,30 @@ def parse():
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain float32 solve beside the main arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["mnist_like", "manifolds", "batched", "serving", "ms"],
-                    default="mnist_like",
-                    help="mnist_like: one 70000 x 784 SLK-BO solve per step; manifolds: one "
-                         "1e6 x 128, L=100, k=10 heat-affinity solve per step; ms: the 70000 x 784 "
-                         "problem solved by SLK-MS (mean-shift modes); batched: 256 uneven problems "
-                         "per step (slk_solve_batched); serving: a Poisson request stream")
+    ap.add_argument("--no-nested", action="store_true",
+                    help="skip the second (70000 x 784) workload carried in the default line")
+    ap.add_argument("--workload", choices=["manifolds", "mnist_like", "batched", "serving", "ms"],
+                    default="manifolds",
+                    help="manifolds: one 1e6 x 128, L=100, k=10 heat-affinity solve per step; "
+                         "mnist_like: one 70000 x 784, L=10, k=5 solve per step; ms: the "
+                         "70000 x 784 problem solved by SLK-MS (mean-shift modes); batched: 256 "
+                         "uneven problems per step (slk_solve_batched); serving: a Poisson "
+                         "request stream")
     ap.add_argument("--instances", type=int, default=256)
-    ap.add_argument("--requests", type=int, default=64, help="serving: requests in the stream")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: mean Poisson arrival rate (req/s)")
+    ap.add_argument("--rate-search", action="store_true",
+                    help="serving: also search the highest sustainable arrival rate")
     ap.add_argument("--rows", type=int, default=None,
                     help="generate the workload with this many points (profiling captures)")
-    args = ap.parse_args()
-    if args.workload == "manifolds":
-        WORKLOAD.update(MANIFOLDS)
+    args = ap.parse_args(argv)
+    base = "mnist_like" if args.workload in ("mnist_like", "ms") else "manifolds"
+    WORKLOAD.clear()
+    WORKLOAD.update(WORKLOADS[base])
     if args.rows:
         WORKLOAD["N"] = args.rows
         WORKLOAD["name"] = f"{WORKLOAD['gen']}_{args.rows}x{WORKLOAD['D']}_L{WORKLOAD['L']}"
+        WORKLOAD["sample_sub"] = min(WORKLOAD["sample_sub"], args.rows)
     return args
 
 
@@ -115,14 +133,22 @@ def dist_env():
     return rank, world, local
 
 
-def make_inputs():
+def make_points(W):
+    """The workload's seeded points (float32, N x D)."""
     from paper_1810_13044_gb300 import inputs
-    if WORKLOAD["gen"] == "manifolds":
-        X, y = inputs.manifolds(N=WORKLOAD["N"], D=WORKLOAD["D"], n_clusters=WORKLOAD["L"])
+    if W["gen"] == "manifolds":
+        X, _ = inputs.manifolds(N=W["N"], D=W["D"], n_clusters=W["L"])
     else:
-        X, y = inputs.mnist_like(N=WORKLOAD["N"], D=WORKLOAD["D"])
-    m0 = inputs.kmeanspp(X, WORKLOAD["L"], seed=1810)
-    return X, m0
+        X, _ = inputs.mnist_like(N=W["N"], D=W["D"])
+    return X
+
+
+def seeds_gpu(W, Xd, ctx):
+    """K-means++ seeds (Section 4.2) of the workload, drawn on the GPU from the
+    seeded draws of inputs.kmeanspp_draws (equal to inputs.kmeanspp)."""
+    from paper_1810_13044_gb300 import inputs, slk
+    first, u = inputs.kmeanspp_draws(W["N"], W["L"], SEED)
+    return slk.kmeanspp(Xd, W["L"], first, u, ctx=ctx)
 
 
 # ------------------------------------------------------------------ clocks
@@ -184,39 +210,65 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ------------------------------------------------------------------ oracle legs
+# ------------------------------------------------------------------ oracle sample
 
-def oracle_sample(X, m0, n_rows=8, inner_per_outer=None, outer=None):
-    """Time the FP64 oracle on a bounded sample of one solve and extrapolate:
-    kNN on n_rows rows (scaled to N rows) + one outer iteration of
-    Algorithm 1 on the full-size problem (unary, z-updates, modes, energy)
-    scaled to the outer count.  Returns (seconds per solve, description)."""
-    import oracle
-    N, L, k, lam = WORKLOAD["N"], WORKLOAD["L"], WORKLOAD["k"], WORKLOAD["lam"]
-    rows = np.linspace(0, N - 1, n_rows).astype(np.int64)
-    t0 = time.perf_counter()
-    idx, d2 = oracle.knn(X, k, rows=rows)
-    t_knn = (time.perf_counter() - t0) * N / n_rows
-    # a kNN-shaped graph for the iteration leg (the exact graph is what costs hours);
-    # above 70000 rows the leg runs on the first 70000 rows and is scaled by N
-    from paper_1810_13044_gb300 import inputs
-    n_it = min(N, 70000)
-    rp, ci, _ = inputs.random_graph(n_it, k, seed=3)
-    w = np.full(n_it * k, 0.5) if WORKLOAD.get("affinity") == "heat" else None
-    sig = float(np.sqrt(np.median(d2)))
-    inner = int(inner_per_outer or 20)
-    outer = int(outer or 1)
-    m_it = m0 if n_it == N else (np.arange(L, dtype=np.int32) * (n_it // L)).astype(np.int32)
-    t0 = time.perf_counter()
-    oracle.solve_graph(X[:n_it], L, rp, ci, w, sig, lam, m_it, max_outer=1, max_inner=inner, tol=-1.0)
-    t_outer = (time.perf_counter() - t0) * N / n_it
-    total = t_knn + t_outer * outer
-    scope = (f"the full {N}x{WORKLOAD['D']} problem" if n_it == N else
-             f"{n_it} of the {N} rows scaled x{N / n_it:.1f}")
-    desc = (f"FP64 oracle, 1 thread: exact kNN of {n_rows} rows scaled x{N // n_rows}, plus one outer "
-            f"iteration ({inner} z-updates, unary, modes, energy) on {scope}, "
-            f"scaled x{outer} outer iterations")
-    return total, desc
+class OracleSample:
+    """The bounded CPU sample of one solve that both the main arm's
+    cpu_baseline and the reference arm time, with the FP64 oracle as it
+    stands on all host cores:
+
+    * kNN: the exact kNN rows of `sample_rows` points of the full problem
+      (each against all N points), scaled to N rows;
+    * Algorithm 1: a whole solve (exact kNN graph, median sigma, K-means++
+      seeds, outer loop to convergence with tol 1e-6 / max_inner 100) of the
+      first `sample_sub` points (a uniform subsample: points are stored in a
+      seeded random order), scaled linearly to N rows (unary, z-updates, mode
+      update and energy are linear in N at fixed L, k).
+
+    The subsample's own kNN graph, sigma and seeds are prepared once and not
+    timed (their cost is covered by the kNN leg)."""
+
+    def __init__(self, W, X):
+        import oracle
+        from paper_1810_13044_gb300 import inputs
+        self.W, self.X = W, X
+        N, k, L = W["N"], W["k"], W["L"]
+        self.rows = np.linspace(0, N - 1, W["sample_rows"]).astype(np.int64)
+        n = min(W["sample_sub"], N)
+        self.Xs = np.ascontiguousarray(X[:n])
+        idx, d2 = oracle.knn(self.Xs, k)
+        self.sig = oracle.sigma(d2, "median")
+        self.rp = np.arange(n + 1, dtype=np.int64) * k
+        self.ci = idx.reshape(-1)
+        self.w = oracle.heat_weights(d2.reshape(-1), self.sig) if W["affinity"] == "heat" else None
+        first, u = inputs.kmeanspp_draws(n, min(L, n), SEED)
+        self.m0 = oracle.kmeanspp(self.Xs, min(L, n), first, u)
+        self.cores = oracle.threads()
+
+    def run(self):
+        """Seconds per solve of the full problem, extrapolated from the sample."""
+        import oracle
+        W, N = self.W, self.W["N"]
+        n = self.Xs.shape[0]
+        t0 = time.perf_counter()
+        oracle.knn(self.X, W["k"], rows=self.rows)
+        t_knn = (time.perf_counter() - t0) * N / len(self.rows)
+        t0 = time.perf_counter()
+        ref = oracle.solve_graph(self.Xs, len(self.m0), self.rp, self.ci, self.w, self.sig, W["lam"],
+                                 self.m0)
+        t_solve = (time.perf_counter() - t0) * N / n
+        self.last = ref
+        return t_knn + t_solve
+
+    def describe(self):
+        W = self.W
+        n = self.Xs.shape[0]
+        r = getattr(self, "last", None)
+        it = f" ({r['outer']} outer iterations, {r['inner_total']} z-updates)" if r else ""
+        return (f"FP64 oracle on {self.cores} threads: exact kNN rows of {len(self.rows)} of the "
+                f"{W['N']} points scaled x{W['N'] / len(self.rows):.0f}, plus a whole Algorithm-1 "
+                f"solve of a {n}-point subsample on its own exact kNN graph{it} scaled "
+                f"x{W['N'] / n:.1f}")
 
 
 # ------------------------------------------------------------------ arms
@@ -224,15 +276,11 @@ def oracle_sample(X, m0, n_rows=8, inner_per_outer=None, outer=None):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    X, m0 = make_inputs()
-    oracle_sample(X, m0, n_rows=2, inner_per_outer=2)   # warm the caches / build
-    for _ in range(max(0, args.warmup - 1)):
-        oracle_sample(X, m0, n_rows=2, inner_per_outer=2)
-    times = []
-    desc = ""
-    for _ in range(args.steps):
-        t, desc = oracle_sample(X, m0, n_rows=4, inner_per_outer=20, outer=2)
-        times.append(t)
+    X = make_points(WORKLOAD)
+    sample = OracleSample(WORKLOAD, X)
+    for _ in range(args.warmup):
+        sample.run()
+    times = [sample.run() for _ in range(args.steps)]
     sec = statistics.median(times)
     value = 1.0 / sec
     line = {
@@ -241,29 +289,37 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD["name"], **{k: WORKLOAD[k] for k in
                                                                           ("N", "D", "L", "k")}},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": sample.cores, "kind": "oracle",
+                         "sample": sample.describe()},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_slk(args, rank, world, local):
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def measure_workload(W, args, ctx, dev, world, stream, main: bool):
+    """Time one workload's solves and the figures around them.  Returns the
+    per-workload dict (device value, e2e, rooflines, plain float32 solve)
+    plus the clock summary and launch count of its timed region."""
     import torch
     import torch.distributed as dist
 
     from paper_1810_13044_gb300 import slk
 
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    X, m0 = make_inputs()
-    N, D, L, k, lam = (WORKLOAD[x] for x in ("N", "D", "L", "k", "lam"))
-    dev = torch.device("cuda", local)
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    N, D, L, k, lam = (W[x] for x in ("N", "D", "L", "k", "lam"))
+    heat = W["affinity"] == "heat"
+    X = make_points(W)
     Xd = torch.from_numpy(X).to(dev)
-    m0d = torch.from_numpy(m0).to(dev)
-    heat = WORKLOAD["affinity"] == "heat"
-    params = slk.default_params(knn_precision=args.precision, affinity=WORKLOAD["affinity"])
-    ctx = slk.context(local)
+    m0d = seeds_gpu(W, Xd, ctx)
+    params = slk.default_params(knn_precision=args.precision, affinity=W["affinity"])
     out = (torch.empty(N, L, device=dev), torch.empty(N, dtype=torch.int32, device=dev),
            torch.empty(L, dtype=torch.int32, device=dev))
 
@@ -272,17 +328,10 @@ def run_slk(args, rank, world, local):
 
     for _ in range(args.warmup):
         _, _, _, stats = step()
-    torch.cuda.synchronize()
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    stream = torch.cuda.current_stream(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0, ev1 = _events(torch)
     ctx.profile(True)
-    with ClockSampler(local) as clk:
+    with ClockSampler(dev.index) as clk:
         barrier()
         ev0.record(stream)
         for _ in range(args.steps):
@@ -298,31 +347,31 @@ def run_slk(args, rank, world, local):
     plain = None
     if not args.no_fp32_compare and args.precision != "fp32":
         # the plain float32 GPU solve at equal labels (same workload, own timing)
-        p32 = slk.default_params(knn_precision="fp32", affinity=WORKLOAD["affinity"])
+        p32 = slk.default_params(knn_precision="fp32", affinity=W["affinity"])
         out32 = (torch.empty(N, L, device=dev), torch.empty(N, dtype=torch.int32, device=dev),
-               torch.empty(L, dtype=torch.int32, device=dev))
+                 torch.empty(L, dtype=torch.int32, device=dev))
         slk.solve(Xd, L, k, lam, m0d, params=p32, ctx=ctx, out=out32)
         barrier()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        steps32 = args.steps if N <= 100000 else 1   # float32 tiles at 1e6 rows take seconds
+        f0, f1 = _events(torch)
+        steps32 = min(args.steps, 5) if N <= 100000 else 1   # float32 tiles at 1e6 rows take seconds
         f0.record(stream)
         for _ in range(steps32):
             slk.solve(Xd, L, k, lam, m0d, params=p32, ctx=ctx, out=out32)
         f1.record(stream)
         barrier()
-        ms32 = f0.elapsed_time(f1)
-        plain = {"value": steps32 / (ms32 / 1e3), "unit": "solves/s", "knn": "fp32",
+        plain = {"value": steps32 / (f0.elapsed_time(f1) / 1e3), "unit": "solves/s", "knn": "fp32",
+                 "steps": steps32,
                  "equal_labels": bool(torch.equal(out32[1], labels_main)),
                  "equal_modes": bool(torch.equal(out32[2], modes_main))}
 
     # bound iterations alone on this solve's graph: N*L*iter/s (fixed 50 updates)
-    g = slk.knn_graph(Xd, k, precision=args.precision, ctx=ctx,
-                      affinity=WORKLOAD["affinity"], sigma=stats["sigma"])
+    g = slk.knn_graph(Xd, k, precision=args.precision, ctx=ctx, affinity=W["affinity"],
+                      sigma=stats["sigma"])
     gw = g.w if heat else None
     A, Z0 = slk.unary(Xd, out[2], stats["sigma"], ctx=ctx)
     Zb, Zp = Z0.clone(), torch.empty_like(Z0)
     slk.bound_iterate(A, g.row_ptr, g.col_idx, gw, lam, Zb, Zp, 50, tol=-1.0, ctx=ctx)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(torch)
     reps = 5
     e0.record(stream)
     for _ in range(reps):
@@ -331,14 +380,14 @@ def run_slk(args, rank, world, local):
     e1.record(stream)
     torch.cuda.synchronize()
     bound_ms = e0.elapsed_time(e1) / reps
-    nl_iter_per_s = N * L * 50 / (bound_ms / 1e3)
+    del g, A, Z0, Zb, Zp
 
     # starting modes (Section 4.2) on the same data, timed alone: N x N float32
     # distance tiles with the kernel-density epilogue
     init_ms = None
     if N <= 200000:
         slk.initial_modes(Xd, m0d, stats["sigma"], ctx=ctx)
-        i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        i0, i1 = _events(torch)
         i0.record(stream)
         slk.initial_modes(Xd, m0d, stats["sigma"], ctx=ctx)
         i1.record(stream)
@@ -347,7 +396,7 @@ def run_slk(args, rank, world, local):
 
     # e2e through the host-buffer entry point (pinned X in, labels + modes out)
     Xh = torch.from_numpy(X).pin_memory()
-    m0h = torch.from_numpy(m0)
+    m0h = m0d.cpu()
     hout = (None, torch.empty(N, dtype=torch.int32).pin_memory(),
             torch.empty(L, dtype=torch.int32).pin_memory())
     slk.solve_host(Xh, L, k, lam, m0h, params=params, ctx=ctx, out=hout)
@@ -356,105 +405,125 @@ def run_slk(args, rank, world, local):
     for _ in range(args.steps):
         slk.solve_host(Xh, L, k, lam, m0h, params=params, ctx=ctx, out=hout)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    _, e2e_value = whole_job(e2e_s * 1e3, args.steps, world, dev)
+    _, e2e_value = whole_job((time.perf_counter() - t0) * 1e3, args.steps, world, dev)
 
-    if rank == 0:
-        peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
-        clocks = clk.summary()
-        # dominant kernel: the distance tiles of the kNN graph
-        cand_ms = ms_phase["knn_cand"] / max(1, calls["knn_cand"])
-        Dp = ((D + 15) // 16) * 16
-        if args.precision == "fp32":
-            flops = 2.0 * N * N * D
-            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-            peak = 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-            roof = {"bound": "alu", "kernel": "knn_cand_fp32_kernel",
-                    "achieved": flops / (cand_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
-                    "traffic": None}
-        else:
-            flops = 2.0 * N * N * D
-            peak = peaks.get("bf16_tflops", 1900.0)
-            roof = {"bound": "tensor", "kernel": "knn_cand_tc_kernel",
-                    "achieved": flops / (cand_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "peak_source": "measured bf16_tflops" if "bf16_tflops" in peaks else "fallback",
-                    "traffic": ncu_traffic("knn_cand_tc_kernel", WORKLOAD["name"])}
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    # the distance tiles of the kNN graph
+    cand_ms = ms_phase["knn_cand"] / max(1, calls["knn_cand"])
+    Dp = ((D + 15) // 16) * 16
+    flops = 2.0 * N * N * D
+    if args.precision == "fp32":
+        roof = {"bound": "alu", "kernel": "knn_cand_fp32_kernel",
+                "achieved": flops / (cand_ms / 1e3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                "traffic": None}
+    else:
+        peak = peaks.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "kernel": "knn_cand_tc_kernel",
+                "achieved": flops / (cand_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": ("of measured bf16_tflops (burst)" if "bf16_tflops" in peaks
+                                else "of fallback"),
+                "traffic": ncu_traffic("knn_cand_tc_kernel", W["name"])}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["launch_ms"] = cand_ms
+    roof["algorithmic"] = f"2*N*N*D = {flops:.3e} flop per launch (Dp={Dp})"
+    # bound iterations: per row and update row_ptr 8 + col 4k (+ w 4k) + a, z_old, z_new 12L
+    # bytes (each neighbour row of Z counted once, the ideal reuse)
+    b_row = 8 + 4 * k + (4 * k if heat else 0) + 12 * L
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    upd = max(1, stats["inner_iters_total"]) * args.steps
+    gbs = N * b_row * upd / (ms_phase["bound"] / 1e3) / 1e9
+    roof_bound = {"bound": "hbm", "kernel": "bound_persistent_kernel", "achieved": gbs,
+                  "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                  "peak_source": "of measured hbm_gbs" if "hbm_gbs" in peaks else "of fallback",
+                  "traffic": ncu_traffic("bound_persistent_kernel", W["name"]),
+                  "algorithmic": f"N*(8+4k{'+4k' if heat else ''}+12L) = {N * b_row / 1e6:.1f} MB "
+                                 f"per update; the solve's bound phase over its "
+                                 f"{stats['inner_iters_total']} updates",
+                  "launch_ms": ms_phase["bound"] / max(1, calls["bound"]),
+                  "rows_sorted_by_mode": N * L * 4 > (64 << 20),
+                  "l2_resident": N * b_row < 100e6,
+                  "fixed_50_updates_gbs": N * b_row * 50 / (bound_ms / 1e3) / 1e9}
+    fb_ms = ms_phase["knn_fallback"] / max(1, calls["knn_fallback"])
+    fb_rows = stats["knn_fallback_rows"]
+    if ms_phase["knn_fallback"] > max(ms_phase["knn_cand"], ms_phase["bound"]) and fb_rows > 0:
+        fflops = 2.0 * fb_rows * N * D
+        roof = {"bound": "alu", "kernel": "knn_fallback_batch_kernel",
+                "achieved": fflops / (fb_ms / 1e3) / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                "traffic": None, "launch_ms": fb_ms,
+                "algorithmic": f"2*rows*N*D = {fflops:.3e} flop per launch ({fb_rows} rows)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["launch_ms"] = cand_ms
-        roof["algorithmic"] = f"2*N*N*D = {flops:.3e} flop per launch (Dp={Dp})"
-        # bound iterations: per row and update row_ptr 8 + col 4k (+ w 4k) + a, z_old, z_new 12L
-        # bytes (each neighbour row of Z counted once, the ideal reuse)
-        b_row = 8 + 4 * k + (4 * k if heat else 0) + 12 * L
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        # the solve's own z-updates: bound phase time over its update count
-        upd = max(1, stats["inner_iters_total"]) * args.steps
-        gbs = N * b_row * upd / (ms_phase["bound"] / 1e3) / 1e9
-        roof_bound = {"bound": "hbm", "kernel": "bound_persistent_kernel", "achieved": gbs,
-                      "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                      "peak_source": "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback",
-                      "traffic": None,
-                      "algorithmic": f"N*(8+4k{'+4k' if heat else ''}+12L) = {N * b_row / 1e6:.1f} MB "
-                                     f"per update; the solve's bound phase over its "
-                                     f"{stats['inner_iters_total']} updates",
-                      "rows_sorted_by_mode": N * L * 4 > (64 << 20),
-                      "l2_resident": N * b_row < 100e6,
-                      "given_order_50_updates_gbs": N * b_row * 50 / (bound_ms / 1e3) / 1e9}
-        # the reported roofline is the kernel that takes the most device time in the step
-        fb_ms = ms_phase["knn_fallback"] / max(1, calls["knn_fallback"])
-        fb_rows = stats["knn_fallback_rows"]
-        bound_step_ms = ms_phase["bound"] / max(1, calls["bound"])
-        if ms_phase["knn_fallback"] > max(ms_phase["knn_cand"], ms_phase["bound"]) and fb_rows > 0:
-            sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-            fflops = 2.0 * fb_rows * N * D
-            roof = {"bound": "alu", "kernel": "knn_fallback_batch_kernel",
-                    "achieved": fflops / (fb_ms / 1e3) / 1e12,
-                    "peak": 152 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12, "unit": "TFLOP/s",
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
-                    "traffic": None, "launch_ms": fb_ms,
-                    "algorithmic": f"2*rows*N*D = {fflops:.3e} flop per launch ({fb_rows} rows)"}
-            roof["frac"] = roof["achieved"] / roof["peak"]
-        elif ms_phase["bound"] > ms_phase["knn_cand"]:
-            roof = dict(roof_bound, launch_ms=bound_step_ms,
-                        note="solve launches run to the inner tolerance; achieved is from the "
-                             "fixed 50-update launches timed beside")
+    elif ms_phase["bound"] > ms_phase["knn_cand"]:
+        roof = dict(roof_bound)
+    res = {
+        "value": value, "unit": "solves/s", "ms_per_step": ms_max / args.steps,
+        "config": {"workload": W["name"], "N": N, "D": D, "L": L, "k": k, "lambda": lam,
+                   "sigma": "median kNN distance", "affinity": W["affinity"],
+                   "seeds": "K-means++ (Section 4.2) drawn on the GPU from seeded draws",
+                   "knn": ("float32 SIMT distance tiles" if args.precision == "fp32" else
+                           "bfloat16 tcgen05 distance tiles for candidates, exact float32 "
+                           "rerank with rounding certificate (same graph as float32)"),
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": f"inputs larger than L2 (X is {N * D * 4 / 1e6:.0f} MB, L2 129 MB)",
+                   "outer_iters": stats["outer_iters"],
+                   "inner_iters_total": stats["inner_iters_total"]},
+        "nl_iter_per_s": N * L * 50 / (bound_ms / 1e3), "bound_ms_per_50_updates": bound_ms,
+        "initial_modes": None if init_ms is None else {
+            "ms": init_ms, "bound": "alu",
+            "achieved_tflops": 2.0 * N * N * D / (init_ms / 1e3) / 1e12, "peak_tflops": fp32_peak,
+            "algorithmic": "2*N*N*D flop (float32 distance tiles) + N*N exp"},
+        "phase_ms_per_step": {k_: v / args.steps for k_, v in ms_phase.items()},
+        "roofline": roof,
+        "roofline_bound": roof_bound,
+        "plain_fp32_gpu": plain,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": N * D * 4 + L * 4,
+                "d2h_bytes_per_step": N * 4 + L * 4},
+        "energy": stats["energy"], "knn_fallback_rows": stats["knn_fallback_rows"],
+    }
+    return res, clk.summary(), launches, X
+
+
+def run_slk(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1810_13044_gb300 import slk
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    ctx = slk.context(local)
+    stream = torch.cuda.current_stream(dev)
+    res, clocks, launches, X = measure_workload(WORKLOAD, args, ctx, dev, world, stream, main=True)
+    nested = {}
+    if (not args.no_nested and WORKLOAD["gen"] == "manifolds" and not args.rows):
+        W2 = WORKLOADS["mnist_like"]
+        r2, c2, l2, _ = measure_workload(W2, args, ctx, dev, world, stream, main=False)
+        r2["clocks"] = c2
+        r2["gpu_launches"] = l2
+        nested[W2["name"]] = r2
+    if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32",
+            "metric": METRIC, "value": res["value"], "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "N": N, "D": D, "L": L, "k": k, "lambda": lam,
-                       "sigma": "median kNN distance", "affinity": WORKLOAD["affinity"],
-                       "knn": ("float32 SIMT distance tiles" if args.precision == "fp32" else
-                               "bfloat16 tcgen05 distance tiles for candidates, exact float32 "
-                               "rerank with rounding certificate (same graph as float32)"),
-                       "parallelism": f"replicas{world}" if world > 1 else "single",
-                       "l2": f"inputs larger than L2 (X is {N * D * 4 / 1e6:.0f} MB, L2 129 MB)",
-                       "outer_iters": stats["outer_iters"],
-                       "inner_iters_total": stats["inner_iters_total"]},
-            "nl_iter_per_s": nl_iter_per_s, "bound_ms_per_50_updates": bound_ms,
-            "initial_modes": None if init_ms is None else {
-                "ms": init_ms, "bound": "alu",
-                "achieved_tflops": 2.0 * N * N * D / (init_ms / 1e3) / 1e12,
-                "peak_tflops": 152 * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12,
-                "algorithmic": "2*N*N*D flop (float32 distance tiles) + N*N exp"},
-            "phase_ms_per_step": {k_: v / args.steps for k_, v in ms_phase.items()},
-            "roofline": roof,
-            "roofline_bound": roof_bound,
-            "plain_fp32_gpu": plain,
-            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": N * D * 4 + L * 4,
-                    "d2h_bytes_per_step": N * 4 + L * 4},
-            "gpu_launches": launches,
-            "clocks": clocks,
-            "energy": stats["energy"], "knn_fallback_rows": stats["knn_fallback_rows"],
+            "config": res["config"],
         }
+        line.update({k_: v for k_, v in res.items() if k_ not in line and k_ != "config"})
+        line["gpu_launches"] = launches
+        line["clocks"] = clocks
+        if nested:
+            line["workloads"] = nested
         if not args.no_cpu_baseline:
-            sec, desc = oracle_sample(X, m0, n_rows=8,
-                                      inner_per_outer=max(1, stats["inner_iters_total"] // max(1, stats["outer_iters"])),
-                                      outer=stats["outer_iters"])
-            line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "solves/s", "cores": 1,
-                                    "kind": "oracle", "sample": desc}
+            sample = OracleSample(WORKLOAD, X)
+            sec = sample.run()
+            line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "solves/s", "cores": sample.cores,
+                                    "kind": "oracle", "sample": sample.describe()}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -483,13 +552,13 @@ def run_ms(args, rank, world, local):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    X, m0 = make_inputs()
+    X = make_points(WORKLOAD)
     N, D, L, k, lam = (WORKLOAD[x] for x in ("N", "D", "L", "k", "lam"))
     dev = torch.device("cuda", local)
     Xd = torch.from_numpy(X).to(dev)
-    m0d = torch.from_numpy(m0).to(dev)
     params = slk.default_params(knn_precision=args.precision)
     ctx = slk.context(local)
+    m0d = seeds_gpu(WORKLOAD, Xd, ctx)
     out = (torch.empty(N, L, device=dev), torch.empty(N, dtype=torch.int32, device=dev),
            torch.empty(L, D, device=dev))
 
@@ -590,14 +659,18 @@ def run_ms(args, rank, world, local):
             "energy": stats["energy"],
         }
         if not args.no_cpu_baseline:
-            sec, desc = oracle_sample(X, m0, n_rows=8,
-                                      inner_per_outer=max(1, stats["inner_iters_total"] // max(1, stats["outer_iters"])),
-                                      outer=stats["outer_iters"])
-            t_ms = oracle_ms_sample(X, m0, stats["sigma"])
+            import oracle
+            from paper_1810_13044_gb300 import inputs
+            sample = OracleSample(WORKLOAD, X)
+            sec = sample.run()
+            first, u = inputs.kmeanspp_draws(N, L, SEED)
+            m0 = oracle.kmeanspp(X, L, first, u)
+            t_ms = oracle_ms_sample(X, m0, sample.sig)
             line["cpu_baseline"] = {"value": 1.0 / (sec + t_ms * ms_iters), "unit": "solves/s",
-                                    "cores": 1, "kind": "oracle",
-                                    "sample": desc + f"; mean-shift: one iteration on 2000 rows scaled "
-                                                     f"x{N // 2000} rows and x{ms_iters} iterations"}
+                                    "cores": sample.cores, "kind": "oracle",
+                                    "sample": sample.describe() + f"; mean-shift: one iteration on "
+                                              f"2000 rows scaled x{N // 2000} rows and x{ms_iters} "
+                                              f"iterations"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
