@@ -181,6 +181,11 @@ typedef struct {
     int32_t max_ms;         /* mean-shift iterations per outer iteration (default 100) */
     float tol_ms;           /* stop them when max_l ||m_l move||_2 <= tol_ms * sigma (default 1e-5) */
     float tol_modes;        /* stop the outer loop when the modes moved <= tol_modes * sigma (default 1e-3) */
+    /* slk_solve, slk_solve_host, slk_solve_ms: */
+    int32_t symmetrize;     /* 1 = iterate on the symmetric affinity (K + K^t) / 2 of the kNN graph
+                               (slk_symmetrize) instead of the directed K; rows then keep the given
+                               order (reorder is ignored).  Default 0.  slk_solve_batched and the
+                               server refuse 1 with SLK_ERR_INVALID_ARG */
 } slk_params;
 
 typedef struct {
@@ -230,6 +235,20 @@ slk_status slk_solve_host(slk_ctx* ctx, const float* X, int64_t N, int32_t D, in
  * Synchronises the context stream. */
 slk_status slk_kmeanspp(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int32_t L,
                         int32_t first, const double* u, int32_t* seeds);
+
+/* The symmetric affinity K' = (K + K^t) / 2 of a sparse K (Prop. 1 assumes a
+ * symmetric psd K; the kNN affinity of Section 4.2 is directed).  Row p of K'
+ * is the union of row p and column p of K by increasing column, with
+ * K'_pq = (K_pq + K_qp) / 2 (float32) and a missing entry counting 0.
+ *   row_ptr [N+1], col_idx [nnz], w [nnz] or NULL (binary): K on the device,
+ *   every row with at most SLK_MAX_K entries (a kNN graph), else
+ *   SLK_ERR_INVALID_ARG.
+ *   out_row_ptr [N+1], out_col [2 nnz], out_w [2 nnz]: device outputs sized
+ *   for the largest case (no entry of K mirrored by another); out_nnz [host,
+ *   nullable] receives out_row_ptr[N].  Synchronises the context stream. */
+slk_status slk_symmetrize(slk_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
+                          const float* w, int64_t N, int64_t* out_row_ptr, int32_t* out_col,
+                          float* out_w, int64_t* out_nnz);
 
 /* Starting modes (Section 4.2: the starting mode of each cluster follows the
  * mode definition of Eq. (1) from the initial assignments): every point is

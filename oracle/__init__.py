@@ -83,6 +83,7 @@ def _load():
         "oracle_initial_modes": (i32, [P, i64, i32, P, i32, f64, P, P, P]),
         "oracle_cluster_density": (i32, [P, i64, i32, P, i32, f64, P, i64, P]),
         "oracle_kmeanspp": (i32, [P, i64, i32, i32, i32, P, P]),
+        "oracle_symmetrize": (i32, [P, P, P, i64, P, P, P, i64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -291,8 +292,9 @@ def solve_graph(X, L, row_ptr, col_idx, w, sig, lam, init_modes,
 
 
 def solve(X, L, k, lam, init_modes, sigma_rule="median", affinity="binary", sig=None,
-          max_outer=50, max_inner=100, tol=1e-6):
-    """Whole SLK-BO: exact kNN graph, kernel width, Algorithm 1."""
+          max_outer=50, max_inner=100, tol=1e-6, symmetric=False):
+    """Whole SLK-BO: exact kNN graph, kernel width, Algorithm 1 (on the
+    symmetric affinity (K + K^t) / 2 when ``symmetric``)."""
     t0 = time.perf_counter()
     idx, d2 = knn(X, k)
     if sig is None:
@@ -300,7 +302,10 @@ def solve(X, L, k, lam, init_modes, sigma_rule="median", affinity="binary", sig=
     N = X.shape[0]
     row_ptr = np.arange(N + 1, dtype=np.int64) * k
     w = heat_weights(d2.reshape(-1), sig) if affinity == "heat" else None
-    out = solve_graph(X, L, row_ptr, idx.reshape(-1), w, sig, lam, init_modes,
+    col = idx.reshape(-1)
+    if symmetric:
+        row_ptr, col, w = symmetrize(row_ptr, col, w, N)
+    out = solve_graph(X, L, row_ptr, col, w, sig, lam, init_modes,
                       max_outer, max_inner, tol)
     out.update(knn_idx=idx, knn_d2=d2, sigma=sig, row_ptr=row_ptr, w=w,
                seconds=time.perf_counter() - t0)
@@ -431,3 +436,20 @@ def kmeanspp(X, L, first, u):
     _check(lib.oracle_kmeanspp(_p(X), X.shape[0], X.shape[1], int(L), int(first),
                                _p(u) if u.size else None, _p(seeds)), "kmeanspp")
     return seeds
+
+
+# ---------------------------------------------------------------- symmetric affinity
+
+def symmetrize(row_ptr, col_idx, w, N):
+    """(K + K^t) / 2 of a CSR K -> (row_ptr, col_idx, w float64); w None: binary K."""
+    lib = _load()
+    rp, ci, ww = _graph(row_ptr, col_idx, w)
+    out_rp = np.empty(int(N) + 1, np.int64)
+    _check(lib.oracle_symmetrize(_p(rp), _p(ci), _p(ww), int(N), _p(out_rp), None, None, 0),
+           "symmetrize")
+    nnz = int(out_rp[-1])
+    out_ci = np.empty(max(nnz, 1), np.int32)
+    out_w = np.empty(max(nnz, 1), np.float64)
+    _check(lib.oracle_symmetrize(_p(rp), _p(ci), _p(ww), int(N), _p(out_rp), _p(out_ci), _p(out_w),
+                                 nnz), "symmetrize")
+    return out_rp, out_ci[:nnz], out_w[:nnz]

@@ -653,3 +653,73 @@ int oracle_kmeanspp(const float* X, int64_t N, int D, int L, int32_t first, cons
     free(closest);
     return 0;
 }
+
+/* ------------------------------------------------------------------ symmetric affinity */
+
+/* The symmetric affinity K' = (K + K^t) / 2 of a sparse K (Prop. 1 assumes a
+ * symmetric, psd K; the kNN affinity of Section 4.2 is directed).  Row p of
+ * K' holds the union of row p of K and column p of K, by increasing column,
+ * with K'_pq = (K_pq + K_qp) / 2, a missing entry counting 0 (w = NULL: K is
+ * binary).  Two passes: out_row_ptr[N + 1] first (out_col / out_w may be
+ * NULL), then the entries (out_cap >= out_row_ptr[N]). */
+static int cmp_i64(const void* a, const void* b)
+{
+    int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+
+int oracle_symmetrize(const int64_t* row_ptr, const int32_t* col_idx, const double* w, int64_t N,
+                      int64_t* out_row_ptr, int32_t* out_col, double* out_w, int64_t out_cap)
+{
+    if (!row_ptr || !col_idx || N < 1 || !out_row_ptr) return -1;
+    int64_t nnz = row_ptr[N];
+    for (int64_t e = 0; e < nnz; ++e)
+        if (col_idx[e] < 0 || col_idx[e] >= N) return -1;
+    /* column p of K: the rows q with an entry (q, p), by increasing q */
+    int64_t* cnt = (int64_t*)calloc((size_t)N + 1, sizeof(int64_t));
+    int64_t* tq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+    double* tw = (double*)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    int64_t* fill = (int64_t*)calloc((size_t)N, sizeof(int64_t));
+    /* per row: (column, weight) pairs before the merge */
+    int64_t* keys = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? 2 * nnz : 1));
+    if (!cnt || !tq || !tw || !fill || !keys) {
+        free(cnt); free(tq); free(tw); free(fill); free(keys);
+        return -2;
+    }
+    for (int64_t e = 0; e < nnz; ++e) cnt[col_idx[e] + 1]++;
+    for (int64_t p = 0; p < N; ++p) cnt[p + 1] += cnt[p];
+    for (int64_t q = 0; q < N; ++q)
+        for (int64_t e = row_ptr[q]; e < row_ptr[q + 1]; ++e) {
+            int64_t p = col_idx[e];
+            int64_t slot = cnt[p] + fill[p]++;
+            tq[slot] = q;
+            tw[slot] = w ? w[e] : 1.0;
+        }
+    int rc = 0;
+    out_row_ptr[0] = 0;
+    for (int64_t p = 0; p < N; ++p) {
+        /* candidate columns: row p of K and column p of K, sorted, duplicates once */
+        int64_t m = 0;
+        for (int64_t e = row_ptr[p]; e < row_ptr[p + 1]; ++e) keys[m++] = col_idx[e];
+        for (int64_t t = cnt[p]; t < cnt[p + 1]; ++t) keys[m++] = tq[t];
+        qsort(keys, (size_t)m, sizeof(int64_t), cmp_i64);
+        int64_t u = 0;
+        for (int64_t i = 0; i < m; ++i)
+            if (i == 0 || keys[i] != keys[i - 1]) keys[u++] = keys[i];
+        out_row_ptr[p + 1] = out_row_ptr[p] + u;
+        if (!out_col) continue;
+        if (out_row_ptr[p + 1] > out_cap) { rc = -1; break; }
+        for (int64_t i = 0; i < u; ++i) {
+            int64_t q = keys[i];
+            double kpq = 0.0, kqp = 0.0;
+            for (int64_t e = row_ptr[p]; e < row_ptr[p + 1]; ++e)
+                if (col_idx[e] == q) kpq += w ? w[e] : 1.0;
+            for (int64_t t = cnt[p]; t < cnt[p + 1]; ++t)
+                if (tq[t] == q) kqp += tw[t];
+            out_col[out_row_ptr[p] + i] = (int32_t)q;
+            if (out_w) out_w[out_row_ptr[p] + i] = 0.5 * (kpq + kqp);
+        }
+    }
+    free(cnt); free(tq); free(tw); free(fill); free(keys);
+    return rc;
+}

@@ -170,6 +170,14 @@ int oracle_cluster_density(const float* X, int64_t N, int D, const int32_t* assi
 int oracle_kmeanspp(const float* X, int64_t N, int D, int L, int32_t first, const double* u,
                     int32_t* seeds);
 
+/* ---- Symmetric affinity (Prop. 1 assumes a symmetric psd K) ----
+ * K' = (K + K^t) / 2 of the CSR K (w = NULL: binary).  Row p of K' is the
+ * union of row p and column p of K by increasing column, K'_pq =
+ * (K_pq + K_qp) / 2 with missing entries 0.  Call once with out_col = NULL
+ * for out_row_ptr[N + 1], then with out_col / out_w of out_row_ptr[N] slots. */
+int oracle_symmetrize(const int64_t* row_ptr, const int32_t* col_idx, const double* w, int64_t N,
+                      int64_t* out_row_ptr, int32_t* out_col, double* out_w, int64_t out_cap);
+
 #ifdef __cplusplus
 }
 #endif

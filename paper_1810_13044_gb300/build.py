@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libslk_gb300.so")
 SOURCES = ["api.cu", "batched.cu", "bound.cu", "init_modes.cu", "kmeanspp.cu", "knn.cu", "knn_tc.cu",
-           "mean_shift.cu", "serve.cu", "sigma.cu", "unary_energy.cu"]
+           "mean_shift.cu", "serve.cu", "sigma.cu", "symmetrize.cu", "unary_energy.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-Werror", "all-warnings"]

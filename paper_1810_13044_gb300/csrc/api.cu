@@ -248,6 +248,7 @@ extern "C" void slk_default_params(slk_params* p) {
     p->max_ms = 100;
     p->tol_ms = 1e-5f;
     p->tol_modes = 1e-3f;
+    p->symmetrize = 0;
 }
 
 // ---------------------------------------------------------------- steps
@@ -412,6 +413,7 @@ namespace {
 constexpr int64_t kReorderBytes = 64ll << 20;   // Z above this: sorted row order
 
 bool use_reorder(const slk_params& p, int64_t N, int L) {
+    if (p.symmetrize) return false;   // rows of variable degree stay in the given order
     return p.reorder > 0 || (p.reorder < 0 && N * (int64_t)L * 4 > kReorderBytes);
 }
 
@@ -436,6 +438,11 @@ struct SolveBufs {
     float* w;
     float* mode_key;
     void* knn_ws;
+    // symmetric affinity (symmetrize): CSR of (K + K^t) / 2 and its scratch
+    int64_t* srow_ptr;
+    int32_t* scol;
+    float* sw;
+    void* sym_ws;
 };
 
 size_t solve_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int L, int k, const slk_params& p) {
@@ -446,6 +453,9 @@ size_t solve_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int L, int k, const 
     b += align_up(sizeof(float) * (size_t)L, 256);
     b += knn_ws_bytes(ctx, N, D, k, p.knn_precision) + 512;
     if (p.refine_init) b += init_modes_ws_bytes(ctx, N, D, L) + 512;
+    if (p.symmetrize)
+        b += align_up(sizeof(int64_t) * (size_t)(N + 1), 256) +
+             2 * align_up(sizeof(float) * (size_t)N * k * 2, 256) + symmetrize_ws_bytes(N, N * k) + 512;
     if (use_reorder(p, N, L))
         b += 3 * align_up(sizeof(int32_t) * (size_t)N, 256) + align_up(sizeof(float) * (size_t)N * D, 256) +
              2 * align_up(sizeof(float) * (size_t)N * L, 256) + 2 * align_up(sizeof(float) * (size_t)N * k, 256) +
@@ -465,6 +475,12 @@ SolveBufs carve_solve(WsCarver& wc, const slk_ctx* ctx, int64_t N, int D, int L,
     b.mode_key = wc.take<float>((size_t)L);
     b.knn_ws = wc.take<unsigned char>(knn_ws_bytes(ctx, N, D, k, p.knn_precision));
     b.init_ws = p.refine_init ? wc.take<unsigned char>(init_modes_ws_bytes(ctx, N, D, L)) : nullptr;
+    if (p.symmetrize) {
+        b.srow_ptr = wc.take<int64_t>((size_t)N + 1);
+        b.scol = wc.take<int32_t>((size_t)N * k * 2);
+        b.sw = wc.take<float>((size_t)N * k * 2);
+        b.sym_ws = wc.take<unsigned char>(symmetrize_ws_bytes(N, N * k));
+    }
     if (use_reorder(p, N, L)) {
         b.perm = wc.take<int32_t>(N);
         b.inv = wc.take<int32_t>(N);
@@ -493,6 +509,7 @@ slk_status check_solve_args(slk_ctx* ctx, const float* X, int64_t N, int32_t D, 
     CHECK_ARG(p.affinity == SLK_AFFINITY_BINARY || p.affinity == SLK_AFFINITY_HEAT, "bad affinity");
     CHECK_ARG(p.knn_precision == SLK_KNN_FP32 || p.knn_precision == SLK_KNN_BF16_RERANK,
               "bad knn_precision");
+    CHECK_ARG(p.symmetrize == 0 || p.symmetrize == 1, "symmetrize must be 0 or 1");
     return SLK_OK;
 }
 
@@ -515,6 +532,21 @@ slk_status solve_device(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int3
         if (r != SLK_OK) return r;
         w = b.w;
     }
+    // the graph the z-updates, modes and energy use: the directed kNN graph
+    // (k entries a row), or its symmetric form (K + K^t) / 2 (variable degree)
+    const int64_t* rp_it = b.row_ptr;
+    const int32_t* col_it = b.col_idx;
+    int kdeg_it = k;
+    if (p.symmetrize) {
+        SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->sym_error, 0, sizeof(unsigned int), s));
+        r = symmetrize_launch(ctx, b.row_ptr, b.col_idx, w, N, N * (int64_t)k, b.srow_ptr, b.scol,
+                              b.sw, b.sym_ws, &st->sym_error);
+        if (r != SLK_OK) return r;
+        rp_it = b.srow_ptr;
+        col_it = b.scol;
+        w = b.sw;
+        kdeg_it = 0;
+    }
     if (p.refine_init) {
         r = init_modes_launch(ctx, X, N, D, init_modes, L, &st->sigma, modes, nullptr, nullptr,
                               b.init_ws, st);
@@ -531,7 +563,7 @@ slk_status solve_device(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int3
     const float* Xc = X;
     float* Ac = b.A;
     float* Zc = Z;
-    const int32_t* colc = b.col_idx;
+    const int32_t* colc = col_it;
     int32_t* labc = labels;
     int32_t* modc = modes;
     DevState hs;
@@ -555,13 +587,13 @@ slk_status solve_device(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int3
             labc = b.labp;
             modc = b.modp;
         }
-        r = bound_launch(ctx, Ac, b.row_ptr, colc, w, N, L, lambda, Zc, b.Zp, p.max_inner,
-                         p.tol_inner, st, k);
+        r = bound_launch(ctx, Ac, rp_it, colc, w, N, L, lambda, Zc, b.Zp, p.max_inner,
+                         p.tol_inner, st, kdeg_it);
         if (r != SLK_OK) return r;
-        r = mode_launch(ctx, Ac, b.Zp, b.row_ptr, colc, w, N, L, lambda, modc, labc, b.mode_key,
+        r = mode_launch(ctx, Ac, b.Zp, rp_it, colc, w, N, L, lambda, modc, labc, b.mode_key,
                         true, st, reorder ? b.perm : nullptr, reorder ? b.inv : nullptr);
         if (r != SLK_OK) return r;
-        r = energy_launch(ctx, Xc, D, labc, b.row_ptr, colc, w, N, L, modc, &st->sigma, lambda, st);
+        r = energy_launch(ctx, Xc, D, labc, rp_it, colc, w, N, L, modc, &st->sigma, lambda, st);
         if (r != SLK_OK) return r;
         r = read_state(ctx, &hs);
         if (r != SLK_OK) return r;
@@ -819,6 +851,19 @@ extern "C" slk_status slk_solve_ms(slk_ctx* ctx, const float* X, int64_t N, int3
         if (r != SLK_OK) return r;
         w = b.w;
     }
+    const int64_t* rp_it = b.row_ptr;
+    const int32_t* col_it = b.col_idx;
+    int kdeg_it = k;
+    if (p.symmetrize) {
+        SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->sym_error, 0, sizeof(unsigned int), s));
+        r = symmetrize_launch(ctx, b.row_ptr, b.col_idx, w, N, N * (int64_t)k, b.srow_ptr, b.scol,
+                              b.sw, b.sym_ws, &st->sym_error);
+        if (r != SLK_OK) return r;
+        rp_it = b.srow_ptr;
+        col_it = b.scol;
+        w = b.sw;
+        kdeg_it = 0;
+    }
     const int32_t* start = init_modes;
     if (p.refine_init) {
         int32_t* refined = wc.take<int32_t>(L);
@@ -837,10 +882,10 @@ extern "C" slk_status slk_solve_ms(slk_ctx* ctx, const float* X, int64_t N, int3
         if (r != SLK_OK) return r;
         r = unary_launch(ctx, X, N, D, nullptr, L, &st->sigma, b.A, Z, mb.Mhi, mb.Mlo);
         if (r != SLK_OK) return r;
-        r = bound_launch(ctx, b.A, b.row_ptr, b.col_idx, w, N, L, lambda, Z, b.Zp, p.max_inner,
-                         p.tol_inner, st, k);
+        r = bound_launch(ctx, b.A, rp_it, col_it, w, N, L, lambda, Z, b.Zp, p.max_inner,
+                         p.tol_inner, st, kdeg_it);
         if (r != SLK_OK) return r;
-        r = logz_launch(ctx, b.A, b.Zp, b.row_ptr, b.col_idx, w, N, L, lambda, labels, mb.LZ, true, st);
+        r = logz_launch(ctx, b.A, b.Zp, rp_it, col_it, w, N, L, lambda, labels, mb.LZ, true, st);
         if (r != SLK_OK) return r;
         SLK_CUDA_TRY(ctx, cudaMemcpyAsync(mb.M64_start, mb.M64, sizeof(double) * (size_t)L * D,
                                           cudaMemcpyDeviceToDevice, s));
@@ -851,7 +896,7 @@ extern "C" slk_status slk_solve_ms(slk_ctx* ctx, const float* X, int64_t N, int3
         if (r != SLK_OK) return r;
         r = ms_split_launch(ctx, mb.M64, (int64_t)L * D, mb.Mhi, mb.Mlo);
         if (r != SLK_OK) return r;
-        r = energy_launch(ctx, X, D, labels, b.row_ptr, b.col_idx, w, N, L, nullptr, &st->sigma,
+        r = energy_launch(ctx, X, D, labels, rp_it, col_it, w, N, L, nullptr, &st->sigma,
                           lambda, st, mb.Mhi, mb.Mlo);
         if (r != SLK_OK) return r;
         r = read_state_ms(ctx, &hs, mb.ms, &mh);
@@ -876,6 +921,38 @@ extern "C" slk_status slk_solve_ms(slk_ctx* ctx, const float* X, int64_t N, int3
 }
 
 // ---------------------------------------------------------------- starting modes
+
+extern "C" slk_status slk_symmetrize(slk_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
+                                     const float* w, int64_t N, int64_t* out_row_ptr,
+                                     int32_t* out_col, float* out_w, int64_t* out_nnz) {
+    BEGIN_CALL(ctx);
+    slk_status r = check_graph(ctx, row_ptr, col_idx, N);
+    if (r != SLK_OK) return r;
+    CHECK_ARG(out_row_ptr && out_col && out_w, "out_row_ptr, out_col and out_w must not be NULL");
+    int64_t nnz = 0;
+    SLK_CUDA_TRY(ctx, cudaMemcpyAsync(&nnz, row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    r = sync_and_check(ctx);
+    if (r != SLK_OK) return r;
+    CHECK_ARG(nnz >= 0 && nnz <= (int64_t)0x3fffffff, "row_ptr[N]=%lld out of range", (long long)nnz);
+    r = ensure_ws(ctx, symmetrize_ws_bytes(N, nnz));
+    if (r != SLK_OK) return r;
+    DevState* st = dstate(ctx);
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->sym_error, 0, sizeof(unsigned int), ctx->stream));
+    r = symmetrize_launch(ctx, row_ptr, col_idx, w, N, nnz, out_row_ptr, out_col, out_w, ctx->ws,
+                          &st->sym_error);
+    if (r != SLK_OK) return r;
+    DevState hs;
+    r = read_state(ctx, &hs);
+    if (r != SLK_OK) return r;
+    CHECK_ARG(hs.sym_error == 0, "a row of the graph has more than %d entries", SLK_MAX_K);
+    if (out_nnz) {
+        SLK_CUDA_TRY(ctx, cudaMemcpyAsync(out_nnz, out_row_ptr + N, sizeof(int64_t),
+                                          cudaMemcpyDeviceToHost, ctx->stream));
+        return sync_and_check(ctx);
+    }
+    return SLK_OK;
+}
 
 extern "C" slk_status slk_kmeanspp(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int32_t L,
                                    int32_t first, const double* u, int32_t* seeds) {

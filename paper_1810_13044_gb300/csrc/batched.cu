@@ -485,6 +485,8 @@ extern "C" slk_status slk_solve_batched(slk_ctx* ctx, const slk_instance* inst, 
         return set_err(ctx, SLK_ERR_INVALID_ARG, "need 1 <= count <= %d instances", SLK_BATCH_MAX_COUNT);
     if (p.max_outer < 1 || p.max_inner < 1)
         return set_err(ctx, SLK_ERR_INVALID_ARG, "max_outer and max_inner must be >= 1");
+    if (p.symmetrize != 0)
+        return set_err(ctx, SLK_ERR_INVALID_ARG, "the batched form runs on the directed kNN graph only");
     for (int b = 0; b < count; ++b) {
         const slk_instance& q = inst[b];
         if (!q.X || !q.init_modes || !q.Z || !q.labels || !q.modes)

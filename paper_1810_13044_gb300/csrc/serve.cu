@@ -551,6 +551,8 @@ extern "C" slk_status slk_server_create(slk_ctx* ctx, const slk_server_config* c
     if (cfg->max_slots < 1 || cfg->max_slots > SLK_BATCH_MAX_COUNT || cfg->memory_bytes < (1 << 20) ||
         cfg->quantum < 1)
         return set_err(ctx, SLK_ERR_INVALID_ARG, "bad server configuration");
+    if (params && params->symmetrize != 0)
+        return set_err(ctx, SLK_ERR_INVALID_ARG, "the server runs on the directed kNN graph only");
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(ctx->device);

@@ -82,6 +82,7 @@ struct DevState {
     unsigned int sel_bar[4];
     unsigned long long sel_cnt;
     unsigned int sel_min_bits;
+    unsigned int sym_error;           // bit 0: a row of the graph to symmetrise is too long
 };
 
 enum : unsigned int { ERR_BARRIER_TIMEOUT = 1u };
@@ -141,6 +142,14 @@ size_t init_modes_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int L);
 slk_status init_modes_launch(slk_ctx* ctx, const float* X, int64_t N, int D, const int32_t* seeds,
                              int L, const float* sigma_dev, int32_t* modes, int32_t* assign,
                              double* density, void* ws, DevState* st);
+
+// K' = (K + K^t) / 2 of a CSR graph whose rows hold at most SLK_MAX_K
+// entries: out_row_ptr [N + 1], out_col / out_w [2 nnz at most].  A longer
+// row sets bit 0 of *err.  Workspace: symmetrize_ws_bytes.
+size_t symmetrize_ws_bytes(int64_t N, int64_t nnz);
+slk_status symmetrize_launch(slk_ctx* ctx, const int64_t* row_ptr, const int32_t* col_idx,
+                             const float* w, int64_t N, int64_t nnz, int64_t* out_row_ptr,
+                             int32_t* out_col, float* out_w, void* ws, unsigned int* err);
 
 // K-means++ seeds from the caller's draws (first, u_host [L - 1] host
 // uniforms in [0, 1)) into seeds [L] (device); workspace kmeanspp_ws_bytes.

@@ -32,7 +32,8 @@ EXPORTS = ["slk_version", "slk_create", "slk_destroy", "slk_set_stream", "slk_la
            "slk_profile_read", "slk_bound_iterate_noalloc", "slk_solve_batched", "slk_server_create",
            "slk_server_destroy", "slk_server_submit", "slk_server_step", "slk_server_poll",
            "slk_server_request_bytes", "slk_unary_vec", "slk_mean_shift", "slk_energy_vec",
-           "slk_solve_ms", "slk_initial_modes", "slk_barrier_selftest", "slk_kmeanspp"]
+           "slk_solve_ms", "slk_initial_modes", "slk_barrier_selftest", "slk_kmeanspp",
+           "slk_symmetrize"]
 PHASES = ["knn_prep", "knn_cand", "knn_rerank", "knn_fallback", "sigma", "unary", "bound", "mode",
           "energy", "mean_shift"]
 
@@ -48,7 +49,8 @@ class Params(ctypes.Structure):
                 ("tol_inner", ctypes.c_float), ("sigma_rule", ctypes.c_int32),
                 ("affinity", ctypes.c_int32), ("knn_precision", ctypes.c_int32),
                 ("refine_init", ctypes.c_int32), ("reorder", ctypes.c_int32),
-                ("max_ms", ctypes.c_int32), ("tol_ms", ctypes.c_float), ("tol_modes", ctypes.c_float)]
+                ("max_ms", ctypes.c_int32), ("tol_ms", ctypes.c_float), ("tol_modes", ctypes.c_float),
+                ("symmetrize", ctypes.c_int32)]
 
 
 class Instance(ctypes.Structure):
@@ -123,6 +125,7 @@ def load(path: str = LIB_PATH):
         "slk_initial_modes": (i32, [P, P, i64, i32, P, i32, f32, P, P, P, ctypes.POINTER(i64)]),
         "slk_barrier_selftest": (i32, [P, i32]),
         "slk_kmeanspp": (i32, [P, P, i64, i32, i32, i32, P, P]),
+        "slk_symmetrize": (i32, [P, P, P, P, i64, P, P, P, ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -456,6 +459,22 @@ def solve_ms(X: torch.Tensor, L: int, k: int, lam: float, init_modes: torch.Tens
                                     _ptr(init_modes), ctypes.byref(p), _ptr(Z), _ptr(labels),
                                     _ptr(M), ctypes.byref(st)), "slk_solve_ms")
     return Z, labels, M, st.as_dict()
+
+
+def symmetrize(row_ptr, col_idx, w, N: int, ctx: Context | None = None):
+    """slk_symmetrize: (K + K^t) / 2 of a device CSR K (w None: binary) ->
+    (row_ptr int64 [N+1], col_idx int32 [nnz'], w float32 [nnz'])."""
+    ctx = ctx or context(row_ptr.device.index)
+    nnz = col_idx.numel()
+    dev = row_ptr.device
+    out_rp = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    out_ci = torch.empty(max(2 * nnz, 1), dtype=torch.int32, device=dev)
+    out_w = torch.empty(max(2 * nnz, 1), dtype=torch.float32, device=dev)
+    n_out = ctypes.c_int64(0)
+    ctx.check(ctx._lib.slk_symmetrize(ctx.handle, _ptr(row_ptr), _ptr(col_idx), _ptr(w), int(N),
+                                      _ptr(out_rp), _ptr(out_ci), _ptr(out_w), ctypes.byref(n_out)),
+              "slk_symmetrize")
+    return out_rp, out_ci[:n_out.value], out_w[:n_out.value]
 
 
 def kmeanspp(X: torch.Tensor, L: int, first: int, u, ctx: Context | None = None) -> torch.Tensor:

@@ -402,3 +402,64 @@ def test_golden_worked_example():
     np.testing.assert_array_equal(res["labels"], gold["labels"])
     np.testing.assert_array_equal(res["modes"], gold["modes"])
     assert res["E"] == pytest.approx(-2 - 2 * math.exp(-0.5), rel=1e-14)
+
+
+# --------------------------------------------------------------------------- symmetric affinity
+
+def _scipy_sym(rp, ci, w, N):
+    import scipy.sparse as sp
+    data = np.ones(len(ci)) if w is None else np.asarray(w, np.float64)
+    K = sp.csr_matrix((data, ci, rp), shape=(N, N))
+    return (0.5 * (K + K.T)).tocsr()
+
+
+@pytest.mark.parametrize("N,k,weighted", [(50, 4, False), (300, 7, True), (2, 1, False), (1000, 10, True)])
+def test_symmetrize_equals_scipy(N, k, weighted):
+    """(K + K^t) / 2 (Prop. 1's symmetric affinity) against scipy.sparse:
+    same pattern by increasing column (entries that cancel to 0 cannot occur
+    with positive weights), same values; mutual edges merge."""
+    rp, ci, w = inputs.random_graph(N, k, seed=N + k, weighted=weighted)
+    srp, sci, sw = oracle.symmetrize(rp, ci, w, N)
+    S = _scipy_sym(rp, ci, w, N)
+    S.sort_indices()
+    np.testing.assert_array_equal(srp, S.indptr)
+    np.testing.assert_array_equal(sci, S.indices)
+    np.testing.assert_allclose(sw, S.data, rtol=0, atol=1e-15)
+    # symmetric: K'_pq = K'_qp
+    D = S.toarray()
+    np.testing.assert_array_equal(D, D.T)
+
+
+def test_symmetrize_mutual_and_one_way_edges_by_hand():
+    # 0 -> 1, 1 -> 0 (mutual), 0 -> 2 (one way), binary
+    rp = np.array([0, 2, 3, 3], np.int64)
+    ci = np.array([1, 2, 0], np.int32)
+    srp, sci, sw = oracle.symmetrize(rp, ci, None, 3)
+    assert list(srp) == [0, 2, 3, 4]
+    assert list(sci) == [1, 2, 0, 0]
+    assert list(sw) == [1.0, 0.5, 1.0, 0.5]
+
+
+def test_solve_on_symmetric_affinity_descends():
+    """Prop. 1 with the symmetrised kNN affinity plus the diagonal shift of
+    footnote 2: the relaxed objective (lambda/2 on the pairwise term) never
+    increases along the oracle's z-updates on oracle.symmetrize's graph."""
+    X, _ = inputs.blobs(N=80, D=4, n_blobs=3, seed=21)
+    idx, _ = oracle.knn(X, 5)
+    N = X.shape[0]
+    rp = np.arange(N + 1, dtype=np.int64) * 5
+    srp, sci, sw = oracle.symmetrize(rp, idx.reshape(-1), None, N)
+    K = np.zeros((N, N))
+    for p in range(N):
+        K[p, sci[srp[p]:srp[p + 1]]] = sw[srp[p]:srp[p + 1]]
+    delta = max(0.0, -np.linalg.eigvalsh(K).min()) + 1e-9
+    rp2, ci2, w2 = _dense_csr(K + delta * np.eye(N))
+    A = oracle.unary(X, inputs.kmeanspp(X, 3, seed=21), 2.0)
+    lam = 1.5
+    Z = softmax(A, axis=1)
+    prev = oracle.relaxed(A, Z, rp2, ci2, w2, lam / 2)
+    for _ in range(25):
+        Z, _, _, _ = oracle.bound_iterate(A, rp2, ci2, w2, lam, Z, 1)
+        cur = oracle.relaxed(A, Z, rp2, ci2, w2, lam / 2)
+        assert cur <= prev + 1e-12
+        prev = cur
