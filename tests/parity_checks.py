@@ -16,9 +16,14 @@ E_RTOL = 1e-6
 KEY_TIE = 1e-5
 
 
-def compare_solve(Z, labels, modes, stats, ref, max_label_ties=1e-3, max_mode_ties=None):
+def compare_solve(Z, labels, modes, stats, ref, max_label_ties=1e-3, max_mode_ties=None,
+                  energy_at=None):
     """Z, labels, modes: numpy arrays of the GPU result; stats: its dict;
-    ref: oracle.solve / solve_graph output.  Returns (mode ties, label ties, max |dZ|)."""
+    ref: oracle.solve / solve_graph output.  When labels or modes differ (at
+    near-ties), the discrete energy of Eq. (1) is no longer the same number
+    on both sides; energy_at(labels, modes) -> the oracle's energy at the
+    GPU's labels and modes is then the value the GPU's energy must match.
+    Returns (mode ties, label ties, max |dZ|)."""
     Zo = ref["Z"]
     N, L = Zo.shape
     assert stats["outer_iters"] == ref["outer"], (stats["outer_iters"], ref["outer"])
@@ -38,5 +43,8 @@ def compare_solve(Z, labels, modes, stats, ref, max_label_ties=1e-3, max_mode_ti
     err = float(np.abs(np.asarray(Z, dtype=np.float64) - Zo).max())
     assert err <= Z_TOL, err
     E = stats["energy"]
-    assert abs(E - ref["E"]) <= E_RTOL * abs(ref["E"]), (E, ref["E"])
+    E_ref = ref["E"]
+    if (mode_ties or bad.size) and energy_at is not None:
+        E_ref = energy_at(gl, gm)
+    assert abs(E - E_ref) <= E_RTOL * abs(E_ref), (E, E_ref, ref["E"])
     return mode_ties, int(bad.size), err

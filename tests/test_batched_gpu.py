@@ -56,7 +56,10 @@ def _blob_problems(shapes, seed0):
     for i, (N, D, L) in enumerate(shapes):
         X, _ = inputs.blobs(N=N, D=D, n_blobs=L, seed=seed0 + i)
         m0 = inputs.kmeanspp(X, L, seed=seed0 + i)
-        ref = oracle.solve(X, L, 5, 1.0, m0)
+        # both sides take the kernel width as the float32 value the C-ABI receives
+        sig = float(np.float32(oracle.sigma(oracle.knn(X, 5)[1], "median")))
+        ref = oracle.solve(X, L, 5, 1.0, m0, sig=sig)
+        ref["X"] = X
         refs.append(ref)
         probs.append(dict(Xh=X, m0h=m0, X=torch.from_numpy(X).cuda(), L=L, k=5, lam=1.0,
                           init_modes=torch.from_numpy(m0).cuda(), sigma=ref["sigma"]))
@@ -74,8 +77,11 @@ def _check_against_oracle(res, refs, exact=True):
             assert np.abs(Z.cpu().numpy() - ref["Z"]).max() <= 1e-5
             assert st["energy"] == pytest.approx(ref["E"], rel=1e-6)
         else:
+            X, L = ref["X"], len(ref["modes"])
+            e_at = lambda gl, gm: oracle.energy(X, gl, ref["row_ptr"], ref["knn_idx"].reshape(-1),
+                                                ref["w"], L, gm, ref["sigma"], 1.0)
             compare_solve(Z.cpu().numpy(), lab.cpu().numpy(), modes.cpu().numpy(), st, ref,
-                          max_label_ties=0.02, max_mode_ties=max(1, len(ref["modes"]) // 10))
+                          max_label_ties=0.02, max_mode_ties=max(1, L // 10), energy_at=e_at)
 
 
 def test_batched_matches_oracle(slk):
@@ -107,8 +113,9 @@ def test_batched_sigma_matches_oracle(slk, precision):
     for pr in probs:
         del pr["sigma"]
     res = slk.solve_batched(probs, params=slk.default_params(knn_precision=precision))
-    for (_, _, _, st), ref in zip(res, refs):
-        assert st["sigma"] == pytest.approx(ref["sigma"], rel=1e-6)
+    for (_, _, _, st), pr, ref in zip(res, probs, refs):
+        want = oracle.sigma(oracle.knn(pr["Xh"], 5)[1], "median")
+        assert st["sigma"] == pytest.approx(want, rel=1e-6)
 
 
 def test_batched_heat_affinity_and_single_problem(slk):

@@ -94,11 +94,12 @@ def mnist_case():
     X, _ = inputs.mnist_like()
     k, L, lam = 5, 10, 1.0
     idx, d2 = oracle_graph(X, k, GOLDEN_MNIST)
-    sig = oracle.sigma(d2, "median")
+    sig64 = oracle.sigma(d2, "median")
+    sig = float(np.float32(sig64))   # the float32 value the C-ABI receives, on both sides
     m0 = inputs.kmeanspp(X, L, seed=1810)
     rp = np.arange(X.shape[0] + 1, dtype=np.int64) * k
     ref = oracle.solve_graph(X, L, rp, idx.reshape(-1), None, sig, lam, m0)
-    return dict(X=X, k=k, L=L, lam=lam, idx=idx, d2=d2, sig=sig, m0=m0, ref=ref)
+    return dict(X=X, k=k, L=L, lam=lam, idx=idx, d2=d2, sig=sig, sig64=sig64, m0=m0, ref=ref)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16_rerank"])
@@ -109,7 +110,7 @@ def test_mnist_like_full_size_solve_matches_oracle(slk, mnist_case, precision):
     g = slk.knn_graph(Xd, k, precision=precision)
     compare_graph(X, k, host(g.col_idx).reshape(-1, k), host(g.dist2).reshape(-1, k),
                   c["idx"], c["d2"])
-    assert slk.sigma(g.dist2, "median") == pytest.approx(c["sig"], rel=1e-6)
+    assert slk.sigma(g.dist2, "median") == pytest.approx(c["sig64"], rel=1e-6)
     p = slk.default_params(knn_precision=precision)
     out = slk.solve(Xd, L, k, c["lam"], dev(c["m0"]), sigma=c["sig"], params=p)
     check_solve(out, c["ref"])
@@ -125,12 +126,13 @@ def manifolds_case():
     X, _ = inputs.manifolds(N=20000)
     k, L, lam = 10, 100, 1.0
     idx, d2 = oracle.knn(X, k)
-    sig = oracle.sigma(d2, "median")
+    sig64 = oracle.sigma(d2, "median")
+    sig = float(np.float32(sig64))
     w = oracle.heat_weights(d2.reshape(-1), sig)
     m0 = inputs.kmeanspp(X, L, seed=1810)
     rp = np.arange(X.shape[0] + 1, dtype=np.int64) * k
     ref = oracle.solve_graph(X, L, rp, idx.reshape(-1), w, sig, lam, m0)
-    return dict(X=X, k=k, L=L, lam=lam, idx=idx, d2=d2, sig=sig, m0=m0, ref=ref)
+    return dict(X=X, k=k, L=L, lam=lam, idx=idx, d2=d2, sig=sig, sig64=sig64, m0=m0, ref=ref)
 
 
 def test_manifolds_subsample_solve_matches_oracle(slk, manifolds_case):
@@ -144,7 +146,7 @@ def test_manifolds_subsample_solve_matches_oracle(slk, manifolds_case):
                   c["idx"], c["d2"])
     np.testing.assert_allclose(host(g.w).reshape(-1, k),
                                oracle.heat_weights(c["d2"], c["sig"]).reshape(-1, k), rtol=1e-5)
-    assert slk.sigma(g.dist2, "median") == pytest.approx(c["sig"], rel=1e-6)
+    assert slk.sigma(g.dist2, "median") == pytest.approx(c["sig64"], rel=1e-6)
     p = slk.default_params(knn_precision="bf16_rerank", affinity="heat")
     out = slk.solve(Xd, L, k, c["lam"], dev(c["m0"]), sigma=c["sig"], params=p)
     check_solve(out, c["ref"])

@@ -70,7 +70,9 @@ def test_solve_on_symmetric_affinity_matches_oracle(slk, case):
         X, _ = inputs.blobs(N=1500, D=4, n_blobs=6, centre_var=6.0, seed=3)
         L, k, lam, aff = 6, 5, 2.0, "binary"
         m0 = np.arange(L, dtype=np.int32)
-    ref = oracle.solve(X, L, k, lam, m0, affinity=aff, symmetric=True)
+    # both sides take the kernel width as the float32 value the C-ABI receives
+    sig = float(np.float32(oracle.sigma(oracle.knn(X, k)[1], "median")))
+    ref = oracle.solve(X, L, k, lam, m0, affinity=aff, sig=sig, symmetric=True)
     p = slk.default_params(affinity=aff, symmetrize=1)
     Z, lab, modes, st = slk.solve(dev(X), L, k, lam, dev(m0), sigma=ref["sigma"], params=p)
     compare_solve(Z.cpu().numpy(), lab.cpu().numpy(), modes.cpu().numpy(), st, ref,
