@@ -771,13 +771,14 @@ def run_batched(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def make_requests(count, dev, seed=1810):
-    """Serving stream: N log-uniform in [1e3, 2e5], D in {64, 512, 4096}, L ~ U[5, 100],
-    k ~ U[5, 10].  Features like the 70000 x 784 workload's, drawn on the device
-    (seeded): per cluster a 10-dim latent Gaussian u ~ N(mu_c, I), mu_c ~ N(0, 9 I),
-    pushed through a fixed random map x = W2 ReLU(W1 u + b1) (256 hidden units),
-    so that the D-dim features have low intrinsic dimension, as image features
-    do.  Initial modes: seeded random distinct points."""
+def make_request_pool(count, dev, seed=1810):
+    """Serving requests: N log-uniform in [1e3, 2e5], D in {64, 512, 4096},
+    L ~ U[5, 100], k ~ U[5, 10].  Features like the 70000 x 784 workload's,
+    drawn on the device (seeded): per cluster a 10-dim latent Gaussian
+    u ~ N(mu_c, I), mu_c ~ N(0, 9 I), pushed through a fixed random map
+    x = W2 ReLU(W1 u + b1) (256 hidden units), so that the D-dim features have
+    low intrinsic dimension, as image features do.  Initial modes: seeded
+    random distinct points.  A stream draws its requests from this pool."""
     import torch
     from paper_1810_13044_gb300 import inputs
     g = inputs.rng(seed)
@@ -800,71 +801,123 @@ def make_requests(count, dev, seed=1810):
     return reqs
 
 
+def serve_stream(slk, ctx, params, pool, seq, arrivals, budget, keep=0):
+    """Serve the requests pool[seq[i]] arriving at arrivals[i] (seconds from
+    the start) on a fresh server; returns (completion times, wall seconds,
+    launches, labels of the first `keep` requests, max requests in system)."""
+    srv = slk.Server(max_slots=64, quantum=10, memory_bytes=budget, params=params, ctx=ctx)
+    done_at, tickets, pending, kept = {}, {}, set(), {}
+    nxt, in_sys_max = 0, 0
+    t0 = time.perf_counter()
+    while nxt < len(seq) or pending:
+        now = time.perf_counter() - t0
+        while nxt < len(seq) and arrivals[nxt] <= now:
+            tk = srv.submit(pool[seq[nxt]])
+            tickets[tk] = nxt
+            pending.add(tk)
+            nxt += 1
+        in_sys_max = max(in_sys_max, len(pending))
+        if not pending:
+            time.sleep(max(0.0, min(0.002, arrivals[nxt] - now)))
+            continue
+        srv.step()
+        now = time.perf_counter() - t0
+        for tk in list(pending):
+            st, res = srv.poll(tk)
+            if st == srv.DONE:
+                i = tickets[tk]
+                done_at[i] = now
+                if i < keep:
+                    kept[i] = (res[1].clone(), res[2].clone())
+                pending.discard(tk)
+    wall = time.perf_counter() - t0
+    srv.close()
+    return np.array([done_at[i] for i in range(len(seq))]), wall, kept, in_sys_max
+
+
 def run_serving(args, rank, world, local):
+    """A fixed-length Poisson stream through the continuous-batching server:
+    p50/p99 latency (from arrival), solves/s, the highest sustainable arrival
+    rate, and the plain per-instance slk_solve loop on the same requests."""
     import torch
 
     from paper_1810_13044_gb300 import slk
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    reqs = make_requests(args.requests, dev)
+    pool = make_request_pool(64, dev)
     g = np.random.Generator(np.random.PCG64(77))
-    arrivals = np.cumsum(g.exponential(1.0 / args.rate, size=len(reqs)))
+    n = args.requests
+    seq = g.integers(0, len(pool), size=n)
+    arrivals = np.cumsum(g.exponential(1.0 / args.rate, size=n))
     params = slk.default_params(knn_precision=args.precision)
     free = torch.cuda.mem_get_info(dev)[0]
     budget = int(min(free * 0.5, 120 << 30))
     ctx = slk.context(local)
-    # warm-up: one small request through a throw-away server
-    w = slk.Server(max_slots=4, quantum=10, memory_bytes=1 << 30, params=params, ctx=ctx)
-    small = make_requests(1, dev, seed=99)[0]
-    t = w.submit(small)
-    w.run_until_done([t])
-    w.close()
-    srv = slk.Server(max_slots=64, quantum=10, memory_bytes=budget, params=params, ctx=ctx)
+    # warm-up: every pool request once through a throw-away server
+    serve_stream(slk, ctx, params, pool, np.arange(len(pool)), np.zeros(len(pool)), budget)
     torch.cuda.synchronize()
+    keep = min(n, 200)
     ctx.profile(True)
-    done_at, tickets, pending = {}, {}, set()
-    nxt = 0
     with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        while nxt < len(reqs) or pending:
-            now = time.perf_counter() - t0
-            while nxt < len(reqs) and arrivals[nxt] <= now:
-                tk = srv.submit(reqs[nxt])
-                tickets[tk] = nxt
-                pending.add(tk)
-                nxt += 1
-            if not pending:
-                time.sleep(max(0.0, min(0.002, arrivals[nxt] - now)))
-                continue
-            srv.step()
-            now = time.perf_counter() - t0
-            for tk in list(pending):
-                st, res = srv.poll(tk)
-                if st == srv.DONE:
-                    done_at[tickets[tk]] = now
-                    pending.discard(tk)
-        wall = time.perf_counter() - t0
+        done, wall, kept, in_sys_max = serve_stream(slk, ctx, params, pool, seq, arrivals, budget,
+                                                    keep=keep)
     _, _, launches = ctx.profile_read()
     ctx.profile(False)
-    srv.close()
-    lat = np.array([done_at[i] - arrivals[i] for i in range(len(reqs))]) * 1e3
-    # each rank serves its own request stream (replicas); whole job over the slowest rank
-    ms_max, value = whole_job(wall * 1e3, len(reqs), world, dev)
+    lat = (done - arrivals) * 1e3
+    ms_max, value = whole_job(wall * 1e3, n, world, dev)
+    # the plain per-instance GPU solve of the same requests, one after another
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    equal = 0
+    for i in range(keep):
+        pr = pool[seq[i]]
+        _, lab1, m1, _ = slk.solve(pr["X"], pr["L"], pr["k"], pr["lam"], pr["init_modes"],
+                                   params=params, ctx=ctx)
+        equal += int(torch.equal(lab1, kept[i][0]) and torch.equal(m1, kept[i][1]))
+    torch.cuda.synchronize()
+    plain = keep / (time.perf_counter() - t0)
+    # the highest arrival rate the server sustains: a stream of 300 requests
+    # at each rate; sustained when the last third's latency stays within 2x
+    # the first third's (the queue does not grow) and throughput keeps up
+    search = []
+    if args.rate_search:
+        for rate in (20.0, 40.0, 60.0, 80.0, 100.0, 150.0):
+            gs = np.random.Generator(np.random.PCG64(int(rate)))
+            m = 300
+            sq = gs.integers(0, len(pool), size=m)
+            arr = np.cumsum(gs.exponential(1.0 / rate, size=m))
+            d, wl, _, ins = serve_stream(slk, ctx, params, pool, sq, arr, budget)
+            la = (d - arr) * 1e3
+            first, last = la[: m // 3], la[-(m // 3):]
+            ok = (np.percentile(last, 99) <= 2.0 * max(np.percentile(first, 99), 1.0)) and \
+                 (m / wl >= 0.9 * rate)
+            search.append({"rate": rate, "served_per_s": m / wl, "p50_ms": float(np.percentile(la, 50)),
+                           "p99_ms": float(np.percentile(la, 99)), "max_in_system": ins,
+                           "sustained": bool(ok)})
+    sustainable = max([r["rate"] for r in search if r["sustained"]], default=None)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-            "steps": len(reqs), "warmup": 1, "ms_per_step": ms_max / len(reqs),
+            "steps": n, "warmup": 1, "ms_per_step": ms_max / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"serving_poisson{int(args.rate)}_{len(reqs)}req",
+            "config": {"workload": f"serving_poisson{int(args.rate)}_{n}req",
                        "N": "log-uniform [1e3, 2e5]", "D": "{64, 512, 4096}", "L": "U[5,100]",
                        "k": "U[5,10]", "knn": args.precision, "arrivals": f"Poisson, mean {args.rate}/s",
+                       "requests": f"{n} drawn from a pool of {len(pool)} (seeded)",
                        "memory_budget_gb": round(budget / 2**30, 1), "slots": 64, "quantum": 10,
-                       "offered_rate": args.rate, "l2": "inputs larger than L2"},
+                       "offered_rate": args.rate, "l2": "inputs larger than L2",
+                       "admission": "FIFO; a request starts when a slot is free and its peak device "
+                                    "state fits the arena; waiting requests queue (no dropping), "
+                                    "so latency is measured from arrival"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
-            "requests": len(reqs), "rows_total": int(sum(r["N"] for r in reqs)),
+            "max_in_system": in_sys_max,
+            "plain_per_instance_gpu": {"value": plain, "unit": "solves/s", "requests": keep,
+                                       "equal_labels_and_modes": f"{equal}/{keep}"},
+            "rate_search": search, "max_sustainable_rate": sustainable,
+            "rows_total": int(sum(pool[i]["N"] for i in seq)),
             "gpu_launches": launches, "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

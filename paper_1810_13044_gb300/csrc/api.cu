@@ -331,7 +331,12 @@ extern "C" slk_status slk_bound_iterate(slk_ctx* ctx, const float* A, const int6
     CHECK_ARG(L >= 1 && L <= SLK_MAX_L, "L=%d must be in [1, %d]", L, SLK_MAX_L);
     CHECK_ARG(max_iters >= 0, "max_iters must be >= 0");
     DevState* st = dstate(ctx);
-    r = bound_launch(ctx, A, row_ptr, col_idx, w, N, L, lambda, Z, Z_prev, max_iters, tol, st);
+    // a kNN-shaped graph (every row the same degree) takes the kernels that
+    // know the degree: cached operands, or the staged pipeline at large N
+    int kdeg = 0;
+    r = uniform_degree(ctx, row_ptr, N, st, &kdeg);
+    if (r != SLK_OK) return r;
+    r = bound_launch(ctx, A, row_ptr, col_idx, w, N, L, lambda, Z, Z_prev, max_iters, tol, st, kdeg);
     if (r != SLK_OK) return r;
     DevState hs;
     r = read_state(ctx, &hs);

@@ -83,6 +83,13 @@ __device__ __forceinline__ float group_max(float v, unsigned mask) {
     for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o, G));
     return v;
 }
+// Maximum over the 32 lanes of a warp in one instruction (exact, as the
+// butterfly of fmaxf).
+__device__ __forceinline__ float warp_max_all(float v) {
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
 template <int G>
 __device__ __forceinline__ float group_sum(float v, unsigned mask) {
 #pragma unroll
@@ -518,6 +525,178 @@ bound_vec4_kernel(const float* __restrict__ A, const int64_t* __restrict__ row_p
     if (blockIdx.x == 0 && threadIdx.x == 0) st->iters_done = it;
 }
 
+// ------------------------------------- staged form for large N (64 < L <= 128)
+//
+// The 16-byte form above keeps about 16 rows per SM in flight, each waiting
+// on its names, then on its neighbours' rows: at 1e6 rows the z-updates are
+// bound by that latency and by the instructions per row, not by HBM (a
+// graph of self-loops runs as slowly as a random one).  Here every warp
+// runs a pipeline of S row stages in shared memory: while it computes row
+// j, the cp.async copies of rows j+1 .. j+S-1 (unary row, previous z row
+// and the kdeg neighbour z rows, 16 bytes a lane) are in flight, and the
+// neighbour names of rows j+S .. j+2S-1 arrive in a ring of 2S slots S rows
+// ahead of their gathers, so no row waits on its names.  Each label sums
+// its edges in CSR order as in the other forms; the soft-max takes the row
+// sum from each lane's own four terms and one reciprocal per row (z = e
+// (1 / sum), within 1.5 ulp of e / sum), fewer instructions than the
+// label-strided order of the other forms, whose bits it therefore does not
+// repeat.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int P>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(P) : "memory");
+}
+
+// Shared memory of one warp: S stages of (2 + kdeg) rows of L4 float4 (unary
+// row, previous z row, neighbour z rows), then 2S slots of kdeg names and
+// kdeg weights.
+__host__ __device__ constexpr size_t staged_warp_bytes(int S, int kdeg, int L4) {
+    return (size_t)S * (2 + kdeg) * L4 * 16 + (size_t)2 * S * kdeg * 8;
+}
+
+// K > 0: every row has K edges, known at compile time (loops unrolled);
+// K = 0: kdeg_rt edges.  Element offsets are 32-bit (N L / 4 < 2^31).
+template <int S, int WPB, int K>
+__global__ void __launch_bounds__(WPB * 32, 1)
+bound_staged_kernel(const float* __restrict__ A, const int32_t* __restrict__ col_idx,
+                    const float* __restrict__ w, int64_t N, int L, float lambda, float* Z0,
+                    float* Z1, int max_iters, float tol, int kdeg_rt, DevState* st) {
+    extern __shared__ __align__(16) unsigned char stage_sm[];
+    __shared__ float red[WPB];
+    const int kdeg = K > 0 ? K : kdeg_rt;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nwarps = gridDim.x * WPB;
+    const uint32_t gwarp = blockIdx.x * WPB + warp;
+    const uint32_t L4 = (uint32_t)L >> 2;
+    const bool act = (uint32_t)lane < L4;
+    const int srows = 2 + kdeg;
+    unsigned char* mine = stage_sm + (size_t)warp * staged_warp_bytes(S, kdeg, (int)L4);
+    float4* stg = reinterpret_cast<float4*>(mine);                        // [S][srows][L4]
+    int32_t* qring = reinterpret_cast<int32_t*>(mine + (size_t)S * srows * L4 * 16);   // [2S][kdeg]
+    float* wring = reinterpret_cast<float*>(qring + 2 * S * kdeg);                     // [2S][kdeg]
+    const float4* A4 = reinterpret_cast<const float4*>(A);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // rows of this warp: gwarp + j nwarps, j < nj
+    const uint32_t nj = ((uint64_t)N > gwarp) ? (uint32_t)(((uint64_t)N - gwarp + nwarps - 1) / nwarps) : 0u;
+    int it = 0;
+    while (it < max_iters) {
+        const float4* Zin4 = reinterpret_cast<const float4*>((it & 1) ? Z1 : Z0);
+        float4* Zout4 = reinterpret_cast<float4*>((it & 1) ? Z0 : Z1);
+        // names and weights of row j into ring slot j % 2S
+        auto fetch_names = [&](uint32_t j) {
+            if (j < nj && lane < kdeg) {
+                const uint32_t e = (gwarp + j * nwarps) * (uint32_t)kdeg + lane;
+                const int slot = (int)(j % (2 * S));
+                cp_async4(qring + slot * kdeg + lane, col_idx + e);
+                if (w) cp_async4(wring + slot * kdeg + lane, w + e);
+            }
+        };
+        // unary row, previous z row and neighbour rows of row j into stage j % S
+        auto fetch_rows = [&](uint32_t j) {
+            if (j < nj && act) {
+                const uint32_t o = (gwarp + j * nwarps) * L4 + lane;
+                float4* sb = stg + (j % S) * srows * L4 + lane;
+                const int32_t* qs = qring + (j % (2 * S)) * kdeg;
+                cp_async16(sb, A4 + o);
+                cp_async16(sb + L4, Zin4 + o);
+#pragma unroll
+                for (int t = 0; t < kdeg; ++t)
+                    cp_async16(sb + (2 + t) * L4, Zin4 + ((uint32_t)qs[t] * L4 + lane));
+            }
+        };
+        // prologue: names of rows 0 .. S-1 (waited for), then the stages of
+        // rows 0 .. S-2 with the names of rows S .. 2S-2 (one group each)
+        for (int j = 0; j < S; ++j) fetch_names(j);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+        for (int j = 0; j < S - 1; ++j) {
+            fetch_rows(j);
+            fetch_names(j + S);
+            cp_async_commit();
+        }
+        float d = 0.f;
+        for (uint32_t j = 0; j < nj; ++j) {
+            // group j + S - 1: the stage of row j+S-1 (its names arrived with
+            // group j-1, waited for in the previous iteration) and the names
+            // of row j+2S-1
+            fetch_rows(j + S - 1);
+            fetch_names(j + 2 * S - 1);
+            cp_async_commit();
+            cp_async_wait<S - 1>();   // group j: the stage of row j
+            __syncwarp();
+            const uint32_t o = (gwarp + j * nwarps) * L4 + lane;
+            const float4* sb = stg + (j % S) * srows * L4 + lane;
+            const float* ws = wring + (j % (2 * S)) * kdeg;
+            float4 b = z4;
+            if (act) {
+#pragma unroll
+                for (int t = 0; t < kdeg; ++t) {
+                    const float wt = w ? ws[t] : 1.f;
+                    const float4 zq = sb[(2 + t) * L4];
+                    b.x = fmaf(wt, zq.x, b.x);
+                    b.y = fmaf(wt, zq.y, b.y);
+                    b.z = fmaf(wt, zq.z, b.z);
+                    b.w = fmaf(wt, zq.w, b.w);
+                }
+            }
+            const float4 av = act ? sb[0] : z4;
+            const float4 zo = act ? sb[L4] : z4;
+            float4 sv;
+            sv.x = act ? fmaf(lambda, b.x, av.x) : -INFINITY;
+            sv.y = act ? fmaf(lambda, b.y, av.y) : -INFINITY;
+            sv.z = act ? fmaf(lambda, b.z, av.z) : -INFINITY;
+            sv.w = act ? fmaf(lambda, b.w, av.w) : -INFINITY;
+            const float m = warp_max_all(fmaxf(fmaxf(sv.x, sv.y), fmaxf(sv.z, sv.w)));
+            // exp(x), x = s - m <= 0, by the fast intrinsic: its error of at
+            // most (2 + 1.16 |x|) ulp of e^x is below 2e-7 absolute for every
+            // x <= 0 (e^x (2 + 1.16 |x|) peaks at x = 0), so z moves by less
+            // than that
+            float4 e;
+            e.x = act ? __expf(sv.x - m) : 0.f;
+            e.y = act ? __expf(sv.y - m) : 0.f;
+            e.z = act ? __expf(sv.z - m) : 0.f;
+            e.w = act ? __expf(sv.w - m) : 0.f;
+            // the row sum from the lanes' own four terms, and one reciprocal
+            // per row: z = e (1 / sum), within 1.5 ulp of e / sum
+            const float sum = group_sum<32>((e.x + e.y) + (e.z + e.w), 0xffffffffu);
+            const float inv = 1.f / sum;
+            if (act) {
+                float4 z;
+                z.x = e.x * inv;
+                z.y = e.y * inv;
+                z.z = e.z * inv;
+                z.w = e.w * inv;
+                d = fmaxf(d, fmaxf(fmaxf(fabsf(z.x - zo.x), fabsf(z.y - zo.y)),
+                                   fmaxf(fabsf(z.z - zo.z), fabsf(z.w - zo.w))));
+                __stcg(Zout4 + o, z);
+            }
+            __syncwarp();   // the stage is refilled by the next iteration's copies
+        }
+        cp_async_wait<0>();
+        __syncwarp();
+        const float bm = block_max(d, red);
+        if (threadIdx.x == 0) atomicMax(&st->delta_bits[it % 3], __float_as_uint(bm));
+        const int r = grid_step(st, gridDim.x, it, tol);
+        if (r < 0) return;
+        ++it;
+        if (r == 1) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->iters_done = it;
+}
+
 // rows_update on operands cached in shared memory: the CTA's rows
 // [r0, r0 + nr) keep their unary terms sA[lr][L], column indices
 // sQ[lr][kdeg] and weights sW[lr][kdeg] (lr = p - r0) there for the whole
@@ -890,6 +1069,8 @@ Shape shape_for(int L) {
     } while (0)
 
 constexpr size_t kCachedSmemMax = 96 * 1024;   // bytes of cached operands per CTA
+constexpr size_t kStagedSmemMax = 200 * 1024;  // stages of the pipelined kernel per CTA
+constexpr int64_t kStagedMinRows = 100000;     // below: the graph sits in L2, latency is short
 
 // Launches bound_cached_kernel when the graph has a fixed degree and every
 // CTA's share of A, col_idx and w fits kCachedSmemMax with all CTAs resident;
@@ -930,6 +1111,35 @@ cudaError_t launch_cached(slk_ctx* ctx, const float* A, const int32_t* col_idx, 
     return cudaSuccess;
 }
 
+// Launches bound_staged_kernel<S, WPB> when its stages fit kStagedSmemMax
+// with one resident CTA per SM; *used says whether it did.
+template <int S, int WPB>
+cudaError_t launch_staged(slk_ctx* ctx, const float* A, const int32_t* col_idx, const float* w,
+                          int64_t N, int L, float lambda, float* Z, float* Z_prev, int max_iters,
+                          float tol, int kdeg, DevState* st, bool* used) {
+    *used = false;
+    auto kern = kdeg == 10 ? bound_staged_kernel<S, WPB, 10>
+              : kdeg == 5  ? bound_staged_kernel<S, WPB, 5>
+                           : bound_staged_kernel<S, WPB, 0>;
+    const size_t smem = WPB * staged_warp_bytes(S, kdeg, L / 4);
+    if (smem > kStagedSmemMax) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem);
+    if (e != cudaSuccess || per_sm < 1) return e;
+    int64_t grid = (int64_t)per_sm * ctx->num_sms;
+    const int64_t vblocks = (N + WPB - 1) / WPB;
+    if (grid > vblocks) grid = vblocks;
+    const float* a_ = A; const int32_t* ci_ = col_idx; const float* w_ = w;
+    int64_t n_ = N; int l_ = L; float lam_ = lambda; float* z0_ = Z; float* z1_ = Z_prev;
+    int mi_ = max_iters; float tol_ = tol; int kd_ = kdeg; DevState* st_ = st;
+    void* args[] = {&a_, &ci_, &w_, &n_, &l_, &lam_, &z0_, &z1_, &mi_, &tol_, &kd_, &st_};
+    *used = true;
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3((unsigned)grid), dim3(WPB * 32), args,
+                                       smem, ctx->stream);
+}
+
 }  // namespace
 
 slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
@@ -961,6 +1171,28 @@ slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
         if (e != cudaSuccess) return cuda_err(ctx, e, "bound_cached_kernel");
         const bool aligned16 = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(Z) |
                                  reinterpret_cast<uintptr_t>(Z_prev)) & 15) == 0;
+        if (!cached && L % 4 == 0 && L > 64 && L <= 128 && aligned16 && kdeg > 0 &&
+            kdeg <= SLK_MAX_K && N >= kStagedMinRows && N * (int64_t)L < ((int64_t)1 << 32)) {
+            // shared-memory pipeline: SLK_BOUND_WPB warps per CTA, the
+            // deepest stage count that fits
+#ifndef SLK_BOUND_WPB
+#define SLK_BOUND_WPB 16
+#endif
+
+            constexpr int WPB = SLK_BOUND_WPB;
+            e = launch_staged<5, WPB>(ctx, A, col_idx, w, N, L, lambda, Z, Z_prev, max_iters, tol,
+                                      kdeg, st, &cached);
+            if (e == cudaSuccess && !cached)
+                e = launch_staged<4, WPB>(ctx, A, col_idx, w, N, L, lambda, Z, Z_prev, max_iters,
+                                          tol, kdeg, st, &cached);
+            if (e == cudaSuccess && !cached)
+                e = launch_staged<3, WPB>(ctx, A, col_idx, w, N, L, lambda, Z, Z_prev, max_iters,
+                                          tol, kdeg, st, &cached);
+            if (e == cudaSuccess && !cached)
+                e = launch_staged<2, WPB>(ctx, A, col_idx, w, N, L, lambda, Z, Z_prev, max_iters,
+                                          tol, kdeg, st, &cached);
+            if (e != cudaSuccess) return cuda_err(ctx, e, "bound_staged_kernel");
+        }
         if (!cached && L % 4 == 0 && L > 64 && L <= 128 && aligned16) {
             auto kern = bound_vec4_kernel;
             int per_sm = 0;
@@ -1016,6 +1248,33 @@ slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
     SLK_COUNT_LAUNCH(ctx, 1);
     swap_if_odd_kernel<<<(unsigned)sgrid, 256, 0, ctx->stream>>>(Z, Z_prev, n, st);
     SLK_LAUNCH_CHECK(ctx, "swap_if_odd_kernel");
+    return SLK_OK;
+}
+
+__global__ void degree_check_kernel(const int64_t* __restrict__ row_ptr, int64_t N,
+                                    unsigned int* __restrict__ mixed) {
+    const int64_t k = row_ptr[1] - row_ptr[0];
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N;
+         p += (int64_t)gridDim.x * blockDim.x)
+        if (row_ptr[p] != k * p || row_ptr[p + 1] - row_ptr[p] != k) atomicOr(mixed, 1u);
+}
+
+slk_status uniform_degree(slk_ctx* ctx, const int64_t* row_ptr, int64_t N, DevState* st, int* kdeg) {
+    *kdeg = 0;
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->deg_mixed, 0, sizeof(unsigned int), ctx->stream));
+    int64_t g = (N + 255) / 256;
+    if (g > (int64_t)ctx->num_sms * 8) g = (int64_t)ctx->num_sms * 8;
+    SLK_COUNT_LAUNCH(ctx, 1);
+    degree_check_kernel<<<(unsigned)g, 256, 0, ctx->stream>>>(row_ptr, N, &st->deg_mixed);
+    SLK_LAUNCH_CHECK(ctx, "degree_check_kernel");
+    int64_t rp[2] = {0, 0};
+    unsigned int mixed = 1;
+    SLK_CUDA_TRY(ctx, cudaMemcpyAsync(rp, row_ptr, sizeof(rp), cudaMemcpyDeviceToHost, ctx->stream));
+    SLK_CUDA_TRY(ctx, cudaMemcpyAsync(&mixed, &st->deg_mixed, sizeof(mixed), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    SLK_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t k = rp[1] - rp[0];
+    if (!mixed && k >= 1 && k <= SLK_MAX_K) *kdeg = (int)k;
     return SLK_OK;
 }
 

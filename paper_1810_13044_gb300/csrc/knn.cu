@@ -31,7 +31,7 @@
 #include "slk_internal.cuh"
 
 int knn_tc_tile_cols();
-int knn_tc_lists_per_split(int kc);
+int knn_tc_lists_per_split(int kc, int ew);
 
 namespace {
 
@@ -456,7 +456,30 @@ knn_cand_query_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
 #pragma unroll
                 for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
             float ra[8], rbv[8];
+            // 16-byte loads when every row starts on a 16-byte boundary and the
+            // four features of a chunk are all inside the row (D % 4 == 0)
+            const bool v4 = (D & 3) == 0 && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
             auto fetch = [&](int k0) {
+                if (v4) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int d = k0 + 4 * (h == 0 ? lq0 : lq1);
+                        const bool in = d < D;
+                        const float4 m4 = in ? __ldg(reinterpret_cast<const float4*>(mu + d))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float4 xa = (pa_row >= 0 && in)
+                                              ? __ldg(reinterpret_cast<const float4*>(X + pa_row * D + d))
+                                              : m4;
+                        const float4 xb = (qb_row >= 0 && in)
+                                              ? __ldg(reinterpret_cast<const float4*>(X + qb_row * D + d))
+                                              : m4;
+                        ra[4 * h + 0] = xa.x - m4.x; ra[4 * h + 1] = xa.y - m4.y;
+                        ra[4 * h + 2] = xa.z - m4.z; ra[4 * h + 3] = xa.w - m4.w;
+                        rbv[4 * h + 0] = xb.x - m4.x; rbv[4 * h + 1] = xb.y - m4.y;
+                        rbv[4 * h + 2] = xb.z - m4.z; rbv[4 * h + 3] = xb.w - m4.w;
+                    }
+                    return;
+                }
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int d = k0 + 4 * (c < 4 ? lq0 : lq1) + (c & 3);
@@ -571,13 +594,16 @@ __device__ __forceinline__ float exact_d2(const float* __restrict__ xp,
     return part;
 }
 
-// Rerank + certificate, one warp per row.  Q = false: every row p < N, the
-// lists of the candidate kernels at ((split Np + p) KC), failures appended to
+// Rerank + certificate, one warp per row.  Lists hold KC entries each; the
+// SEL best of their union (SEL >= KC: several lists of a split together, as
+// the two column halves of the 8-warp tensor-core kernel) are the candidates
+// whose last one bounds the rest.  Q = false: every row p < N, the lists of
+// the candidate kernels at ((list Np + p) KC), failures appended to
 // fb_list.  Q = true: the rows fb_in[f], f < *count_in, left open by the
 // bfloat16 stage, their float32 query lists at ((split N + f) KC), norms of
 // the float32 operand (rho <= u ||v||), failures appended to fb_list /
 // *count_out.
-template <int KC, bool Q, int E = MAXE>
+template <int KC, bool Q, int E = MAXE, int SEL = KC>
 __global__ void __launch_bounds__(256, 4)
 knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, int splits,
                   int64_t Np, const float* __restrict__ cand_d, const int32_t* __restrict__ cand_i,
@@ -588,8 +614,8 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
                   long long* count_out = nullptr) {
     __shared__ float s_d[8][32 * E];   // each warp's staged lists (256 threads)
     __shared__ int s_i[8][32 * E];
-    __shared__ float s_od[8][KC];      // and its KC selected candidates
-    __shared__ int s_oi[8][KC];
+    __shared__ float s_od[8][SEL];     // and its SEL selected candidates
+    __shared__ int s_oi[8][SEL];
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     const double u = 5.9604644775390625e-08;  // 2^-24
@@ -683,15 +709,15 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
             const bool valid = xi != kNoIdx && xi != (int)p;
             nv += __popc(__ballot_sync(0xffffffffu, valid));
             const int r = rk[m] - (rk[m] > self_rank ? 1 : 0);
-            if (valid && r < KC) {
+            if (valid && r < SEL) {
                 od_[r] = sd[e];
                 oi_[r] = xi;
             }
         }
         __syncwarp();
         // candidate c lives on lane c % 32, slot c / 32
-        constexpr int CPL = (KC + 31) / 32;
-        const int nc = nv < KC ? nv : KC;
+        constexpr int CPL = (SEL + 31) / 32;
+        const int nc = nv < SEL ? nv : SEL;
         int ci[CPL];
         float cd[CPL];
 #pragma unroll
@@ -700,11 +726,11 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
             ci[h] = c < nc ? oi_[c] : kNoIdx;
             cd[h] = c < nc ? od_[c] : kInf;
         }
-        float T = nc == KC ? od_[KC - 1] : kInf;
+        float T = nc == SEL ? od_[SEL - 1] : kInf;
         __syncwarp();   // read before the next row's lists are staged
         // Lower bound T on dt of every point that is not a candidate: a column
         // a split rejected has dt >= that split's last list entry (when its
-        // list is full); an entry of the union left out has dt >= the KC-th
+        // list is full); an entry of the union left out has dt >= the SEL-th
         // selected one.
         {
             float ts = kInf;
@@ -1053,6 +1079,7 @@ int choose_kc(int k) { return (k + 4 <= 16) ? 16 : 32; }
 struct KnnPlan {
     int64_t Np;
     int Dp, kc, splits, row_blocks, n_tiles;
+    int ew;      // epilogue warps of the tensor-core kernel (lists per split: ew / 4)
     int lists;   // candidate lists per row: splits x lists per split
     bool bf16;
 };
@@ -1078,9 +1105,16 @@ int tc_splits(int row_blocks, int n_tiles, int num_sms, int max_splits) {
 KnnPlan make_plan(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
     KnnPlan pl{};
     pl.bf16 = (precision == SLK_KNN_BF16_RERANK);
-    // bfloat16 candidates carry a larger rounding error: keep a longer list
-    // (KC / k >= 5) so that the certificate still holds for most rows
-    pl.kc = pl.bf16 ? (k <= 6 ? 32 : 64) : choose_kc(k);
+    // bfloat16 candidates carry a larger rounding error: keep about 5k
+    // candidates per row and split so that the certificate still holds for
+    // most rows -- for k > 6 two lists of 32 (the column halves of every
+    // tile, one per epilogue warp of a pair), whose smaller last entry
+    // bounds every rejected column like the last entry of one list of 64
+#ifndef SLK_TC_BF16_KC64
+#define SLK_TC_BF16_KC64 0
+#endif
+    pl.kc = pl.bf16 ? ((k <= 6 || !SLK_TC_BF16_KC64) ? 32 : 64) : choose_kc(k);
+    pl.ew = (pl.bf16 && k > 6 && pl.kc == 32) ? 8 : 4;
     // the tensor-core tiles read 256-row column tiles: keep them inside the matrix
     pl.Np = (int64_t)align_up((size_t)N, pl.bf16 ? 256 : 128);
     pl.Dp = (int)align_up((size_t)D, pl.bf16 ? 64 : BK);
@@ -1102,7 +1136,7 @@ KnnPlan make_plan(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
     pl.splits = best;
     pl.lists = pl.splits;
     if (pl.bf16) {
-        const int per = knn_tc_lists_per_split(pl.kc);
+        const int per = knn_tc_lists_per_split(pl.kc, pl.ew);
         const int tiles_tc = (int)((pl.Np + knn_tc_tile_cols() - 1) / knn_tc_tile_cols());
         pl.splits = tc_splits(pl.row_blocks, tiles_tc, ctx->num_sms > 0 ? ctx->num_sms : 148,
                               max_splits / per);
@@ -1127,7 +1161,7 @@ size_t knn_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int k, int precision) 
 }
 
 slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const float* norms,
-                                int64_t N, int Dp, int64_t Np, int kc, int splits,
+                                int64_t N, int Dp, int64_t Np, int kc, int ew, int splits,
                                 float* cand_d, int32_t* cand_i, unsigned int* err_flag);
 
 namespace {
@@ -1211,7 +1245,7 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     SLK_COUNT_LAUNCH(ctx, 1);
     if (pl.bf16) {
         slk_status r = knn_cand_bf16_launch(ctx, (const __nv_bfloat16*)xt, norms, N, pl.Dp, pl.Np,
-                                            pl.kc, pl.splits, cand_d, cand_i, &st->knn_error);
+                                            pl.kc, pl.ew, pl.splits, cand_d, cand_i, &st->knn_error);
         if (r != SLK_OK) return r;
         // 2^-23: products exact, each accumulator add off by at most one ulp
         // (truncating adds); an assumption about the tensor-core accumulator
@@ -1239,10 +1273,16 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
         // entries per lane: the splits' lists, KC each, over 32 lanes
         const int per_lane = (pl.lists * pl.kc + 31) / 32;
 #define SLK_RERANK(KC_, E_)                                                                   \
-    knn_rerank_kernel<KC_, false, E_><<<(unsigned)grid, 256, 0, s>>>(X, N, D, pl.Dp, k, pl.lists, \
-                                                                     pl.Np, cand_d, cand_i, norms, \
-                                                                     rho, u_acc, row_ptr, col_idx, \
-                                                                     dist2, fb, st)
+    do {                                                                                      \
+        if (pl.kc == 32 && pl.ew == 8)                                                        \
+            knn_rerank_kernel<32, false, E_, 64><<<(unsigned)grid, 256, 0, s>>>(              \
+                X, N, D, pl.Dp, k, pl.lists, pl.Np, cand_d, cand_i, norms, rho, u_acc, row_ptr, \
+                col_idx, dist2, fb, st);                                                      \
+        else                                                                                  \
+            knn_rerank_kernel<KC_, false, E_><<<(unsigned)grid, 256, 0, s>>>(                 \
+                X, N, D, pl.Dp, k, pl.lists, pl.Np, cand_d, cand_i, norms, rho, u_acc, row_ptr, \
+                col_idx, dist2, fb, st);                                                      \
+    } while (0)
 #define SLK_RERANK_E(KC_)                                                                     \
     if (per_lane <= 4) SLK_RERANK(KC_, 4);                                                    \
     else if (per_lane <= 8) SLK_RERANK(KC_, 8);                                               \

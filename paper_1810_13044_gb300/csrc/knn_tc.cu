@@ -59,11 +59,31 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 #ifndef SLK_TC_PIPE
 #define SLK_TC_PIPE 0
 #endif
-// Epilogue of the KC = 32 kernel without block barriers per tile (column
-// norms from global memory); the KC = 64 kernel, whose epilogue dominates at
-// small D, keeps the shared-memory staging.
+// Epilogue without block barriers per tile (column norms read by 16-byte
+// loads from global memory, L1 hits after the first warp), for the KC = 32
+// and the KC = 64 kernel; 0 stages the norms in shared memory behind a
+// barrier of the epilogue warps per tile (measured faster for KC = 64 at
+// D = 128: 552 ms against 797 ms at 1e6 x 128).
 #ifndef SLK_TC_NOBAR
 #define SLK_TC_NOBAR 1
+#endif
+#ifndef SLK_TC_NOBAR64
+#define SLK_TC_NOBAR64 0
+#endif
+#ifndef SLK_TC_NOBAR8
+#define SLK_TC_NOBAR8 0
+#endif
+// 8 epilogue warps: 1 keeps the TMEM load of the next 16 columns in flight
+// while the current ones are filtered (measured slower at 1e6 x 128: 612
+// against 428 ms; the second register set spills around the merges)
+#ifndef SLK_TC_PIPE8
+#define SLK_TC_PIPE8 0
+#endif
+// Epilogue warps of the KC = 64 kernel: 4, or 8 (two per SM sub-partition,
+// each with half of a row's columns and its own list of 64, 16-column TMEM
+// loads; the 10-warp CTA then has 168 registers a thread and spills).
+#ifndef SLK_TC_EW64
+#define SLK_TC_EW64 4
 #endif
 
 // CTA pairs (cta_group::2) for the KC = 32 kernel: the two CTAs of a cluster
@@ -96,11 +116,16 @@ template <int EW, bool PAIR = false, int KC = 32> struct TcEpi {
     static constexpr int vote = (EW == 8) ? 16 : 32;  // columns per vote
     // more than 3 x 48 KiB of operand stages leaves room only for 31 slots
     static constexpr bool tight = !PAIR && TC_STAGES * (A_BYTES + B_BYTES) > 3u * 49152u;
-    // KC = 64 (an epilogue-bound kernel at small D) merges right away instead
-    static constexpr bool defer = (KC == 32) && !tight;
+    // KC = 64 (an epilogue-bound kernel at small D) merges right away instead,
+    // and so do 8 epilogue warps (their two column halves' buffers of 47
+    // slots would not fit beside 3 stages)
+    static constexpr bool defer = (KC == 32) && !tight && EW == 4;
     static constexpr int app = tight ? 16 : vote;     // columns per append
     static constexpr int buf = defer ? 31 + app : 15 + app;   // buffer slots per row and half
     static constexpr int threads = 64 + 32 * EW;
+    // columns per TMEM load: 16 with 8 epilogue warps (the registers of a
+    // 10-warp CTA: 168 a thread), else 32
+    static constexpr int chunk = (EW == 8) ? 16 : 32;
 };
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
@@ -275,6 +300,34 @@ __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32
         : "r"(taddr)
         : "memory");
 }
+template <int C>
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[C]) {
+    static_assert(C == 16, "16-column load");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+template <int C>
+__device__ __forceinline__ void tmem_wait_regs(uint32_t (&r)[C]) {
+    static_assert(C == 16, "16-column wait");
+    asm volatile(
+        "tcgen05.wait::ld.sync.aligned;"
+        : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+          "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+          "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+        :
+        : "memory");
+}
+template <int C>
+__device__ __forceinline__ void tmem_ld_issue(uint32_t taddr, uint32_t (&r)[C]) {
+    if constexpr (C == 32) tmem_ld32_issue(taddr, r);
+    else tmem_ld16_issue<C>(taddr, r);
+}
 __device__ __forceinline__ void tmem_wait_regs(uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.wait::ld.sync.aligned;"
@@ -391,7 +444,8 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     using E = TcEpi<EW, PAIR, TC_KC>;
     constexpr int STAGES = E::stages;
     constexpr int H = E::halves, VOTE = E::vote, APP = E::app, NT = 32 * EW;
-    constexpr int CH_PER_HALF = TC_N / 32 / H;   // 32-column TMEM loads per thread and tile
+    constexpr int C = E::chunk;                  // columns per TMEM load
+    constexpr int CH_PER_HALF = TC_N / C / H;    // TMEM loads per thread and tile
     extern __shared__ uint8_t smem_raw[];
     TcSmem<EW, PAIR, TC_KC>& s = *reinterpret_cast<TcSmem<EW, PAIR, TC_KC>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -600,12 +654,12 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 // distances of one 32-column chunk, filtered in votes of VOTE
                 // columns against the row's threshold (the row's own column,
                 // distance ~0, is kept here and dropped by the rerank)
-                auto process = [&](const uint32_t (&rv)[32], int ch) {
-                    float v[32];   // w = fl(||xt_q||^2 - 2 dot)
+                auto process = [&](const uint32_t (&rv)[C], int ch) {
+                    float v[C];   // w = fl(||xt_q||^2 - 2 dot)
                     if constexpr (NOBAR) {
-                        const float4* n4 = reinterpret_cast<const float4*>(ncol_g + ch * 32);
+                        const float4* n4 = reinterpret_cast<const float4*>(ncol_g + ch * C);
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
+                        for (int q = 0; q < C / 4; ++q) {
                             const float4 c4 = __ldg(n4 + q);
                             v[4 * q + 0] = fmaf(-2.f, __uint_as_float(rv[4 * q + 0]), c4.x);
                             v[4 * q + 1] = fmaf(-2.f, __uint_as_float(rv[4 * q + 1]), c4.y);
@@ -614,11 +668,11 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         }
                     } else {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            v[j] = fmaf(-2.f, __uint_as_float(rv[j]), s.ncol[acc][ch * 32 + j]);
+                        for (int j = 0; j < C; ++j)
+                            v[j] = fmaf(-2.f, __uint_as_float(rv[j]), s.ncol[acc][ch * C + j]);
                     }
 #pragma unroll
-                    for (int g0 = 0; g0 < 32; g0 += VOTE) {
+                    for (int g0 = 0; g0 < C; g0 += VOTE) {
                         // w < thr - ||xt_p||^2 (rounded up) whenever dt < thr; a
                         // padding row (infinite norm) gets NaN and never passes
                         const float thr_w = __fsub_ru(ld[TC_KC - 1], np_);
@@ -650,7 +704,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                                     for (int j = g0 + 8 * q; j < g0 + 8 * q + 8; ++j) {
                                         if (v[j] < thr_w) {
                                             s.buf_d[h][cnt][r] = __fadd_rn(v[j], np_);
-                                            s.buf_i[h][cnt][r] = (int)(col0 + ch * 32 + j);
+                                            s.buf_i[h][cnt][r] = (int)(col0 + ch * C + j);
                                             ++cnt;
                                         }
                                     }
@@ -677,15 +731,15 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 if constexpr (PIPE) {
                 // two register sets: the load of chunk c + 1 is in flight while
                 // chunk c is filtered
-                uint32_t ra[32], rb2[32];
-                tmem_ld32_issue(tbase + ch0 * 32, ra);
+                uint32_t ra[C], rb2[C];
+                tmem_ld_issue<C>(tbase + ch0 * C, ra);
                 tmem_wait_regs(ra);
 #pragma unroll 1
                 for (int cc = 0; cc < CH_PER_HALF; cc += 2) {
-                    tmem_ld32_issue(tbase + (ch0 + cc + 1) * 32, rb2);
+                    tmem_ld_issue<C>(tbase + (ch0 + cc + 1) * C, rb2);
                     process(ra, ch0 + cc);
                     tmem_wait_regs(rb2);
-                    if (cc + 2 < CH_PER_HALF) tmem_ld32_issue(tbase + (ch0 + cc + 2) * 32, ra);
+                    if (cc + 2 < CH_PER_HALF) tmem_ld_issue<C>(tbase + (ch0 + cc + 2) * C, ra);
                     else release();
                     process(rb2, ch0 + cc + 1);
                     if (cc + 2 < CH_PER_HALF) tmem_wait_regs(ra);
@@ -693,8 +747,8 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 } else {
 #pragma unroll 1
                 for (int cc = 0; cc < CH_PER_HALF; ++cc) {
-                    uint32_t rv[32];
-                    tmem_ld32_issue(tbase + (ch0 + cc) * 32, rv);
+                    uint32_t rv[C];
+                    tmem_ld_issue(tbase + (ch0 + cc) * C, rv);
                     tmem_wait_regs(rv);
                     if (cc == CH_PER_HALF - 1) release();
                     process(rv, ch0 + cc);
@@ -775,14 +829,16 @@ int knn_tc_tile_cols() { return TC_N; }
 // Candidate lists one split of the tensor-core kernel writes per row: two
 // column halves with 8 epilogue warps (KC = 32), one with 4 (KC = 64, whose
 // lists need the registers of a 6-warp CTA).
-int knn_tc_lists_per_split(int kc) {
-    return kc == 32 ? TcEpi<SLK_TC_EW32>::halves : TcEpi<4>::halves;
+int knn_tc_lists_per_split(int kc, int ew) {
+    (void)kc;
+    return ew / 4;
 }
 
 slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const float* norms,
-                                int64_t N, int Dp, int64_t Np, int kc, int splits, float* cand_d,
-                                int32_t* cand_i, unsigned int* err_flag) {
+                                int64_t N, int Dp, int64_t Np, int kc, int ew, int splits,
+                                float* cand_d, int32_t* cand_i, unsigned int* err_flag) {
     if (kc != 32 && kc != 64) return set_err(ctx, SLK_ERR_INVALID_ARG, "bf16 candidates need KC=32 or 64");
+    if (ew != 4 && ew != 8) return set_err(ctx, SLK_ERR_INVALID_ARG, "4 or 8 epilogue warps");
     if (Dp % TC_BK != 0 || Np % TC_M != 0)
         return set_err(ctx, SLK_ERR_INVALID_ARG, "bad padded shape %lld x %d", (long long)Np, Dp);
     if ((reinterpret_cast<uintptr_t>(xt) & 15) != 0)
@@ -839,20 +895,29 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
         cfg.numAttrs = 1;
         SLK_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, ta, tb2, norms, N, Np, Dp, n_tiles, splits,
                                              row_blocks, cand_d, cand_i, err_flag));
-    } else if (kc == 32) {
-        constexpr int EW = SLK_TC_EW32;
-        auto kern = knn_cand_tc_kernel<32, EW, SLK_TC_PIPE != 0, SLK_TC_NOBAR != 0>;
-        const size_t smem = tc_smem_bytes<EW>();
+    } else if (kc == 32 && ew == 4) {
+        auto kern = knn_cand_tc_kernel<32, 4, SLK_TC_PIPE != 0, SLK_TC_NOBAR != 0>;
+        const size_t smem = tc_smem_bytes<4>();
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem));
-        kern<<<grid, TcEpi<EW>::threads, smem, ctx->stream>>>(
+        kern<<<grid, TcEpi<4>::threads, smem, ctx->stream>>>(
+            ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
+    } else if (kc == 32) {
+        // 8 epilogue warps: the column norms staged in shared memory (measured
+        // faster here than per-warp global loads: 426 against 469 ms at 1e6 x 128)
+        auto kern = knn_cand_tc_kernel<32, 8, SLK_TC_PIPE8 != 0, SLK_TC_NOBAR8 != 0>;
+        const size_t smem = tc_smem_bytes<8>();
+        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        kern<<<grid, TcEpi<8>::threads, smem, ctx->stream>>>(
             ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
     } else {
-        auto kern = knn_cand_tc_kernel<64, 4, false, false>;
-        const size_t smem = tc_smem_bytes<4, false, 64>();
+        constexpr int EW = SLK_TC_EW64;
+        auto kern = knn_cand_tc_kernel<64, EW, false, SLK_TC_NOBAR64 != 0>;
+        const size_t smem = tc_smem_bytes<EW, false, 64>();
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem));
-        kern<<<grid, TcEpi<4, false, 64>::threads, smem, ctx->stream>>>(
+        kern<<<grid, TcEpi<EW, false, 64>::threads, smem, ctx->stream>>>(
             ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
     }
     SLK_LAUNCH_CHECK(ctx, "knn_cand_tc_kernel");

@@ -83,6 +83,7 @@ struct DevState {
     unsigned long long sel_cnt;
     unsigned int sel_min_bits;
     unsigned int sym_error;           // bit 0: a row of the graph to symmetrise is too long
+    unsigned int deg_mixed;           // 1: the rows of a CSR graph do not all have one degree
 };
 
 enum : unsigned int { ERR_BARRIER_TIMEOUT = 1u };
@@ -179,6 +180,10 @@ slk_status bound_launch(slk_ctx* ctx, const float* A, const int64_t* row_ptr,
                         const int32_t* col_idx, const float* w, int64_t N, int L, float lambda,
                         float* Z, float* Z_prev, int max_iters, float tol, DevState* st,
                         int kdeg = 0);   // kdeg > 0: every row has kdeg entries (row_ptr[p] = kdeg p)
+
+// Degree shared by every row of a CSR graph (row_ptr[p] = k p), or 0 if the
+// degrees differ or k > SLK_MAX_K.  Synchronises the stream.
+slk_status uniform_degree(slk_ctx* ctx, const int64_t* row_ptr, int64_t N, DevState* st, int* kdeg);
 
 // One block waits at the device-wide barrier of the persistent z-update
 // kernels for a second block that is never launched; the wait gives up after
