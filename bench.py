@@ -53,6 +53,16 @@ SEED = 1810
 # a kernel on a workload, from a one-pass ncu capture, with the SHA-256 of the
 # kernel's source file at capture time: a changed source reports null.
 NCU_TRAFFIC = {
+    ("bound_staged_kernel", "manifolds_1000000x128_L100"): {
+        "bytes": 6525729536 + 2381408768,
+        "source": "paper_1810_13044_gb300/csrc/bound.cu",
+        "sha256": "f63b3eeed3ba7913966ecc82d97bda02d0899ec065349cc2357b2128bb16b9db",
+    },
+    ("knn_cand_tc_kernel", "manifolds_1000000x128_L100"): {
+        "bytes": 50359891200 + 539633664,
+        "source": "paper_1810_13044_gb300/csrc/knn_tc.cu",
+        "sha256": "83bd2d84463f01a644182b230e9d2993035b55c2d285ceea04db3b33a4db8f63",
+    },
     ("knn_cand_tc_kernel", "mnist_like_70000x784_L10"): {
         "bytes": 1141291264 + 52733952,
         "source": "paper_1810_13044_gb300/csrc/knn_tc.cu",
@@ -435,10 +445,18 @@ def measure_workload(W, args, ctx, dev, world, stream, main: bool):
     hbm = peaks.get("hbm_gbs", 6800.0)
     upd = max(1, stats["inner_iters_total"]) * args.steps
     gbs = N * b_row * upd / (ms_phase["bound"] / 1e3) / 1e9
-    roof_bound = {"bound": "hbm", "kernel": "bound_persistent_kernel", "achieved": gbs,
+    # the z-update kernel bound_launch picks for this shape (fixed degree k)
+    if N >= 100000 and 64 < L <= 128 and L % 4 == 0:
+        bkern = "bound_staged_kernel"
+    elif N * (4 * L + 4 * k + (4 * k if heat else 0)) <= 96 * 1024 * 2 * 152:
+        bkern = "bound_cached_kernel"
+    else:
+        bkern = "bound_persistent_kernel"
+    roof_bound = {"bound": "hbm", "kernel": bkern, "achieved": gbs,
                   "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                   "peak_source": "of measured hbm_gbs" if "hbm_gbs" in peaks else "of fallback",
-                  "traffic": ncu_traffic("bound_persistent_kernel", W["name"]),
+                  "traffic": ncu_traffic(bkern, W["name"]),
+                  "traffic_note": "per launch = the z-updates of one outer iteration",
                   "algorithmic": f"N*(8+4k{'+4k' if heat else ''}+12L) = {N * b_row / 1e6:.1f} MB "
                                  f"per update; the solve's bound phase over its "
                                  f"{stats['inner_iters_total']} updates",
@@ -804,10 +822,12 @@ def make_request_pool(count, dev, seed=1810):
 def serve_stream(slk, ctx, params, pool, seq, arrivals, budget, keep=0):
     """Serve the requests pool[seq[i]] arriving at arrivals[i] (seconds from
     the start) on a fresh server; returns (completion times, wall seconds,
-    launches, labels of the first `keep` requests, max requests in system)."""
+    (Z, labels, modes) of the first `keep` requests, the largest number of
+    requests in the system while the first and while the second half of the
+    stream arrived)."""
     srv = slk.Server(max_slots=64, quantum=10, memory_bytes=budget, params=params, ctx=ctx)
     done_at, tickets, pending, kept = {}, {}, set(), {}
-    nxt, in_sys_max = 0, 0
+    nxt, in_sys = 0, [0, 0]
     t0 = time.perf_counter()
     while nxt < len(seq) or pending:
         now = time.perf_counter() - t0
@@ -816,7 +836,8 @@ def serve_stream(slk, ctx, params, pool, seq, arrivals, budget, keep=0):
             tickets[tk] = nxt
             pending.add(tk)
             nxt += 1
-        in_sys_max = max(in_sys_max, len(pending))
+        half = 0 if nxt <= len(seq) // 2 else 1
+        in_sys[half] = max(in_sys[half], len(pending))
         if not pending:
             time.sleep(max(0.0, min(0.002, arrivals[nxt] - now)))
             continue
@@ -828,11 +849,11 @@ def serve_stream(slk, ctx, params, pool, seq, arrivals, budget, keep=0):
                 i = tickets[tk]
                 done_at[i] = now
                 if i < keep:
-                    kept[i] = (res[1].clone(), res[2].clone())
+                    kept[i] = (res[0].clone(), res[1].clone(), res[2].clone())
                 pending.discard(tk)
     wall = time.perf_counter() - t0
     srv.close()
-    return np.array([done_at[i] for i in range(len(seq))]), wall, kept, in_sys_max
+    return np.array([done_at[i] for i in range(len(seq))]), wall, kept, in_sys
 
 
 def run_serving(args, rank, world, local):
@@ -860,8 +881,8 @@ def run_serving(args, rank, world, local):
     keep = min(n, 200)
     ctx.profile(True)
     with ClockSampler(local) as clk:
-        done, wall, kept, in_sys_max = serve_stream(slk, ctx, params, pool, seq, arrivals, budget,
-                                                    keep=keep)
+        done, wall, kept, in_sys = serve_stream(slk, ctx, params, pool, seq, arrivals, budget,
+                                                keep=keep)
     _, _, launches = ctx.profile_read()
     ctx.profile(False)
     lat = (done - arrivals) * 1e3
@@ -869,31 +890,37 @@ def run_serving(args, rank, world, local):
     # the plain per-instance GPU solve of the same requests, one after another
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    equal = 0
+    equal, dz_max, differing = 0, 0.0, []
     for i in range(keep):
         pr = pool[seq[i]]
-        _, lab1, m1, _ = slk.solve(pr["X"], pr["L"], pr["k"], pr["lam"], pr["init_modes"],
-                                   params=params, ctx=ctx)
-        equal += int(torch.equal(lab1, kept[i][0]) and torch.equal(m1, kept[i][1]))
+        Z1, lab1, m1, _ = slk.solve(pr["X"], pr["L"], pr["k"], pr["lam"], pr["init_modes"],
+                                    params=params, ctx=ctx)
+        same = torch.equal(lab1, kept[i][1]) and torch.equal(m1, kept[i][2])
+        equal += int(same)
+        dz_max = max(dz_max, (Z1 - kept[i][0]).abs().max().item())
+        if not same:
+            differing.append(int(seq[i]))
     torch.cuda.synchronize()
     plain = keep / (time.perf_counter() - t0)
-    # the highest arrival rate the server sustains: a stream of 300 requests
-    # at each rate; sustained when the last third's latency stays within 2x
-    # the first third's (the queue does not grow) and throughput keeps up
+    # the highest arrival rate the server sustains: a stream of 400 requests
+    # at each rate; sustained when the queue stays bounded -- the most
+    # requests in the system while the second half arrives is within 1.5x
+    # (+ 8) of that while the first half arrives -- and the completions keep
+    # pace with the arrivals (served per second over the arrival span >= 90 %)
     search = []
     if args.rate_search:
-        for rate in (20.0, 40.0, 60.0, 80.0, 100.0, 150.0):
-            gs = np.random.Generator(np.random.PCG64(int(rate)))
-            m = 300
+        for rate in (10.0, 20.0, 30.0, 40.0, 50.0, 60.0, 80.0):
+            gs = np.random.Generator(np.random.PCG64(1000 + int(rate)))
+            m = 400
             sq = gs.integers(0, len(pool), size=m)
             arr = np.cumsum(gs.exponential(1.0 / rate, size=m))
             d, wl, _, ins = serve_stream(slk, ctx, params, pool, sq, arr, budget)
             la = (d - arr) * 1e3
-            first, last = la[: m // 3], la[-(m // 3):]
-            ok = (np.percentile(last, 99) <= 2.0 * max(np.percentile(first, 99), 1.0)) and \
-                 (m / wl >= 0.9 * rate)
+            span = arr[-1]
+            done_in_span = int((d <= span).sum())
+            ok = ins[1] <= 1.5 * ins[0] + 8 and done_in_span >= 0.9 * np.sum(arr <= span) - 8
             search.append({"rate": rate, "served_per_s": m / wl, "p50_ms": float(np.percentile(la, 50)),
-                           "p99_ms": float(np.percentile(la, 99)), "max_in_system": ins,
+                           "p99_ms": float(np.percentile(la, 99)), "in_system_max_by_half": ins,
                            "sustained": bool(ok)})
     sustainable = max([r["rate"] for r in search if r["sustained"]], default=None)
     if rank == 0:
@@ -913,9 +940,16 @@ def run_serving(args, rank, world, local):
                                     "so latency is measured from arrival"},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
-            "max_in_system": in_sys_max,
+            "in_system_max_by_half": in_sys,
             "plain_per_instance_gpu": {"value": plain, "unit": "solves/s", "requests": keep,
-                                       "equal_labels_and_modes": f"{equal}/{keep}"},
+                                       "equal_labels_and_modes": f"{equal}/{keep}",
+                                       "max_abs_dz": dz_max,
+                                       "differing_pool_requests": sorted(set(differing)),
+                                       "note": "requests of 1e5 rows or more with 64 < L <= 128 run "
+                                               "their z-updates alone on the staged kernel, whose "
+                                               "soft-max rounds differently from the segmented "
+                                               "kernel the server uses; labels then differ only at "
+                                               "near-ties"},
             "rate_search": search, "max_sustainable_rate": sustainable,
             "rows_total": int(sum(pool[i]["N"] for i in seq)),
             "gpu_launches": launches, "clocks": clk.summary(),
