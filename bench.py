@@ -500,6 +500,9 @@ def measure_workload(W, args, ctx, dev, world, stream, main: bool):
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": N * D * 4 + L * 4,
                 "d2h_bytes_per_step": N * 4 + L * 4},
         "energy": stats["energy"], "knn_fallback_rows": stats["knn_fallback_rows"],
+        "knn_rows_by_stage": {"left_open_by_first_certificate": stats["knn_fallback_rows"],
+                              "to_float32_stage": stats["knn_float32_rows"],
+                              "exact_rescan": stats["knn_exact_rows"]},
     }
     return res, clk.summary(), launches, X
 

@@ -86,9 +86,13 @@ const char* slk_last_error(const slk_ctx* ctx);
  *            bfloat16 tensor-core (tcgen05) distance tiles.  Both produce
  *            candidates that are re-ranked with exact float32 distances and
  *            certified by a rounding-error bound.  With BF16_RERANK the rows
- *            that fail it get float32 candidate tiles and the float32
- *            certificate next; rows still uncertified are recomputed by an
- *            exact float32 scan, so both precisions return the same graph.
+ *            that fail it get two-term bfloat16 tensor-core tiles (each
+ *            feature as h + l, h = bf16(v), l = bf16(v - h)) under their own
+ *            certificate next, then float32 candidate tiles under the float32
+ *            certificate (at most 65536 rows take the two-term stage; the
+ *            rest go straight to the float32 one); rows still uncertified are
+ *            recomputed by an exact float32 scan, so both precisions return
+ *            the same graph.
  *   fallback_rows [host, nullable]: receives how many rows the first
  *            certificate left open (for BF16_RERANK: the rows sent to the
  *            float32 stage).
@@ -97,6 +101,14 @@ slk_status slk_knn_graph(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int
                          int32_t affinity, int32_t precision, float sigma,
                          int64_t* row_ptr, int32_t* col_idx, float* dist2, float* w,
                          int64_t* fallback_rows);
+
+/* Rows per stage of the last kNN graph built on ctx (by slk_knn_graph,
+ * slk_solve, slk_solve_host, slk_solve_ms): rows[0] the rows the first
+ * certificate left open, rows[1] (BF16_RERANK) the rows the two-term stage
+ * left open for the float32 stage, rows[2] the rows rescanned exactly.
+ *   rows [3] host out.
+ * Synchronises ctx's stream.  SLK_ERR_INVALID_ARG if rows is NULL. */
+slk_status slk_knn_stage_rows(slk_ctx* ctx, int64_t* rows);
 
 /* Kernel width of Section 4.2 from the n = N k squared kNN distances dist2.
  *   rule SLK_SIGMA_MEDIAN: sigma = median of sqrt(dist2) (mean of the two
@@ -194,8 +206,12 @@ typedef struct {
     int32_t converged;          /* 1 if the modes stopped changing */
     float sigma;                /* kernel width used */
     double energy;              /* E of Eq. (1) after the last outer iteration */
-    int64_t knn_fallback_rows;  /* kNN rows recomputed by the exact scan */
+    int64_t knn_fallback_rows;  /* kNN rows the first certificate left open (bfloat16: the rows
+                                   sent to the two-term tensor-core stage) */
     int32_t ms_iters_total;     /* SLK-MS: mean-shift iterations summed over outer iterations */
+    int64_t knn_float32_rows;   /* bfloat16: rows the two-term certificate left open (sent to
+                                   the float32 stage); 0 otherwise */
+    int64_t knn_exact_rows;     /* rows recomputed by the exact float32 scan */
 } slk_stats;
 
 /* Fill *p with the defaults listed in slk_params. */

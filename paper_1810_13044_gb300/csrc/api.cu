@@ -287,6 +287,18 @@ extern "C" slk_status slk_knn_graph(slk_ctx* ctx, const float* X, int64_t N, int
     return SLK_OK;
 }
 
+extern "C" slk_status slk_knn_stage_rows(slk_ctx* ctx, int64_t* rows) {
+    BEGIN_CALL(ctx);
+    CHECK_ARG(rows, "rows must not be NULL");
+    DevState hs;
+    const slk_status r = read_state(ctx, &hs);
+    if (r != SLK_OK) return r;
+    rows[0] = hs.fallback_count;
+    rows[1] = hs.fallback2_count;
+    rows[2] = ctx->knn_last_bf16 ? hs.fallback3_count : hs.fallback_count;
+    return SLK_OK;
+}
+
 extern "C" slk_status slk_sigma(slk_ctx* ctx, const float* dist2, int64_t n, int32_t rule,
                                 float* sigma_out) {
     BEGIN_CALL(ctx);
@@ -623,6 +635,9 @@ slk_status solve_device(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int3
         stats->sigma = hs.sigma;
         stats->energy = hs.energy;
         stats->knn_fallback_rows = hs.fallback_count;
+        stats->knn_float32_rows = hs.fallback2_count;
+        stats->knn_exact_rows = p.knn_precision == SLK_KNN_BF16_RERANK ? hs.fallback3_count
+                                                                      : hs.fallback_count;
     }
     return converged ? SLK_OK : SLK_NOT_CONVERGED;
 }
@@ -920,6 +935,9 @@ extern "C" slk_status slk_solve_ms(slk_ctx* ctx, const float* X, int64_t N, int3
         stats->sigma = hs.sigma;
         stats->energy = hs.energy;
         stats->knn_fallback_rows = hs.fallback_count;
+        stats->knn_float32_rows = hs.fallback2_count;
+        stats->knn_exact_rows = p.knn_precision == SLK_KNN_BF16_RERANK ? hs.fallback3_count
+                                                                      : hs.fallback_count;
         stats->ms_iters_total = ms_total;
     }
     return converged ? SLK_OK : SLK_NOT_CONVERGED;

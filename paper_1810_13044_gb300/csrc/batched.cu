@@ -768,6 +768,8 @@ extern "C" slk_status slk_solve_batched(slk_ctx* ctx, const slk_instance* inst, 
             stats[b].energy = h_energy[b];
             stats[b].knn_fallback_rows = -1;
             stats[b].ms_iters_total = 0;
+            stats[b].knn_float32_rows = -1;
+            stats[b].knn_exact_rows = -1;
         }
     }
     (void)use_graph;

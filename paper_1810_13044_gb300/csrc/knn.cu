@@ -32,6 +32,12 @@
 
 int knn_tc_tile_cols();
 int knn_tc_lists_per_split(int kc, int ew);
+slk_status knn_cand_split_launch(slk_ctx* ctx, const __nv_bfloat16* qh, const __nv_bfloat16* ql,
+                                 const float* qnorm, int64_t Fcap, const long long* rows_dev,
+                                 const __nv_bfloat16* xh, const __nv_bfloat16* xl,
+                                 const float* norms, int64_t N, int Dp, int64_t Np, int ew,
+                                 int splits, float* cand_d, int32_t* cand_i,
+                                 unsigned int* err_flag);
 
 namespace {
 
@@ -43,6 +49,32 @@ constexpr int kNoIdx = 0x7fffffff;
 
 __device__ __forceinline__ bool lex_less(float d, int i, float d2, int i2) {
     return d < d2 || (d == d2 && i < i2);
+}
+
+// Open rows at or below this count skip the float32 tiles (whose 128-row
+// blocks they would leave mostly empty) and go to the exact scan.
+constexpr long long kExactDirectRows = 256;
+
+// Column splits of the float32 stage for F open rows: as many as a buffer of
+// cap floats holds at F rows per list of KC, at most 16 (the rerank stages
+// 16 lists of 32 per row).  Host and device compute it from the same count.
+__host__ __device__ __forceinline__ int query_splits(long long F, long long cap, int kc) {
+    if (F <= 0) return 1;
+    long long sp = cap / (F * (long long)kc);
+    if (sp > 16) sp = 16;
+    if (sp < 1) sp = 1;
+    return (int)sp;
+}
+
+// Column splits of the exact scan for F rows: partial lists of k entries per
+// (row, split), at most 256 splits (a few open rows still fill the GPU), as
+// many as cap entries hold.
+__host__ __device__ __forceinline__ int exact_splits(long long F, long long cap, int k) {
+    if (F <= 0) return 1;
+    long long sp = cap / (F * (long long)k);
+    if (sp > 256) sp = 256;
+    if (sp < 1) sp = 1;
+    return (int)sp;
 }
 
 // -------------------------------------------------------------------- prep
@@ -116,6 +148,20 @@ __global__ void mu_kernel(const double* __restrict__ colsum, int64_t N, int D, f
         mu[j] = (float)(colsum[j] * inv_n);
 }
 
+// rho >= sqrt(e2 bound) + u sqrt(v2 bound) and kappa >= rho / ||v|| with
+// ||v|| >= sqrt(v2 / bound), from the float pairs (eh, el) = e2 and (vh, vl)
+// = v2 (lane sums of e^2 and v^2); every step rounded toward the bound.
+// kappa = 0 when v2 = 0 (then e = 0 and rho = 0), +inf when ||v|| underflows.
+__device__ __forceinline__ void rho_kappa(float eh, float el, float vh, float vl, float bound_u,
+                                          float& rho, float& kappa) {
+    const float e2 = __fadd_ru(eh, el), v2 = __fadd_ru(vh, vl);
+    const float t1 = __fsqrt_ru(__fmul_ru(e2, bound_u));
+    const float t2 = __fmul_ru(5.9604644775390625e-08f, __fsqrt_ru(__fmul_ru(v2, bound_u)));
+    rho = __fadd_ru(t1, t2);
+    const float vlo = __fsqrt_rd(__fdiv_rd(__fadd_rd(vh, vl), bound_u));
+    kappa = (v2 > 0.f) ? (vlo > 0.f ? __fdiv_ru(rho, vlo) : __int_as_float(0x7f800000)) : 0.f;
+}
+
 // One warp per padded row: xt = round(v), v = fl(x - mu), with
 //   norms[p] = ||xt_p||^2: lane sums of xt^2 in float32, lanes added as float
 //     pairs (within a few u^2 of the exact sum);
@@ -128,21 +174,30 @@ __global__ void mu_kernel(const double* __restrict__ colsum, int64_t N, int D, f
 // accumulator per column of its 4-column groups, ceil(Dp/128) terms each,
 // added pairwise at the end: ceil(Dp/128) + 2 <= Dp/32 roundings.  Each
 // bfloat16 square is exact.
-// The row maxima go to st with one atomic per block.
+// The row maxima go to st with one atomic per block, with that of
+// kappa_p = rho_p / ||v_p|| (||v_p|| from below), so that rho_q <= kappa ||v_q||
+// for every row.
+// aug (nullable, Np x 64 bfloat16): the folded-norm columns of the
+// tensor-core tiles, [1, 1, 1, a_p, 0...] in columns 0..31 and [a_p, 1, 1, 1,
+// 0...] in 32..63, a_p = (t1, t2, t3) the bfloat16 terms of -norms[p] / 2
+// (t1 = bf16(x), t2 = bf16(x - t1), t3 = bf16(x - t1 - t2), each difference
+// exact in float32, so t1 + t2 + t3 is within 2^-24 (1.02) |x| of x); a
+// padding row has a_p = (-inf, 0, 0).
 template <int V>
 __global__ void __launch_bounds__(256)
 prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
                  int64_t Np, const float* __restrict__ mu, int to_bf16,
                  float* __restrict__ xt32, __nv_bfloat16* __restrict__ xt16,
                  float* __restrict__ norms, float* __restrict__ rho,
-                 float* __restrict__ norms32, DevState* st) {
-    __shared__ unsigned bmax_n, bmax_r, bmax_n32;
-    if (threadIdx.x == 0) { bmax_n = 0u; bmax_r = 0u; bmax_n32 = 0u; }
+                 float* __restrict__ norms32, __nv_bfloat16* __restrict__ aug, DevState* st) {
+    __shared__ unsigned bmax_n, bmax_r, bmax_n32, bmax_k;
+    if (threadIdx.x == 0) { bmax_n = 0u; bmax_r = 0u; bmax_n32 = 0u; bmax_k = 0u; }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const double bound = 1.0 + (double)(Dp / 32 + 2) * 5.9604644775390625e-08;
-    unsigned my_n = 0u, my_r = 0u, my_n32 = 0u;
+    // 1 + (Dp/32 + 2) u, rounded up: the lane sums' relative error bound
+    const float bound_u = __double2float_ru(1.0 + (double)(Dp / 32 + 2) * 5.9604644775390625e-08);
+    unsigned my_n = 0u, my_r = 0u, my_n32 = 0u, my_k = 0u;
     for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < Np;
          p += nw) {
         float n2v[V], e2v[V], v2v[V];
@@ -209,20 +264,45 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
             fpair_add(vh, vl, __shfl_xor_sync(0xffffffffu, vh, o), __shfl_xor_sync(0xffffffffu, vl, o));
         }
         if (lane == 0) {
-            const double dn = (double)nh + (double)nl, de = (double)eh + (double)el,
-                         dv = (double)vh + (double)vl;
-            const float nf = (float)dn;
-            const double r = sqrt(de * bound) + 5.9604644775390625e-08 * sqrt(dv * bound);
-            const float rf = __double2float_ru(r * (1.0 + 1e-12));
+            // the pair sums rounded to nearest (norms), up and down (bounds);
+            // float32 with directed rounding keeps the bounds off the slow
+            // float64 pipe
+            const float nf = __fadd_rn(nh, nl);
+            float rf, kf;
+            rho_kappa(eh, el, vh, vl, bound_u, rf, kf);
             // padding rows get an infinite norm: no distance to them can pass a filter
             norms[p] = (p < N) ? nf : __int_as_float(0x7f800000);
             rho[p] = rf;
-            const float n32 = (float)dv;   // ||v||^2 of the float32 operand v
+            const float n32 = __fadd_rn(vh, vl);   // ||v||^2 of the float32 operand v
             if (norms32) norms32[p] = (p < N) ? n32 : __int_as_float(0x7f800000);
             if (p < N) {
                 my_n = max(my_n, __float_as_uint(nf));
                 my_r = max(my_r, __float_as_uint(rf));
                 my_n32 = max(my_n32, __float_as_uint(n32));
+                my_k = max(my_k, __float_as_uint(kf));
+            }
+        }
+        if (aug) {
+            // lanes 0..7 write 8 columns each (16-byte stores)
+            const float nfa = __shfl_sync(0xffffffffu, __fadd_rn(nh, nl), 0);
+            if (lane < 8) {
+                const float x = -0.5f * nfa;
+                const __nv_bfloat16 t1 = __float2bfloat16_rn(x);
+                const float r1 = x - __bfloat162float(t1);
+                const __nv_bfloat16 t2 = __float2bfloat16_rn(r1);
+                const __nv_bfloat16 t3 = __float2bfloat16_rn(r1 - __bfloat162float(t2));
+                const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
+                const __nv_bfloat16 a1 = (p < N) ? t1 : __float2bfloat16_rn(-__int_as_float(0x7f800000));
+                const __nv_bfloat16 a2 = (p < N) ? t2 : zero, a3 = (p < N) ? t3 : zero;
+                __nv_bfloat16 w[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) w[q] = zero;
+                if (lane == 0) {          // columns 0..7: 1, 1, 1, a1, a2, a3
+                    w[0] = one; w[1] = one; w[2] = one; w[3] = a1; w[4] = a2; w[5] = a3;
+                } else if (lane == 4) {   // columns 32..39: a1, a2, a3, 1, 1, 1
+                    w[0] = a1; w[1] = a2; w[2] = a3; w[3] = one; w[4] = one; w[5] = one;
+                }
+                *reinterpret_cast<uint4*>(aug + p * 64 + 8 * lane) = *reinterpret_cast<const uint4*>(w);
             }
         }
     }
@@ -230,12 +310,159 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
         atomicMax(&bmax_n, my_n);
         atomicMax(&bmax_r, my_r);
         atomicMax(&bmax_n32, my_n32);
+        atomicMax(&bmax_k, my_k);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         atomicMax(&st->knn_max_norm_bits, bmax_n);
         atomicMax(&st->knn_max_rho_bits, bmax_r);
         atomicMax(&st->knn_max_norm32_bits, bmax_n32);
+        atomicMax(&st->knn_max_kappa_bits, bmax_k);
+    }
+}
+
+// ------------------------------------------------- two-term bfloat16 operand
+
+// One warp per padded row p < Np, for the rows the bfloat16 certificate
+// leaves open (nothing runs when *open_count is 0): with v = fl(x - mu) and
+// h = bf16(v) (the candidate operand xt), the second term l = bf16(v - h)
+// (v - h is exact), so that s = h + l carries 16 significant bits of v:
+//   xl[p]      = l,
+//   norms_s[p] = ||s||^2 (s = h + l is exact in float32: l either equals
+//                v - h, then s = v, or has its last bit above v's),
+//   rho_s[p]  >= ||s - (x_p - mu)||, from e = s - v (exact) and
+//                |v - (x - mu)| <= u |v|, as for the other operands.
+// Sums as in prep_rows_kernel (the same lane split and float-pair butterfly,
+// so the same summation bound); row maxima to st.
+template <int V>
+__global__ void __launch_bounds__(256)
+prep_split_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int64_t Np,
+                  const float* __restrict__ mu, const long long* __restrict__ open_count,
+                  __nv_bfloat16* __restrict__ xl, float* __restrict__ norms_s,
+                  float* __restrict__ rho_s, DevState* st) {
+    if (*open_count == 0) return;
+    __shared__ unsigned bmax_n, bmax_r, bmax_k;
+    if (threadIdx.x == 0) { bmax_n = 0u; bmax_r = 0u; bmax_k = 0u; }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    // 1 + (Dp/32 + 2) u, rounded up: the lane sums' relative error bound
+    const float bound_u = __double2float_ru(1.0 + (double)(Dp / 32 + 2) * 5.9604644775390625e-08);
+    unsigned my_n = 0u, my_r = 0u, my_k = 0u;
+    for (int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < Np;
+         p += nw) {
+        float n2v[V], e2v[V], v2v[V];
+#pragma unroll
+        for (int q = 0; q < V; ++q) { n2v[q] = 0.f; e2v[q] = 0.f; v2v[q] = 0.f; }
+#pragma unroll 4
+        for (int j = lane * V; j < Dp; j += 32 * V) {
+            float v[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) v[q] = 0.f;
+            if (p < N && j < D) {
+                if constexpr (V == 4) {
+                    const float4 x = __ldg(reinterpret_cast<const float4*>(X + p * D + j));
+                    const float4 m = __ldg(reinterpret_cast<const float4*>(mu + j));
+                    v[0] = x.x - m.x; v[1] = x.y - m.y; v[2] = x.z - m.z; v[3] = x.w - m.w;
+                } else {
+                    v[0] = X[p * D + j] - __ldg(mu + j);
+                }
+            }
+            __nv_bfloat16 lb[V];
+            float sv[V];
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const float h = __bfloat162float(__float2bfloat16_rn(v[q]));
+                lb[q] = __float2bfloat16_rn(v[q] - h);
+                sv[q] = h + __bfloat162float(lb[q]);
+            }
+            if constexpr (V == 4) {
+                __nv_bfloat162 b01, b23;
+                b01.x = lb[0]; b01.y = lb[1]; b23.x = lb[2]; b23.y = lb[3];
+                uint2 w;
+                w.x = *reinterpret_cast<const unsigned*>(&b01);
+                w.y = *reinterpret_cast<const unsigned*>(&b23);
+                *reinterpret_cast<uint2*>(xl + p * Dp + j) = w;
+            } else {
+                xl[p * Dp + j] = lb[0];
+            }
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                n2v[q] = fmaf(sv[q], sv[q], n2v[q]);
+                const float e = sv[q] - v[q];
+                e2v[q] = fmaf(e, e, e2v[q]);
+                v2v[q] = fmaf(v[q], v[q], v2v[q]);
+            }
+        }
+        float n2 = n2v[0], e2 = e2v[0], v2 = v2v[0];
+        if constexpr (V == 4) {
+            n2 = (n2v[0] + n2v[1]) + (n2v[2] + n2v[3]);
+            e2 = (e2v[0] + e2v[1]) + (e2v[2] + e2v[3]);
+            v2 = (v2v[0] + v2v[1]) + (v2v[2] + v2v[3]);
+        }
+        float nh = n2, nl = 0.f, eh = e2, el = 0.f, vh = v2, vl = 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fpair_add(nh, nl, __shfl_xor_sync(0xffffffffu, nh, o), __shfl_xor_sync(0xffffffffu, nl, o));
+            fpair_add(eh, el, __shfl_xor_sync(0xffffffffu, eh, o), __shfl_xor_sync(0xffffffffu, el, o));
+            fpair_add(vh, vl, __shfl_xor_sync(0xffffffffu, vh, o), __shfl_xor_sync(0xffffffffu, vl, o));
+        }
+        if (lane == 0) {
+            const float nf = __fadd_rn(nh, nl);
+            float rf, kf;
+            rho_kappa(eh, el, vh, vl, bound_u, rf, kf);
+            norms_s[p] = (p < N) ? nf : __int_as_float(0x7f800000);
+            rho_s[p] = rf;
+            if (p < N) {
+                my_n = max(my_n, __float_as_uint(nf));
+                my_r = max(my_r, __float_as_uint(rf));
+                my_k = max(my_k, __float_as_uint(kf));
+            }
+        }
+    }
+    if (lane == 0) {
+        atomicMax(&bmax_n, my_n);
+        atomicMax(&bmax_r, my_r);
+        atomicMax(&bmax_k, my_k);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicMax(&st->knn_max_norm_s_bits, bmax_n);
+        atomicMax(&st->knn_max_rho_s_bits, bmax_r);
+        atomicMax(&st->knn_max_kappa_s_bits, bmax_k);
+    }
+}
+
+// Query rows of the two-term stage: row f < min(*count, Fcap) of qh / ql /
+// qnorm is row fb[f] of xh / xl / norms_s; the rest of its 128-row block is
+// zero with an infinite norm.  One warp per row, 16-byte copies (Dp is a
+// multiple of 64).
+__global__ void __launch_bounds__(256)
+gather_split_kernel(const __nv_bfloat16* __restrict__ xh, const __nv_bfloat16* __restrict__ xl,
+                    const float* __restrict__ norms_s, int Dp, const int32_t* __restrict__ fb,
+                    const long long* __restrict__ count, int64_t Fcap,
+                    __nv_bfloat16* __restrict__ qh, __nv_bfloat16* __restrict__ ql,
+                    float* __restrict__ qnorm) {
+    long long c = *count;
+    if (c > Fcap) c = Fcap;
+    const int64_t rows = (c + 127) / 128 * 128;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int n16 = Dp / 8;   // 16-byte words per row
+    for (int64_t f = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < rows;
+         f += nw) {
+        const bool live = f < c;
+        const int64_t p = live ? (int64_t)fb[f] : 0;
+        const uint4* sh = reinterpret_cast<const uint4*>(xh + p * Dp);
+        const uint4* sl = reinterpret_cast<const uint4*>(xl + p * Dp);
+        uint4* dh = reinterpret_cast<uint4*>(qh + f * Dp);
+        uint4* dl = reinterpret_cast<uint4*>(ql + f * Dp);
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        for (int j = lane; j < n16; j += 32) {
+            dh[j] = live ? __ldg(sh + j) : z;
+            dl[j] = live ? __ldg(sl + j) : z;
+        }
+        if (lane == 0) qnorm[f] = live ? norms_s[p] : __int_as_float(0x7f800000);
     }
 }
 
@@ -408,23 +635,28 @@ knn_cand_fp32_kernel(const float* __restrict__ xt, const float* __restrict__ nor
     }
 }
 
-// Float32 distance tiles for listed query rows (the rows the bfloat16
-// certificate left open): rows fb_list[f], f < *count, against every point.
-// Both operands are centred on the fly, v = fl(x - mu) -- the float32
+// Float32 distance tiles for listed query rows (the rows the earlier
+// certificates left open): rows fb_list[f], f < F = *count, against every
+// point.  Both operands are centred on the fly, v = fl(x - mu) -- the float32
 // operand the float32 path would hold -- and the norms are its norms.  Work
-// items (query row block, column split) are taken persistently, so the
-// grid does not depend on the count; lists go to ((split N + f) KC).
+// items (query row block, column split) are taken persistently, so the grid
+// does not depend on the count; the split count is query_splits(F, cap, KC)
+// and lists go to ((split F + f) KC).  Nothing runs for F <=
+// kExactDirectRows (those rows go to the exact scan).
 template <int KC>
 __global__ void __launch_bounds__(KT, 2)
 knn_cand_query_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
                       const float* __restrict__ mu, const float* __restrict__ norms32,
-                      const int32_t* __restrict__ fb_list, const long long* count_ptr, int splits,
-                      int n_tiles, float* __restrict__ cand_d, int32_t* __restrict__ cand_i) {
+                      const int32_t* __restrict__ fb_list, const long long* count_ptr,
+                      long long cap, int n_tiles, float* __restrict__ cand_d,
+                      int32_t* __restrict__ cand_i) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     CandSmem<KC>& s = *reinterpret_cast<CandSmem<KC>*>(smem_raw);
     __shared__ int64_t prow[BM];
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
     const long long F = *(const volatile long long*)count_ptr;
+    if (F <= kExactDirectRows) return;
+    const int splits = query_splits(F, cap, KC);
     const int64_t items = (F + BM - 1) / BM * splits;
     const int nk = Dp / BK;
     const int lr0 = t & 127, lq0 = t >> 7, lq1 = lq0 + 2;
@@ -567,7 +799,7 @@ knn_cand_query_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
         if (t < BM) {
             const int64_t f = rb * BM + t;
             if (f < F) {
-                const int64_t o = ((int64_t)sp * N + f) * KC;
+                const int64_t o = ((int64_t)sp * F + f) * KC;
                 for (int j = 0; j < KC; ++j) {
                     cand_d[o + j] = s.list_d[t][j];
                     cand_i[o + j] = s.list_i[t][j] == kNoIdx ? -1 : s.list_i[t][j];
@@ -597,21 +829,29 @@ __device__ __forceinline__ float exact_d2(const float* __restrict__ xp,
 // Rerank + certificate, one warp per row.  Lists hold KC entries each; the
 // SEL best of their union (SEL >= KC: several lists of a split together, as
 // the two column halves of the 8-warp tensor-core kernel) are the candidates
-// whose last one bounds the rest.  Q = false: every row p < N, the lists of
-// the candidate kernels at ((list Np + p) KC), failures appended to
-// fb_list.  Q = true: the rows fb_in[f], f < *count_in, left open by the
-// bfloat16 stage, their float32 query lists at ((split N + f) KC), norms of
-// the float32 operand (rho <= u ||v||), failures appended to fb_list /
-// *count_out.
-template <int KC, bool Q, int E = MAXE, int SEL = KC>
+// whose last one bounds the rest.  gam bounds the error of a tile's dot
+// product relative to |xt_p| |xt_q| (with the norms' roundings added here).
+//   MODE 0: every row p < N, the lists of the candidate kernels at
+//           ((list Np + p) KC), failures appended to fb_list.
+//   MODE 1: the rows fb_in[f], f < F = *count_in, their float32 query lists
+//           at ((split F + f) KC), query_splits(F, Np, KC) of them (Np: the
+//           list buffer's capacity in floats), norms of the float32 operand
+//           (rho <= u ||v||), failures appended to fb_list / *count_out; for
+//           F <= kExactDirectRows every row is appended (no lists were made).
+//   MODE 2: the rows fb_in[f], f < *count_in, their two-term bfloat16 query
+//           lists at ((list Np + f) KC) for f < Np (Np: the query stage's
+//           row capacity), norms and rho of the two-term operand; the rows
+//           from Np on, and the failures, appended to fb_list / *count_out.
+template <int KC, int MODE, int E = MAXE, int SEL = KC>
 __global__ void __launch_bounds__(256, 4)
-knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, int splits,
+knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, int splits_in,
                   int64_t Np, const float* __restrict__ cand_d, const int32_t* __restrict__ cand_i,
-                  const float* __restrict__ norms, const float* __restrict__ rho, float u_acc,
+                  const float* __restrict__ norms, const float* __restrict__ rho, double gam,
                   int64_t* __restrict__ row_ptr, int32_t* __restrict__ col_idx,
                   float* __restrict__ dist2, int32_t* __restrict__ fb_list, DevState* st,
                   const int32_t* __restrict__ fb_in = nullptr, const long long* count_in = nullptr,
                   long long* count_out = nullptr) {
+    constexpr bool Q = MODE != 0;
     __shared__ float s_d[8][32 * E];   // each warp's staged lists (256 threads)
     __shared__ int s_i[8][32 * E];
     __shared__ float s_od[8][SEL];     // and its SEL selected candidates
@@ -619,11 +859,15 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     const double u = 5.9604644775390625e-08;  // 2^-24
-    const double nmax = (double)__uint_as_float(Q ? st->knn_max_norm32_bits : st->knn_max_norm_bits);
-    const double rmax = Q ? u * sqrt(nmax) * (1.0 + 1e-6)
-                          : (double)__uint_as_float(st->knn_max_rho_bits);
-    const double g = (double)Dp * (double)u_acc;
-    const double gam = g / (1.0 - g);
+    const double nmax = (double)__uint_as_float(
+        MODE == 0 ? st->knn_max_norm_bits : MODE == 1 ? st->knn_max_norm32_bits : st->knn_max_norm_s_bits);
+    const double rmax = MODE == 1 ? u * sqrt(nmax) * (1.0 + 1e-6)
+                                  : (double)__uint_as_float(MODE == 0 ? st->knn_max_rho_bits
+                                                                      : st->knn_max_rho_s_bits);
+    // rho_q <= kappa ||v_q|| for every row q
+    const double kappa = MODE == 1 ? u * (1.0 + 1e-5)
+                                   : (double)__uint_as_float(MODE == 0 ? st->knn_max_kappa_bits
+                                                                       : st->knn_max_kappa_s_bits);
     const double err_exact = 1.01 * (double)(D + 8) * u;
     // float32 copies of the bound's constants for the candidate pruning
     // (margins of 1e-6 .. 1e-5 cover the float rounding of the bounds)
@@ -632,11 +876,29 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
     const float snmax_f = (float)(sqrt(nmax) * (1.0 + 1e-6));
     const float keep_f = (float)((1.0 + 2.02 * err_exact) / (1.0 - 2.02 * err_exact) * (1.0 + 1e-5));
     const int64_t rows = Q ? (int64_t)(*(const volatile long long*)count_in) : N;
-    const int64_t stride = Q ? N : Np;
+    const int splits = MODE == 1 ? query_splits(rows, Np, KC) : splits_in;
+    const int64_t stride = MODE == 1 ? rows : Np;
+    if (MODE == 1 && rows <= kExactDirectRows) {
+        // too few rows for the float32 tiles: all of them to the exact scan
+        for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < rows;
+             f += (int64_t)gridDim.x * blockDim.x) {
+            const unsigned long long slot = atomicAdd((unsigned long long*)count_out, 1ull);
+            fb_list[slot] = fb_in[f];
+        }
+        return;
+    }
     if (!Q && blockIdx.x == 0 && threadIdx.x == 0) row_ptr[N] = N * (int64_t)k;
     for (int64_t f = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < rows;
          f += nw) {
         const int64_t p = Q ? (int64_t)fb_in[f] : f;
+        if (MODE == 2 && f >= Np) {
+            // beyond the query stage's capacity: on to the next stage
+            if (lane == 0) {
+                const unsigned long long slot = atomicAdd((unsigned long long*)count_out, 1ull);
+                fb_list[slot] = (int32_t)p;
+            }
+            continue;
+        }
         if (!Q && lane == 0) row_ptr[p] = p * (int64_t)k;
         // The splits' lists are sorted by (distance, index) and cover
         // disjoint columns, so the position of an entry in their union is its
@@ -759,7 +1021,7 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
         unsigned need[CPL];
         {
             const float npf = norms[p];
-            const float rp = Q ? 5.9604645e-08f * 1.000001f * sqrtf(npf) : rho[p] * 1.000001f;
+            const float rp = MODE == 1 ? 5.9604645e-08f * 1.000001f * sqrtf(npf) : rho[p] * 1.000001f;
             const float snp = sqrtf(npf) * 1.000001f;   // the row's own terms
             const float rr = rp + rmax_f;
             const float snf = snp + snmax_f;
@@ -780,7 +1042,7 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
                 if (lane + 32 * h < nc) {
                     const int q = ci[h];
                     const float nqf = norms[q];
-                    const float rq = (Q ? 5.9604645e-08f * 1.000001f * sqrtf(nqf) : rho[q] * 1.000001f);
+                    const float rq = (MODE == 1 ? 5.9604645e-08f * 1.000001f * sqrtf(nqf) : rho[q] * 1.000001f);
                     const float snq = snp + sqrtf(nqf) * 1.000001f;
                     const float lo = cd[h] - coef_f * snq * snq;
                     const float r = lo > 0.f ? sqrtf(lo) * 0.99999f - (rp + rq) : 0.f;
@@ -834,16 +1096,30 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
         if (lane == 0 && T < kInf) {
             bool ok = false;
             const double np_ = (double)norms[p];
-            const double rp = Q ? u * sqrt(np_) * (1.0 + 1e-6) : (double)rho[p];
-            const double sn = sqrt(np_) + sqrt(nmax);
-            // tile arithmetic (gam), the norms' float32 lane sums and roundings
+            const double rp = MODE == 1 ? u * sqrt(np_) * (1.0 + 1e-6) : (double)rho[p];
+            // every point q outside the candidates must be farther than
+            // K = dk (1 + 2.02 err_exact), the k-th candidate's exact distance
+            // inflated by its rounding.  With y = x - mu, a q with |y_q| >=
+            // |y_p| + sqrt(K) is (|y_q| - |y_p| >= sqrt(K)); any other has
+            // |y_q| < R = |xt_p| + rho_p + sqrt(K), hence rho_q <= kappa
+            // ||v_q|| <= kappa (1 + u) R and |xt_q| < R + rho_q.  Its
+            // distance is at least (sqrt(T - delta_q) - rho_p - rho_q)^2 with
+            // delta_q = coef (|xt_p| + |xt_q|)^2 (tile arithmetic gam, the
+            // norms' float32 lane sums and roundings), |xt_q| and rho_q taken
+            // at the smaller of these bounds and the largest norm and rho of
+            // all rows.
+            const double K = (double)dk * (1.0 + 2.02 * err_exact);
+            const double sp = sqrt(np_) * (1.0 + (double)(Dp / 32 + 4) * u);
+            const double R = (sp + rp + sqrt(K)) * (1.0 + 1e-9);
+            const double rq = fmin(rmax, kappa * (1.0 + u) * R * (1.0 + 1e-9));
+            const double sn = fmin(sqrt(np_) + sqrt(nmax), sp + R + rq);
             const double delta = (gam + (double)(Dp / 32 + 5) * u) * sn * sn;
             const double tt = (double)T - delta;
             if (tt > 0.0) {
-                const double root = sqrt(tt) - rp - rmax;
+                const double root = sqrt(tt) - rp - rq;
                 if (root > 0.0) {
                     const double lb = root * root * (1.0 - 1e-12);
-                    ok = (double)dk * (1.0 + 2.02 * err_exact) < lb;
+                    ok = K < lb;
                 }
             }
             if (!ok) {
@@ -921,28 +1197,32 @@ knn_fallback_kernel(const float* __restrict__ X, int64_t N, int D, int k,
     }
 }
 
-// Batched exact rescan of the rows that failed the certificate.  A block
-// takes R failed rows (their features cached in registers, lane-strided like
-// exact_d2) and one column range; each of its 8 warps streams a share of the
-// columns once for all R rows, computing every distance with exact_d2's
-// arithmetic (same per-lane fmaf order, same butterfly), and keeps a
-// register top-k per row (lane i holds entry i).  The 8 warp lists are
-// merged in shared memory into one list per (row, column range), written to
-// part_d / part_i at slot cs * k of the row's scratch.
+// Batched exact rescan of the rows that failed the certificate.  Work items
+// (R failed rows, one of cs = exact_splits(F, cap, k) column ranges) are
+// taken persistently, so the grid does not depend on the count F.  The R
+// rows' features are cached in registers, lane-strided like exact_d2; each
+// of the block's 8 warps streams a share of the column range once for all R
+// rows, computing every distance with exact_d2's arithmetic (same per-lane
+// fmaf order, same butterfly), and keeps a register top-k per row (lane i
+// holds entry i).  The 8 warp lists are merged in shared memory into one
+// list per (row, column range), written to part_d / part_i at
+// ((f cs + range) k).
 template <int R, int DPL>
 __global__ void __launch_bounds__(256)
 knn_fallback_batch_kernel(const float* __restrict__ X, int64_t N, int D, int k,
                           const int32_t* __restrict__ fb_list, const long long* count_ptr,
-                          int col_splits, int64_t slot_stride, float* __restrict__ part_d,
+                          long long cap, float* __restrict__ part_d,
                           int32_t* __restrict__ part_i) {
     __shared__ float md[8][R][32];
     __shared__ int mi[8][R][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long count = *(const volatile long long*)count_ptr;
     const long long nbatch = (count + R - 1) / R;
-    const int cs = blockIdx.y;
-    const int64_t q0 = (int64_t)cs * N / col_splits, q1 = (int64_t)(cs + 1) * N / col_splits;
-    for (long long b = blockIdx.x; b < nbatch; b += gridDim.x) {
+    const int col_splits = exact_splits(count, cap, k);
+    for (long long item = blockIdx.x; item < nbatch * col_splits; item += gridDim.x) {
+        const long long b = item / col_splits;
+        const int cs = (int)(item % col_splits);
+        const int64_t q0 = (int64_t)cs * N / col_splits, q1 = (int64_t)(cs + 1) * N / col_splits;
         int64_t prow[R];
         float xr[R][DPL];
         float ld[R], lastd[R];
@@ -1000,7 +1280,6 @@ knn_fallback_batch_kernel(const float* __restrict__ X, int64_t N, int D, int k,
         for (int r = warp; r < R; r += 8) {
             const long long f = b * R + r;
             if (f >= count) continue;
-            const int64_t p = fb_list[f];
             float ed[8];
             int ei[8];
 #pragma unroll
@@ -1021,8 +1300,8 @@ knn_fallback_batch_kernel(const float* __restrict__ X, int64_t N, int D, int k,
                 for (int m = 0; m < 8; ++m)
                     if (ei[m] == bi) { ed[m] = kInf; ei[m] = kNoIdx; }
                 if (lane == 0) {
-                    part_d[p * slot_stride + (int64_t)cs * k + c] = bd;
-                    part_i[p * slot_stride + (int64_t)cs * k + c] = bi;
+                    part_d[(f * col_splits + cs) * k + c] = bd;
+                    part_i[(f * col_splits + cs) * k + c] = bi;
                 }
             }
         }
@@ -1030,47 +1309,58 @@ knn_fallback_batch_kernel(const float* __restrict__ X, int64_t N, int D, int k,
     }
 }
 
-// Merge the col_splits partial lists of every failed row into its k nearest.
+// Merge the partial lists of every failed row (cs = exact_splits(F, cap, k)
+// of k entries at ((f cs) k)) into its k nearest: chunks of 7 entries per
+// lane beside the running k best (lane i holds entry i), k rounds of a warp
+// minimum per chunk.
 __global__ void __launch_bounds__(256)
 knn_fallback_merge_kernel(int k, const int32_t* __restrict__ fb_list, const long long* count_ptr,
-                          int col_splits, int64_t slot_stride, const float* __restrict__ part_d,
+                          long long cap, const float* __restrict__ part_d,
                           const int32_t* __restrict__ part_i, int32_t* __restrict__ col_idx,
                           float* __restrict__ dist2) {
     const int lane = threadIdx.x & 31;
     const long long count = *(const volatile long long*)count_ptr;
+    const int col_splits = exact_splits(count, cap, k);
+    const int total = col_splits * k;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t f = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); f < count;
          f += nw) {
         const int64_t p = fb_list[f];
-        float ed[8];
-        int ei[8];
+        const float* pd = part_d + f * total;
+        const int32_t* pi = part_i + f * total;
+        float bestd = kInf;   // lane i < k: the i-th best so far
+        int besti = kNoIdx;
+        for (int e0 = 0; e0 < total; e0 += 7 * 32) {
+            float ed[8];
+            int ei[8];
+            ed[7] = bestd;
+            ei[7] = besti;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const int e = lane + 32 * m;
-            ed[m] = kInf;
-            ei[m] = kNoIdx;
-            if (e < col_splits * k) {
-                ed[m] = part_d[p * slot_stride + e];
-                ei[m] = part_i[p * slot_stride + e];
+            for (int m = 0; m < 7; ++m) {
+                const int e = e0 + lane + 32 * m;
+                ed[m] = e < total ? pd[e] : kInf;
+                ei[m] = e < total ? pi[e] : kNoIdx;
+            }
+            for (int c = 0; c < k; ++c) {
+                float bd = kInf;
+                int bi = kNoIdx;
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    if (lex_less(ed[m], ei[m], bd, bi)) { bd = ed[m]; bi = ei[m]; }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (lex_less(od, oi, bd, bi)) { bd = od; bi = oi; }
+                }
+                // the winner is unique (distinct indices): remove it where it sits
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    if (ei[m] == bi && ed[m] == bd) { ed[m] = kInf; ei[m] = kNoIdx; }
+                if (lane == c) { bestd = bd; besti = bi; }
             }
         }
-        for (int c = 0; c < k; ++c) {
-            float bd = kInf;
-            int bi = kNoIdx;
-#pragma unroll
-            for (int m = 0; m < 8; ++m)
-                if (lex_less(ed[m], ei[m], bd, bi)) { bd = ed[m]; bi = ei[m]; }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float od = __shfl_xor_sync(0xffffffffu, bd, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (lex_less(od, oi, bd, bi)) { bd = od; bi = oi; }
-            }
-#pragma unroll
-            for (int m = 0; m < 8; ++m)
-                if (ei[m] == bi) { ed[m] = kInf; ei[m] = kNoIdx; }
-            if (lane == 0) { col_idx[p * k + c] = bi; dist2[p * k + c] = bd; }
-        }
+        if (lane < k) { col_idx[p * k + lane] = besti; dist2[p * k + lane] = bestd; }
     }
 }
 
@@ -1082,7 +1372,16 @@ struct KnnPlan {
     int ew;      // epilogue warps of the tensor-core kernel (lists per split: ew / 4)
     int lists;   // candidate lists per row: splits x lists per split
     bool bf16;
+    bool aug;    // tensor-core tiles with the norms folded into one more K slice
+    // two-term stage (bfloat16 only): row capacity (a multiple of 128),
+    // column splits and lists (of 32) per row
+    int64_t fcap;
+    int ssplits, slists;
 };
+
+// Rows the two-term tensor-core stage takes at most; the open rows beyond
+// it go to the float32 stage.
+constexpr int64_t kSplitRowCap = 65536;
 
 // Column splits for the persistent tensor-core kernel.  Every split restarts
 // the rows' candidate lists, so prefer few, long work items (row block x
@@ -1115,9 +1414,16 @@ KnnPlan make_plan(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
 #endif
     pl.kc = pl.bf16 ? ((k <= 6 || !SLK_TC_BF16_KC64) ? 32 : 64) : choose_kc(k);
     pl.ew = (pl.bf16 && k > 6 && pl.kc == 32) ? 8 : 4;
+    // where the tiles' epilogue outweighs their MMAs (small D), fold the
+    // norms into the MMAs: the epilogue then reads no norms and takes no
+    // barrier per tile
+#ifndef SLK_TC_AUG_MAX_DP
+#define SLK_TC_AUG_MAX_DP 0
+#endif
     // the tensor-core tiles read 256-row column tiles: keep them inside the matrix
     pl.Np = (int64_t)align_up((size_t)N, pl.bf16 ? 256 : 128);
     pl.Dp = (int)align_up((size_t)D, pl.bf16 ? 64 : BK);
+    pl.aug = pl.bf16 && pl.kc == 32 && pl.Dp <= SLK_TC_AUG_MAX_DP;
     pl.row_blocks = (int)(pl.Np / BM);
     pl.n_tiles = (int)(pl.Np / BN);
     const int max_splits = (32 * MAXE) / pl.kc;
@@ -1141,6 +1447,11 @@ KnnPlan make_plan(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
         pl.splits = tc_splits(pl.row_blocks, tiles_tc, ctx->num_sms > 0 ? ctx->num_sms : 148,
                               max_splits / per);
         pl.lists = pl.splits * per;
+        // the open rows are few: split the columns as far as the rerank's
+        // staging (32 MAXE entries per row) and 8 tiles per item allow
+        pl.fcap = std::min<int64_t>((int64_t)align_up((size_t)N, 128), kSplitRowCap);
+        pl.ssplits = std::max(1, std::min((32 * MAXE) / (32 * per), tiles_tc / 8));
+        pl.slists = pl.ssplits * per;
     }
     return pl;
 }
@@ -1157,12 +1468,21 @@ size_t knn_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int k, int precision) 
     b += align_up(sizeof(float) * pl.Np, 256) + align_up(sizeof(float) * D, 256);   // norms32, mu
     b += align_up(sizeof(int32_t) * N, 256);                                         // second list
     b += align_up(sizeof(int32_t) * (size_t)N, 256);
+    if (pl.aug) b += align_up(2 * 64 * (size_t)pl.Np, 256);   // folded-norm columns
+    if (pl.bf16) {
+        // two-term stage: xl, norms_s, rho_s, query rows (h, l, norms), lists, third list
+        b += align_up(2 * (size_t)pl.Np * pl.Dp, 256) + 2 * align_up(sizeof(float) * pl.Np, 256);
+        b += 2 * align_up(2 * (size_t)pl.fcap * pl.Dp, 256) + align_up(sizeof(float) * pl.fcap, 256);
+        b += 2 * align_up(sizeof(float) * (size_t)pl.slists * pl.fcap * 32, 256);
+        b += align_up(sizeof(int32_t) * (size_t)N, 256);
+    }
     return b + 4096;
 }
 
 slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const float* norms,
-                                int64_t N, int Dp, int64_t Np, int kc, int ew, int splits,
-                                float* cand_d, int32_t* cand_i, unsigned int* err_flag);
+                                const __nv_bfloat16* aug, int64_t N, int Dp, int64_t Np, int kc,
+                                int ew, int splits, float* cand_d, int32_t* cand_i,
+                                unsigned int* err_flag);
 
 namespace {
 
@@ -1170,7 +1490,7 @@ namespace {
 // loads where the row layout and the summation bound allow them.
 slk_status launch_prep(slk_ctx* ctx, const float* X, int64_t N, int D, int Dp, int64_t Np,
                        double* colsum, float* mu, float* xt32, __nv_bfloat16* xt16,
-                       float* norms, float* rho, float* norms32, DevState* st) {
+                       float* norms, float* rho, float* norms32, __nv_bfloat16* aug, DevState* st) {
     cudaStream_t s = ctx->stream;
     const bool v4 = D % 4 == 0 && Dp >= 128 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
                     (reinterpret_cast<uintptr_t>(mu) & 15) == 0;
@@ -1188,10 +1508,10 @@ slk_status launch_prep(slk_ctx* ctx, const float* X, int64_t N, int D, int Dp, i
     const int to_bf16 = xt16 != nullptr ? 1 : 0;
     if (v4)
         prep_rows_kernel<4><<<(unsigned)pg, 256, 0, s>>>(X, N, D, Dp, Np, mu, to_bf16, xt32, xt16,
-                                                         norms, rho, norms32, st);
+                                                         norms, rho, norms32, aug, st);
     else
         prep_rows_kernel<1><<<(unsigned)pg, 256, 0, s>>>(X, N, D, Dp, Np, mu, to_bf16, xt32, xt16,
-                                                         norms, rho, norms32, st);
+                                                         norms, rho, norms32, aug, st);
     SLK_LAUNCH_CHECK(ctx, "prep_rows_kernel");
     return SLK_OK;
 }
@@ -1205,13 +1525,14 @@ slk_status knn_prep_fp32_launch(slk_ctx* ctx, const float* X, int64_t N, int D, 
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(colsum, 0, sizeof(double) * D, s));
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_bits, 0, 2 * sizeof(unsigned int), s));
     SLK_COUNT_LAUNCH(ctx, 2);
-    return launch_prep(ctx, X, N, D, Dp, Np, colsum, mu, xt, nullptr, norms, rho, nullptr, st);
+    return launch_prep(ctx, X, N, D, Dp, Np, colsum, mu, xt, nullptr, norms, rho, nullptr, nullptr, st);
 }
 
 slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int k,
                             int precision, int64_t* row_ptr, int32_t* col_idx, float* dist2,
                             void* ws, DevState* st) {
     const KnnPlan pl = make_plan(ctx, N, D, k, precision);
+    ctx->knn_last_bf16 = pl.bf16;
     WsCarver wc(ws);
     double* colsum = wc.take<double>(D);
     void* xt = wc.take<unsigned char>((pl.bf16 ? 2 : 4) * (size_t)pl.Np * pl.Dp);
@@ -1223,6 +1544,19 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     float* norms32 = wc.take<float>(pl.Np);
     float* mu = wc.take<float>(D);
     int32_t* fb2 = wc.take<int32_t>(N);
+    // two-term stage
+    const size_t nd_s = pl.bf16 ? (size_t)pl.Np * pl.Dp : 0, np_s = pl.bf16 ? (size_t)pl.Np : 0;
+    const size_t fd_s = pl.bf16 ? (size_t)pl.fcap * pl.Dp : 0, f_s = pl.bf16 ? (size_t)pl.fcap : 0;
+    __nv_bfloat16* xl16 = wc.take<__nv_bfloat16>(nd_s);
+    float* norms_s = wc.take<float>(np_s);
+    float* rho_s = wc.take<float>(np_s);
+    __nv_bfloat16* qh = wc.take<__nv_bfloat16>(fd_s);
+    __nv_bfloat16* ql = wc.take<__nv_bfloat16>(fd_s);
+    float* qnorm = wc.take<float>(f_s);
+    float* scand_d = wc.take<float>(pl.bf16 ? (size_t)pl.slists * pl.fcap * 32 : 0);
+    int32_t* scand_i = wc.take<int32_t>(pl.bf16 ? (size_t)pl.slists * pl.fcap * 32 : 0);
+    int32_t* fb3 = wc.take<int32_t>(pl.bf16 ? (size_t)N : 0);
+    __nv_bfloat16* aug = wc.take<__nv_bfloat16>(pl.aug ? 64 * (size_t)pl.Np : 0);
     cudaStream_t s = ctx->stream;
 
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(colsum, 0, sizeof(double) * D, s));
@@ -1230,22 +1564,25 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_bits, 0, 3 * sizeof(unsigned int), s));
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm32_bits, 0, sizeof(unsigned int), s));
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->fallback2_count, 0, sizeof(long long), s));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_s_bits, 0, 4 * sizeof(unsigned int), s));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->fallback3_count, 0, sizeof(long long), s));
     {
         PhaseScope ps(ctx, SLK_PHASE_KNN_PREP);
         SLK_COUNT_LAUNCH(ctx, 3);
         const slk_status r = launch_prep(ctx, X, N, D, pl.Dp, pl.Np, colsum, mu,
                                          pl.bf16 ? nullptr : (float*)xt,
                                          pl.bf16 ? (__nv_bfloat16*)xt : nullptr, norms, rho,
-                                         pl.bf16 ? norms32 : nullptr, st);
+                                         pl.bf16 ? norms32 : nullptr, pl.aug ? aug : nullptr, st);
         if (r != SLK_OK) return r;
     }
-    float u_acc;
+    float u_acc;   // rounding unit of a tile's dot-product accumulation
     {
     PhaseScope ps(ctx, SLK_PHASE_KNN_CAND);
     SLK_COUNT_LAUNCH(ctx, 1);
     if (pl.bf16) {
-        slk_status r = knn_cand_bf16_launch(ctx, (const __nv_bfloat16*)xt, norms, N, pl.Dp, pl.Np,
-                                            pl.kc, pl.ew, pl.splits, cand_d, cand_i, &st->knn_error);
+        slk_status r = knn_cand_bf16_launch(ctx, (const __nv_bfloat16*)xt, norms,
+                                            pl.aug ? aug : nullptr, N, pl.Dp, pl.Np, pl.kc, pl.ew,
+                                            pl.splits, cand_d, cand_i, &st->knn_error);
         if (r != SLK_OK) return r;
         // 2^-23: products exact, each accumulator add off by at most one ulp
         // (truncating adds); an assumption about the tensor-core accumulator
@@ -1272,15 +1609,20 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
         if (grid > (int64_t)ctx->num_sms * 16) grid = (int64_t)ctx->num_sms * 16;
         // entries per lane: the splits' lists, KC each, over 32 lanes
         const int per_lane = (pl.lists * pl.kc + 31) / 32;
+        // folded norms: 6 more products a dot, and the aug terms' magnitudes
+        // (about (n_p + n_q) / 2) join the products' sum: 2 |p| |q| + n_p +
+        // n_q = (|p| + |q|)^2, so the bound keeps its form with a 1.01 factor
+        const double g = (double)(pl.Dp + (pl.aug ? 6 : 0)) * (double)u_acc;
+        const double gam = (pl.aug ? 1.01 : 1.0) * g / (1.0 - g);
 #define SLK_RERANK(KC_, E_)                                                                   \
     do {                                                                                      \
         if (pl.kc == 32 && pl.ew == 8)                                                        \
-            knn_rerank_kernel<32, false, E_, 64><<<(unsigned)grid, 256, 0, s>>>(              \
-                X, N, D, pl.Dp, k, pl.lists, pl.Np, cand_d, cand_i, norms, rho, u_acc, row_ptr, \
+            knn_rerank_kernel<32, 0, E_, 64><<<(unsigned)grid, 256, 0, s>>>(                  \
+                X, N, D, pl.Dp, k, pl.lists, pl.Np, cand_d, cand_i, norms, rho, gam, row_ptr,   \
                 col_idx, dist2, fb, st);                                                      \
         else                                                                                  \
-            knn_rerank_kernel<KC_, false, E_><<<(unsigned)grid, 256, 0, s>>>(                 \
-                X, N, D, pl.Dp, k, pl.lists, pl.Np, cand_d, cand_i, norms, rho, u_acc, row_ptr, \
+            knn_rerank_kernel<KC_, 0, E_><<<(unsigned)grid, 256, 0, s>>>(                     \
+                X, N, D, pl.Dp, k, pl.lists, pl.Np, cand_d, cand_i, norms, rho, gam, row_ptr,   \
                 col_idx, dist2, fb, st);                                                      \
     } while (0)
 #define SLK_RERANK_E(KC_)                                                                     \
@@ -1301,13 +1643,64 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
         const int32_t* exact_list = fb;
         const long long* exact_count = &st->fallback_count;
         if (pl.bf16) {
-            // float32 distance tiles of the open rows against every point, then
-            // the rerank under the float32 certificate; its failures go on
-            // float32 lists of at least 2k candidates (the gap between the k-th and the
-            // last decides the certificate)
+            // (a) two-term bfloat16 tiles of the open rows on the tensor cores
+            // (h . h + h . l + l . h of s = h + l, about 16 significant bits
+            // of v), the rerank under their certificate; its failures, and
+            // open rows beyond the stage's capacity, go on to (b)
+            const bool v4 = D % 4 == 0 && pl.Dp >= 128 && (reinterpret_cast<uintptr_t>(X) & 15) == 0 &&
+                            (reinterpret_cast<uintptr_t>(mu) & 15) == 0;
+            int64_t pg = (pl.Np + 7) / 8;
+            if (pg > (int64_t)ctx->num_sms * 64) pg = (int64_t)ctx->num_sms * 64;
+            SLK_COUNT_LAUNCH(ctx, 4);
+            if (v4)
+                prep_split_kernel<4><<<(unsigned)pg, 256, 0, s>>>(X, N, D, pl.Dp, pl.Np, mu,
+                                                                  &st->fallback_count, xl16, norms_s,
+                                                                  rho_s, st);
+            else
+                prep_split_kernel<1><<<(unsigned)pg, 256, 0, s>>>(X, N, D, pl.Dp, pl.Np, mu,
+                                                                  &st->fallback_count, xl16, norms_s,
+                                                                  rho_s, st);
+            SLK_LAUNCH_CHECK(ctx, "prep_split_kernel");
+            int64_t gg = (pl.fcap + 7) / 8;
+            if (gg > (int64_t)ctx->num_sms * 16) gg = (int64_t)ctx->num_sms * 16;
+            gather_split_kernel<<<(unsigned)gg, 256, 0, s>>>((const __nv_bfloat16*)xt, xl16, norms_s,
+                                                            pl.Dp, fb, &st->fallback_count, pl.fcap,
+                                                            qh, ql, qnorm);
+            SLK_LAUNCH_CHECK(ctx, "gather_split_kernel");
+            slk_status r = knn_cand_split_launch(ctx, qh, ql, qnorm, pl.fcap, &st->fallback_count,
+                                                 (const __nv_bfloat16*)xt, xl16, norms_s, N, pl.Dp,
+                                                 pl.Np, pl.ew, pl.ssplits, scand_d, scand_i,
+                                                 &st->knn_error);
+            if (r != SLK_OK) return r;
+            {
+                // dot products of 3 Dp bfloat16 products (2^-23 accumulator
+                // unit, as above), |h|, |l| within 1.004 |s| and 0.0040 |s|,
+                // plus the dropped l . l term (at most 1.016 2^-16 |s_p| |s_q|)
+                const double g3 = 3.0 * (double)pl.Dp * 1.1920928955078125e-07;
+                const double gam_s = 1.02 * g3 / (1.0 - g3) + 1.02 * 1.52587890625e-05;
+                const unsigned rgrid = (unsigned)(ctx->num_sms * 4);
+                const int per_lane = (pl.slists * 32 + 31) / 32;
+#define SLK_RERANK_S(E_, SEL_)                                                                \
+    knn_rerank_kernel<32, 2, E_, SEL_><<<rgrid, 256, 0, s>>>(                                 \
+        X, N, D, pl.Dp, k, pl.slists, pl.fcap, scand_d, scand_i, norms_s, rho_s, gam_s, row_ptr, \
+        col_idx, dist2, fb2, st, fb, &st->fallback_count, &st->fallback2_count)
+                if (pl.ew == 8) {
+                    if (per_lane <= 8) SLK_RERANK_S(8, 64);
+                    else SLK_RERANK_S(16, 64);
+                } else {
+                    if (per_lane <= 8) SLK_RERANK_S(8, 32);
+                    else SLK_RERANK_S(16, 32);
+                }
+#undef SLK_RERANK_S
+                SLK_LAUNCH_CHECK(ctx, "knn_rerank_kernel (two-term stage)");
+            }
+            // (b) float32 distance tiles of the rows still open against every
+            // point, then the rerank under the float32 certificate; its
+            // failures go on float32 lists of at least 2k candidates (the gap
+            // between the k-th and the last decides the certificate)
             const int kcq = (2 * k <= 16) ? 16 : 32;
-            int qsplits = (int)std::min<int64_t>(8, (int64_t)pl.lists * pl.kc / kcq);
-            if (qsplits < 1) qsplits = 1;
+            // column splits chosen on the device from the count (query_splits)
+            const long long qcap = (long long)pl.lists * pl.Np * pl.kc;
             const int n_tiles = (int)((N + BN - 1) / BN);
             SLK_COUNT_LAUNCH(ctx, 2);
             const unsigned qgrid = (unsigned)(ctx->num_sms * 2);
@@ -1316,40 +1709,38 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
         auto kern = knn_cand_query_kernel<KC_>;                                               \
         const int smem = (int)sizeof(CandSmem<KC_>);                                          \
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
-        kern<<<qgrid, KT, smem, s>>>(X, N, D, pl.Dp, mu, norms32, fb, &st->fallback_count,    \
-                                     qsplits, n_tiles, cand_d, cand_i);                       \
+        kern<<<qgrid, KT, smem, s>>>(X, N, D, pl.Dp, mu, norms32, fb2, &st->fallback2_count,  \
+                                     qcap, n_tiles, cand_d, cand_i);                          \
     }
             if (kcq == 16) SLK_QCAND(16) else SLK_QCAND(32)
 #undef SLK_QCAND
             SLK_LAUNCH_CHECK(ctx, "knn_cand_query_kernel");
             const unsigned rgrid = (unsigned)(ctx->num_sms * 4);   // grid-stride over the open rows
-            const float u32 = 5.9604644775390625e-08f;
+            const double g32 = (double)pl.Dp * 5.9604644775390625e-08;
+            const double gam32 = g32 / (1.0 - g32);
             if (kcq == 16)
-                knn_rerank_kernel<16, true><<<rgrid, 256, 0, s>>>(
-                    X, N, D, pl.Dp, k, qsplits, N, cand_d, cand_i, norms32, nullptr, u32, row_ptr,
-                    col_idx, dist2, fb2, st, fb, &st->fallback_count, &st->fallback2_count);
+                knn_rerank_kernel<16, 1><<<rgrid, 256, 0, s>>>(
+                    X, N, D, pl.Dp, k, 0, qcap, cand_d, cand_i, norms32, nullptr, gam32, row_ptr,
+                    col_idx, dist2, fb3, st, fb2, &st->fallback2_count, &st->fallback3_count);
             else
-                knn_rerank_kernel<32, true><<<rgrid, 256, 0, s>>>(
-                    X, N, D, pl.Dp, k, qsplits, N, cand_d, cand_i, norms32, nullptr, u32, row_ptr,
-                    col_idx, dist2, fb2, st, fb, &st->fallback_count, &st->fallback2_count);
+                knn_rerank_kernel<32, 1><<<rgrid, 256, 0, s>>>(
+                    X, N, D, pl.Dp, k, 0, qcap, cand_d, cand_i, norms32, nullptr, gam32, row_ptr,
+                    col_idx, dist2, fb3, st, fb2, &st->fallback2_count, &st->fallback3_count);
             SLK_LAUNCH_CHECK(ctx, "knn_rerank_kernel (float32 stage)");
-            exact_list = fb2;
-            exact_count = &st->fallback2_count;
+            exact_list = fb3;
+            exact_count = &st->fallback3_count;
         }
-        // partial lists of the batched rescan reuse the row's candidate
-        // scratch: lists * KC slots per row, of which col_splits * k are used
-        const int64_t slot_stride = (int64_t)pl.lists * pl.kc;
-        int cs = (int)(slot_stride / k);
-        if (cs > 8) cs = 8;
+        // the batched rescan's partial lists reuse the candidate buffer
+        // (its lists are read by now): cs column ranges of k entries for each
+        // of the F open rows, cs chosen on the device from F
+        const long long cap = (long long)pl.lists * pl.Np * pl.kc;
         const int dpl = (D + 31) / 32;
-        if (cs >= 1 && dpl <= 32) {
+        if (dpl <= 32) {
             SLK_COUNT_LAUNCH(ctx, 2);
-            // the rescan scratch is laid out per row (slot_stride entries), so
-            // it may reuse cand_d / cand_i once the rerank is done with them
-            dim3 grid((unsigned)((ctx->num_sms * 2 + cs - 1) / cs), (unsigned)cs);
+            const unsigned grid = (unsigned)(ctx->num_sms * 2);
 #define SLK_FB(R_, DPL_)                                                                     \
     knn_fallback_batch_kernel<R_, DPL_><<<grid, 256, 0, s>>>(X, N, D, k, exact_list, exact_count, \
-                                                             cs, slot_stride, cand_d, cand_i)
+                                                             cap, cand_d, cand_i)
             if (dpl <= 4) SLK_FB(16, 4);
             else if (dpl <= 8) SLK_FB(8, 8);
             else if (dpl <= 16) SLK_FB(4, 16);
@@ -1357,7 +1748,7 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
 #undef SLK_FB
             SLK_LAUNCH_CHECK(ctx, "knn_fallback_batch_kernel");
             knn_fallback_merge_kernel<<<(unsigned)(ctx->num_sms * 2), 256, 0, s>>>(
-                k, exact_list, exact_count, cs, slot_stride, cand_d, cand_i, col_idx, dist2);
+                k, exact_list, exact_count, cap, cand_d, cand_i, col_idx, dist2);
             SLK_LAUNCH_CHECK(ctx, "knn_fallback_merge_kernel");
         } else {
         SLK_COUNT_LAUNCH(ctx, 1);

@@ -216,6 +216,16 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     d |= (uint64_t)(TC_ROWB == 128 ? 2 : 4) << 61;   // 128- or 64-byte swizzle
     return d;
 }
+// The same for 64-byte swizzle rows (32 bf16): 8-row atoms 512 bytes apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((8 * 64) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;   // 64-byte swizzle
+    return d;
+}
 // Instruction descriptor: D fp32, A/B bf16, both K-major, N = 256, M = 128.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                             ((uint32_t)(TC_M >> 4) << 24);
@@ -435,12 +445,29 @@ __device__ __forceinline__ void item_range(int item, int splits, int n_tiles, in
 // PAIR: launched in clusters of two; an item's row block is a pair of
 // 128-row blocks (rank r of the cluster takes block 2 rb + r), both CTAs walk
 // the same items, and only the leader's MMA warp issues.
-template <int TC_KC, int EW, bool PIPE, bool NOBAR, bool PAIR = false>
+// AUG: one more K slice of 32 columns (64-byte swizzle) from the aug matrix
+// (tmA2 reads its columns 0..31 for the A rows, tmB2 its columns 32..63 for
+// the B rows): [1, 1, 1, a_p] against [a_q, 1, 1, 1], a the three bfloat16
+// terms of -||xt||^2 / 2, so that the accumulator holds -dt / 2 and the
+// epilogue needs no norms (padding rows and columns carry -inf there).
+// SPLIT: the two-term operands s = h + l of listed query rows against every
+// point.  The accumulator sums three passes over the K slices, h_p . h_q
+// (tmA, tmB), h_p . l_q (tmA, tmB2) and l_p . h_q (tmA2, tmB); the rows are
+// the first min(*rows_dev, 128 row_blocks) query rows, their norms in
+// row_norms (+inf for padding rows); lists go to ((list Np + f) KC), Np
+// being the list stride.  Otherwise tmA2 / tmB2 / row_norms / rows_dev are
+// unused and the rows are the points themselves.
+template <int TC_KC, int EW, bool PIPE, bool NOBAR, bool PAIR = false, bool SPLIT = false,
+          bool AUG = false>
 __global__ void __launch_bounds__(TcEpi<EW, PAIR, TC_KC>::threads, 1)
 knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const float* __restrict__ norms, int64_t N, int64_t Np, int Dp, int n_tiles,
-                   int splits, int row_blocks, float* __restrict__ cand_d,
+                   const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
+                   const float* __restrict__ norms, const float* __restrict__ row_norms,
+                   const long long* __restrict__ rows_dev, int64_t N, int64_t Np, int Dp,
+                   int n_tiles, int splits, int row_blocks, float* __restrict__ cand_d,
                    int32_t* __restrict__ cand_i, unsigned int* __restrict__ err_flag) {
+    static_assert(!(SPLIT && PAIR), "split query rows run on single CTAs");
+    static_assert(!(AUG && (PAIR || SPLIT)), "the folded norms are for single-CTA point tiles");
     using E = TcEpi<EW, PAIR, TC_KC>;
     constexpr int STAGES = E::stages;
     constexpr int H = E::halves, VOTE = E::vote, APP = E::app, NT = 32 * EW;
@@ -450,7 +477,16 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     TcSmem<EW, PAIR, TC_KC>& s = *reinterpret_cast<TcSmem<EW, PAIR, TC_KC>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nkb = Dp / TC_BK;
+    const int nkb0 = Dp / TC_BK;                   // K slices of one operand pass
+    const int nkb = SPLIT ? 3 * nkb0 : (AUG ? nkb0 + 1 : nkb0);   // K slices per tile
+    if constexpr (SPLIT) {
+        // query rows counted on the device (every thread reads the same value)
+        long long rows = *rows_dev;
+        const long long cap = (long long)row_blocks * TC_M;
+        if (rows > cap) rows = cap;
+        if (rows < 0) rows = 0;
+        row_blocks = (int)((rows + TC_M - 1) / TC_M);
+    }
     const uint32_t rank = PAIR ? cluster_rank() : 0u;
     const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;      // CTA or cluster
     const int n_units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
@@ -499,6 +535,10 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+            if constexpr (SPLIT) {
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA2)) : "memory");
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB2)) : "memory");
+            }
             uint32_t iter = 0;
             bool ok = true;
             for (int item = item_begin; item < item_end && ok; ++item) {
@@ -518,9 +558,29 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                             tma_load_2d_pair(s.a[st], &tmA, bar, kb * TC_BK, arow);
                             tma_load_2d_pair(s.b[st], &tmB, bar, kb * TC_BK, bcol);
                         } else {
+                            const CUtensorMap* ma = &tmA;
+                            const CUtensorMap* mb = &tmB;
+                            int kx = kb;
+                            if constexpr (AUG) {
+                                if (kb == nkb0) {
+                                    // the folded norms: 32 columns of A (x = 0) and B (x = 32)
+                                    mbar_expect_tx(&s.full[st], (A_BYTES + B_BYTES) / 2);
+                                    tma_load_2d(s.a[st], &tmA2, &s.full[st], 0, arow);
+                                    tma_load_2d(s.b[st], &tmB2, &s.full[st], 32, bcol);
+                                    ++iter;
+                                    continue;
+                                }
+                            }
+                            if constexpr (SPLIT) {
+                                // passes h . h, h . l, l . h
+                                const int part = kb / nkb0;
+                                kx = kb - part * nkb0;
+                                if (part == 2) ma = &tmA2;
+                                if (part == 1) mb = &tmB2;
+                            }
                             mbar_expect_tx(&s.full[st], A_BYTES + B_BYTES);
-                            tma_load_2d(s.a[st], &tmA, &s.full[st], kb * TC_BK, arow);
-                            tma_load_2d(s.b[st], &tmB, &s.full[st], kb * TC_BK, bcol);
+                            tma_load_2d(s.a[st], ma, &s.full[st], kx * TC_BK, arow);
+                            tma_load_2d(s.b[st], mb, &s.full[st], kx * TC_BK, bcol);
                         }
                         ++iter;
                     }
@@ -563,6 +623,16 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         const uint32_t st = iter % STAGES;
                         if (!(ok = mbar_wait(&s.full[st], (iter / STAGES) & 1, abort))) break;
                         tc_fence_after();
+                        if (AUG && kb == nkb0) {
+                            // folded norms: two K = 16 steps in 64-byte swizzle rows
+                            const uint64_t da = sw64_desc(su32(s.a[st]));
+                            const uint64_t db = sw64_desc(su32(s.b[st]));
+                            umma(d_tmem, da, db, 1u);
+                            umma(d_tmem, da + 2u, db + 2u, 1u);
+                            umma_commit(&s.empty[st]);
+                            ++iter;
+                            continue;
+                        }
                         const uint64_t da = sw128_desc(su32(s.a[st]));
                         const uint64_t db = sw128_desc(su32(s.b[st]));
 #pragma unroll
@@ -631,7 +701,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 }
             }
             // padding rows / columns get an infinite norm: their distances never pass
-            const float np_ = (p < N) ? norms[p] : __int_as_float(0x7f800000);
+            const float np_ = SPLIT ? row_norms[p] : ((p < N) ? norms[p] : __int_as_float(0x7f800000));
             for (int t = t0; t < t1; ++t) {
                 const uint32_t acc = tcount & 1, use = tcount >> 1;
                 const int64_t col0 = (int64_t)t * TC_N;
@@ -639,7 +709,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 // addresses, L1 hits after the first warp; padding rows hold an
                 // infinite norm), each warp waits for the accumulator on its own
                 const float* ncol_g = norms + col0;
-                if constexpr (NOBAR) {
+                if constexpr (NOBAR || AUG) {
                     ok = mbar_wait(&s.tfull[acc], use & 1, abort);
                     if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
                 } else {
@@ -655,8 +725,11 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 // columns against the row's threshold (the row's own column,
                 // distance ~0, is kept here and dropped by the rerank)
                 auto process = [&](const uint32_t (&rv)[C], int ch) {
-                    float v[C];   // w = fl(||xt_q||^2 - 2 dot)
-                    if constexpr (NOBAR) {
+                    float v[C];   // w = fl(||xt_q||^2 - 2 dot); AUG: dt / 2
+                    if constexpr (AUG) {
+#pragma unroll
+                        for (int j = 0; j < C; ++j) v[j] = -__uint_as_float(rv[j]);
+                    } else if constexpr (NOBAR) {
                         const float4* n4 = reinterpret_cast<const float4*>(ncol_g + ch * C);
 #pragma unroll
                         for (int q = 0; q < C / 4; ++q) {
@@ -674,8 +747,10 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll
                     for (int g0 = 0; g0 < C; g0 += VOTE) {
                         // w < thr - ||xt_p||^2 (rounded up) whenever dt < thr; a
-                        // padding row (infinite norm) gets NaN and never passes
-                        const float thr_w = __fsub_ru(ld[TC_KC - 1], np_);
+                        // padding row (infinite norm) gets NaN and never passes.
+                        // AUG: dt / 2 < thr / 2 (both exact), padding rows and
+                        // columns give +inf
+                        const float thr_w = AUG ? 0.5f * ld[TC_KC - 1] : __fsub_ru(ld[TC_KC - 1], np_);
                         float m8[VOTE / 8];
 #pragma unroll
                         for (int q = 0; q < VOTE / 8; ++q) {
@@ -703,7 +778,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll
                                     for (int j = g0 + 8 * q; j < g0 + 8 * q + 8; ++j) {
                                         if (v[j] < thr_w) {
-                                            s.buf_d[h][cnt][r] = __fadd_rn(v[j], np_);
+                                            s.buf_d[h][cnt][r] = AUG ? 2.f * v[j] : __fadd_rn(v[j], np_);
                                             s.buf_i[h][cnt][r] = (int)(col0 + ch * C + j);
                                             ++cnt;
                                         }
@@ -835,8 +910,9 @@ int knn_tc_lists_per_split(int kc, int ew) {
 }
 
 slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const float* norms,
-                                int64_t N, int Dp, int64_t Np, int kc, int ew, int splits,
-                                float* cand_d, int32_t* cand_i, unsigned int* err_flag) {
+                                const __nv_bfloat16* aug, int64_t N, int Dp, int64_t Np, int kc,
+                                int ew, int splits, float* cand_d, int32_t* cand_i,
+                                unsigned int* err_flag) {
     if (kc != 32 && kc != 64) return set_err(ctx, SLK_ERR_INVALID_ARG, "bf16 candidates need KC=32 or 64");
     if (ew != 4 && ew != 8) return set_err(ctx, SLK_ERR_INVALID_ARG, "4 or 8 epilogue warps");
     if (Dp % TC_BK != 0 || Np % TC_M != 0)
@@ -859,6 +935,25 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
         return set_err(ctx, SLK_ERR_CUDA, "tensor map encoding failed (%d, %d)", (int)r1, (int)r2);
+    // folded norms: the aug matrix (Np x 64 bf16), 32-column boxes in 64-byte swizzle
+    CUtensorMap ta2 = ta, tb2a = tb;
+    const bool use_aug = aug != nullptr && kc == 32 && !(SLK_TC_PAIR != 0 && (Np / TC_M) % 2 == 0);
+    if (use_aug) {
+        if ((reinterpret_cast<uintptr_t>(aug) & 15) != 0)
+            return set_err(ctx, SLK_ERR_INVALID_ARG, "aug operand not 16-byte aligned");
+        const cuuint64_t adims[2] = {64, (cuuint64_t)Np};
+        const cuuint64_t astr[1] = {128};
+        const cuuint32_t abox_a[2] = {32, TC_M};
+        const cuuint32_t abox_b[2] = {32, TC_N};
+        CUresult r3 = enc(&ta2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)aug, adims, astr, abox_a,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r4 = enc(&tb2a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)aug, adims, astr, abox_b,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r3 != CUDA_SUCCESS || r4 != CUDA_SUCCESS)
+            return set_err(ctx, SLK_ERR_CUDA, "tensor map encoding failed (%d, %d)", (int)r3, (int)r4);
+    }
     const int row_blocks = (int)(Np / TC_M);
     const int n_tiles = (int)((Np + TC_N - 1) / TC_N);
     const int n_items = row_blocks * splits;
@@ -893,15 +988,33 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        SLK_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, ta, tb2, norms, N, Np, Dp, n_tiles, splits,
+        SLK_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, ta, tb2, ta, tb2, norms, norms,
+                                             (const long long*)nullptr, N, Np, Dp, n_tiles, splits,
                                              row_blocks, cand_d, cand_i, err_flag));
+    } else if (use_aug && ew == 4) {
+        auto kern = knn_cand_tc_kernel<32, 4, false, false, false, false, true>;
+        const size_t smem = tc_smem_bytes<4>();
+        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        kern<<<grid, TcEpi<4>::threads, smem, ctx->stream>>>(
+            ta, tb, ta2, tb2a, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks, cand_d,
+            cand_i, err_flag);
+    } else if (use_aug) {
+        auto kern = knn_cand_tc_kernel<32, 8, false, false, false, false, true>;
+        const size_t smem = tc_smem_bytes<8>();
+        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        kern<<<grid, TcEpi<8>::threads, smem, ctx->stream>>>(
+            ta, tb, ta2, tb2a, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks, cand_d,
+            cand_i, err_flag);
     } else if (kc == 32 && ew == 4) {
         auto kern = knn_cand_tc_kernel<32, 4, SLK_TC_PIPE != 0, SLK_TC_NOBAR != 0>;
         const size_t smem = tc_smem_bytes<4>();
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem));
         kern<<<grid, TcEpi<4>::threads, smem, ctx->stream>>>(
-            ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
+            ta, tb, ta, tb, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks, cand_d,
+            cand_i, err_flag);
     } else if (kc == 32) {
         // 8 epilogue warps: the column norms staged in shared memory (measured
         // faster here than per-warp global loads: 426 against 469 ms at 1e6 x 128)
@@ -910,7 +1023,8 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem));
         kern<<<grid, TcEpi<8>::threads, smem, ctx->stream>>>(
-            ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
+            ta, tb, ta, tb, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks, cand_d,
+            cand_i, err_flag);
     } else {
         constexpr int EW = SLK_TC_EW64;
         auto kern = knn_cand_tc_kernel<64, EW, false, SLK_TC_NOBAR64 != 0>;
@@ -918,8 +1032,68 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem));
         kern<<<grid, TcEpi<EW, false, 64>::threads, smem, ctx->stream>>>(
-            ta, tb, norms, N, Np, Dp, n_tiles, splits, row_blocks, cand_d, cand_i, err_flag);
+            ta, tb, ta, tb, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks, cand_d,
+            cand_i, err_flag);
     }
     SLK_LAUNCH_CHECK(ctx, "knn_cand_tc_kernel");
+    return SLK_OK;
+}
+
+// Two-term bfloat16 tiles of listed query rows (see the SPLIT form of the
+// kernel): A operands qh / ql (Fcap rows, Fcap a multiple of 128), B operands
+// xh / xl (Np rows, a multiple of 256), both Dp columns; the number of
+// query rows is read on the device from *rows_dev (at most Fcap are taken),
+// so the launch does not wait for the stage before it.  Lists of KC = 32,
+// ew / 4 per split, at ((list Fcap + f) 32).
+slk_status knn_cand_split_launch(slk_ctx* ctx, const __nv_bfloat16* qh, const __nv_bfloat16* ql,
+                                 const float* qnorm, int64_t Fcap, const long long* rows_dev,
+                                 const __nv_bfloat16* xh, const __nv_bfloat16* xl,
+                                 const float* norms, int64_t N, int Dp, int64_t Np, int ew,
+                                 int splits, float* cand_d, int32_t* cand_i,
+                                 unsigned int* err_flag) {
+    if (ew != 4 && ew != 8) return set_err(ctx, SLK_ERR_INVALID_ARG, "4 or 8 epilogue warps");
+    if (Dp % TC_BK != 0 || Np % TC_N != 0 || Fcap % TC_M != 0 || Fcap <= 0)
+        return set_err(ctx, SLK_ERR_INVALID_ARG, "bad padded shape %lld / %lld x %d", (long long)Fcap,
+                       (long long)Np, Dp);
+    const void* ptrs[4] = {qh, ql, xh, xl};
+    for (const void* q : ptrs)
+        if ((reinterpret_cast<uintptr_t>(q) & 15) != 0)
+            return set_err(ctx, SLK_ERR_INVALID_ARG, "bf16 operand not 16-byte aligned");
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return set_err(ctx, SLK_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    CUtensorMap maps[4];
+    const cuuint64_t strides[1] = {(cuuint64_t)Dp * 2};
+    const cuuint32_t estr[2] = {1, 1};
+    for (int m = 0; m < 4; ++m) {
+        const bool a = m < 2;
+        const cuuint64_t dims[2] = {(cuuint64_t)Dp, (cuuint64_t)(a ? Fcap : Np)};
+        const cuuint32_t box[2] = {TC_BK, (cuuint32_t)(a ? TC_M : TC_N)};
+        const CUresult r = enc(&maps[m], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptrs[m]),
+                               dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, kTcSwizzle,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return set_err(ctx, SLK_ERR_CUDA, "tensor map encoding failed (%d)", (int)r);
+    }
+    const int row_cap_blocks = (int)(Fcap / TC_M);
+    const int n_tiles = (int)(Np / TC_N);
+    const int grid = ctx->num_sms > 0 ? ctx->num_sms : 148;   // persistent: items are counted on the device
+    if (ew == 4) {
+        auto kern = knn_cand_tc_kernel<32, 4, SLK_TC_PIPE != 0, SLK_TC_NOBAR != 0, false, true>;
+        const size_t smem = tc_smem_bytes<4>();
+        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        kern<<<grid, TcEpi<4>::threads, smem, ctx->stream>>>(
+            maps[0], maps[2], maps[1], maps[3], norms, qnorm, rows_dev, N, Fcap, Dp, n_tiles, splits,
+            row_cap_blocks, cand_d, cand_i, err_flag);
+    } else {
+        auto kern = knn_cand_tc_kernel<32, 8, SLK_TC_PIPE8 != 0, SLK_TC_NOBAR8 != 0, false, true>;
+        const size_t smem = tc_smem_bytes<8>();
+        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        kern<<<grid, TcEpi<8>::threads, smem, ctx->stream>>>(
+            maps[0], maps[2], maps[1], maps[3], norms, qnorm, rows_dev, N, Fcap, Dp, n_tiles, splits,
+            row_cap_blocks, cand_d, cand_i, err_flag);
+    }
+    SLK_LAUNCH_CHECK(ctx, "knn_cand_tc_kernel (split query rows)");
     return SLK_OK;
 }

@@ -843,6 +843,8 @@ extern "C" slk_status slk_server_step(slk_server* sv, int32_t* n_running, int32_
             r.stats.sigma = sv->h_sigma[slot];
             r.stats.energy = sv->h_energy[slot];
             r.stats.knn_fallback_rows = -1;
+            r.stats.knn_float32_rows = -1;
+            r.stats.knn_exact_rows = -1;
             r.state = 3;
             arena_free(sv, r.mem);
             r.mem = {0, 0};

@@ -35,6 +35,8 @@ struct slk_ctx {
     long long prof_calls[SLK_PHASE_COUNT] = {};
     // candidates recomputed exactly by the last starting-mode call
     long long init_candidates = 0;
+    // the last kNN graph used bfloat16 candidates (its stage counters mean so)
+    bool knn_last_bf16 = false;
     // auxiliary streams (batched graph building), created on first use
     std::vector<cudaStream_t> aux;
     std::vector<cudaEvent_t> aux_ev;
@@ -76,7 +78,7 @@ struct DevState {
     unsigned int knn_max_rho_bits;    // float bits of max rounding perturbation norm
     unsigned int knn_error;           // bit 1: a tensor-core pipeline wait timed out
     unsigned int knn_max_norm32_bits; // float bits of max float32-operand norm^2
-    long long fallback2_count;        // rows left for the exact scan after the float32 stage
+    long long fallback2_count;        // rows left for the float32 stage after the two-term stage
     // one-launch median: grid barrier words, count of values <= the lower
     // middle order statistic, smallest value above it (bits)
     unsigned int sel_bar[4];
@@ -84,6 +86,11 @@ struct DevState {
     unsigned int sel_min_bits;
     unsigned int sym_error;           // bit 0: a row of the graph to symmetrise is too long
     unsigned int deg_mixed;           // 1: the rows of a CSR graph do not all have one degree
+    unsigned int knn_max_norm_s_bits; // float bits of max two-term bfloat16 operand norm^2
+    unsigned int knn_max_rho_s_bits;  // float bits of max two-term rounding perturbation norm
+    unsigned int knn_max_kappa_bits;  // float bits of max rho_p / ||v_p|| (candidate operand)
+    unsigned int knn_max_kappa_s_bits;// float bits of max rho_s_p / ||v_p|| (two-term operand)
+    long long fallback3_count;        // rows left for the exact scan after the float32 stage
 };
 
 enum : unsigned int { ERR_BARRIER_TIMEOUT = 1u };

@@ -33,7 +33,7 @@ EXPORTS = ["slk_version", "slk_create", "slk_destroy", "slk_set_stream", "slk_la
            "slk_server_destroy", "slk_server_submit", "slk_server_step", "slk_server_poll",
            "slk_server_request_bytes", "slk_unary_vec", "slk_mean_shift", "slk_energy_vec",
            "slk_solve_ms", "slk_initial_modes", "slk_barrier_selftest", "slk_kmeanspp",
-           "slk_symmetrize"]
+           "slk_symmetrize", "slk_knn_stage_rows"]
 PHASES = ["knn_prep", "knn_cand", "knn_rerank", "knn_fallback", "sigma", "unary", "bound", "mode",
           "energy", "mean_shift"]
 
@@ -69,7 +69,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("outer_iters", ctypes.c_int32), ("inner_iters_total", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("sigma", ctypes.c_float),
                 ("energy", ctypes.c_double), ("knn_fallback_rows", ctypes.c_int64),
-                ("ms_iters_total", ctypes.c_int32)]
+                ("ms_iters_total", ctypes.c_int32), ("knn_float32_rows", ctypes.c_int64),
+                ("knn_exact_rows", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -126,6 +127,7 @@ def load(path: str = LIB_PATH):
         "slk_barrier_selftest": (i32, [P, i32]),
         "slk_kmeanspp": (i32, [P, P, i64, i32, i32, i32, P, P]),
         "slk_symmetrize": (i32, [P, P, P, P, i64, P, P, P, ctypes.POINTER(i64)]),
+        "slk_knn_stage_rows": (i32, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -243,6 +245,8 @@ class Graph:
     w: torch.Tensor | None  # float32 [N*k] or None (binary)
     k: int
     fallback_rows: int = -1
+    # rows left open by the first certificate, sent to the float32 stage, rescanned exactly
+    stage_rows: tuple = (-1, -1, -1)
 
 
 def knn_graph(X: torch.Tensor, k: int, affinity="binary", precision="fp32", sigma=0.0,
@@ -259,7 +263,16 @@ def knn_graph(X: torch.Tensor, k: int, affinity="binary", precision="fp32", sigm
     ctx.check(ctx._lib.slk_knn_graph(ctx.handle, _ptr(X), N, D, k, AFFINITY[affinity],
                                      PRECISION[precision], float(sigma), _ptr(row_ptr), _ptr(col),
                                      _ptr(d2), _ptr(w), ctypes.byref(fb)), "slk_knn_graph")
-    return Graph(row_ptr, col, d2, w, k, fb.value)
+    return Graph(row_ptr, col, d2, w, k, fb.value, knn_stage_rows(ctx))
+
+
+def knn_stage_rows(ctx: Context | None = None) -> tuple:
+    """(rows the first certificate left open, rows sent to the float32 stage,
+    rows rescanned exactly) of the last kNN graph built on ctx."""
+    ctx = ctx or context()
+    rows = (ctypes.c_int64 * 3)()
+    ctx.check(ctx._lib.slk_knn_stage_rows(ctx.handle, rows), "slk_knn_stage_rows")
+    return tuple(int(r) for r in rows)
 
 
 def sigma(dist2: torch.Tensor, rule="median", ctx: Context | None = None) -> float:

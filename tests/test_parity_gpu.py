@@ -103,30 +103,88 @@ def test_knn_integer_lattice_exact_ties(slk, N, D, k, top, seed, precision):
     np.testing.assert_array_equal(host(g.dist2).reshape(N, k).astype(np.float64), o_d2)
 
 
+def two_clusters(N, D, c, seed, spread=1.0):
+    """Two Gaussian clusters at +-c along the first axis."""
+    g = inputs.rng(seed)
+    X = g.normal(0.0, spread, size=(N, D))
+    X[: N // 2, 0] += c
+    X[N // 2:, 0] -= c
+    return X.astype(np.float32)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16_rerank"])
 def test_knn_all_rows_through_exact_rescan(slk, precision):
     """Two tight clusters 2000 apart: the centred norms dwarf the neighbour
-    distances, no row can be certified, and every row goes through the
-    batched exact rescan (which must still match the oracle)."""
-    g = inputs.rng(31)
+    distances, no row can be certified by any stage, and every row goes
+    through the batched exact rescan (which must still match the oracle)."""
     N, D, k = 3000, 16, 7
-    X = g.normal(0.0, 1e-2, size=(N, D))
-    X[: N // 2, 0] += 1000.0
-    X[N // 2:, 0] -= 1000.0
-    X = X.astype(np.float32)
+    X = two_clusters(N, D, 1000.0, 31, spread=1e-2)
     o_idx, o_d2 = oracle.knn(X, k)
     gr = slk.knn_graph(dev(X), k, precision=precision)
     assert gr.fallback_rows > N // 2
+    assert gr.stage_rows[2] > N // 2
     check_knn(X, k, host(gr.col_idx).reshape(N, k), host(gr.dist2).reshape(N, k), o_idx, o_d2,
               max_tie_rows=0.02)
+
+
+def test_knn_two_term_stage_after_bf16(slk):
+    """Two unit-variance clusters 400 apart in 64 dimensions: centred norms of
+    about 200 against neighbour distances of about 10 leave most rows outside
+    the bfloat16 certificate (operand rounding about 2^-9 of the norm), and
+    the two-term bfloat16 tiles (h + l, about 16 significant bits) certify
+    nearly all of them, so hardly any row reaches the float32 stage."""
+    N, D, k = 4000, 64, 10
+    X = two_clusters(N, D, 200.0, 61)
+    o_idx, o_d2 = oracle.knn(X, k)
+    gr = slk.knn_graph(dev(X), k, precision="bf16_rerank")
+    open1, open2, exact = gr.stage_rows
+    assert open1 == gr.fallback_rows and open1 > N // 2, gr.stage_rows
+    assert open2 <= max(8, open1 // 20), gr.stage_rows
+    assert exact <= open2
+    check_knn(X, k, host(gr.col_idx).reshape(N, k), host(gr.dist2).reshape(N, k), o_idx, o_d2,
+              max_tie_rows=0.02)
+
+
+def test_knn_float32_stage_after_two_term(slk):
+    """The same clusters 800 apart: the two-term tiles' accumulation bound
+    (3 Dp products a dot) fails as well, and the float32 tiles with their
+    certificate take the rows over."""
+    N, D, k = 4000, 64, 10
+    X = two_clusters(N, D, 400.0, 62)
+    o_idx, o_d2 = oracle.knn(X, k)
+    gr = slk.knn_graph(dev(X), k, precision="bf16_rerank")
+    open1, open2, exact = gr.stage_rows
+    assert open1 > N // 2 and open2 > N // 2, gr.stage_rows
+    assert exact <= max(8, open2 // 20), gr.stage_rows
+    check_knn(X, k, host(gr.col_idx).reshape(N, k), host(gr.dist2).reshape(N, k), o_idx, o_d2,
+              max_tie_rows=0.02)
+
+
+def test_knn_two_term_stage_capacity(slk):
+    """150000 points in two clusters 140 apart (16 dimensions): more than
+    65536 rows fail the bfloat16 certificate; the two-term stage takes the
+    first 65536 of them and passes the rest straight to the float32 stage,
+    so that stage receives at least the excess.  Sampled rows against the
+    oracle."""
+    N, D, k = 150000, 16, 10
+    X = two_clusters(N, D, 70.0, 63)
+    gr = slk.knn_graph(dev(X), k, precision="bf16_rerank")
+    open1, open2, exact = gr.stage_rows
+    cap = 65536
+    assert open1 > cap, gr.stage_rows
+    assert open1 - cap <= open2 <= open1 - cap + cap // 50, gr.stage_rows
+    rows = inputs.rng(64).choice(N, size=1500, replace=False)
+    o_idx, o_d2 = oracle.knn(X, k, rows=rows)
+    check_knn(X, k, host(gr.col_idx).reshape(N, k)[rows], host(gr.dist2).reshape(N, k)[rows],
+              o_idx, o_d2, rows=rows, max_tie_rows=0.02)
 
 
 @pytest.mark.parametrize("D", [32, 130])
 def test_knn_float32_stage_after_bf16(slk, D):
     """Clusters far from the data mean (centred norms ~ 900 with unit
-    neighbour distances): the bfloat16 certificate cannot hold, the float32
-    query tiles and their certificate take the rows over, and the graph
-    still matches the oracle on every row."""
+    neighbour distances): neither the bfloat16 nor the two-term certificate
+    can hold, the float32 query tiles and their certificate take the rows
+    over, and the graph still matches the oracle on every row."""
     g = inputs.rng(41 + D)
     N, k = 1500, 7
     c = g.normal(0.0, 30.0, size=(3, D))
@@ -134,6 +192,7 @@ def test_knn_float32_stage_after_bf16(slk, D):
     o_idx, o_d2 = oracle.knn(X, k)
     gr = slk.knn_graph(dev(X), k, precision="bf16_rerank")
     assert gr.fallback_rows > N // 10
+    assert gr.stage_rows[1] > 0
     check_knn(X, k, host(gr.col_idx).reshape(N, k), host(gr.dist2).reshape(N, k), o_idx, o_d2,
               max_tie_rows=0.02)
 
