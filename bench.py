@@ -59,9 +59,9 @@ NCU_TRAFFIC = {
         "sha256": "f63b3eeed3ba7913966ecc82d97bda02d0899ec065349cc2357b2128bb16b9db",
     },
     ("knn_cand_tc_kernel", "manifolds_1000000x128_L100"): {
-        "bytes": 50359891200 + 539633664,
+        "bytes": 68245677312 + 540001792,
         "source": "paper_1810_13044_gb300/csrc/knn_tc.cu",
-        "sha256": "83bd2d84463f01a644182b230e9d2993035b55c2d285ceea04db3b33a4db8f63",
+        "sha256": "4b54c0ae7ac45d4b8da62466e53935ed94a8f9aea226828aabb9571982ad5b33",
     },
     ("knn_cand_tc_kernel", "mnist_like_70000x784_L10"): {
         "bytes": 1141291264 + 52733952,

@@ -177,9 +177,9 @@ __device__ __forceinline__ void rho_kappa(float eh, float el, float vh, float vl
 // The row maxima go to st with one atomic per block, with that of
 // kappa_p = rho_p / ||v_p|| (||v_p|| from below), so that rho_q <= kappa ||v_q||
 // for every row.
-// aug (nullable, Np x 64 bfloat16): the folded-norm columns of the
-// tensor-core tiles, [1, 1, 1, a_p, 0...] in columns 0..31 and [a_p, 1, 1, 1,
-// 0...] in 32..63, a_p = (t1, t2, t3) the bfloat16 terms of -norms[p] / 2
+// aug (nullable, Np x 32 bfloat16): the folded-norm columns of the
+// tensor-core tiles, [1, 1, 1, a_p, 0...] in columns 0..15 and [a_p, 1, 1, 1,
+// 0...] in 16..31, a_p = (t1, t2, t3) the bfloat16 terms of -norms[p] / 2
 // (t1 = bf16(x), t2 = bf16(x - t1), t3 = bf16(x - t1 - t2), each difference
 // exact in float32, so t1 + t2 + t3 is within 2^-24 (1.02) |x| of x); a
 // padding row has a_p = (-inf, 0, 0).
@@ -283,9 +283,9 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
             }
         }
         if (aug) {
-            // lanes 0..7 write 8 columns each (16-byte stores)
+            // lanes 0..3 write 8 columns each (16-byte stores)
             const float nfa = __shfl_sync(0xffffffffu, __fadd_rn(nh, nl), 0);
-            if (lane < 8) {
+            if (lane < 4) {
                 const float x = -0.5f * nfa;
                 const __nv_bfloat16 t1 = __float2bfloat16_rn(x);
                 const float r1 = x - __bfloat162float(t1);
@@ -299,10 +299,10 @@ prep_rows_kernel(const float* __restrict__ X, int64_t N, int D, int Dp,
                 for (int q = 0; q < 8; ++q) w[q] = zero;
                 if (lane == 0) {          // columns 0..7: 1, 1, 1, a1, a2, a3
                     w[0] = one; w[1] = one; w[2] = one; w[3] = a1; w[4] = a2; w[5] = a3;
-                } else if (lane == 4) {   // columns 32..39: a1, a2, a3, 1, 1, 1
+                } else if (lane == 2) {   // columns 16..23: a1, a2, a3, 1, 1, 1
                     w[0] = a1; w[1] = a2; w[2] = a3; w[3] = one; w[4] = one; w[5] = one;
                 }
-                *reinterpret_cast<uint4*>(aug + p * 64 + 8 * lane) = *reinterpret_cast<const uint4*>(w);
+                *reinterpret_cast<uint4*>(aug + p * 32 + 8 * lane) = *reinterpret_cast<const uint4*>(w);
             }
         }
     }
@@ -1379,8 +1379,8 @@ struct KnnPlan {
     int ssplits, slists;
 };
 
-// Rows the two-term tensor-core stage takes at most; the open rows beyond
-// it go to the float32 stage.
+// Rows the two-term tensor-core stage takes at most (fewer at large D, see
+// make_plan); the open rows beyond it go to the float32 stage.
 constexpr int64_t kSplitRowCap = 65536;
 
 // Column splits for the persistent tensor-core kernel.  Every split restarts
@@ -1418,7 +1418,7 @@ KnnPlan make_plan(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
     // norms into the MMAs: the epilogue then reads no norms and takes no
     // barrier per tile
 #ifndef SLK_TC_AUG_MAX_DP
-#define SLK_TC_AUG_MAX_DP 0
+#define SLK_TC_AUG_MAX_DP 256
 #endif
     // the tensor-core tiles read 256-row column tiles: keep them inside the matrix
     pl.Np = (int64_t)align_up((size_t)N, pl.bf16 ? 256 : 128);
@@ -1449,7 +1449,10 @@ KnnPlan make_plan(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
         pl.lists = pl.splits * per;
         // the open rows are few: split the columns as far as the rerank's
         // staging (32 MAXE entries per row) and 8 tiles per item allow
-        pl.fcap = std::min<int64_t>((int64_t)align_up((size_t)N, 128), kSplitRowCap);
+        // at most 65536 rows, and query operands (h and l) of at most 64 MiB
+        const int64_t by_mem = std::max<int64_t>(128, ((int64_t)1 << 24) / pl.Dp / 128 * 128);
+        pl.fcap = std::min<int64_t>(std::min<int64_t>((int64_t)align_up((size_t)N, 128), kSplitRowCap),
+                                    by_mem);
         pl.ssplits = std::max(1, std::min((32 * MAXE) / (32 * per), tiles_tc / 8));
         pl.slists = pl.ssplits * per;
     }
@@ -1468,7 +1471,7 @@ size_t knn_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int k, int precision) 
     b += align_up(sizeof(float) * pl.Np, 256) + align_up(sizeof(float) * D, 256);   // norms32, mu
     b += align_up(sizeof(int32_t) * N, 256);                                         // second list
     b += align_up(sizeof(int32_t) * (size_t)N, 256);
-    if (pl.aug) b += align_up(2 * 64 * (size_t)pl.Np, 256);   // folded-norm columns
+    if (pl.aug) b += align_up(2 * 32 * (size_t)pl.Np, 256);   // folded-norm columns
     if (pl.bf16) {
         // two-term stage: xl, norms_s, rho_s, query rows (h, l, norms), lists, third list
         b += align_up(2 * (size_t)pl.Np * pl.Dp, 256) + 2 * align_up(sizeof(float) * pl.Np, 256);
@@ -1556,7 +1559,7 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     float* scand_d = wc.take<float>(pl.bf16 ? (size_t)pl.slists * pl.fcap * 32 : 0);
     int32_t* scand_i = wc.take<int32_t>(pl.bf16 ? (size_t)pl.slists * pl.fcap * 32 : 0);
     int32_t* fb3 = wc.take<int32_t>(pl.bf16 ? (size_t)N : 0);
-    __nv_bfloat16* aug = wc.take<__nv_bfloat16>(pl.aug ? 64 * (size_t)pl.Np : 0);
+    __nv_bfloat16* aug = wc.take<__nv_bfloat16>(pl.aug ? 32 * (size_t)pl.Np : 0);
     cudaStream_t s = ctx->stream;
 
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(colsum, 0, sizeof(double) * D, s));

@@ -92,6 +92,26 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 #ifndef SLK_TC_PAIR
 #define SLK_TC_PAIR 0
 #endif
+// Folded-norm kernel with 8 epilogue warps: columns per TMEM load (16 or
+// 32), pipelined loads (1: the next 16 columns in flight while the current
+// ones are filtered, merges only between chunks, 16 entries at a time) and
+// the columns per vote group of its narrowing (8 or 4).  Measured at
+// 1e6 x 128: 16 columns pipelined 340 ms; unpipelined 357 (32 columns 387,
+// vote groups of 4 360); pipelined with full 32-entry merges spilled (422)
+#ifndef SLK_TC_AUG_C8
+#define SLK_TC_AUG_C8 16
+#endif
+#ifndef SLK_TC_AUG_PIPE
+#define SLK_TC_AUG_PIPE 1
+#endif
+#ifndef SLK_TC_AUG_G
+#define SLK_TC_AUG_G 8
+#endif
+// Sleep between the producer's and the MMA warp's barrier polls (ns; 0:
+// poll).  Measured at 1e6 x 128: 100 ns 334 ms, 400 ns 350 ms, polling 329 ms
+#ifndef SLK_TC_SPIN_NS
+#define SLK_TC_SPIN_NS 0
+#endif
 // Buffered entries (per lane) that trigger a merge after a tile (KC = 32).
 #ifndef SLK_TC_MERGE_AT
 #define SLK_TC_MERGE_AT 24
@@ -177,12 +197,15 @@ __device__ __forceinline__ bool mbar_test_cl(unsigned long long* b, uint32_t par
     return ok != 0;
 }
 // Bounded wait for phase `parity` of barrier b.  Gives up (false) after
-// kWaitNs or once another role has raised abort.
-template <bool CL = false>
+// kWaitNs or once another role has raised abort.  SLEEP_NS > 0 sleeps
+// between polls (the producer and MMA warps, which mostly wait: their polls
+// would otherwise take issue slots from the epilogue warps on their SMSPs).
+template <bool CL = false, int SLEEP_NS = 0>
 __device__ __noinline__ bool mbar_wait(unsigned long long* b, uint32_t parity, volatile int* abort) {
     if (CL ? mbar_test_cl(b, parity) : mbar_test(b, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     while (true) {
+        if constexpr (SLEEP_NS > 0) __nanosleep(SLEEP_NS);
         if (CL ? mbar_test_cl(b, parity) : mbar_test(b, parity)) return true;
         if (*abort) return false;
         if (globaltimer_ns() - t0 > kWaitNs) {
@@ -216,14 +239,14 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     d |= (uint64_t)(TC_ROWB == 128 ? 2 : 4) << 61;   // 128- or 64-byte swizzle
     return d;
 }
-// The same for 64-byte swizzle rows (32 bf16): 8-row atoms 512 bytes apart.
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+// The same for 32-byte swizzle rows (16 bf16): 8-row atoms 256 bytes apart.
+__device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;
-    d |= (uint64_t)((8 * 64) >> 4) << 32;
+    d |= (uint64_t)((8 * 32) >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;   // 64-byte swizzle
+    d |= (uint64_t)6 << 61;   // 32-byte swizzle
     return d;
 }
 // Instruction descriptor: D fp32, A/B bf16, both K-major, N = 256, M = 128.
@@ -415,6 +438,59 @@ __device__ __forceinline__ void merge_topk(float (&ld)[KC], int (&li)[KC], const
         }
 }
 
+// NB (16) entries sorted ascending (bitonic network in registers).
+template <int NB>
+__device__ __forceinline__ void bitonic_sort_n(float (&d)[NB], int (&i)[NB]) {
+#pragma unroll
+    for (int k = 2; k <= NB; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int x = 0; x < NB; ++x) {
+                const int l = x ^ j;
+                if (l > x) cas(d[x], i[x], d[l], i[l], (x & k) == 0);
+            }
+}
+
+// merge_topk for 16 sorted entries (padded with +inf to KC): only the last 16
+// slots of the list can take one of them.
+template <int KC>
+__device__ __forceinline__ void merge_topk16(float (&ld)[KC], int (&li)[KC], const float (&bd)[16],
+                                             const int (&bi)[16]) {
+#pragma unroll
+    for (int x = KC - 16; x < KC; ++x) {
+        const float od = bd[KC - 1 - x];
+        const int oi = bi[KC - 1 - x];
+        if (od < ld[x] || (od == ld[x] && oi < li[x])) { ld[x] = od; li[x] = oi; }
+    }
+#pragma unroll
+    for (int j = KC / 2; j > 0; j >>= 1)
+#pragma unroll
+        for (int x = 0; x < KC; ++x) {
+            const int l = x ^ j;
+            if (l > x) cas(ld[x], li[x], ld[l], li[l], true);
+        }
+}
+
+// flush_buffer in rounds of 16 entries: half the registers of a 32-entry sort.
+template <int KC, class S>
+__device__ __forceinline__ void flush_buffer16(S& s, int h, int r, int& cnt,
+                                               float (&ld)[KC], int (&li)[KC]) {
+    for (int base = 0; __any_sync(0xffffffffu, cnt > base); base += 16) {
+        float bd[16];
+        int bi[16];
+#pragma unroll
+        for (int x = 0; x < 16; ++x) {
+            const bool have = base + x < cnt;
+            bd[x] = have ? s.buf_d[h][base + x][r] : __int_as_float(0x7f800000);
+            bi[x] = have ? s.buf_i[h][base + x][r] : kNoIdx;
+        }
+        bitonic_sort_n<16>(bd, bi);
+        merge_topk16<KC>(ld, li, bd, bi);
+    }
+    cnt = 0;
+}
+
 // Warp-synchronous: fold every lane's buffered entries into its top-KC.
 template <int KC, class S>
 __device__ __forceinline__ void flush_buffer(S& s, int h, int r, int& cnt,
@@ -445,11 +521,12 @@ __device__ __forceinline__ void item_range(int item, int splits, int n_tiles, in
 // PAIR: launched in clusters of two; an item's row block is a pair of
 // 128-row blocks (rank r of the cluster takes block 2 rb + r), both CTAs walk
 // the same items, and only the leader's MMA warp issues.
-// AUG: one more K slice of 32 columns (64-byte swizzle) from the aug matrix
-// (tmA2 reads its columns 0..31 for the A rows, tmB2 its columns 32..63 for
-// the B rows): [1, 1, 1, a_p] against [a_q, 1, 1, 1], a the three bfloat16
-// terms of -||xt||^2 / 2, so that the accumulator holds -dt / 2 and the
-// epilogue needs no norms (padding rows and columns carry -inf there).
+// AUG: one more K slice of 16 columns (32-byte swizzle, one K = 16 MMA)
+// from the aug matrix (tmA2 reads its columns 0..15 for the A rows, tmB2 its
+// columns 16..31 for the B rows): [1, 1, 1, a_p] against [a_q, 1, 1, 1], a
+// the three bfloat16 terms of -||xt||^2 / 2, so that the accumulator holds
+// -dt / 2 and the epilogue needs no norms (padding rows and columns carry
+// -inf there).
 // SPLIT: the two-term operands s = h + l of listed query rows against every
 // point.  The accumulator sums three passes over the K slices, h_p . h_q
 // (tmA, tmB), h_p . l_q (tmA, tmB2) and l_p . h_q (tmA2, tmB); the rows are
@@ -471,7 +548,9 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     using E = TcEpi<EW, PAIR, TC_KC>;
     constexpr int STAGES = E::stages;
     constexpr int H = E::halves, VOTE = E::vote, APP = E::app, NT = 32 * EW;
-    constexpr int C = E::chunk;                  // columns per TMEM load
+    // columns per TMEM load (the folded-norm epilogue of 8 warps keeps no
+    // second value array, so it has the registers for 32)
+    constexpr int C = (AUG && EW == 8) ? SLK_TC_AUG_C8 : E::chunk;
     constexpr int CH_PER_HALF = TC_N / C / H;    // TMEM loads per thread and tile
     extern __shared__ uint8_t smem_raw[];
     TcSmem<EW, PAIR, TC_KC>& s = *reinterpret_cast<TcSmem<EW, PAIR, TC_KC>*>(
@@ -549,7 +628,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     const int bcol = t * TC_N + (int)rank * (TC_N / 2);   // rank 0 unless PAIR
                     for (int kb = 0; kb < nkb; ++kb) {
                         const uint32_t st = iter % STAGES, use = iter / STAGES;
-                        if (use > 0 && !(ok = mbar_wait(&s.empty[st], (use - 1) & 1, abort))) break;
+                        if (use > 0 && !(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.empty[st], (use - 1) & 1, abort))) break;
                         if constexpr (PAIR) {
                             // both CTAs' loads complete on the leader's barrier, whose
                             // one arrival (the leader's) expects the bytes of both
@@ -563,10 +642,10 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                             int kx = kb;
                             if constexpr (AUG) {
                                 if (kb == nkb0) {
-                                    // the folded norms: 32 columns of A (x = 0) and B (x = 32)
-                                    mbar_expect_tx(&s.full[st], (A_BYTES + B_BYTES) / 2);
+                                    // the folded norms: 16 columns of A (x = 0) and B (x = 16)
+                                    mbar_expect_tx(&s.full[st], (A_BYTES + B_BYTES) / 4);
                                     tma_load_2d(s.a[st], &tmA2, &s.full[st], 0, arow);
-                                    tma_load_2d(s.b[st], &tmB2, &s.full[st], 32, bcol);
+                                    tma_load_2d(s.b[st], &tmB2, &s.full[st], 16, bcol);
                                     ++iter;
                                     continue;
                                 }
@@ -616,19 +695,18 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 for (int t = t0; t < t1 && ok; ++t) {
                     const uint32_t acc = tcount & 1, use = tcount >> 1;
                     // with CTA pairs the epilogues of both CTAs release the accumulator
-                    if (use > 0 && !(ok = mbar_wait<PAIR>(&s.tempty[acc], (use - 1) & 1, abort))) break;
+                    if (use > 0 && !(ok = mbar_wait<PAIR, SLK_TC_SPIN_NS>(&s.tempty[acc], (use - 1) & 1, abort))) break;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + acc * TC_N;
                     for (int kb = 0; kb < nkb; ++kb) {
                         const uint32_t st = iter % STAGES;
-                        if (!(ok = mbar_wait(&s.full[st], (iter / STAGES) & 1, abort))) break;
+                        if (!(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.full[st], (iter / STAGES) & 1, abort))) break;
                         tc_fence_after();
                         if (AUG && kb == nkb0) {
-                            // folded norms: two K = 16 steps in 64-byte swizzle rows
-                            const uint64_t da = sw64_desc(su32(s.a[st]));
-                            const uint64_t db = sw64_desc(su32(s.b[st]));
+                            // folded norms: one K = 16 step in 32-byte swizzle rows
+                            const uint64_t da = sw32_desc(su32(s.a[st]));
+                            const uint64_t db = sw32_desc(su32(s.b[st]));
                             umma(d_tmem, da, db, 1u);
-                            umma(d_tmem, da + 2u, db + 2u, 1u);
                             umma_commit(&s.empty[st]);
                             ++iter;
                             continue;
@@ -724,12 +802,68 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 // distances of one 32-column chunk, filtered in votes of VOTE
                 // columns against the row's threshold (the row's own column,
                 // distance ~0, is kept here and dropped by the rerank)
-                auto process = [&](const uint32_t (&rv)[C], int ch) {
-                    float v[C];   // w = fl(||xt_q||^2 - 2 dot); AUG: dt / 2
-                    if constexpr (AUG) {
+                // AUG, pipelined loads: appends only (the caller flushes at
+                // chunk boundaries, keeping room for C appends)
+                constexpr bool AUG_PIPE = AUG && (SLK_TC_AUG_PIPE != 0);
+                auto process_aug = [&](const uint32_t (&rv)[C], int ch) {
+                    // the accumulator holds -dt / 2: a column passes when it
+                    // exceeds -thr / 2 (dt < thr; both scalings exact); padding
+                    // rows and columns hold -inf and never pass.  Votes narrow
+                    // down by groups of G columns, each group's maximum by a tree.
+                    constexpr int G = SLK_TC_AUG_G;
 #pragma unroll
-                        for (int j = 0; j < C; ++j) v[j] = -__uint_as_float(rv[j]);
-                    } else if constexpr (NOBAR) {
+                    for (int g0 = 0; g0 < C; g0 += VOTE) {
+                        const float hthr = -0.5f * ld[TC_KC - 1];
+                        float mg[VOTE / G];
+#pragma unroll
+                        for (int q = 0; q < VOTE / G; ++q) {
+                            float t[G];
+#pragma unroll
+                            for (int j = 0; j < G; ++j) t[j] = __uint_as_float(rv[g0 + G * q + j]);
+#pragma unroll
+                            for (int w = G / 2; w > 0; w >>= 1)
+#pragma unroll
+                                for (int j = 0; j < w; ++j) t[j] = fmaxf(t[j], t[j + w]);
+                            mg[q] = t[0];
+                        }
+                        float mx = mg[0];
+#pragma unroll
+                        for (int q = 1; q < VOTE / G; ++q) mx = fmaxf(mx, mg[q]);
+                        if (__any_sync(0xffffffffu, mx > hthr)) {
+#pragma unroll
+                            for (int a0 = 0; a0 < VOTE; a0 += APP) {
+                                if constexpr (E::defer && !AUG_PIPE) {
+                                    if (__any_sync(0xffffffffu, cnt > E::buf - APP))
+                                        flush_buffer<TC_KC>(s, h, r, cnt, ld, li);
+                                }
+#pragma unroll
+                                for (int q = a0 / G; q < (a0 + APP) / G; ++q) {
+                                    if (!__any_sync(0xffffffffu, mg[q] > hthr)) continue;
+#pragma unroll
+                                    for (int j = g0 + G * q; j < g0 + G * q + G; ++j) {
+                                        const float a = __uint_as_float(rv[j]);
+                                        if (a > hthr) {
+                                            s.buf_d[h][cnt][r] = -2.f * a;
+                                            s.buf_i[h][cnt][r] = (int)(col0 + ch * C + j);
+                                            ++cnt;
+                                        }
+                                    }
+                                }
+                                if constexpr (!E::defer && !AUG_PIPE) {
+                                    if (__any_sync(0xffffffffu, cnt >= 16))
+                                        flush_buffer<TC_KC>(s, h, r, cnt, ld, li);
+                                }
+                            }
+                        }
+                    }
+                };
+                auto process = [&](const uint32_t (&rv)[C], int ch) {
+                    if constexpr (AUG) {
+                        process_aug(rv, ch);
+                        return;
+                    }
+                    float v[C];   // w = fl(||xt_q||^2 - 2 dot)
+                    if constexpr (NOBAR) {
                         const float4* n4 = reinterpret_cast<const float4*>(ncol_g + ch * C);
 #pragma unroll
                         for (int q = 0; q < C / 4; ++q) {
@@ -747,10 +881,8 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll
                     for (int g0 = 0; g0 < C; g0 += VOTE) {
                         // w < thr - ||xt_p||^2 (rounded up) whenever dt < thr; a
-                        // padding row (infinite norm) gets NaN and never passes.
-                        // AUG: dt / 2 < thr / 2 (both exact), padding rows and
-                        // columns give +inf
-                        const float thr_w = AUG ? 0.5f * ld[TC_KC - 1] : __fsub_ru(ld[TC_KC - 1], np_);
+                        // padding row (infinite norm) gets NaN and never passes
+                        const float thr_w = __fsub_ru(ld[TC_KC - 1], np_);
                         float m8[VOTE / 8];
 #pragma unroll
                         for (int q = 0; q < VOTE / 8; ++q) {
@@ -778,7 +910,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll
                                     for (int j = g0 + 8 * q; j < g0 + 8 * q + 8; ++j) {
                                         if (v[j] < thr_w) {
-                                            s.buf_d[h][cnt][r] = AUG ? 2.f * v[j] : __fadd_rn(v[j], np_);
+                                            s.buf_d[h][cnt][r] = __fadd_rn(v[j], np_);
                                             s.buf_i[h][cnt][r] = (int)(col0 + ch * C + j);
                                             ++cnt;
                                         }
@@ -803,7 +935,26 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     }
                 };
                 const int ch0 = h * CH_PER_HALF;
-                if constexpr (PIPE) {
+                if constexpr (AUG_PIPE) {
+                    // the load of the next chunk is in flight while one is
+                    // filtered; merges happen only at chunk boundaries, with one
+                    // chunk's values live, keeping room for C appends
+                    static_assert(E::buf >= 15 + C, "room for a chunk's appends");
+                    uint32_t ra[C], rb2[C];
+                    tmem_ld_issue<C>(tbase + ch0 * C, ra);
+#pragma unroll 1
+                    for (int cc = 0; cc < CH_PER_HALF; cc += 2) {
+                        tmem_wait_regs(ra);
+                        if (__any_sync(0xffffffffu, cnt > E::buf - C)) flush_buffer16<TC_KC>(s, h, r, cnt, ld, li);
+                        tmem_ld_issue<C>(tbase + (ch0 + cc + 1) * C, rb2);
+                        process(ra, ch0 + cc);
+                        tmem_wait_regs(rb2);
+                        if (cc + 2 >= CH_PER_HALF) release();
+                        if (__any_sync(0xffffffffu, cnt > E::buf - C)) flush_buffer16<TC_KC>(s, h, r, cnt, ld, li);
+                        if (cc + 2 < CH_PER_HALF) tmem_ld_issue<C>(tbase + (ch0 + cc + 2) * C, ra);
+                        process(rb2, ch0 + cc + 1);
+                    }
+                } else if constexpr (PIPE) {
                 // two register sets: the load of chunk c + 1 is in flight while
                 // chunk c is filtered
                 uint32_t ra[C], rb2[C];
@@ -935,21 +1086,21 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS)
         return set_err(ctx, SLK_ERR_CUDA, "tensor map encoding failed (%d, %d)", (int)r1, (int)r2);
-    // folded norms: the aug matrix (Np x 64 bf16), 32-column boxes in 64-byte swizzle
+    // folded norms: the aug matrix (Np x 32 bf16), 16-column boxes in 32-byte swizzle
     CUtensorMap ta2 = ta, tb2a = tb;
     const bool use_aug = aug != nullptr && kc == 32 && !(SLK_TC_PAIR != 0 && (Np / TC_M) % 2 == 0);
     if (use_aug) {
         if ((reinterpret_cast<uintptr_t>(aug) & 15) != 0)
             return set_err(ctx, SLK_ERR_INVALID_ARG, "aug operand not 16-byte aligned");
-        const cuuint64_t adims[2] = {64, (cuuint64_t)Np};
-        const cuuint64_t astr[1] = {128};
-        const cuuint32_t abox_a[2] = {32, TC_M};
-        const cuuint32_t abox_b[2] = {32, TC_N};
+        const cuuint64_t adims[2] = {32, (cuuint64_t)Np};
+        const cuuint64_t astr[1] = {64};
+        const cuuint32_t abox_a[2] = {16, TC_M};
+        const cuuint32_t abox_b[2] = {16, TC_N};
         CUresult r3 = enc(&ta2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)aug, adims, astr, abox_a,
-                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         CUresult r4 = enc(&tb2a, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)aug, adims, astr, abox_b,
-                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r3 != CUDA_SUCCESS || r4 != CUDA_SUCCESS)
             return set_err(ctx, SLK_ERR_CUDA, "tensor map encoding failed (%d, %d)", (int)r3, (int)r4);
