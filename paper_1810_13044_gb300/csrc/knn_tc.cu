@@ -107,6 +107,10 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 #ifndef SLK_TC_AUG_G
 #define SLK_TC_AUG_G 8
 #endif
+// Group maxima of the folded-norm epilogue by the three-input max.f32
+#ifndef SLK_TC_MAX3
+#define SLK_TC_MAX3 1
+#endif
 // Sleep between the producer's and the MMA warp's barrier polls (ns; 0:
 // poll).  Measured at 1e6 x 128: 100 ns 334 ms, 400 ns 350 ms, polling 329 ms
 #ifndef SLK_TC_SPIN_NS
@@ -238,6 +242,12 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     d |= (uint64_t)1 << 46;                 // version
     d |= (uint64_t)(TC_ROWB == 128 ? 2 : 4) << 61;   // 128- or 64-byte swizzle
     return d;
+}
+// max(a, b, c) in one instruction (sm_100 and later)
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 // The same for 32-byte swizzle rows (16 bf16): 8-row atoms 256 bytes apart.
 __device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
@@ -820,11 +830,18 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                             float t[G];
 #pragma unroll
                             for (int j = 0; j < G; ++j) t[j] = __uint_as_float(rv[g0 + G * q + j]);
+                            if constexpr (G == 8 && SLK_TC_MAX3) {
+                                // three-input maximum: 4 instructions, depth 2
+                                const float u0 = fmax3(t[0], t[1], t[2]);
+                                const float u1 = fmax3(t[3], t[4], t[5]);
+                                mg[q] = fmax3(u0, u1, fmaxf(t[6], t[7]));
+                            } else {
 #pragma unroll
-                            for (int w = G / 2; w > 0; w >>= 1)
+                                for (int w = G / 2; w > 0; w >>= 1)
 #pragma unroll
-                                for (int j = 0; j < w; ++j) t[j] = fmaxf(t[j], t[j + w]);
-                            mg[q] = t[0];
+                                    for (int j = 0; j < w; ++j) t[j] = fmaxf(t[j], t[j + w]);
+                                mg[q] = t[0];
+                            }
                         }
                         float mx = mg[0];
 #pragma unroll
