@@ -34,6 +34,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "slk_internal.cuh"
 
 namespace {
@@ -169,6 +171,36 @@ struct TcSmem {
 };
 template <int EW, bool PAIR = false, int KC = 32>
 constexpr size_t tc_smem_bytes() { return sizeof(TcSmem<EW, PAIR, KC>) + 1024; }
+
+// Resident A block for the folded-norm tiles at Dp <= 128 (1) and its ring
+// of B slices
+#ifndef SLK_TC_RES
+#define SLK_TC_RES 1
+#endif
+#ifndef SLK_TC_RES_STAGES
+#define SLK_TC_RES_STAGES 3
+#endif
+// Shared memory of the resident-A form: the row block's A slices (Dp <= 128,
+// two of 64 columns) and its folded-norm slice are loaded once per row block
+// and stay; the ring carries only B slices, the last slice of a tile with the
+// B side of the folded norms.  Per tile the TMA moves 72 KiB instead of 108.
+template <int EW>
+struct TcSmemRes {
+    using E = TcEpi<EW, false, 32>;
+    static constexpr int stages = SLK_TC_RES_STAGES;
+    uint8_t a[2][A_BYTES];           // 1024-byte aligned (swizzle atoms)
+    uint8_t a_aug[A_BYTES / 4];      // 128 rows x 32 bytes
+    uint8_t b[stages][B_BYTES];
+    uint8_t b_aug[stages][B_BYTES / 4];
+    float buf_d[E::halves][E::buf][TC_M];
+    int buf_i[E::halves][E::buf][TC_M];
+    float ncol[2][TC_N];
+    unsigned long long full[stages], empty[stages], tfull[2], tempty[2], afull, aempty;
+    uint32_t tmem_base;
+    int abort;
+};
+template <int EW>
+constexpr size_t tc_smem_res_bytes() { return sizeof(TcSmemRes<EW>) + 1024; }
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -545,7 +577,7 @@ __device__ __forceinline__ void item_range(int item, int splits, int n_tiles, in
 // being the list stride.  Otherwise tmA2 / tmB2 / row_norms / rows_dev are
 // unused and the rows are the points themselves.
 template <int TC_KC, int EW, bool PIPE, bool NOBAR, bool PAIR = false, bool SPLIT = false,
-          bool AUG = false>
+          bool AUG = false, bool RES = false>
 __global__ void __launch_bounds__(TcEpi<EW, PAIR, TC_KC>::threads, 1)
 knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB2,
@@ -555,16 +587,17 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                    int32_t* __restrict__ cand_i, unsigned int* __restrict__ err_flag) {
     static_assert(!(SPLIT && PAIR), "split query rows run on single CTAs");
     static_assert(!(AUG && (PAIR || SPLIT)), "the folded norms are for single-CTA point tiles");
+    static_assert(!RES || (AUG && TC_KC == 32), "a resident A block goes with the folded norms");
     using E = TcEpi<EW, PAIR, TC_KC>;
-    constexpr int STAGES = E::stages;
+    using SMT = std::conditional_t<RES, TcSmemRes<EW>, TcSmem<EW, PAIR, TC_KC>>;
+    constexpr int STAGES = RES ? SLK_TC_RES_STAGES : E::stages;
     constexpr int H = E::halves, VOTE = E::vote, APP = E::app, NT = 32 * EW;
     // columns per TMEM load (the folded-norm epilogue of 8 warps keeps no
     // second value array, so it has the registers for 32)
     constexpr int C = (AUG && EW == 8) ? SLK_TC_AUG_C8 : E::chunk;
     constexpr int CH_PER_HALF = TC_N / C / H;    // TMEM loads per thread and tile
     extern __shared__ uint8_t smem_raw[];
-    TcSmem<EW, PAIR, TC_KC>& s = *reinterpret_cast<TcSmem<EW, PAIR, TC_KC>*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    SMT& s = *reinterpret_cast<SMT*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb0 = Dp / TC_BK;                   // K slices of one operand pass
     const int nkb = SPLIT ? 3 * nkb0 : (AUG ? nkb0 + 1 : nkb0);   // K slices per tile
@@ -595,6 +628,10 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             mbar_init(&s.tfull[i], 1);
             mbar_init(&s.tempty[i], PAIR ? 2 * EW : EW);
         }
+        if constexpr (RES) {
+            mbar_init(&s.afull, 1);
+            mbar_init(&s.aempty, 1);
+        }
         s.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -624,10 +661,62 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         if (lane == 0) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-            if constexpr (SPLIT) {
+            if constexpr (SPLIT || AUG) {
                 asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA2)) : "memory");
                 asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB2)) : "memory");
             }
+            if constexpr (RES) {
+                // A slices (and their folded-norm slice) once per row block,
+                // after the MMA warp has released the previous block; the ring
+                // carries B slices only
+                uint32_t iter = 0, aload = 0;
+                bool ok = true;
+                int cur_rb = -1;
+                for (int item = item_begin; item < item_end && ok; ++item) {
+                    int rb, t0, t1, sp;
+                    item_range(item, splits, n_tiles, rb, t0, t1, sp);
+                    if (rb != cur_rb) {
+                        if (aload > 0 &&
+                            !(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.aempty, (aload - 1) & 1, abort)))
+                            break;
+                        const int arow = rb * TC_M;
+                        mbar_expect_tx(&s.afull, (uint32_t)nkb0 * A_BYTES + A_BYTES / 4);
+                        for (int kb = 0; kb < nkb0; ++kb) tma_load_2d(s.a[kb], &tmA, &s.afull, kb * TC_BK, arow);
+                        tma_load_2d(s.a_aug, &tmA2, &s.afull, 0, arow);
+                        ++aload;
+                        cur_rb = rb;
+                    }
+                    for (int t = t0; t < t1 && ok; ++t) {
+                        const int bcol = t * TC_N;
+                        for (int kb = 0; kb < nkb0; ++kb) {
+                            const uint32_t st = iter % STAGES, use = iter / STAGES;
+                            if (use > 0 &&
+                                !(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.empty[st], (use - 1) & 1, abort)))
+                                break;
+                            const bool last = kb == nkb0 - 1;
+                            mbar_expect_tx(&s.full[st], B_BYTES + (last ? B_BYTES / 4 : 0u));
+                            tma_load_2d(s.b[st], &tmB, &s.full[st], kb * TC_BK, bcol);
+                            if (last) tma_load_2d(s.b_aug[st], &tmB2, &s.full[st], 16, bcol);
+                            ++iter;
+                        }
+                    }
+                }
+                // drain: every issued load must have landed before the CTA leaves
+                if (!ok || *abort) {
+                    const uint32_t first = iter > STAGES ? iter - STAGES : 0;
+                    for (uint32_t i = first; i < iter; ++i) {
+                        const unsigned long long t0 = globaltimer_ns();
+                        while (!mbar_test(&s.full[i % STAGES], (i / STAGES) & 1) &&
+                               globaltimer_ns() - t0 < kWaitNs) {
+                        }
+                    }
+                    if (aload > 0) {
+                        const unsigned long long t0 = globaltimer_ns();
+                        while (!mbar_test(&s.afull, (aload - 1) & 1) && globaltimer_ns() - t0 < kWaitNs) {
+                        }
+                    }
+                }
+            } else {
             uint32_t iter = 0;
             bool ok = true;
             for (int item = item_begin; item < item_end && ok; ++item) {
@@ -693,10 +782,67 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     }
                 }
             }
+            }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
-        if (lane == 0 && rank == 0) {
+        if constexpr (RES) {
+            if (lane == 0) {
+                uint32_t iter = 0, tcount = 0, aload = 0;
+                bool ok = true;
+                int cur_rb = -1;
+                for (int item = item_begin; item < item_end && ok; ++item) {
+                    int rb, t0, t1, sp;
+                    item_range(item, splits, n_tiles, rb, t0, t1, sp);
+                    if (rb != cur_rb) {
+                        // release the previous block once its MMAs complete, then
+                        // wait for the new one
+                        if (cur_rb >= 0) umma_commit(&s.aempty);
+                        if (!(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.afull, aload & 1, abort))) break;
+                        tc_fence_after();
+                        ++aload;
+                        cur_rb = rb;
+                    }
+                    for (int t = t0; t < t1 && ok; ++t) {
+                        const uint32_t acc = tcount & 1, use = tcount >> 1;
+                        if (use > 0 &&
+                            !(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.tempty[acc], (use - 1) & 1, abort)))
+                            break;
+                        tc_fence_after();
+                        const uint32_t d_tmem = tmem + acc * TC_N;
+                        for (int kb = 0; kb < nkb0; ++kb) {
+                            const uint32_t st = iter % STAGES;
+                            if (!(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.full[st], (iter / STAGES) & 1, abort)))
+                                break;
+                            tc_fence_after();
+                            const uint64_t da = sw128_desc(su32(s.a[kb]));
+                            const uint64_t db = sw128_desc(su32(s.b[st]));
+#pragma unroll
+                            for (int k = 0; k < TC_BK / 16; ++k)
+                                umma(d_tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
+                                     (kb | k) != 0 ? 1u : 0u);
+                            if (kb == nkb0 - 1)   // folded norms: one K = 16 step, 32-byte swizzle
+                                umma(d_tmem, sw32_desc(su32(s.a_aug)), sw32_desc(su32(s.b_aug[st])), 1u);
+                            umma_commit(&s.empty[st]);
+                            ++iter;
+                        }
+                        if (!ok) break;
+                        umma_commit(&s.tfull[acc]);
+                        ++tcount;
+                    }
+                }
+                if (!ok || *abort) {
+                    // let the MMAs already issued finish before TMEM is released
+                    if (iter > 0) {
+                        const uint32_t i = iter - 1;
+                        const unsigned long long t0 = globaltimer_ns();
+                        while (!mbar_test(&s.empty[i % STAGES], (i / STAGES) & 1) &&
+                               globaltimer_ns() - t0 < kWaitNs) {
+                        }
+                    }
+                }
+            }
+        } else if (lane == 0 && rank == 0) {
             uint32_t iter = 0, tcount = 0;
             bool ok = true;
             for (int item = item_begin; item < item_end && ok; ++item) {
@@ -765,6 +911,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         int li[TC_KC];
         int cnt = 0;
         int run_rb = -1, run_sp = 0;   // the row block whose list is being built
+        bool hit = false;              // a chunk appended since the last room check (warp-uniform)
         for (int item = item_begin; item < item_end && ok; ++item) {
             int rb, t0, t1, sp;
             item_range(item, splits, n_tiles, rb, t0, t1, sp);
@@ -813,7 +960,8 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 // columns against the row's threshold (the row's own column,
                 // distance ~0, is kept here and dropped by the rerank)
                 // AUG, pipelined loads: appends only (the caller flushes at
-                // chunk boundaries, keeping room for C appends)
+                // chunk boundaries, keeping room for C appends, and only after a
+                // chunk with a hit: `hit` is set by the warp-uniform vote)
                 constexpr bool AUG_PIPE = AUG && (SLK_TC_AUG_PIPE != 0);
                 auto process_aug = [&](const uint32_t (&rv)[C], int ch) {
                     // the accumulator holds -dt / 2: a column passes when it
@@ -847,6 +995,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll
                         for (int q = 1; q < VOTE / G; ++q) mx = fmaxf(mx, mg[q]);
                         if (__any_sync(0xffffffffu, mx > hthr)) {
+                            hit = true;
 #pragma unroll
                             for (int a0 = 0; a0 < VOTE; a0 += APP) {
                                 if constexpr (E::defer && !AUG_PIPE) {
@@ -962,12 +1111,18 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll 1
                     for (int cc = 0; cc < CH_PER_HALF; cc += 2) {
                         tmem_wait_regs(ra);
-                        if (__any_sync(0xffffffffu, cnt > E::buf - C)) flush_buffer16<TC_KC>(s, h, r, cnt, ld, li);
+                        if (hit) {
+                            hit = false;
+                            if (__any_sync(0xffffffffu, cnt > E::buf - C)) flush_buffer16<TC_KC>(s, h, r, cnt, ld, li);
+                        }
                         tmem_ld_issue<C>(tbase + (ch0 + cc + 1) * C, rb2);
                         process(ra, ch0 + cc);
                         tmem_wait_regs(rb2);
                         if (cc + 2 >= CH_PER_HALF) release();
-                        if (__any_sync(0xffffffffu, cnt > E::buf - C)) flush_buffer16<TC_KC>(s, h, r, cnt, ld, li);
+                        if (hit) {
+                            hit = false;
+                            if (__any_sync(0xffffffffu, cnt > E::buf - C)) flush_buffer16<TC_KC>(s, h, r, cnt, ld, li);
+                        }
                         if (cc + 2 < CH_PER_HALF) tmem_ld_issue<C>(tbase + (ch0 + cc + 2) * C, ra);
                         process(rb2, ch0 + cc + 1);
                     }
@@ -1159,6 +1314,25 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
         SLK_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, ta, tb2, ta, tb2, norms, norms,
                                              (const long long*)nullptr, N, Np, Dp, n_tiles, splits,
                                              row_blocks, cand_d, cand_i, err_flag));
+    } else if (use_aug && SLK_TC_RES != 0 && Dp <= 2 * TC_BK) {
+        // resident A block (Dp <= 128)
+        if (ew == 4) {
+            auto kern = knn_cand_tc_kernel<32, 4, false, false, false, false, true, true>;
+            const size_t smem = tc_smem_res_bytes<4>();
+            SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem));
+            kern<<<grid, TcEpi<4>::threads, smem, ctx->stream>>>(
+                ta, tb, ta2, tb2a, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks,
+                cand_d, cand_i, err_flag);
+        } else {
+            auto kern = knn_cand_tc_kernel<32, 8, false, false, false, false, true, true>;
+            const size_t smem = tc_smem_res_bytes<8>();
+            SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem));
+            kern<<<grid, TcEpi<8>::threads, smem, ctx->stream>>>(
+                ta, tb, ta2, tb2a, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks,
+                cand_d, cand_i, err_flag);
+        }
     } else if (use_aug && ew == 4) {
         auto kern = knn_cand_tc_kernel<32, 4, false, false, false, false, true>;
         const size_t smem = tc_smem_bytes<4>();
