@@ -59,14 +59,14 @@ NCU_TRAFFIC = {
         "sha256": "f63b3eeed3ba7913966ecc82d97bda02d0899ec065349cc2357b2128bb16b9db",
     },
     ("knn_cand_tc_kernel", "manifolds_1000000x128_L100"): {
-        "bytes": 68245677312 + 540001792,
+        "bytes": 775667442176 + 530011648,
         "source": "paper_1810_13044_gb300/csrc/knn_tc.cu",
-        "sha256": "4b54c0ae7ac45d4b8da62466e53935ed94a8f9aea226828aabb9571982ad5b33",
+        "sha256": "e791db2fdf5bce5e1c75b9feefe7a759bea0d581448fe80e99acca6199d1014f",
     },
     ("knn_cand_tc_kernel", "mnist_like_70000x784_L10"): {
-        "bytes": 1141291264 + 52733952,
+        "bytes": 1142387200 + 53179392,
         "source": "paper_1810_13044_gb300/csrc/knn_tc.cu",
-        "sha256": "f1cfb1769353c79491e3282b9cbfdc350725504ecf50738d4421afa789e2be89",
+        "sha256": "e791db2fdf5bce5e1c75b9feefe7a759bea0d581448fe80e99acca6199d1014f",
     },
 }
 
