@@ -59,14 +59,14 @@ NCU_TRAFFIC = {
         "sha256": "f63b3eeed3ba7913966ecc82d97bda02d0899ec065349cc2357b2128bb16b9db",
     },
     ("knn_cand_tc_kernel", "manifolds_1000000x128_L100"): {
-        "bytes": 775667442176 + 530011648,
+        "bytes": 19366642688 + 528892928,
         "source": "paper_1810_13044_gb300/csrc/knn_tc.cu",
-        "sha256": "e791db2fdf5bce5e1c75b9feefe7a759bea0d581448fe80e99acca6199d1014f",
+        "sha256": "a03e4138c570178b9d1bad4871b6959473fb7e3d6bc4cd37d0d20a71f51b4e21",
     },
     ("knn_cand_tc_kernel", "mnist_like_70000x784_L10"): {
         "bytes": 1142387200 + 53179392,
         "source": "paper_1810_13044_gb300/csrc/knn_tc.cu",
-        "sha256": "e791db2fdf5bce5e1c75b9feefe7a759bea0d581448fe80e99acca6199d1014f",
+        "sha256": "a03e4138c570178b9d1bad4871b6959473fb7e3d6bc4cd37d0d20a71f51b4e21",
     },
 }
 

@@ -1485,7 +1485,7 @@ size_t knn_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int k, int precision) 
 slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const float* norms,
                                 const __nv_bfloat16* aug, int64_t N, int Dp, int64_t Np, int kc,
                                 int ew, int splits, float* cand_d, int32_t* cand_i,
-                                unsigned int* err_flag);
+                                unsigned int* err_flag, unsigned long long* sweep);
 
 namespace {
 
@@ -1569,6 +1569,7 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->fallback2_count, 0, sizeof(long long), s));
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_max_norm_s_bits, 0, 4 * sizeof(unsigned int), s));
     SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->fallback3_count, 0, sizeof(long long), s));
+    SLK_CUDA_TRY(ctx, cudaMemsetAsync(&st->knn_sweep, 0, sizeof(unsigned long long), s));
     {
         PhaseScope ps(ctx, SLK_PHASE_KNN_PREP);
         SLK_COUNT_LAUNCH(ctx, 3);
@@ -1585,7 +1586,8 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     if (pl.bf16) {
         slk_status r = knn_cand_bf16_launch(ctx, (const __nv_bfloat16*)xt, norms,
                                             pl.aug ? aug : nullptr, N, pl.Dp, pl.Np, pl.kc, pl.ew,
-                                            pl.splits, cand_d, cand_i, &st->knn_error);
+                                            pl.splits, cand_d, cand_i, &st->knn_error,
+                                            &st->knn_sweep);
         if (r != SLK_OK) return r;
         // 2^-23: products exact, each accumulator add off by at most one ulp
         // (truncating adds); an assumption about the tensor-core accumulator

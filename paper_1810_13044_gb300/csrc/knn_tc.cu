@@ -196,11 +196,45 @@ struct TcSmemRes {
     int buf_i[E::halves][E::buf][TC_M];
     float ncol[2][TC_N];
     unsigned long long full[stages], empty[stages], tfull[2], tempty[2], afull, aempty;
+    unsigned long long colbar[8];   // tile column handed from the producer to the epilogue
+    int tcol[8];
     uint32_t tmem_base;
     int abort;
 };
 template <int EW>
 constexpr size_t tc_smem_res_bytes() { return sizeof(TcSmemRes<EW>) + 1024; }
+
+// Resident A block with CTA pairs: each CTA of a cluster keeps its own 128
+// A rows and receives half of every B slice (128 of the 256 columns) and of
+// its folded-norm slice; the pair's MMA (M = 256) reads both halves.  Half
+// the B bytes per SM, so the ring holds twice the slices.  Measured at
+// 1e6 x 128: 379 ms against 288 for single CTAs (each tile waits for the
+// slower of the two epilogues), so it is compiled but off by default.
+#ifndef SLK_TC_RESP
+#define SLK_TC_RESP 0
+#endif
+#ifndef SLK_TC_RESP_STAGES
+#define SLK_TC_RESP_STAGES 6
+#endif
+template <int EW>
+struct TcSmemResPair {
+    using E = TcEpi<EW, true, 32>;
+    static constexpr int stages = SLK_TC_RESP_STAGES;
+    uint8_t a[2][A_BYTES];
+    uint8_t a_aug[A_BYTES / 4];
+    uint8_t b[stages][B_BYTES / 2];      // 128 B rows x 128 bytes
+    uint8_t b_aug[stages][B_BYTES / 8];  // 128 B rows x 32 bytes
+    float buf_d[E::halves][E::buf][TC_M];
+    int buf_i[E::halves][E::buf][TC_M];
+    float ncol[2][TC_N];
+    unsigned long long full[stages], empty[stages], tfull[2], tempty[2], afull, aempty;
+    unsigned long long colbar[8];
+    int tcol[8];
+    uint32_t tmem_base;
+    int abort;
+};
+template <int EW>
+constexpr size_t tc_smem_resp_bytes() { return sizeof(TcSmemResPair<EW>) + 1024; }
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -584,13 +618,18 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                    const float* __restrict__ norms, const float* __restrict__ row_norms,
                    const long long* __restrict__ rows_dev, int64_t N, int64_t Np, int Dp,
                    int n_tiles, int splits, int row_blocks, float* __restrict__ cand_d,
-                   int32_t* __restrict__ cand_i, unsigned int* __restrict__ err_flag) {
+                   int32_t* __restrict__ cand_i, unsigned int* __restrict__ err_flag,
+                   unsigned long long* __restrict__ sweep) {
     static_assert(!(SPLIT && PAIR), "split query rows run on single CTAs");
-    static_assert(!(AUG && (PAIR || SPLIT)), "the folded norms are for single-CTA point tiles");
+    static_assert(!(AUG && (SPLIT || (PAIR && !RES))), "folded norms: single CTAs, or pairs with a resident A");
     static_assert(!RES || (AUG && TC_KC == 32), "a resident A block goes with the folded norms");
     using E = TcEpi<EW, PAIR, TC_KC>;
-    using SMT = std::conditional_t<RES, TcSmemRes<EW>, TcSmem<EW, PAIR, TC_KC>>;
-    constexpr int STAGES = RES ? SLK_TC_RES_STAGES : E::stages;
+    using SMT = std::conditional_t<RES, std::conditional_t<PAIR, TcSmemResPair<EW>, TcSmemRes<EW>>,
+                                   TcSmem<EW, PAIR, TC_KC>>;
+    constexpr int STAGES = RES ? (PAIR ? SLK_TC_RESP_STAGES : SLK_TC_RES_STAGES) : E::stages;
+    // bytes of one CTA's B slice (a half with CTA pairs) and of its folded-norm part
+    constexpr uint32_t B_SLICE = E::b_bytes;
+    constexpr uint32_t B_AUG = B_SLICE / 4;
     constexpr int H = E::halves, VOTE = E::vote, APP = E::app, NT = 32 * EW;
     // columns per TMEM load (the folded-norm epilogue of 8 warps keeps no
     // second value array, so it has the registers for 32)
@@ -631,6 +670,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         if constexpr (RES) {
             mbar_init(&s.afull, 1);
             mbar_init(&s.aempty, 1);
+            for (int i = 0; i < 8; ++i) mbar_init(&s.colbar[i], 1);
         }
         s.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -669,50 +709,94 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 // A slices (and their folded-norm slice) once per row block,
                 // after the MMA warp has released the previous block; the ring
                 // carries B slices only
-                uint32_t iter = 0, aload = 0;
+                uint32_t iter = 0, aload = 0, tseq = 0;
                 bool ok = true;
                 int cur_rb = -1;
                 for (int item = item_begin; item < item_end && ok; ++item) {
                     int rb, t0, t1, sp;
                     item_range(item, splits, n_tiles, rb, t0, t1, sp);
+                    // single CTAs sweep a row block's columns starting where the
+                    // other CTAs are (the global count of tiles issued, per CTA,
+                    // modulo the range) and wrap around, so that CTAs that drift
+                    // apart still read the same B tiles from L2; the candidate
+                    // lists do not depend on the order
+                    const int nt = t1 - t0;
+                    int off = 0;
+                    if (!PAIR && sweep != nullptr && nt > 0)
+                        off = (int)((*(volatile unsigned long long*)sweep / (unsigned long long)n_units) %
+                                    (unsigned long long)nt);
                     if (rb != cur_rb) {
                         if (aload > 0 &&
                             !(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.aempty, (aload - 1) & 1, abort)))
                             break;
-                        const int arow = rb * TC_M;
-                        mbar_expect_tx(&s.afull, (uint32_t)nkb0 * A_BYTES + A_BYTES / 4);
-                        for (int kb = 0; kb < nkb0; ++kb) tma_load_2d(s.a[kb], &tmA, &s.afull, kb * TC_BK, arow);
-                        tma_load_2d(s.a_aug, &tmA2, &s.afull, 0, arow);
+                        const int arow = (PAIR ? 2 * rb + (int)rank : rb) * TC_M;
+                        const uint32_t abytes = (uint32_t)nkb0 * A_BYTES + A_BYTES / 4;
+                        if constexpr (PAIR) {
+                            // both CTAs' A loads complete on the leader's barrier
+                            const uint32_t abar = mapa_rank(&s.afull, 0);
+                            if (rank == 0) mbar_expect_tx(&s.afull, 2 * abytes);
+                            for (int kb = 0; kb < nkb0; ++kb)
+                                tma_load_2d_pair(s.a[kb], &tmA, abar, kb * TC_BK, arow);
+                            tma_load_2d_pair(s.a_aug, &tmA2, abar, 0, arow);
+                        } else {
+                            mbar_expect_tx(&s.afull, abytes);
+                            for (int kb = 0; kb < nkb0; ++kb)
+                                tma_load_2d(s.a[kb], &tmA, &s.afull, kb * TC_BK, arow);
+                            tma_load_2d(s.a_aug, &tmA2, &s.afull, 0, arow);
+                        }
                         ++aload;
                         cur_rb = rb;
                     }
-                    for (int t = t0; t < t1 && ok; ++t) {
-                        const int bcol = t * TC_N;
+                    for (int i = 0; i < nt && ok; ++i) {
+                        const int t = t0 + (off + i) % nt;
+                        // the tile's column block for the epilogue (released by the arrival)
+                        const uint32_t slot = tseq & 7u;
+                        s.tcol[slot] = t;
+                        mbar_arrive(&s.colbar[slot]);
+                        ++tseq;
+                        if (!PAIR && sweep != nullptr && (tseq & 15u) == 0u) atomicAdd(sweep, 16ull);
+                        const int bcol = t * TC_N + (int)rank * (TC_N / 2);   // rank 0 unless PAIR
                         for (int kb = 0; kb < nkb0; ++kb) {
                             const uint32_t st = iter % STAGES, use = iter / STAGES;
                             if (use > 0 &&
                                 !(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.empty[st], (use - 1) & 1, abort)))
                                 break;
                             const bool last = kb == nkb0 - 1;
-                            mbar_expect_tx(&s.full[st], B_BYTES + (last ? B_BYTES / 4 : 0u));
-                            tma_load_2d(s.b[st], &tmB, &s.full[st], kb * TC_BK, bcol);
-                            if (last) tma_load_2d(s.b_aug[st], &tmB2, &s.full[st], 16, bcol);
+                            const uint32_t bytes = B_SLICE + (last ? B_AUG : 0u);
+                            if constexpr (PAIR) {
+                                const uint32_t bar = mapa_rank(&s.full[st], 0);
+                                if (rank == 0) mbar_expect_tx(&s.full[st], 2 * bytes);
+                                tma_load_2d_pair(s.b[st], &tmB, bar, kb * TC_BK, bcol);
+                                if (last) tma_load_2d_pair(s.b_aug[st], &tmB2, bar, 16, bcol);
+                            } else {
+                                mbar_expect_tx(&s.full[st], bytes);
+                                tma_load_2d(s.b[st], &tmB, &s.full[st], kb * TC_BK, bcol);
+                                if (last) tma_load_2d(s.b_aug[st], &tmB2, &s.full[st], 16, bcol);
+                            }
                             ++iter;
                         }
                     }
                 }
                 // drain: every issued load must have landed before the CTA leaves
                 if (!ok || *abort) {
-                    const uint32_t first = iter > STAGES ? iter - STAGES : 0;
-                    for (uint32_t i = first; i < iter; ++i) {
-                        const unsigned long long t0 = globaltimer_ns();
-                        while (!mbar_test(&s.full[i % STAGES], (i / STAGES) & 1) &&
-                               globaltimer_ns() - t0 < kWaitNs) {
+                    if (!PAIR || rank == 0) {
+                        const uint32_t first = iter > STAGES ? iter - STAGES : 0;
+                        for (uint32_t i = first; i < iter; ++i) {
+                            const unsigned long long t0 = globaltimer_ns();
+                            while (!mbar_test(&s.full[i % STAGES], (i / STAGES) & 1) &&
+                                   globaltimer_ns() - t0 < kWaitNs) {
+                            }
                         }
-                    }
-                    if (aload > 0) {
+                        if (aload > 0) {
+                            const unsigned long long t0 = globaltimer_ns();
+                            while (!mbar_test(&s.afull, (aload - 1) & 1) && globaltimer_ns() - t0 < kWaitNs) {
+                            }
+                        }
+                    } else {
+                        // the peer's loads complete on the leader's barriers: give
+                        // them time to land (a load takes microseconds)
                         const unsigned long long t0 = globaltimer_ns();
-                        while (!mbar_test(&s.afull, (aload - 1) & 1) && globaltimer_ns() - t0 < kWaitNs) {
+                        while (globaltimer_ns() - t0 < 1000000ull) {
                         }
                     }
                 }
@@ -787,7 +871,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if constexpr (RES) {
-            if (lane == 0) {
+            if (lane == 0 && rank == 0) {
                 uint32_t iter = 0, tcount = 0, aload = 0;
                 bool ok = true;
                 int cur_rb = -1;
@@ -797,7 +881,10 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     if (rb != cur_rb) {
                         // release the previous block once its MMAs complete, then
                         // wait for the new one
-                        if (cur_rb >= 0) umma_commit(&s.aempty);
+                        if (cur_rb >= 0) {
+                            if constexpr (PAIR) umma_commit_pair(&s.aempty);
+                            else umma_commit(&s.aempty);
+                        }
                         if (!(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.afull, aload & 1, abort))) break;
                         tc_fence_after();
                         ++aload;
@@ -805,8 +892,9 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     }
                     for (int t = t0; t < t1 && ok; ++t) {
                         const uint32_t acc = tcount & 1, use = tcount >> 1;
+                        // with CTA pairs the epilogues of both CTAs release the accumulator
                         if (use > 0 &&
-                            !(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.tempty[acc], (use - 1) & 1, abort)))
+                            !(ok = mbar_wait<PAIR, SLK_TC_SPIN_NS>(&s.tempty[acc], (use - 1) & 1, abort)))
                             break;
                         tc_fence_after();
                         const uint32_t d_tmem = tmem + acc * TC_N;
@@ -818,16 +906,27 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                             const uint64_t da = sw128_desc(su32(s.a[kb]));
                             const uint64_t db = sw128_desc(su32(s.b[st]));
 #pragma unroll
-                            for (int k = 0; k < TC_BK / 16; ++k)
-                                umma(d_tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
-                                     (kb | k) != 0 ? 1u : 0u);
-                            if (kb == nkb0 - 1)   // folded norms: one K = 16 step, 32-byte swizzle
-                                umma(d_tmem, sw32_desc(su32(s.a_aug)), sw32_desc(su32(s.b_aug[st])), 1u);
-                            umma_commit(&s.empty[st]);
+                            for (int k = 0; k < TC_BK / 16; ++k) {
+                                if constexpr (PAIR)
+                                    umma_pair(d_tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
+                                              (kb | k) != 0 ? 1u : 0u);
+                                else
+                                    umma(d_tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
+                                         (kb | k) != 0 ? 1u : 0u);
+                            }
+                            if (kb == nkb0 - 1) {   // folded norms: one K = 16 step, 32-byte swizzle
+                                if constexpr (PAIR)
+                                    umma_pair(d_tmem, sw32_desc(su32(s.a_aug)), sw32_desc(su32(s.b_aug[st])), 1u);
+                                else
+                                    umma(d_tmem, sw32_desc(su32(s.a_aug)), sw32_desc(su32(s.b_aug[st])), 1u);
+                            }
+                            if constexpr (PAIR) umma_commit_pair(&s.empty[st]);
+                            else umma_commit(&s.empty[st]);
                             ++iter;
                         }
                         if (!ok) break;
-                        umma_commit(&s.tfull[acc]);
+                        if constexpr (PAIR) umma_commit_pair(&s.tfull[acc]);
+                        else umma_commit(&s.tfull[acc]);
                         ++tcount;
                     }
                 }
@@ -939,7 +1038,15 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             const float np_ = SPLIT ? row_norms[p] : ((p < N) ? norms[p] : __int_as_float(0x7f800000));
             for (int t = t0; t < t1; ++t) {
                 const uint32_t acc = tcount & 1, use = tcount >> 1;
-                const int64_t col0 = (int64_t)t * TC_N;
+                int tc = t;
+                if constexpr (RES) {
+                    // the producer's sweep order: the tile's column block from its ring
+                    const uint32_t slot = tcount & 7u;
+                    ok = mbar_wait(&s.colbar[slot], (tcount >> 3) & 1u, abort);
+                    if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                    tc = s.tcol[slot];
+                }
+                const int64_t col0 = (int64_t)tc * TC_N;
                 // NOBAR: column norms straight from global memory (uniform
                 // addresses, L1 hits after the first warp; padding rows hold an
                 // infinite norm), each warp waits for the accumulator on its own
@@ -1235,7 +1342,7 @@ int knn_tc_lists_per_split(int kc, int ew) {
 slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const float* norms,
                                 const __nv_bfloat16* aug, int64_t N, int Dp, int64_t Np, int kc,
                                 int ew, int splits, float* cand_d, int32_t* cand_i,
-                                unsigned int* err_flag) {
+                                unsigned int* err_flag, unsigned long long* sweep) {
     if (kc != 32 && kc != 64) return set_err(ctx, SLK_ERR_INVALID_ARG, "bf16 candidates need KC=32 or 64");
     if (ew != 4 && ew != 8) return set_err(ctx, SLK_ERR_INVALID_ARG, "4 or 8 epilogue warps");
     if (Dp % TC_BK != 0 || Np % TC_M != 0)
@@ -1313,7 +1420,49 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
         cfg.numAttrs = 1;
         SLK_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, ta, tb2, ta, tb2, norms, norms,
                                              (const long long*)nullptr, N, Np, Dp, n_tiles, splits,
-                                             row_blocks, cand_d, cand_i, err_flag));
+                                             row_blocks, cand_d, cand_i, err_flag,
+                                             (unsigned long long*)nullptr));
+    } else if (use_aug && SLK_TC_RES != 0 && SLK_TC_RESP != 0 && Dp <= 2 * TC_BK && ew == 8 &&
+               row_blocks % 2 == 0) {
+        // resident A block with CTA pairs: clusters of two over 256-row blocks,
+        // B slices and their folded-norm part in halves
+        CUtensorMap tbh, tb2h;
+        const cuuint32_t box_bh[2] = {TC_BK, TC_N / 2};
+        CUresult r5 = enc(&tbh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)xt, dims, strides, box_bh,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, kTcSwizzle,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        const cuuint64_t adims[2] = {32, (cuuint64_t)Np};
+        const cuuint64_t astr[1] = {64};
+        const cuuint32_t abox_bh[2] = {16, TC_N / 2};
+        CUresult r6 = enc(&tb2h, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)aug, adims, astr, abox_bh,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r5 != CUDA_SUCCESS || r6 != CUDA_SUCCESS)
+            return set_err(ctx, SLK_ERR_CUDA, "tensor map encoding failed (%d, %d)", (int)r5, (int)r6);
+        auto kern = knn_cand_tc_kernel<32, 8, false, false, true, false, true, true>;
+        const size_t smem = tc_smem_resp_bytes<8>();
+        SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        const int pair_items = (row_blocks / 2) * splits;
+        int clusters = ctx->num_sms / 2;
+        if (clusters > pair_items) clusters = pair_items;
+        if (clusters < 1) clusters = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(2 * clusters));
+        cfg.blockDim = dim3(TcEpi<8, true>::threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = ctx->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        SLK_CUDA_TRY(ctx, cudaLaunchKernelEx(&cfg, kern, ta, tbh, ta2, tb2h, norms, norms,
+                                             (const long long*)nullptr, N, Np, Dp, n_tiles, splits,
+                                             row_blocks, cand_d, cand_i, err_flag,
+                                             (unsigned long long*)nullptr));
     } else if (use_aug && SLK_TC_RES != 0 && Dp <= 2 * TC_BK) {
         // resident A block (Dp <= 128)
         if (ew == 4) {
@@ -1323,7 +1472,7 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                                                    (int)smem));
             kern<<<grid, TcEpi<4>::threads, smem, ctx->stream>>>(
                 ta, tb, ta2, tb2a, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks,
-                cand_d, cand_i, err_flag);
+                cand_d, cand_i, err_flag, sweep);
         } else {
             auto kern = knn_cand_tc_kernel<32, 8, false, false, false, false, true, true>;
             const size_t smem = tc_smem_res_bytes<8>();
@@ -1331,7 +1480,7 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                                                    (int)smem));
             kern<<<grid, TcEpi<8>::threads, smem, ctx->stream>>>(
                 ta, tb, ta2, tb2a, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks,
-                cand_d, cand_i, err_flag);
+                cand_d, cand_i, err_flag, sweep);
         }
     } else if (use_aug && ew == 4) {
         auto kern = knn_cand_tc_kernel<32, 4, false, false, false, false, true>;
@@ -1340,7 +1489,7 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                                                (int)smem));
         kern<<<grid, TcEpi<4>::threads, smem, ctx->stream>>>(
             ta, tb, ta2, tb2a, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks, cand_d,
-            cand_i, err_flag);
+            cand_i, err_flag, nullptr);
     } else if (use_aug) {
         auto kern = knn_cand_tc_kernel<32, 8, false, false, false, false, true>;
         const size_t smem = tc_smem_bytes<8>();
@@ -1348,7 +1497,7 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                                                (int)smem));
         kern<<<grid, TcEpi<8>::threads, smem, ctx->stream>>>(
             ta, tb, ta2, tb2a, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks, cand_d,
-            cand_i, err_flag);
+            cand_i, err_flag, nullptr);
     } else if (kc == 32 && ew == 4) {
         auto kern = knn_cand_tc_kernel<32, 4, SLK_TC_PIPE != 0, SLK_TC_NOBAR != 0>;
         const size_t smem = tc_smem_bytes<4>();
@@ -1356,7 +1505,7 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                                                (int)smem));
         kern<<<grid, TcEpi<4>::threads, smem, ctx->stream>>>(
             ta, tb, ta, tb, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks, cand_d,
-            cand_i, err_flag);
+            cand_i, err_flag, nullptr);
     } else if (kc == 32) {
         // 8 epilogue warps: the column norms staged in shared memory (measured
         // faster here than per-warp global loads: 426 against 469 ms at 1e6 x 128)
@@ -1366,7 +1515,7 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                                                (int)smem));
         kern<<<grid, TcEpi<8>::threads, smem, ctx->stream>>>(
             ta, tb, ta, tb, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks, cand_d,
-            cand_i, err_flag);
+            cand_i, err_flag, nullptr);
     } else {
         constexpr int EW = SLK_TC_EW64;
         auto kern = knn_cand_tc_kernel<64, EW, false, SLK_TC_NOBAR64 != 0>;
@@ -1375,7 +1524,7 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                                                (int)smem));
         kern<<<grid, TcEpi<EW, false, 64>::threads, smem, ctx->stream>>>(
             ta, tb, ta, tb, norms, norms, nullptr, N, Np, Dp, n_tiles, splits, row_blocks, cand_d,
-            cand_i, err_flag);
+            cand_i, err_flag, nullptr);
     }
     SLK_LAUNCH_CHECK(ctx, "knn_cand_tc_kernel");
     return SLK_OK;
@@ -1426,7 +1575,7 @@ slk_status knn_cand_split_launch(slk_ctx* ctx, const __nv_bfloat16* qh, const __
                                                (int)smem));
         kern<<<grid, TcEpi<4>::threads, smem, ctx->stream>>>(
             maps[0], maps[2], maps[1], maps[3], norms, qnorm, rows_dev, N, Fcap, Dp, n_tiles, splits,
-            row_cap_blocks, cand_d, cand_i, err_flag);
+            row_cap_blocks, cand_d, cand_i, err_flag, nullptr);
     } else {
         auto kern = knn_cand_tc_kernel<32, 8, SLK_TC_PIPE8 != 0, SLK_TC_NOBAR8 != 0, false, true>;
         const size_t smem = tc_smem_bytes<8>();
@@ -1434,7 +1583,7 @@ slk_status knn_cand_split_launch(slk_ctx* ctx, const __nv_bfloat16* qh, const __
                                                (int)smem));
         kern<<<grid, TcEpi<8>::threads, smem, ctx->stream>>>(
             maps[0], maps[2], maps[1], maps[3], norms, qnorm, rows_dev, N, Fcap, Dp, n_tiles, splits,
-            row_cap_blocks, cand_d, cand_i, err_flag);
+            row_cap_blocks, cand_d, cand_i, err_flag, nullptr);
     }
     SLK_LAUNCH_CHECK(ctx, "knn_cand_tc_kernel (split query rows)");
     return SLK_OK;

@@ -91,6 +91,7 @@ struct DevState {
     unsigned int knn_max_kappa_bits;  // float bits of max rho_p / ||v_p|| (candidate operand)
     unsigned int knn_max_kappa_s_bits;// float bits of max rho_s_p / ||v_p|| (two-term operand)
     long long fallback3_count;        // rows left for the exact scan after the float32 stage
+    unsigned long long knn_sweep;     // tiles issued by the tensor-core kNN kernel (sweep alignment)
 };
 
 enum : unsigned int { ERR_BARRIER_TIMEOUT = 1u };
