@@ -1059,11 +1059,34 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
         for (int h = 0; h < CPL; ++h) myd[h] = kInf;
 #pragma unroll
         for (int h = 0; h < CPL; ++h) {
-            for (unsigned msk = need[h]; msk != 0u; msk &= msk - 1u) {   // warp-uniform
-                const int b = __ffs(msk) - 1;
-                const int q = __shfl_sync(0xffffffffu, ci[h], b);
-                const float d = exact_d2(xp, X + (int64_t)q * D, D, lane);
-                if (lane == b) myd[h] = d;
+            // four candidates at a time: their row gathers overlap; each one's
+            // sum has exact_d2's per-lane order and butterfly (the same bits)
+            unsigned msk = need[h];   // warp-uniform
+            while (msk != 0u) {
+                int b[4], q[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    b[c] = msk != 0u ? __ffs(msk) - 1 : -1;
+                    if (msk != 0u) msk &= msk - 1u;
+                    q[c] = __shfl_sync(0xffffffffu, ci[h], b[c] < 0 ? 0 : b[c]);
+                }
+                float part[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int j = lane; j < D; j += 32) {
+                    const float a = xp[j];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (b[c] >= 0) {
+                            const float df = a - X[(int64_t)q[c] * D + j];
+                            part[c] = fmaf(df, df, part[c]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) part[c] += __shfl_xor_sync(0xffffffffu, part[c], o);
+                    if (b[c] >= 0 && lane == b[c]) myd[h] = part[c];
+                }
             }
         }
         // rank of each candidate by (exact distance, index) among the
