@@ -89,10 +89,10 @@ const char* slk_last_error(const slk_ctx* ctx);
  *            that fail it get two-term bfloat16 tensor-core tiles (each
  *            feature as h + l, h = bf16(v), l = bf16(v - h)) under their own
  *            certificate next, then float32 candidate tiles under the float32
- *            certificate (at most 65536 rows take the two-term stage; the
- *            rest go straight to the float32 one); rows still uncertified are
- *            recomputed by an exact float32 scan, so both precisions return
- *            the same graph.
+ *            certificate (the two-term stage from 100000 points on, for at
+ *            most 65536 rows; the rest go straight to the float32 one); rows
+ *            still uncertified are recomputed by an exact float32 scan, so
+ *            both precisions return the same graph.
  *   fallback_rows [host, nullable]: receives how many rows the first
  *            certificate left open (for BF16_RERANK: the rows sent to the
  *            float32 stage).
@@ -104,8 +104,10 @@ slk_status slk_knn_graph(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int
 
 /* Rows per stage of the last kNN graph built on ctx (by slk_knn_graph,
  * slk_solve, slk_solve_host, slk_solve_ms): rows[0] the rows the first
- * certificate left open, rows[1] (BF16_RERANK) the rows the two-term stage
- * left open for the float32 stage, rows[2] the rows rescanned exactly.
+ * certificate left open, rows[1] (BF16_RERANK) the rows sent to the float32
+ * stage (left open by the two-term stage, or below 100000 points, where that
+ * stage is skipped, by the first certificate), rows[2] the rows rescanned
+ * exactly.
  *   rows [3] host out.
  * Synchronises ctx's stream.  SLK_ERR_INVALID_ARG if rows is NULL. */
 slk_status slk_knn_stage_rows(slk_ctx* ctx, int64_t* rows);
@@ -209,8 +211,10 @@ typedef struct {
     int64_t knn_fallback_rows;  /* kNN rows the first certificate left open (bfloat16: the rows
                                    sent to the two-term tensor-core stage) */
     int32_t ms_iters_total;     /* SLK-MS: mean-shift iterations summed over outer iterations */
-    int64_t knn_float32_rows;   /* bfloat16: rows the two-term certificate left open (sent to
-                                   the float32 stage); 0 otherwise */
+    int64_t knn_float32_rows;   /* bfloat16: rows sent to the float32 stage (those the
+                                   two-term certificate left open; below 100000 points, where
+                                   the two-term stage is skipped, those the first certificate
+                                   left open); 0 otherwise */
     int64_t knn_exact_rows;     /* rows recomputed by the exact float32 scan */
 } slk_stats;
 

@@ -294,7 +294,8 @@ extern "C" slk_status slk_knn_stage_rows(slk_ctx* ctx, int64_t* rows) {
     const slk_status r = read_state(ctx, &hs);
     if (r != SLK_OK) return r;
     rows[0] = hs.fallback_count;
-    rows[1] = hs.fallback2_count;
+    rows[1] = ctx->knn_last_two_term ? hs.fallback2_count
+                                     : (ctx->knn_last_bf16 ? hs.fallback_count : 0);
     rows[2] = ctx->knn_last_bf16 ? hs.fallback3_count : hs.fallback_count;
     return SLK_OK;
 }
@@ -635,7 +636,8 @@ slk_status solve_device(slk_ctx* ctx, const float* X, int64_t N, int32_t D, int3
         stats->sigma = hs.sigma;
         stats->energy = hs.energy;
         stats->knn_fallback_rows = hs.fallback_count;
-        stats->knn_float32_rows = hs.fallback2_count;
+        stats->knn_float32_rows = ctx->knn_last_two_term ? hs.fallback2_count
+                                  : (ctx->knn_last_bf16 ? hs.fallback_count : 0);
         stats->knn_exact_rows = p.knn_precision == SLK_KNN_BF16_RERANK ? hs.fallback3_count
                                                                       : hs.fallback_count;
     }
@@ -935,7 +937,8 @@ extern "C" slk_status slk_solve_ms(slk_ctx* ctx, const float* X, int64_t N, int3
         stats->sigma = hs.sigma;
         stats->energy = hs.energy;
         stats->knn_fallback_rows = hs.fallback_count;
-        stats->knn_float32_rows = hs.fallback2_count;
+        stats->knn_float32_rows = ctx->knn_last_two_term ? hs.fallback2_count
+                                  : (ctx->knn_last_bf16 ? hs.fallback_count : 0);
         stats->knn_exact_rows = p.knn_precision == SLK_KNN_BF16_RERANK ? hs.fallback3_count
                                                                       : hs.fallback_count;
         stats->ms_iters_total = ms_total;

@@ -67,12 +67,12 @@ __host__ __device__ __forceinline__ int query_splits(long long F, long long cap,
 }
 
 // Column splits of the exact scan for F rows: partial lists of k entries per
-// (row, split), at most 256 splits (a few open rows still fill the GPU), as
+// (row, split), at most 1024 splits (a few open rows still fill the GPU), as
 // many as cap entries hold.
 __host__ __device__ __forceinline__ int exact_splits(long long F, long long cap, int k) {
     if (F <= 0) return 1;
     long long sp = cap / (F * (long long)k);
-    if (sp > 256) sp = 256;
+    if (sp > 1024) sp = 1024;
     if (sp < 1) sp = 1;
     return (int)sp;
 }
@@ -1066,8 +1066,19 @@ knn_rerank_kernel(const float* __restrict__ X, int64_t N, int D, int Dp, int k, 
         for (int h = 0; h < CPL; ++h) myd[h] = kInf;
 #pragma unroll
         for (int h = 0; h < CPL; ++h) {
-            // four candidates at a time: their row gathers overlap; each one's
-            // sum has exact_d2's per-lane order and butterfly (the same bits)
+            if (D > 256) {
+                // long rows: a candidate's own loads already overlap
+                for (unsigned msk = need[h]; msk != 0u; msk &= msk - 1u) {   // warp-uniform
+                    const int b = __ffs(msk) - 1;
+                    const int q = __shfl_sync(0xffffffffu, ci[h], b);
+                    const float d = exact_d2(xp, X + (int64_t)q * D, D, lane);
+                    if (lane == b) myd[h] = d;
+                }
+                continue;
+            }
+            // short rows: four candidates at a time, their row gathers overlap;
+            // each one's sum has exact_d2's per-lane order and butterfly (the
+            // same bits)
             unsigned msk = need[h];   // warp-uniform
             while (msk != 0u) {
                 int b[4], q[4];
@@ -1412,8 +1423,9 @@ struct KnnPlan {
     int lists;   // candidate lists per row: splits x lists per split
     bool bf16;
     bool aug;    // tensor-core tiles with the norms folded into one more K slice
-    // two-term stage (bfloat16 only): row capacity (a multiple of 128),
-    // column splits and lists (of 32) per row
+    // two-term stage (bfloat16 and N >= kTwoTermMinRows): row capacity (a
+    // multiple of 128), column splits and lists (of 32) per row
+    bool two_term;
     int64_t fcap;
     int ssplits, slists;
 };
@@ -1421,6 +1433,10 @@ struct KnnPlan {
 // Rows the two-term tensor-core stage takes at most (fewer at large D, see
 // make_plan); the open rows beyond it go to the float32 stage.
 constexpr int64_t kSplitRowCap = 65536;
+// Below this many points the open rows go straight to the float32 stage (its
+// tiles over N points are cheap there, and the two-term stage's four launches
+// would cost more than they save: the batched form runs many such graphs).
+constexpr int64_t kTwoTermMinRows = 100000;
 
 // Column splits for the persistent tensor-core kernel.  Every split restarts
 // the rows' candidate lists, so prefer few, long work items (row block x
@@ -1494,6 +1510,7 @@ KnnPlan make_plan(const slk_ctx* ctx, int64_t N, int D, int k, int precision) {
                                     by_mem);
         pl.ssplits = std::max(1, std::min((32 * MAXE) / (32 * per), tiles_tc / 8));
         pl.slists = pl.ssplits * per;
+        pl.two_term = N >= kTwoTermMinRows;
     }
     return pl;
 }
@@ -1511,13 +1528,13 @@ size_t knn_ws_bytes(const slk_ctx* ctx, int64_t N, int D, int k, int precision) 
     b += align_up(sizeof(int32_t) * N, 256);                                         // second list
     b += align_up(sizeof(int32_t) * (size_t)N, 256);
     if (pl.aug) b += align_up(2 * 32 * (size_t)pl.Np, 256);   // folded-norm columns
-    if (pl.bf16) {
-        // two-term stage: xl, norms_s, rho_s, query rows (h, l, norms), lists, third list
+    if (pl.bf16 && pl.two_term) {
+        // two-term stage: xl, norms_s, rho_s, query rows (h, l, norms), lists
         b += align_up(2 * (size_t)pl.Np * pl.Dp, 256) + 2 * align_up(sizeof(float) * pl.Np, 256);
         b += 2 * align_up(2 * (size_t)pl.fcap * pl.Dp, 256) + align_up(sizeof(float) * pl.fcap, 256);
         b += 2 * align_up(sizeof(float) * (size_t)pl.slists * pl.fcap * 32, 256);
-        b += align_up(sizeof(int32_t) * (size_t)N, 256);
     }
+    if (pl.bf16) b += align_up(sizeof(int32_t) * (size_t)N, 256);   // third list
     return b + 4096;
 }
 
@@ -1575,6 +1592,7 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
                             void* ws, DevState* st) {
     const KnnPlan pl = make_plan(ctx, N, D, k, precision);
     ctx->knn_last_bf16 = pl.bf16;
+    ctx->knn_last_two_term = pl.bf16 && pl.two_term;
     WsCarver wc(ws);
     double* colsum = wc.take<double>(D);
     void* xt = wc.take<unsigned char>((pl.bf16 ? 2 : 4) * (size_t)pl.Np * pl.Dp);
@@ -1587,16 +1605,17 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
     float* mu = wc.take<float>(D);
     int32_t* fb2 = wc.take<int32_t>(N);
     // two-term stage
-    const size_t nd_s = pl.bf16 ? (size_t)pl.Np * pl.Dp : 0, np_s = pl.bf16 ? (size_t)pl.Np : 0;
-    const size_t fd_s = pl.bf16 ? (size_t)pl.fcap * pl.Dp : 0, f_s = pl.bf16 ? (size_t)pl.fcap : 0;
+    const bool tt = pl.bf16 && pl.two_term;
+    const size_t nd_s = tt ? (size_t)pl.Np * pl.Dp : 0, np_s = tt ? (size_t)pl.Np : 0;
+    const size_t fd_s = tt ? (size_t)pl.fcap * pl.Dp : 0, f_s = tt ? (size_t)pl.fcap : 0;
     __nv_bfloat16* xl16 = wc.take<__nv_bfloat16>(nd_s);
     float* norms_s = wc.take<float>(np_s);
     float* rho_s = wc.take<float>(np_s);
     __nv_bfloat16* qh = wc.take<__nv_bfloat16>(fd_s);
     __nv_bfloat16* ql = wc.take<__nv_bfloat16>(fd_s);
     float* qnorm = wc.take<float>(f_s);
-    float* scand_d = wc.take<float>(pl.bf16 ? (size_t)pl.slists * pl.fcap * 32 : 0);
-    int32_t* scand_i = wc.take<int32_t>(pl.bf16 ? (size_t)pl.slists * pl.fcap * 32 : 0);
+    float* scand_d = wc.take<float>(tt ? (size_t)pl.slists * pl.fcap * 32 : 0);
+    int32_t* scand_i = wc.take<int32_t>(tt ? (size_t)pl.slists * pl.fcap * 32 : 0);
     int32_t* fb3 = wc.take<int32_t>(pl.bf16 ? (size_t)N : 0);
     __nv_bfloat16* aug = wc.take<__nv_bfloat16>(pl.aug ? 32 * (size_t)pl.Np : 0);
     cudaStream_t s = ctx->stream;
@@ -1687,6 +1706,12 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
         const int32_t* exact_list = fb;
         const long long* exact_count = &st->fallback_count;
         if (pl.bf16) {
+            // the float32 stage's input and its failures (for the exact scan)
+            const int32_t* f32_in = fb;
+            const long long* f32_cnt = &st->fallback_count;
+            if (pl.two_term) {
+            f32_in = fb2;
+            f32_cnt = &st->fallback2_count;
             // (a) two-term bfloat16 tiles of the open rows on the tensor cores
             // (h . h + h . l + l . h of s = h + l, about 16 significant bits
             // of v), the rerank under their certificate; its failures, and
@@ -1738,6 +1763,7 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
 #undef SLK_RERANK_S
                 SLK_LAUNCH_CHECK(ctx, "knn_rerank_kernel (two-term stage)");
             }
+            }
             // (b) float32 distance tiles of the rows still open against every
             // point, then the rerank under the float32 certificate; its
             // failures go on float32 lists of at least 2k candidates (the gap
@@ -1753,8 +1779,8 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
         auto kern = knn_cand_query_kernel<KC_>;                                               \
         const int smem = (int)sizeof(CandSmem<KC_>);                                          \
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
-        kern<<<qgrid, KT, smem, s>>>(X, N, D, pl.Dp, mu, norms32, fb2, &st->fallback2_count,  \
-                                     qcap, n_tiles, cand_d, cand_i);                          \
+        kern<<<qgrid, KT, smem, s>>>(X, N, D, pl.Dp, mu, norms32, f32_in, f32_cnt, qcap,      \
+                                     n_tiles, cand_d, cand_i);                                \
     }
             if (kcq == 16) SLK_QCAND(16) else SLK_QCAND(32)
 #undef SLK_QCAND
@@ -1765,11 +1791,11 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
             if (kcq == 16)
                 knn_rerank_kernel<16, 1><<<rgrid, 256, 0, s>>>(
                     X, N, D, pl.Dp, k, 0, qcap, cand_d, cand_i, norms32, nullptr, gam32, row_ptr,
-                    col_idx, dist2, fb3, st, fb2, &st->fallback2_count, &st->fallback3_count);
+                    col_idx, dist2, fb3, st, f32_in, f32_cnt, &st->fallback3_count);
             else
                 knn_rerank_kernel<32, 1><<<rgrid, 256, 0, s>>>(
                     X, N, D, pl.Dp, k, 0, qcap, cand_d, cand_i, norms32, nullptr, gam32, row_ptr,
-                    col_idx, dist2, fb3, st, fb2, &st->fallback2_count, &st->fallback3_count);
+                    col_idx, dist2, fb3, st, f32_in, f32_cnt, &st->fallback3_count);
             SLK_LAUNCH_CHECK(ctx, "knn_rerank_kernel (float32 stage)");
             exact_list = fb3;
             exact_count = &st->fallback3_count;

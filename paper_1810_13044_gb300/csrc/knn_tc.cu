@@ -113,6 +113,11 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 #ifndef SLK_TC_MAX3
 #define SLK_TC_MAX3 1
 #endif
+// Fraction of the SMs the point-tile kernels run on (1: all; a probe of how
+// the operand feed scales)
+#ifndef SLK_TC_GRID_DIV
+#define SLK_TC_GRID_DIV 1
+#endif
 // Sleep between the producer's and the MMA warp's barrier polls (ns; 0:
 // poll).  Measured at 1e6 x 128: 100 ns 334 ms, 400 ns 350 ms, polling 329 ms
 #ifndef SLK_TC_SPIN_NS
@@ -127,6 +132,11 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 #endif
 constexpr uint32_t A_BYTES = TC_M * TC_BK * 2;  // 16 KiB (BK = 64)
 constexpr uint32_t B_BYTES = TC_N * TC_BK * 2;  // 32 KiB (BK = 64)
+// the folded-norm slice: 16 bf16 (32 bytes) per row
+constexpr uint32_t AUG_A_BYTES = TC_M * 32;     // 4 KiB
+constexpr uint32_t AUG_B_BYTES = TC_N * 32;     // 8 KiB
+// the resident A block covers Dp <= 128
+constexpr int RES_MAX_DP = 128;
 
 // A vote checks VOTE columns at once and the survivors of APP columns are
 // appended to a per-row buffer of BUF slots.  The buffer is merged into the
@@ -188,10 +198,10 @@ template <int EW>
 struct TcSmemRes {
     using E = TcEpi<EW, false, 32>;
     static constexpr int stages = SLK_TC_RES_STAGES;
-    uint8_t a[2][A_BYTES];           // 1024-byte aligned (swizzle atoms)
-    uint8_t a_aug[A_BYTES / 4];      // 128 rows x 32 bytes
+    uint8_t a[RES_MAX_DP / TC_BK][A_BYTES];   // 1024-byte aligned (swizzle atoms)
+    uint8_t a_aug[AUG_A_BYTES];      // 128 rows x 32 bytes
     uint8_t b[stages][B_BYTES];
-    uint8_t b_aug[stages][B_BYTES / 4];
+    uint8_t b_aug[stages][AUG_B_BYTES];
     float buf_d[E::halves][E::buf][TC_M];
     int buf_i[E::halves][E::buf][TC_M];
     float ncol[2][TC_N];
@@ -220,10 +230,10 @@ template <int EW>
 struct TcSmemResPair {
     using E = TcEpi<EW, true, 32>;
     static constexpr int stages = SLK_TC_RESP_STAGES;
-    uint8_t a[2][A_BYTES];
-    uint8_t a_aug[A_BYTES / 4];
+    uint8_t a[RES_MAX_DP / TC_BK][A_BYTES];
+    uint8_t a_aug[AUG_A_BYTES];
     uint8_t b[stages][B_BYTES / 2];      // 128 B rows x 128 bytes
-    uint8_t b_aug[stages][B_BYTES / 8];  // 128 B rows x 32 bytes
+    uint8_t b_aug[stages][AUG_B_BYTES / 2];  // 128 B rows x 32 bytes
     float buf_d[E::halves][E::buf][TC_M];
     int buf_i[E::halves][E::buf][TC_M];
     float ncol[2][TC_N];
@@ -629,7 +639,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     constexpr int STAGES = RES ? (PAIR ? SLK_TC_RESP_STAGES : SLK_TC_RES_STAGES) : E::stages;
     // bytes of one CTA's B slice (a half with CTA pairs) and of its folded-norm part
     constexpr uint32_t B_SLICE = E::b_bytes;
-    constexpr uint32_t B_AUG = B_SLICE / 4;
+    constexpr uint32_t B_AUG = PAIR ? AUG_B_BYTES / 2 : AUG_B_BYTES;
     constexpr int H = E::halves, VOTE = E::vote, APP = E::app, NT = 32 * EW;
     // columns per TMEM load (the folded-norm epilogue of 8 warps keeps no
     // second value array, so it has the registers for 32)
@@ -730,7 +740,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                             !(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.aempty, (aload - 1) & 1, abort)))
                             break;
                         const int arow = (PAIR ? 2 * rb + (int)rank : rb) * TC_M;
-                        const uint32_t abytes = (uint32_t)nkb0 * A_BYTES + A_BYTES / 4;
+                        const uint32_t abytes = (uint32_t)nkb0 * A_BYTES + AUG_A_BYTES;
                         if constexpr (PAIR) {
                             // both CTAs' A loads complete on the leader's barrier
                             const uint32_t abar = mapa_rank(&s.afull, 0);
@@ -826,7 +836,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                             if constexpr (AUG) {
                                 if (kb == nkb0) {
                                     // the folded norms: 16 columns of A (x = 0) and B (x = 16)
-                                    mbar_expect_tx(&s.full[st], (A_BYTES + B_BYTES) / 4);
+                                    mbar_expect_tx(&s.full[st], AUG_A_BYTES + AUG_B_BYTES);
                                     tma_load_2d(s.a[st], &tmA2, &s.full[st], 0, arow);
                                     tma_load_2d(s.b[st], &tmB2, &s.full[st], 16, bcol);
                                     ++iter;
@@ -1387,7 +1397,10 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
     const int row_blocks = (int)(Np / TC_M);
     const int n_tiles = (int)((Np + TC_N - 1) / TC_N);
     const int n_items = row_blocks * splits;
-    int grid = ctx->num_sms;
+    // a resident A block pays a pipeline drain per row block: only for long
+    // sweeps (the batched form's small graphs have items of a few tiles)
+    const bool res_ok = SLK_TC_RES != 0 && Dp <= RES_MAX_DP && n_tiles / splits >= 64;
+    int grid = ctx->num_sms / SLK_TC_GRID_DIV;
     if (grid > n_items) grid = n_items;
     if (kc == 32 && SLK_TC_PAIR != 0 && row_blocks % 2 == 0) {
         // CTA pairs: clusters of two over 256-row blocks, B tiles in halves
@@ -1422,7 +1435,7 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                                              (const long long*)nullptr, N, Np, Dp, n_tiles, splits,
                                              row_blocks, cand_d, cand_i, err_flag,
                                              (unsigned long long*)nullptr));
-    } else if (use_aug && SLK_TC_RES != 0 && SLK_TC_RESP != 0 && Dp <= 2 * TC_BK && ew == 8 &&
+    } else if (use_aug && res_ok && SLK_TC_RESP != 0 && ew == 8 &&
                row_blocks % 2 == 0) {
         // resident A block with CTA pairs: clusters of two over 256-row blocks,
         // B slices and their folded-norm part in halves
@@ -1463,7 +1476,7 @@ slk_status knn_cand_bf16_launch(slk_ctx* ctx, const __nv_bfloat16* xt, const flo
                                              (const long long*)nullptr, N, Np, Dp, n_tiles, splits,
                                              row_blocks, cand_d, cand_i, err_flag,
                                              (unsigned long long*)nullptr));
-    } else if (use_aug && SLK_TC_RES != 0 && Dp <= 2 * TC_BK) {
+    } else if (use_aug && res_ok) {
         // resident A block (Dp <= 128)
         if (ew == 4) {
             auto kern = knn_cand_tc_kernel<32, 4, false, false, false, false, true, true>;

@@ -37,6 +37,7 @@ struct slk_ctx {
     long long init_candidates = 0;
     // the last kNN graph used bfloat16 candidates (its stage counters mean so)
     bool knn_last_bf16 = false;
+    bool knn_last_two_term = false;   // ... and ran the two-term stage
     // auxiliary streams (batched graph building), created on first use
     std::vector<cudaStream_t> aux;
     std::vector<cudaEvent_t> aux_ev;

@@ -128,33 +128,51 @@ def test_knn_all_rows_through_exact_rescan(slk, precision):
 
 
 def test_knn_two_term_stage_after_bf16(slk):
-    """Two unit-variance clusters 400 apart in 64 dimensions: centred norms of
-    about 200 against neighbour distances of about 10 leave most rows outside
+    """100000 points in two unit-variance clusters 200 apart (64 dimensions;
+    the two-term stage runs from 100000 points on): centred norms of about 100
+    against small neighbour distances leave about a third of the rows outside
     the bfloat16 certificate (operand rounding about 2^-9 of the norm), and
     the two-term bfloat16 tiles (h + l, about 16 significant bits) certify
-    nearly all of them, so hardly any row reaches the float32 stage."""
-    N, D, k = 4000, 64, 10
-    X = two_clusters(N, D, 200.0, 61)
-    o_idx, o_d2 = oracle.knn(X, k)
+    nearly all of them, so hardly any row reaches the float32 stage.  Sampled
+    rows against the oracle."""
+    N, D, k = 100000, 64, 10
+    X = two_clusters(N, D, 100.0, 61)
     gr = slk.knn_graph(dev(X), k, precision="bf16_rerank")
     open1, open2, exact = gr.stage_rows
-    assert open1 == gr.fallback_rows and open1 > N // 2, gr.stage_rows
+    assert open1 == gr.fallback_rows and N // 10 < open1 < 65536, gr.stage_rows
     assert open2 <= max(8, open1 // 20), gr.stage_rows
     assert exact <= open2
-    check_knn(X, k, host(gr.col_idx).reshape(N, k), host(gr.dist2).reshape(N, k), o_idx, o_d2,
-              max_tie_rows=0.02)
+    rows = np.concatenate([inputs.rng(65).choice(N, size=1200, replace=False), [0, N - 1]])
+    o_idx, o_d2 = oracle.knn(X, k, rows=rows)
+    check_knn(X, k, host(gr.col_idx).reshape(N, k)[rows], host(gr.dist2).reshape(N, k)[rows],
+              o_idx, o_d2, rows=rows, max_tie_rows=0.02)
 
 
 def test_knn_float32_stage_after_two_term(slk):
     """The same clusters 800 apart: the two-term tiles' accumulation bound
     (3 Dp products a dot) fails as well, and the float32 tiles with their
     certificate take the rows over."""
-    N, D, k = 4000, 64, 10
+    N, D, k = 100000, 64, 10
     X = two_clusters(N, D, 400.0, 62)
-    o_idx, o_d2 = oracle.knn(X, k)
     gr = slk.knn_graph(dev(X), k, precision="bf16_rerank")
     open1, open2, exact = gr.stage_rows
     assert open1 > N // 2 and open2 > N // 2, gr.stage_rows
+    assert exact <= max(8, open2 // 20), gr.stage_rows
+    rows = np.concatenate([inputs.rng(66).choice(N, size=1200, replace=False), [0, N - 1]])
+    o_idx, o_d2 = oracle.knn(X, k, rows=rows)
+    check_knn(X, k, host(gr.col_idx).reshape(N, k)[rows], host(gr.dist2).reshape(N, k)[rows],
+              o_idx, o_d2, rows=rows, max_tie_rows=0.02)
+
+
+def test_knn_small_graph_skips_two_term_stage(slk):
+    """Below 100000 points the rows the bfloat16 certificate leaves open go
+    straight to the float32 stage (4000 points, clusters 400 apart)."""
+    N, D, k = 4000, 64, 10
+    X = two_clusters(N, D, 200.0, 61)
+    o_idx, o_d2 = oracle.knn(X, k)
+    gr = slk.knn_graph(dev(X), k, precision="bf16_rerank")
+    open1, open2, exact = gr.stage_rows
+    assert open1 > N // 2 and open2 == open1, gr.stage_rows
     assert exact <= max(8, open2 // 20), gr.stage_rows
     check_knn(X, k, host(gr.col_idx).reshape(N, k), host(gr.dist2).reshape(N, k), o_idx, o_d2,
               max_tie_rows=0.02)
