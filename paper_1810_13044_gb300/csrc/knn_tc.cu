@@ -114,7 +114,8 @@ constexpr int TC_STAGES = SLK_TC_STAGES;
 #define SLK_TC_MAX3 1
 #endif
 // Fraction of the SMs the point-tile kernels run on (1: all; a probe of how
-// the operand feed scales)
+// the operand feed scales: on half the SMs the 1e6 x 128 tiles take 578 ms
+// against 293, so their limit is per SM)
 #ifndef SLK_TC_GRID_DIV
 #define SLK_TC_GRID_DIV 1
 #endif
@@ -170,6 +171,8 @@ constexpr int kNoIdx = 0x7fffffff;
 template <int EW, bool PAIR = false, int KC = 32>
 struct TcSmem {
     using E = TcEpi<EW, PAIR, KC>;
+    static constexpr int stages = E::stages;
+    static constexpr int buf = E::buf;
     uint8_t a[E::stages][A_BYTES];   // 1024-byte aligned stages (swizzle atoms)
     uint8_t b[E::stages][E::b_bytes];
     float buf_d[E::halves][E::buf][TC_M];   // per-row append buffer
@@ -183,9 +186,22 @@ template <int EW, bool PAIR = false, int KC = 32>
 constexpr size_t tc_smem_bytes() { return sizeof(TcSmem<EW, PAIR, KC>) + 1024; }
 
 // Resident A block for the folded-norm tiles at Dp <= 128 (1) and its ring
-// of B slices
+// of B slices: with the folded-norm B slices in a ring of their own
+// (AUGRING), 8 epilogue warps get STAGES8 B stages and append buffers of BUF
+// slots.  Measured at 1e6 x 128: 4 stages with 20 slots 414 ms against 294
+// for 3 stages with 31 (the merges that a smaller buffer forces cost more
+// than the deeper ring saves), so AUGRING is off by default
 #ifndef SLK_TC_RES
 #define SLK_TC_RES 1
+#endif
+#ifndef SLK_TC_RES_AUGRING
+#define SLK_TC_RES_AUGRING 0
+#endif
+#ifndef SLK_TC_RES_STAGES8
+#define SLK_TC_RES_STAGES8 4
+#endif
+#ifndef SLK_TC_RES_BUF
+#define SLK_TC_RES_BUF 20
 #endif
 #ifndef SLK_TC_RES_STAGES
 #define SLK_TC_RES_STAGES 3
@@ -197,15 +213,21 @@ constexpr size_t tc_smem_bytes() { return sizeof(TcSmem<EW, PAIR, KC>) + 1024; }
 template <int EW>
 struct TcSmemRes {
     using E = TcEpi<EW, false, 32>;
-    static constexpr int stages = SLK_TC_RES_STAGES;
+    // the tile's folded-norm B slice in a ring of its own (2 slots), which
+    // leaves room for a 4th B stage beside append buffers of 20 slots with 8
+    // epilogue warps
+    static constexpr bool augring = SLK_TC_RES_AUGRING != 0;
+    static constexpr int stages = (EW == 8 && augring) ? SLK_TC_RES_STAGES8 : SLK_TC_RES_STAGES;
+    static constexpr int buf = (EW == 8 && augring) ? SLK_TC_RES_BUF : E::buf;
     uint8_t a[RES_MAX_DP / TC_BK][A_BYTES];   // 1024-byte aligned (swizzle atoms)
     uint8_t a_aug[AUG_A_BYTES];      // 128 rows x 32 bytes
     uint8_t b[stages][B_BYTES];
-    uint8_t b_aug[stages][AUG_B_BYTES];
-    float buf_d[E::halves][E::buf][TC_M];
-    int buf_i[E::halves][E::buf][TC_M];
+    uint8_t b_aug[augring ? 2 : stages][AUG_B_BYTES];
+    float buf_d[E::halves][buf][TC_M];
+    int buf_i[E::halves][buf][TC_M];
     float ncol[2][TC_N];
     unsigned long long full[stages], empty[stages], tfull[2], tempty[2], afull, aempty;
+    unsigned long long augfull[2], augempty[2];
     unsigned long long colbar[8];   // tile column handed from the producer to the epilogue
     int tcol[8];
     uint32_t tmem_base;
@@ -230,6 +252,7 @@ template <int EW>
 struct TcSmemResPair {
     using E = TcEpi<EW, true, 32>;
     static constexpr int stages = SLK_TC_RESP_STAGES;
+    static constexpr int buf = E::buf;
     uint8_t a[RES_MAX_DP / TC_BK][A_BYTES];
     uint8_t a_aug[AUG_A_BYTES];
     uint8_t b[stages][B_BYTES / 2];      // 128 B rows x 128 bytes
@@ -636,7 +659,9 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     using E = TcEpi<EW, PAIR, TC_KC>;
     using SMT = std::conditional_t<RES, std::conditional_t<PAIR, TcSmemResPair<EW>, TcSmemRes<EW>>,
                                    TcSmem<EW, PAIR, TC_KC>>;
-    constexpr int STAGES = RES ? (PAIR ? SLK_TC_RESP_STAGES : SLK_TC_RES_STAGES) : E::stages;
+    constexpr int STAGES = RES ? SMT::stages : E::stages;
+    constexpr int BUF = SMT::buf;   // append-buffer slots per row and half
+    constexpr bool AUGR = RES && !PAIR && (SLK_TC_RES_AUGRING != 0);   // folded-norm B slices in their own ring
     // bytes of one CTA's B slice (a half with CTA pairs) and of its folded-norm part
     constexpr uint32_t B_SLICE = E::b_bytes;
     constexpr uint32_t B_AUG = PAIR ? AUG_B_BYTES / 2 : AUG_B_BYTES;
@@ -681,6 +706,12 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             mbar_init(&s.afull, 1);
             mbar_init(&s.aempty, 1);
             for (int i = 0; i < 8; ++i) mbar_init(&s.colbar[i], 1);
+        }
+        if constexpr (AUGR) {
+            for (int i = 0; i < 2; ++i) {
+                mbar_init(&s.augfull[i], 1);
+                mbar_init(&s.augempty[i], 1);
+            }
         }
         s.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -766,12 +797,21 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         ++tseq;
                         if (!PAIR && sweep != nullptr && (tseq & 15u) == 0u) atomicAdd(sweep, 16ull);
                         const int bcol = t * TC_N + (int)rank * (TC_N / 2);   // rank 0 unless PAIR
+                        if constexpr (AUGR) {
+                            // the tile's folded-norm B slice into its own 2-slot ring
+                            const uint32_t tix = tseq - 1, as = tix & 1u, ause = tix >> 1;
+                            if (ause > 0 &&
+                                !(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.augempty[as], (ause - 1) & 1, abort)))
+                                break;
+                            mbar_expect_tx(&s.augfull[as], AUG_B_BYTES);
+                            tma_load_2d(s.b_aug[as], &tmB2, &s.augfull[as], 16, bcol);
+                        }
                         for (int kb = 0; kb < nkb0; ++kb) {
                             const uint32_t st = iter % STAGES, use = iter / STAGES;
                             if (use > 0 &&
                                 !(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.empty[st], (use - 1) & 1, abort)))
                                 break;
-                            const bool last = kb == nkb0 - 1;
+                            const bool last = kb == nkb0 - 1 && !AUGR;
                             const uint32_t bytes = B_SLICE + (last ? B_AUG : 0u);
                             if constexpr (PAIR) {
                                 const uint32_t bar = mapa_rank(&s.full[st], 0);
@@ -800,6 +840,15 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         if (aload > 0) {
                             const unsigned long long t0 = globaltimer_ns();
                             while (!mbar_test(&s.afull, (aload - 1) & 1) && globaltimer_ns() - t0 < kWaitNs) {
+                            }
+                        }
+                        if constexpr (AUGR) {
+                            // the last two folded-norm loads
+                            for (uint32_t i = tseq > 2 ? tseq - 2 : 0; i < tseq; ++i) {
+                                const unsigned long long t0 = globaltimer_ns();
+                                while (!mbar_test(&s.augfull[i & 1u], (i >> 1) & 1u) &&
+                                       globaltimer_ns() - t0 < kWaitNs) {
+                                }
                             }
                         }
                     } else {
@@ -925,10 +974,19 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                                          (kb | k) != 0 ? 1u : 0u);
                             }
                             if (kb == nkb0 - 1) {   // folded norms: one K = 16 step, 32-byte swizzle
-                                if constexpr (PAIR)
+                                if constexpr (AUGR) {
+                                    const uint32_t as = tcount & 1u;
+                                    if (!(ok = mbar_wait<false, SLK_TC_SPIN_NS>(&s.augfull[as], (tcount >> 1) & 1u,
+                                                                                abort)))
+                                        break;
+                                    tc_fence_after();
+                                    umma(d_tmem, sw32_desc(su32(s.a_aug)), sw32_desc(su32(s.b_aug[as])), 1u);
+                                    umma_commit(&s.augempty[as]);
+                                } else if constexpr (PAIR) {
                                     umma_pair(d_tmem, sw32_desc(su32(s.a_aug)), sw32_desc(su32(s.b_aug[st])), 1u);
-                                else
+                                } else {
                                     umma(d_tmem, sw32_desc(su32(s.a_aug)), sw32_desc(su32(s.b_aug[st])), 1u);
+                                }
                             }
                             if constexpr (PAIR) umma_commit_pair(&s.empty[st]);
                             else umma_commit(&s.empty[st]);
@@ -1222,7 +1280,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     // the load of the next chunk is in flight while one is
                     // filtered; merges happen only at chunk boundaries, with one
                     // chunk's values live, keeping room for C appends
-                    static_assert(E::buf >= 15 + C, "room for a chunk's appends");
+                    static_assert(BUF >= C, "room for a chunk's appends");
                     uint32_t ra[C], rb2[C];
                     tmem_ld_issue<C>(tbase + ch0 * C, ra);
 #pragma unroll 1
@@ -1230,7 +1288,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         tmem_wait_regs(ra);
                         if (hit) {
                             hit = false;
-                            if (__any_sync(0xffffffffu, cnt > E::buf - C)) flush_buffer16<TC_KC>(s, h, r, cnt, ld, li);
+                            if (__any_sync(0xffffffffu, cnt > BUF - C)) flush_buffer16<TC_KC>(s, h, r, cnt, ld, li);
                         }
                         tmem_ld_issue<C>(tbase + (ch0 + cc + 1) * C, rb2);
                         process(ra, ch0 + cc);
@@ -1238,7 +1296,7 @@ knn_cand_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                         if (cc + 2 >= CH_PER_HALF) release();
                         if (hit) {
                             hit = false;
-                            if (__any_sync(0xffffffffu, cnt > E::buf - C)) flush_buffer16<TC_KC>(s, h, r, cnt, ld, li);
+                            if (__any_sync(0xffffffffu, cnt > BUF - C)) flush_buffer16<TC_KC>(s, h, r, cnt, ld, li);
                         }
                         if (cc + 2 < CH_PER_HALF) tmem_ld_issue<C>(tbase + (ch0 + cc + 2) * C, ra);
                         process(rb2, ch0 + cc + 1);
