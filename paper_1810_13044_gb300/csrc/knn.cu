@@ -55,6 +55,9 @@ __device__ __forceinline__ bool lex_less(float d, int i, float d2, int i2) {
 // blocks they would leave mostly empty) and go to the exact scan.
 constexpr long long kExactDirectRows = 256;
 
+// Longest row the wide exact rescan stages in shared memory (bytes).
+constexpr size_t kWideSmemMax = 200 * 1024;
+
 // Column splits of the float32 stage for F open rows: as many as a buffer of
 // cap floats holds at F rows per list of KC, at most 16 (the rerank stages
 // 16 lists of 32 per row).  Host and device compute it from the same count.
@@ -1239,6 +1242,81 @@ knn_fallback_kernel(const float* __restrict__ X, int64_t N, int D, int k,
     }
 }
 
+// Exact rescan for long rows (D above the 32 x 32 features the batched form
+// keeps in registers): work items (one failed row, one of cs =
+// exact_splits(F, cap, k) column ranges) taken persistently, so that a few
+// rows still spread over every SM.  The row's features are staged in shared
+// memory; each of the 8 warps streams a share of the range, computing every
+// distance with exact_d2 (the same per-lane order and butterfly) and keeping
+// a register top-k (lane i holds entry i); the 8 lists are merged into the
+// (row, range) partial list at ((f cs + range) k), as the batched form does.
+__global__ void __launch_bounds__(256)
+knn_fallback_wide_kernel(const float* __restrict__ X, int64_t N, int D, int k,
+                         const int32_t* __restrict__ fb_list, const long long* count_ptr,
+                         long long cap, float* __restrict__ part_d, int32_t* __restrict__ part_i) {
+    extern __shared__ float xs[];   // D floats: the row's features
+    __shared__ float md[8][32];
+    __shared__ int mi[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long count = *(const volatile long long*)count_ptr;
+    const int col_splits = exact_splits(count, cap, k);
+    for (long long item = blockIdx.x; item < count * col_splits; item += gridDim.x) {
+        const long long f = item / col_splits;
+        const int cs = (int)(item % col_splits);
+        const int64_t p = fb_list[f];
+        const int64_t q0 = (int64_t)cs * N / col_splits, q1 = (int64_t)(cs + 1) * N / col_splits;
+        __syncthreads();   // the previous item is done with xs and md / mi
+        for (int j = threadIdx.x; j < D; j += blockDim.x) xs[j] = X[p * D + j];
+        __syncthreads();
+        float ld = kInf;
+        int li = kNoIdx;
+        for (int64_t q = q0 + warp; q < q1; q += 8) {
+            if (q == p) continue;
+            const float d = exact_d2(xs, X + q * D, D, lane);
+            const float lastd = __shfl_sync(0xffffffffu, ld, k - 1);
+            const int lasti = __shfl_sync(0xffffffffu, li, k - 1);
+            if (!lex_less(d, (int)q, lastd, lasti)) continue;
+            const bool less = lane < k && lex_less(d, (int)q, ld, li);
+            const int pos = __ffs(__ballot_sync(0xffffffffu, less)) - 1;
+            const float upd = __shfl_up_sync(0xffffffffu, ld, 1);
+            const int upi = __shfl_up_sync(0xffffffffu, li, 1);
+            if (lane < k) {
+                if (lane == pos) { ld = d; li = (int)q; }
+                else if (lane > pos) { ld = upd; li = upi; }
+            }
+        }
+        md[warp][lane] = lane < k ? ld : kInf;
+        mi[warp][lane] = lane < k ? li : kNoIdx;
+        __syncthreads();
+        if (warp == 0) {
+            float ed[8];
+            int ei[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) { ed[m] = md[m][lane]; ei[m] = mi[m][lane]; }
+            for (int c = 0; c < k; ++c) {
+                float bd = kInf;
+                int bi = kNoIdx;
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    if (lex_less(ed[m], ei[m], bd, bi)) { bd = ed[m]; bi = ei[m]; }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (lex_less(od, oi, bd, bi)) { bd = od; bi = oi; }
+                }
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    if (ei[m] == bi) { ed[m] = kInf; ei[m] = kNoIdx; }
+                if (lane == 0) {
+                    part_d[(f * col_splits + cs) * k + c] = bd;
+                    part_i[(f * col_splits + cs) * k + c] = bi;
+                }
+            }
+        }
+    }
+}
+
 // Batched exact rescan of the rows that failed the certificate.  Work items
 // (R failed rows, one of cs = exact_splits(F, cap, k) column ranges) are
 // taken persistently, so the grid does not depend on the count F.  The R
@@ -1817,6 +1895,18 @@ slk_status knn_graph_launch(slk_ctx* ctx, const float* X, int64_t N, int D, int 
             else SLK_FB(2, 32);
 #undef SLK_FB
             SLK_LAUNCH_CHECK(ctx, "knn_fallback_batch_kernel");
+            knn_fallback_merge_kernel<<<(unsigned)(ctx->num_sms * 2), 256, 0, s>>>(
+                k, exact_list, exact_count, cap, cand_d, cand_i, col_idx, dist2);
+            SLK_LAUNCH_CHECK(ctx, "knn_fallback_merge_kernel");
+        } else if ((size_t)D * sizeof(float) <= kWideSmemMax) {
+            // long rows: staged in shared memory, (row, column range) items
+            SLK_COUNT_LAUNCH(ctx, 2);
+            const int smem = (int)((size_t)D * sizeof(float));
+            SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(knn_fallback_wide_kernel,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+            knn_fallback_wide_kernel<<<(unsigned)(ctx->num_sms * 4), 256, smem, s>>>(
+                X, N, D, k, exact_list, exact_count, cap, cand_d, cand_i);
+            SLK_LAUNCH_CHECK(ctx, "knn_fallback_wide_kernel");
             knn_fallback_merge_kernel<<<(unsigned)(ctx->num_sms * 2), 256, 0, s>>>(
                 k, exact_list, exact_count, cap, cand_d, cand_i, col_idx, dist2);
             SLK_LAUNCH_CHECK(ctx, "knn_fallback_merge_kernel");

@@ -127,6 +127,24 @@ def test_knn_all_rows_through_exact_rescan(slk, precision):
               max_tie_rows=0.02)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16_rerank"])
+@pytest.mark.parametrize("N,D,k,sample", [(2500, 1100, 10, None), (3000, 4100, 24, 150)])
+def test_knn_long_rows_through_exact_rescan(slk, N, D, k, sample, precision):
+    """Rows longer than the 1024 features the batched rescan keeps in
+    registers go through the shared-memory rescan over (row, column range)
+    items; two tight clusters far apart send every row there."""
+    X = two_clusters(N, D, 1000.0, 37, spread=1e-2)
+    rows = None if sample is None else np.sort(inputs.rng(38).choice(N, sample, replace=False))
+    o_idx, o_d2 = oracle.knn(X, k, rows=rows)
+    gr = slk.knn_graph(dev(X), k, precision=precision)
+    assert gr.stage_rows[2] > N // 2
+    g_idx = host(gr.col_idx).reshape(N, k)
+    g_d2 = host(gr.dist2).reshape(N, k)
+    if rows is not None:
+        g_idx, g_d2 = g_idx[rows], g_d2[rows]
+    check_knn(X, k, g_idx, g_d2, o_idx, o_d2, rows=rows, max_tie_rows=0.02)
+
+
 def test_knn_two_term_stage_after_bf16(slk):
     """100000 points in two unit-variance clusters 200 apart (64 dimensions;
     the two-term stage runs from 100000 points on): centred norms of about 100
