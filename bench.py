@@ -891,8 +891,15 @@ def run_serving(args, rank, world, local):
     lat = (done - arrivals) * 1e3
     ms_max, value = whole_job(wall * 1e3, n, world, dev)
     # the plain per-instance GPU solve of the same requests, one after another
+    # (all n of them, timed), then the first `keep` again against the server's
+    # results (untimed)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    for i in range(n):
+        pr = pool[seq[i]]
+        slk.solve(pr["X"], pr["L"], pr["k"], pr["lam"], pr["init_modes"], params=params, ctx=ctx)
+    torch.cuda.synchronize()
+    plain = n / (time.perf_counter() - t0)
     equal, dz_max, differing = 0, 0.0, []
     for i in range(keep):
         pr = pool[seq[i]]
@@ -903,8 +910,6 @@ def run_serving(args, rank, world, local):
         dz_max = max(dz_max, (Z1 - kept[i][0]).abs().max().item())
         if not same:
             differing.append(int(seq[i]))
-    torch.cuda.synchronize()
-    plain = keep / (time.perf_counter() - t0)
     # the highest arrival rate the server sustains: a stream of 400 requests
     # at each rate; sustained when the queue stays bounded -- the most
     # requests in the system while the second half arrives is within 1.5x
@@ -944,8 +949,8 @@ def run_serving(args, rank, world, local):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
             "in_system_max_by_half": in_sys,
-            "plain_per_instance_gpu": {"value": plain, "unit": "solves/s", "requests": keep,
-                                       "equal_labels_and_modes": f"{equal}/{keep}",
+            "plain_per_instance_gpu": {"value": plain, "unit": "solves/s", "requests": n,
+                                       "equal_labels_and_modes": f"{equal}/{keep} (the first {keep})",
                                        "max_abs_dz": dz_max,
                                        "differing_pool_requests": sorted(set(differing)),
                                        "note": "requests of 1e5 rows or more with 64 < L <= 128 run "

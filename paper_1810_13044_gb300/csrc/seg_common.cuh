@@ -87,13 +87,12 @@ __device__ __forceinline__ float gsum(float v, unsigned m, int G) {
     return v;
 }
 
-// Logits s = a + lambda b of row p (lane gl of a G-lane group; labels
-// gl + G j), b summed in CSR order with windowed gathers from Zin.
+// Pairwise term b of row p (lane gl of a G-lane group; labels gl + G j):
+// the neighbours' iterates summed in CSR order with windowed gathers from Zin.
 template <int W>
-__device__ __forceinline__ void seg_logits(const SegInfo& si, int64_t p, int gl, unsigned gm,
-                                           const float* Zin, bool with_pair, float (&s)[kLPL]) {
+__device__ __forceinline__ void seg_pair(const SegInfo& si, int64_t p, int gl, unsigned gm,
+                                         const float* Zin, bool with_pair, float (&b)[kLPL]) {
     const int G = si.G, L = si.L;
-    float b[kLPL];
 #pragma unroll
     for (int j = 0; j < kLPL; ++j) b[j] = 0.f;
     if (with_pair) {
@@ -139,6 +138,15 @@ __device__ __forceinline__ void seg_logits(const SegInfo& si, int64_t p, int gl,
             }
         }
     }
+}
+
+// Logits s = a + lambda b of row p (b as in seg_pair).
+template <int W>
+__device__ __forceinline__ void seg_logits(const SegInfo& si, int64_t p, int gl, unsigned gm,
+                                           const float* Zin, bool with_pair, float (&s)[kLPL]) {
+    const int G = si.G, L = si.L;
+    float b[kLPL];
+    seg_pair<W>(si, p, gl, gm, Zin, with_pair, b);
     const float* ap = si.A + p * (int64_t)L;
 #pragma unroll
     for (int j = 0; j < kLPL; ++j) {

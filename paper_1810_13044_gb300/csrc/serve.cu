@@ -204,8 +204,18 @@ __global__ void srv_start_inner_kernel(int S, SlotDev sd, SegState* ss) {
 }
 
 // ---- up to `quantum` z-updates of every iterating slot
+// Resident CTAs per SM and neighbour window of the z-update kernel, measured
+// on eight requests of 120633 x 18 (k = 10, 300 updates each) served
+// together: 1 CTA / window 8 (155 registers) 470 ms, 2 / 8 307 ms,
+// 3 / 8 301 ms (spills), 3 / 4 258 ms, 3 / 2 262 ms, 4 / 2 283 ms.
+#ifndef SLK_SRV_BOUND_MINB
+#define SLK_SRV_BOUND_MINB 3
+#endif
+#ifndef SLK_SRV_BOUND_W
+#define SLK_SRV_BOUND_W 4
+#endif
 template <int THREADS, int W>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, SLK_SRV_BOUND_MINB)
 srv_bound_kernel(const SegInfo* __restrict__ seg, int S, SlotDev sd, int quantum, int max_inner,
                  float tol, SegState* ss) {
     extern __shared__ int pref[];
@@ -232,11 +242,29 @@ srv_bound_kernel(const SegInfo* __restrict__ seg, int S, SlotDev sd, int quantum
         };
         slot_scan<THREADS>(S, pref, wsum, live, [&](int s) { return n_tiles(seg[s]); });
         const int total = pref[S];
+        // each lane's max |dz| over this warp's tiles of one slot, published
+        // with one atomic when the warp moves to another slot (a warp's tiles
+        // are consecutive in slot order)
+        int cur = -1, cur_u = 0;
+        float dacc = 0.f;
+        auto flush = [&]() {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dacc = fmaxf(dacc, __shfl_xor_sync(0xffffffffu, dacc, o));
+            if (lane == 0 && cur >= 0 && dacc > 0.f)
+                atomicMax(&sd.delta[3 * cur + cur_u % 3], __float_as_uint(dacc));
+            dacc = 0.f;
+        };
+        SegInfo si;
+        int cur_end = 0;   // the first tile past the current slot's
         for (int64_t wi = gwarp; wi < total; wi += nwarps) {
-            const int s = find_slot(pref, S, wi);
-            SegInfo si;
-            load_seg(seg, s, si);
-            const int u = sd.it_base[s] + it;
+            if (cur < 0 || wi >= cur_end) {
+                flush();
+                cur = find_slot(pref, S, wi);
+                cur_end = pref[cur + 1];
+                load_seg(seg, cur, si);
+                cur_u = sd.it_base[cur] + it;
+            }
+            const int s = cur, u = cur_u;
             const int rpt = rows_per_tile(si);
             const int64_t row0 = (wi - pref[s]) * (int64_t)rpt;
             const int nrows = (int)((si.N - row0) < rpt ? (si.N - row0) : (int64_t)rpt);
@@ -247,8 +275,21 @@ srv_bound_kernel(const SegInfo* __restrict__ seg, int S, SlotDev sd, int quantum
             float d = 0.f;
             if (grp < nrows) {
                 const int64_t p = row0 + grp;
+                const int64_t off = p * (int64_t)si.L;
+                // the row's unary term and previous iterate, loaded before the
+                // neighbour gathers so that their latency overlaps them
+                float av[kLPL], zo[kLPL];
+#pragma unroll
+                for (int j = 0; j < kLPL; ++j) {
+                    const int l = gl + G * j;
+                    av[j] = (l < si.L) ? __ldg(si.A + off + l) : 0.f;
+                    zo[j] = (l < si.L) ? __ldcg(Zin + off + l) : 0.f;
+                }
                 float sv[kLPL];
-                seg_logits<W>(si, p, gl, gm, Zin, true, sv);
+                seg_pair<W>(si, p, gl, gm, Zin, true, sv);
+#pragma unroll
+                for (int j = 0; j < kLPL; ++j)
+                    sv[j] = (gl + G * j < si.L) ? fmaf(si.lambda, sv[j], av[j]) : -INFINITY;
                 float m = sv[0];
 #pragma unroll
                 for (int j = 1; j < kLPL; ++j) m = fmaxf(m, sv[j]);
@@ -260,21 +301,19 @@ srv_bound_kernel(const SegInfo* __restrict__ seg, int S, SlotDev sd, int quantum
                     sum += e[j];
                 }
                 sum = gsum(sum, gm, G);
-                const int64_t off = p * (int64_t)si.L;
 #pragma unroll
                 for (int j = 0; j < kLPL; ++j) {
                     const int l = gl + G * j;
                     if (l < si.L) {
                         const float z = e[j] / sum;
-                        d = fmaxf(d, fabsf(z - __ldcg(Zin + off + l)));
+                        d = fmaxf(d, fabsf(z - zo[j]));
                         __stcg(Zout + off + l, z);
                     }
                 }
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
-            if (lane == 0) atomicMax(&sd.delta[3 * s + u % 3], __float_as_uint(d));
+            dacc = fmaxf(dacc, d);
         }
+        flush();
         const int r = seg_step(ss, gridDim.x);
         if (r < 0) return;
         if (r == 1) break;
@@ -315,10 +354,36 @@ srv_mode_kernel(const SegInfo* __restrict__ seg, int S, SlotDev sd) {
                    [&](int s) { return n_tiles(seg[s]); });
     const int total = pref[S];
     const int64_t nwarps = (int64_t)gridDim.x * 8;
+    // each lane's best keys over this warp's tiles of one slot (its labels
+    // gl + G j), merged across groups and published when the warp moves to
+    // another slot
+    int cur = -1, cur_G = 32, cur_L = 0;
+    unsigned long long best[kLPL];
+#pragma unroll
+    for (int j = 0; j < kLPL; ++j) best[j] = 0ull;
+    auto flush = [&]() {
+#pragma unroll
+        for (int j = 0; j < kLPL; ++j) {
+            for (int o = cur_G; o < 32; o <<= 1) {
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best[j], o);
+                if (ob > best[j]) best[j] = ob;
+            }
+            const int l = lane + cur_G * j;
+            if (cur >= 0 && lane < cur_G && l < cur_L && best[j])
+                atomicMax(&sd.best[(int64_t)cur * SLK_BATCH_MAX_L + l], best[j]);
+            best[j] = 0ull;
+        }
+    };
     for (int64_t wi = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); wi < total; wi += nwarps) {
         const int s = find_slot(pref, S, wi);
         SegInfo si;
         load_seg(seg, s, si);
+        if (s != cur) {
+            flush();
+            cur = s;
+            cur_G = si.G;
+            cur_L = si.L;
+        }
         const int rpt = rows_per_tile(si);
         const int64_t row0 = (wi - pref[s]) * (int64_t)rpt;
         const int nrows = (int)((si.N - row0) < rpt ? (si.N - row0) : (int64_t)rpt);
@@ -326,9 +391,6 @@ srv_mode_kernel(const SegInfo* __restrict__ seg, int S, SlotDev sd) {
         const unsigned gm = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (grp * G));
         const bool live = grp < nrows;
         const int64_t p = row0 + (live ? grp : 0);
-        unsigned long long best[kLPL];
-#pragma unroll
-        for (int j = 0; j < kLPL; ++j) best[j] = 0ull;
         if (live) {
             float sv[kLPL];
             seg_logits<W>(si, p, gl, gm, si.Zs, sd.fin[s] > 0, sv);
@@ -354,22 +416,16 @@ srv_mode_kernel(const SegInfo* __restrict__ seg, int S, SlotDev sd) {
 #pragma unroll
             for (int j = 0; j < kLPL; ++j) {
                 const int l = gl + G * j;
-                if (l < si.L)
-                    best[j] = ((unsigned long long)float_to_ordered((sv[j] - m) - lse1) << 32) |
-                              (unsigned long long)(0xffffffffu - (unsigned)p);
+                if (l < si.L) {
+                    const unsigned long long key =
+                        ((unsigned long long)float_to_ordered((sv[j] - m) - lse1) << 32) |
+                        (unsigned long long)(0xffffffffu - (unsigned)p);
+                    if (key > best[j]) best[j] = key;
+                }
             }
-        }
-#pragma unroll
-        for (int j = 0; j < kLPL; ++j) {
-            for (int o = G; o < 32; o <<= 1) {
-                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best[j], o);
-                if (ob > best[j]) best[j] = ob;
-            }
-            const int l = lane + G * j;
-            if (lane < G && l < si.L && best[j])
-                atomicMax(&sd.best[(int64_t)s * SLK_BATCH_MAX_L + l], best[j]);
         }
     }
+    flush();
 }
 
 __global__ void srv_mode_finish_kernel(const SegInfo* __restrict__ seg, int S, SlotDev sd) {
@@ -399,16 +455,29 @@ srv_energy_kernel(const SegInfo* __restrict__ seg, int S, SlotDev sd) {
                    [&](int s) { return n_tiles(seg[s]); });
     const int total = pref[S];
     const int64_t nwarps = (int64_t)gridDim.x * 8;
+    // each lane's float64 sum over this warp's tiles of one slot, added to the
+    // slot's energy when the warp moves to another slot
+    int cur = -1;
+    double acc = 0.0;
+    auto flush = [&]() {
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0 && cur >= 0) atomicAdd(&sd.energy[cur], acc);
+        acc = 0.0;
+    };
     for (int64_t wi = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); wi < total; wi += nwarps) {
         const int s = find_slot(pref, S, wi);
         SegInfo si;
         load_seg(seg, s, si);
+        if (s != cur) {
+            flush();
+            cur = s;
+        }
         const int rpt = rows_per_tile(si);
         const int64_t row0 = (wi - pref[s]) * (int64_t)rpt;
         const int nrows = (int)((si.N - row0) < rpt ? (si.N - row0) : (int64_t)rpt);
         const double sg = (double)*si.sigma;
         const double inv2s2 = 1.0 / (2.0 * sg * sg);
-        double acc = 0.0, my_d2 = 0.0, my_cut = 0.0;
+        double my_d2 = 0.0, my_cut = 0.0;
         bool mine = false;
         int slot = 0;
         for (int r = 0; r < nrows; ++r) {
@@ -437,9 +506,8 @@ srv_energy_kernel(const SegInfo* __restrict__ seg, int S, SlotDev sd) {
             }
         }
         if (mine) acc += -exp(-my_d2 * inv2s2) + 0.5 * (double)si.lambda * 2.0 * my_cut;
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) atomicAdd(&sd.energy[s], acc);
     }
+    flush();
 }
 
 // End of an outer iteration: count it, then either the next outer iteration
@@ -724,9 +792,12 @@ slk_status admit(slk_server* sv, int64_t id) {
     si.N = q.N;
     si.L = q.L;
     si.D = q.D;
+    // lanes per row: every label of L <= 8 on its own lane; above, two
+    // labels per lane up to L = 32 (8 or 16 lanes), then 32 lanes with up to
+    // kLPL labels each -- more rows per warp for the gathers in flight
     int g = 1;
-    while (g < q.L && g < 32) g <<= 1;
-    si.G = g;
+    while (g < q.L && g < 8) g <<= 1;
+    si.G = q.L <= 8 ? g : q.L <= 16 ? 8 : q.L <= 32 ? 16 : 32;
     si.moff = slot * SLK_BATCH_MAX_L;
     si.lambda = q.lambda;
     si.kdeg = q.k;
@@ -808,7 +879,7 @@ extern "C" slk_status slk_server_step(slk_server* sv, int32_t* n_running, int32_
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(srv_energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pref_smem));
         srv_unary_kernel<<<grid_tiles, 256, pref_smem, s>>>(sv->d_seg, S, sv->sd);
         srv_start_inner_kernel<<<1, 256, 0, s>>>(S, sv->sd, sv->d_ss);
-        auto kern = srv_bound_kernel<256, 8>;
+        auto kern = srv_bound_kernel<256, SLK_SRV_BOUND_W>;
         SLK_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pref_smem));
         int per_sm = 0;
         SLK_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, pref_smem));
