@@ -438,6 +438,10 @@ int pow2_at_least(int x) {
     return g;
 }
 
+// Lanes per row of an instance in the segment-indexed kernels; the tile
+// tables and the kernels' tile counts both come from it.
+int seg_group(int L) { return std::min(32, pow2_at_least(L)); }
+
 slk_status launch_seg_bound(slk_ctx* ctx, const TuneChoice& tc, const SegInfo* seg,
                             const SegTile* tiles, const int* tile0, int count, int64_t ntiles,
                             int max_iters, float tol, SegState* ss, unsigned* delta, int* iters,
@@ -506,8 +510,7 @@ extern "C" slk_status slk_solve_batched(slk_ctx* ctx, const slk_instance* inst, 
         z_total += q.N * q.L;
         nnz_total += q.N * q.k;
         L_total += q.L;
-        const int G = std::min(32, pow2_at_least(q.L));
-        const int rows_per_tile = 32 / G;
+        const int rows_per_tile = 32 / seg_group(q.L);
         ntiles += (q.N + rows_per_tile - 1) / rows_per_tile;
         nutiles += (q.N + 31) / 32;
     }
@@ -588,7 +591,7 @@ extern "C" slk_status slk_solve_batched(slk_ctx* ctx, const slk_instance* inst, 
         si.N = q.N;
         si.L = q.L;
         si.D = q.D;
-        si.G = std::min(32, pow2_at_least(q.L));
+        si.G = seg_group(q.L);
         si.moff = moff;
         si.lambda = q.lambda;
         si.kdeg = q.k;
@@ -623,6 +626,8 @@ extern "C" slk_status slk_solve_batched(slk_ctx* ctx, const slk_instance* inst, 
         SLK_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->aux_ev[i], 0));
     }
     // tables and per-instance state (pageable copies: staged by the driver)
+    if ((int64_t)tiles.size() != ntiles || (int64_t)utiles.size() != nutiles)
+        return set_err(ctx, SLK_ERR_INVALID_ARG, "batched tile tables disagree with their counts");
     SLK_CUDA_TRY(ctx, cudaMemcpyAsync(d_seg, seg.data(), sizeof(SegInfo) * count, cudaMemcpyHostToDevice, s));
     SLK_CUDA_TRY(ctx, cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(SegTile) * ntiles, cudaMemcpyHostToDevice, s));
     SLK_CUDA_TRY(ctx, cudaMemcpyAsync(d_utiles, utiles.data(), sizeof(SegTile) * nutiles, cudaMemcpyHostToDevice, s));

@@ -208,6 +208,18 @@ __global__ void srv_start_inner_kernel(int S, SlotDev sd, SegState* ss) {
 // on eight requests of 120633 x 18 (k = 10, 300 updates each) served
 // together: 1 CTA / window 8 (155 registers) 470 ms, 2 / 8 307 ms,
 // 3 / 8 301 ms (spills), 3 / 4 258 ms, 3 / 2 262 ms, 4 / 2 283 ms.
+// Lanes per row of the segment-indexed kernels (0: as the plain z-update
+// kernels, so that a request's soft-max sums run in the plain kernels' order;
+// 1: the fewest that hold L at kLPL labels per lane, at least 4).  Measured
+// on eight requests of 120633 x 18 served together: 262 ms with 0, 185 ms
+// with 1 (the plain loop: 178 ms).  On the 2000-request stream 1 served
+// 92.4 requests/s against 91.2 for the plain loop, but only 163 of the
+// first 200 requests kept the plain loop's labels and modes (190 with 0):
+// the other summation order moves trajectories that pass near a tie or the
+// tolerance
+#ifndef SLK_SRV_G_RULE
+#define SLK_SRV_G_RULE 0
+#endif
 #ifndef SLK_SRV_BOUND_MINB
 #define SLK_SRV_BOUND_MINB 3
 #endif
@@ -792,12 +804,21 @@ slk_status admit(slk_server* sv, int64_t id) {
     si.N = q.N;
     si.L = q.L;
     si.D = q.D;
+#if SLK_SRV_G_RULE == 1
+    // lanes per row: the fewest (a power of two, at least 4) that hold the
+    // row's labels at kLPL per lane -- more rows per warp for the gathers in
+    // flight
+    int g = 4;
+    while (g * kLPL < q.L) g <<= 1;
+    si.G = g;
+#else
     // lanes per row: every label of L <= 8 on its own lane; above, two
     // labels per lane up to L = 32 (8 or 16 lanes), then 32 lanes with up to
     // kLPL labels each -- more rows per warp for the gathers in flight
     int g = 1;
     while (g < q.L && g < 8) g <<= 1;
     si.G = q.L <= 8 ? g : q.L <= 16 ? 8 : q.L <= 32 ? 16 : 32;
+#endif
     si.moff = slot * SLK_BATCH_MAX_L;
     si.lambda = q.lambda;
     si.kdeg = q.k;
