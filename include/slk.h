@@ -463,6 +463,7 @@ enum {
     SLK_PHASE_MODE,
     SLK_PHASE_ENERGY,
     SLK_PHASE_MEANSHIFT,        /* SLK-MS mode iterations */
+    SLK_PHASE_TRANSFER,         /* host <-> device copies of the host-buffer entry points */
     SLK_PHASE_COUNT
 };
 slk_status slk_profile(slk_ctx* ctx, int32_t enable);

@@ -684,15 +684,21 @@ extern "C" slk_status slk_solve_host(slk_ctx* ctx, const float* X, int64_t N, in
     int32_t* dmodes = wc.take<int32_t>((size_t)L);
     const SolveBufs b = carve_solve(wc, ctx, N, D, L, k, p);
     cudaStream_t s = ctx->stream;
-    SLK_CUDA_TRY(ctx, cudaMemcpyAsync(dX, X, sizeof(float) * (size_t)N * D, cudaMemcpyHostToDevice, s));
-    SLK_CUDA_TRY(ctx, cudaMemcpyAsync(dinit, init_modes, sizeof(int32_t) * L, cudaMemcpyHostToDevice, s));
+    {
+        PhaseScope ps(ctx, SLK_PHASE_TRANSFER);
+        SLK_CUDA_TRY(ctx, cudaMemcpyAsync(dX, X, sizeof(float) * (size_t)N * D, cudaMemcpyHostToDevice, s));
+        SLK_CUDA_TRY(ctx, cudaMemcpyAsync(dinit, init_modes, sizeof(int32_t) * L, cudaMemcpyHostToDevice, s));
+    }
     const slk_status rs = solve_device(ctx, dX, N, D, L, k, lambda, sigma, dinit, p, dZ, dlab, dmodes,
                                        stats, b);
     if (rs != SLK_OK && rs != SLK_NOT_CONVERGED) return rs;
-    SLK_CUDA_TRY(ctx, cudaMemcpyAsync(labels, dlab, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToHost, s));
-    SLK_CUDA_TRY(ctx, cudaMemcpyAsync(modes, dmodes, sizeof(int32_t) * L, cudaMemcpyDeviceToHost, s));
-    if (Z)
-        SLK_CUDA_TRY(ctx, cudaMemcpyAsync(Z, dZ, sizeof(float) * (size_t)N * L, cudaMemcpyDeviceToHost, s));
+    {
+        PhaseScope ps(ctx, SLK_PHASE_TRANSFER);
+        SLK_CUDA_TRY(ctx, cudaMemcpyAsync(labels, dlab, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToHost, s));
+        SLK_CUDA_TRY(ctx, cudaMemcpyAsync(modes, dmodes, sizeof(int32_t) * L, cudaMemcpyDeviceToHost, s));
+        if (Z)
+            SLK_CUDA_TRY(ctx, cudaMemcpyAsync(Z, dZ, sizeof(float) * (size_t)N * L, cudaMemcpyDeviceToHost, s));
+    }
     r = sync_and_check(ctx);
     if (r != SLK_OK) return r;
     return rs;

@@ -35,7 +35,7 @@ EXPORTS = ["slk_version", "slk_create", "slk_destroy", "slk_set_stream", "slk_la
            "slk_solve_ms", "slk_initial_modes", "slk_barrier_selftest", "slk_kmeanspp",
            "slk_symmetrize", "slk_knn_stage_rows"]
 PHASES = ["knn_prep", "knn_cand", "knn_rerank", "knn_fallback", "sigma", "unary", "bound", "mode",
-          "energy", "mean_shift"]
+          "energy", "mean_shift", "transfer"]
 
 
 class SlkError(RuntimeError):
