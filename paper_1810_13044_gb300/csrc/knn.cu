@@ -1358,12 +1358,19 @@ knn_fallback_batch_kernel(const float* __restrict__ X, int64_t N, int D, int k,
             }
             ld[r] = kInf; li[r] = kNoIdx; lastd[r] = kInf; lasti[r] = kNoIdx;
         }
+        // the next column's features are loaded while this one is summed
+        float xq[DPL];
+#pragma unroll
+        for (int t = 0; t < DPL; ++t) {
+            const int j = lane + 32 * t;
+            xq[t] = (q0 + warp < q1 && j < D) ? X[(q0 + warp) * D + j] : 0.f;
+        }
         for (int64_t q = q0 + warp; q < q1; q += 8) {
-            float xq[DPL];
+            float xn[DPL];
 #pragma unroll
             for (int t = 0; t < DPL; ++t) {
                 const int j = lane + 32 * t;
-                xq[t] = (j < D) ? X[q * D + j] : 0.f;
+                xn[t] = (q + 8 < q1 && j < D) ? X[(q + 8) * D + j] : 0.f;
             }
             // every row's lane sums, then their butterflies side by side (the
             // R chains overlap), then the insertions; each sum in exact_d2's order
@@ -1398,6 +1405,8 @@ knn_fallback_batch_kernel(const float* __restrict__ X, int64_t N, int D, int k,
                 lastd[r] = __shfl_sync(0xffffffffu, ld[r], k - 1);
                 lasti[r] = __shfl_sync(0xffffffffu, li[r], k - 1);
             }
+#pragma unroll
+            for (int t = 0; t < DPL; ++t) xq[t] = xn[t];
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
