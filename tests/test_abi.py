@@ -34,6 +34,18 @@ def test_binding_covers_header():
     assert sorted(slk.EXPORTS) == _declared()
 
 
+def test_binding_phase_names_follow_header_enum():
+    """slk_profile_read fills one slot per SLK_PHASE_* value; the binding
+    names them in the same order."""
+    from paper_1810_13044_gb300 import slk
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"SLK_PHASE_KNN_PREP\s*=\s*0\s*,(.*?)SLK_PHASE_COUNT", src, flags=re.S)
+    assert body is not None
+    names = ["KNN_PREP"] + re.findall(r"SLK_PHASE_([A-Z_]+)", body.group(1))
+    assert len(names) == len(slk.PHASES)
+    assert [n.lower() for n in names] == [p.replace("mean_shift", "meanshift") for p in slk.PHASES]
+
+
 def test_version_and_no_device_status(lib):
     lib.slk_version.restype = ctypes.c_char_p
     assert b"sm_103a" in lib.slk_version()
