@@ -568,6 +568,27 @@ def test_solve_mnist_like_full_size(slk):
     assert st2["energy"] == pytest.approx(st["energy"], rel=1e-12)
 
 
+def test_host_solve_profiles_its_transfers(slk):
+    """The host-buffer solve records its copies as the transfer phase (one
+    scope for the copies in, one for the copies out); the device solve has
+    none."""
+    X, _ = inputs.blobs(seed=1810)
+    L, k, lam = 5, 5, 1.0
+    m0 = np.arange(L, dtype=np.int32) * 7
+    ctx = slk.context(0)
+    ctx.profile(True)
+    slk.solve_host(torch.from_numpy(X).pin_memory(), L, k, lam, torch.from_numpy(m0), ctx=ctx)
+    ms, calls, _ = ctx.profile_read()
+    ctx.profile(False)
+    assert calls["transfer"] == 2 and ms["transfer"] > 0.0
+    assert calls["knn_cand"] >= 1
+    ctx.profile(True)
+    slk.solve(dev(X), L, k, lam, dev(m0), ctx=ctx)
+    ms, calls, _ = ctx.profile_read()
+    ctx.profile(False)
+    assert calls["transfer"] == 0
+
+
 # --------------------------------------------------------------- bad arguments
 
 def test_invalid_arguments_are_rejected(slk):
